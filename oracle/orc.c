@@ -1,0 +1,411 @@
+/*
+ * FP64 CPU oracle for the coupled D3Q19 BGK lattice Boltzmann step with the
+ * Ota-Suzuki-Inamuro multi-direct-forcing immersed boundary loop
+ * (Beny & Latt, "Efficient LBM on GPUs for dense moving objects using
+ * immersed boundary condition", arXiv:1904.02108).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain definition that the
+ * CUDA library is checked against.  Only the test-suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may load it.  It shares no code, no
+ * header and no table with the CUDA library.
+ *
+ * Every loop runs in the order the paper states the method, in double
+ * precision, with no blocking or fusion.  Readings of places where the paper
+ * is silent or garbled are marked "Reading:".
+ *
+ * Layout: cell n = (z*ny + y)*nx + x; populations f[i*N + n]; Eulerian
+ * vectors U[c*N + n] (c = 0,1,2); Lagrangian vectors v[3*k + c].
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 19
+
+/* D3Q19 velocity set (Sec. 2): one rest vector, six axis vectors and twelve
+ * face diagonals such as [1,-1,0]. */
+static const int E[Q][3] = {
+    {0, 0, 0},
+    {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1},
+};
+
+/* Lattice weights t_i of Eq. 3 for D3Q19: 1/3 (rest), 1/18 (axis), 1/36
+ * (diagonal). */
+static double weight(int i) {
+  if (i == 0) return 1.0 / 3.0;
+  if (i <= 6) return 1.0 / 18.0;
+  return 1.0 / 36.0;
+}
+
+static long wrap(long a, long n) {
+  long r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+void orc_velocity_set(int *e, double *t) {
+  for (int i = 0; i < Q; i++) {
+    for (int c = 0; c < 3; c++) e[3 * i + c] = E[i][c];
+    t[i] = weight(i);
+  }
+}
+
+/* Eq. 3 with the density factor.  Reading: Eq. 3 is printed without rho, but
+ * step 4 of the Sec. 2 summary evaluates Eq(i, rho, U^G); mass conservation
+ * needs the factor. */
+double orc_equilibrium(int i, double rho, const double U[3]) {
+  double eu = E[i][0] * U[0] + E[i][1] * U[1] + E[i][2] * U[2];
+  double uu = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+  return rho * weight(i) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+}
+
+/* Populations at equilibrium for given rho (NULL: 1) and U (NULL: 0). */
+void orc_init_equilibrium(int nx, int ny, int nz, const double *rho,
+                          const double *U, double *f) {
+  long N = (long)nx * ny * nz;
+  for (long n = 0; n < N; n++) {
+    double r = rho ? rho[n] : 1.0;
+    double u[3] = {0.0, 0.0, 0.0};
+    if (U)
+      for (int c = 0; c < 3; c++) u[c] = U[c * N + n];
+    for (int i = 0; i < Q; i++) f[i * N + n] = orc_equilibrium(i, r, u);
+  }
+}
+
+/* Eq. 1: rho = sum_i f_i, U = (1/rho) sum_i e_i f_i on every cell. */
+void orc_moments(int nx, int ny, int nz, const double *f, double *rho,
+                 double *U) {
+  long N = (long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (long n = 0; n < N; n++) {
+    double r = 0.0, m[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; i++) {
+      double fi = f[i * N + n];
+      r += fi;
+      for (int c = 0; c < 3; c++) m[c] += E[i][c] * fi;
+    }
+    if (rho) rho[n] = r;
+    for (int c = 0; c < 3; c++) U[c * N + n] = m[c] / r;
+  }
+}
+
+/* Steps 3-5 of the Sec. 2 summary: U^G = U + tau*G, then the BGK relaxation
+ * of Eq. 2 towards Eq(i, rho, U^G).  G may be NULL (no force). */
+void orc_collide(int nx, int ny, int nz, double tau, double *f,
+                 const double *rho, const double *U, const double *G) {
+  long N = (long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (long n = 0; n < N; n++) {
+    double uG[3];
+    for (int c = 0; c < 3; c++)
+      uG[c] = U[c * N + n] + (G ? tau * G[c * N + n] : 0.0);
+    for (int i = 0; i < Q; i++) {
+      double fi = f[i * N + n];
+      f[i * N + n] = fi + (orc_equilibrium(i, rho[n], uG) - fi) / tau;
+    }
+  }
+}
+
+/* Eq. 4: f_i(X + e_i, t+1) = f_i(X, t).  Reading: the paper states no
+ * boundary; the domain is periodic in all three directions. */
+void orc_stream(int nx, int ny, int nz, const double *fin, double *fout) {
+  long N = (long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (long z = 0; z < nz; z++)
+    for (long y = 0; y < ny; y++)
+      for (long x = 0; x < nx; x++) {
+        long n = (z * ny + y) * nx + x;
+        for (int i = 0; i < Q; i++) {
+          long xd = wrap(x + E[i][0], nx), yd = wrap(y + E[i][1], ny),
+               zd = wrap(z + E[i][2], nz);
+          fout[i * N + (zd * ny + yd) * nx + xd] = fin[i * N + n];
+        }
+      }
+}
+
+/* Sec. 3 weighting function w(r), support |r| < 2.
+ * kernel 0: cosine four-point kernel (1 + cos(pi r / 2)) / 4.
+ * kernel 1: Peskin's four-point kernel.  Reading: the second branch is
+ * printed as sqrt(1 - 7 + 12|r| - 4r^2); the Peskin kernel has
+ * sqrt(-7 + 12|r| - 4r^2) there, which is also the only form that is
+ * continuous at |r| = 1 and vanishes at |r| = 2. */
+double orc_delta(int kernel, double r) {
+  double a = fabs(r);
+  if (a >= 2.0) return 0.0;
+  if (kernel == 0) return 0.25 * (1.0 + cos(M_PI * a / 2.0));
+  if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * a * a)) / 8.0;
+  double q = -7.0 + 12.0 * a - 4.0 * a * a;
+  if (q < 0.0) q = 0.0; /* rounding at a -> 2 */
+  return (5.0 - 2.0 * a - sqrt(q)) / 8.0;
+}
+
+/* The 5x5x5 neighbourhood round(x)-2 .. round(x)+2 of Alg. 2, with the
+ * product weight w(|x-X|) w(|y-Y|) w(|z-Z|).  Cells outside |r| < 2 carry
+ * weight zero.  Indices wrap periodically. */
+typedef struct {
+  long idx[125];
+  double w[125];
+} stencil_t;
+
+static void stencil(int nx, int ny, int nz, int kernel, const double *xk,
+                    stencil_t *st) {
+  long r0 = lround(xk[0]), r1 = lround(xk[1]), r2 = lround(xk[2]);
+  double wx[5], wy[5], wz[5];
+  for (int a = 0; a < 5; a++) {
+    wx[a] = orc_delta(kernel, xk[0] - (double)(r0 - 2 + a));
+    wy[a] = orc_delta(kernel, xk[1] - (double)(r1 - 2 + a));
+    wz[a] = orc_delta(kernel, xk[2] - (double)(r2 - 2 + a));
+  }
+  int m = 0;
+  for (int c = 0; c < 5; c++)
+    for (int b = 0; b < 5; b++)
+      for (int a = 0; a < 5; a++) {
+        long X = r0 - 2 + a, Y = r1 - 2 + b, Z = r2 - 2 + c;
+        st->idx[m] = (wrap(Z, nz) * ny + wrap(Y, ny)) * nx + wrap(X, nx);
+        st->w[m] = wx[a] * wy[b] * wz[c];
+        m++;
+      }
+}
+
+/* Interpolation, fluid -> surface (Sec. 3, Alg. 1):
+ * u(k) = sum_X U(X) w(|x_k - X|) w(|y_k - Y|) w(|z_k - Z|). */
+void orc_interpolate(int nx, int ny, int nz, int kernel, const double *U,
+                     long np, const double *x, double *u) {
+  long N = (long)nx * ny * nz;
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < np; k++) {
+    stencil_t st;
+    stencil(nx, ny, nz, kernel, x + 3 * k, &st);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int m = 0; m < 125; m++)
+      for (int c = 0; c < 3; c++) acc[c] += U[c * N + st.idx[m]] * st.w[m];
+    for (int c = 0; c < 3; c++) u[3 * k + c] = acc[c];
+  }
+}
+
+/* Spreading, surface -> fluid (Sec. 3, Alg. 2):
+ * F(X) += sum_k v(k) w(|x_k - X|) w(|y_k - Y|) w(|z_k - Z|).
+ * Accumulates into F; points are visited in index order. */
+void orc_spread(int nx, int ny, int nz, int kernel, long np, const double *x,
+                const double *v, double *F) {
+  long N = (long)nx * ny * nz;
+  for (long k = 0; k < np; k++) {
+    stencil_t st;
+    stencil(nx, ny, nz, kernel, x + 3 * k, &st);
+    for (int m = 0; m < 125; m++)
+      for (int c = 0; c < 3; c++) F[c * N + st.idx[m]] += v[3 * k + c] * st.w[m];
+  }
+}
+
+/* Rigid-body kinematics of Alg. 1: x(t) = M(t) [x_rest, 1] with M(t) the 4x4
+ * affine map of a rotation by phi(t) = phase_b + omega_b t about the z axis
+ * through centre_b, and the surface velocity u_k = x(t) - x(t-1).
+ * Reading: u_k is the backward difference printed in Alg. 1, with x(t-1)
+ * taken from M(t-1) (also at t = 0). */
+static void affine_rotation_z(const double *c, double phi, double M[4][4]) {
+  double cs = cos(phi), sn = sin(phi);
+  double R[3][3] = {{cs, -sn, 0.0}, {sn, cs, 0.0}, {0.0, 0.0, 1.0}};
+  for (int a = 0; a < 3; a++) {
+    double t = c[a];
+    for (int b = 0; b < 3; b++) {
+      M[a][b] = R[a][b];
+      t -= R[a][b] * c[b];
+    }
+    M[a][3] = t;
+  }
+  M[3][0] = M[3][1] = M[3][2] = 0.0;
+  M[3][3] = 1.0;
+}
+
+void orc_kinematics(long np, const double *xrest, const int *body,
+                    const double *centre, const double *omega,
+                    const double *phase, long t, double *x, double *ut) {
+  for (long k = 0; k < np; k++) {
+    int b = body[k];
+    double Mt[4][4], Mp[4][4];
+    affine_rotation_z(centre + 3 * b, phase[b] + omega[b] * (double)t, Mt);
+    affine_rotation_z(centre + 3 * b, phase[b] + omega[b] * (double)(t - 1), Mp);
+    double h[4] = {xrest[3 * k], xrest[3 * k + 1], xrest[3 * k + 2], 1.0};
+    for (int a = 0; a < 3; a++) {
+      double xa = 0.0, xp = 0.0;
+      for (int b2 = 0; b2 < 4; b2++) {
+        xa += Mt[a][b2] * h[b2];
+        xp += Mp[a][b2] * h[b2];
+      }
+      x[3 * k + a] = xa;
+      if (ut) ut[3 * k + a] = xa - xp;
+    }
+  }
+}
+
+static double norm_field(long N, const double *F) {
+  double s = 0.0;
+  for (long n = 0; n < 3 * N; n++) s += F[n] * F[n];
+  return sqrt(s);
+}
+
+static double norm_points(long np, const double *v) {
+  double s = 0.0;
+  for (long n = 0; n < 3 * np; n++) s += v[n] * v[n];
+  return sqrt(s);
+}
+
+/* The multi-direct-forcing fixed point of Sec. 3.
+ *
+ *   U_0 = U0 + S[du_init]               (du_init = 0 in the paper)
+ *   for n = 0, 1, ...:
+ *     u_n(k)  = I[U_n](k)
+ *     g_n(k)  = u_k - u_n(k)
+ *     du(k)  += g_n(k) s(k)
+ *     U_{n+1} = U_n + S[g_n s]          (literal: U_n + S[g_n])
+ *   G = S[du]
+ *
+ * Readings: the first estimate includes g_0 (the text's du = 0 + g_0 s, not
+ * the algorithm listing's du = 0); the Eulerian update carries s(k) like the
+ * Lagrangian one, so that U_N = U0 + G (literal = 1 restores the printed form
+ * without s).  Residual eps_n = ||S[s g_n]|| / ||S[s u_t]|| (both over the
+ * lattice, FP64); if the denominator vanishes, ||S[s (u_t - I[U0])]|| is used,
+ * then 1.  Pointwise residual ||g_n|| / ||u_t|| with the same fallback.
+ *
+ * n_iter > 0: exactly n_iter iterations.  n_iter == 0: iterate until
+ * eps_n <= tol or max_iter iterations.  Returns the number of iterations.
+ * eps, eps_pt: arrays of at least (n_iter or max_iter) entries, or NULL.
+ */
+int orc_ibm(int nx, int ny, int nz, int kernel, const double *U0, long np,
+            const double *x, const double *ut, const double *s, int n_iter,
+            double tol, int max_iter, int literal, const double *du_init,
+            double *du, double *G, double *eps, double *eps_pt) {
+  long N = (long)nx * ny * nz;
+  double *Un = malloc(sizeof(double) * 3 * N);
+  double *inc = malloc(sizeof(double) * 3 * N);
+  double *tmp = malloc(sizeof(double) * 3 * N);
+  double *un = malloc(sizeof(double) * 3 * np);
+  double *v = malloc(sizeof(double) * 3 * np);
+  memcpy(Un, U0, sizeof(double) * 3 * N);
+  for (long n = 0; n < 3 * np; n++) du[n] = du_init ? du_init[n] : 0.0;
+  if (du_init) orc_spread(nx, ny, nz, kernel, np, x, du_init, Un);
+
+  /* residual denominators */
+  for (long k = 0; k < np; k++)
+    for (int c = 0; c < 3; c++) v[3 * k + c] = s[k] * ut[3 * k + c];
+  memset(tmp, 0, sizeof(double) * 3 * N);
+  orc_spread(nx, ny, nz, kernel, np, x, v, tmp);
+  double den = norm_field(N, tmp);
+  double den_pt = norm_points(np, ut);
+  if (den == 0.0 || den_pt == 0.0) {
+    orc_interpolate(nx, ny, nz, kernel, U0, np, x, un);
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++)
+        v[3 * k + c] = ut[3 * k + c] - un[3 * k + c];
+    if (den_pt == 0.0) den_pt = norm_points(np, v);
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++) v[3 * k + c] *= s[k];
+    if (den == 0.0) {
+      memset(tmp, 0, sizeof(double) * 3 * N);
+      orc_spread(nx, ny, nz, kernel, np, x, v, tmp);
+      den = norm_field(N, tmp);
+    }
+    if (den == 0.0) den = 1.0;
+    if (den_pt == 0.0) den_pt = 1.0;
+  }
+
+  int n = 0;
+  for (;;) {
+    orc_interpolate(nx, ny, nz, kernel, Un, np, x, un);
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++) {
+        double g = ut[3 * k + c] - un[3 * k + c];
+        du[3 * k + c] += g * s[k];
+        v[3 * k + c] = literal ? g : g * s[k];
+      }
+    memset(inc, 0, sizeof(double) * 3 * N);
+    orc_spread(nx, ny, nz, kernel, np, x, v, inc);
+    for (long m = 0; m < 3 * N; m++) Un[m] += inc[m];
+    double e;
+    if (literal) {
+      for (long k = 0; k < np; k++)
+        for (int c = 0; c < 3; c++) v[3 * k + c] *= s[k];
+      memset(tmp, 0, sizeof(double) * 3 * N);
+      orc_spread(nx, ny, nz, kernel, np, x, v, tmp);
+      e = norm_field(N, tmp) / den;
+    } else {
+      e = norm_field(N, inc) / den;
+    }
+    double gp = 0.0;
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++) {
+        double g = ut[3 * k + c] - un[3 * k + c];
+        gp += g * g;
+      }
+    if (eps) eps[n] = e;
+    if (eps_pt) eps_pt[n] = sqrt(gp) / den_pt;
+    n++;
+    if (n_iter > 0) {
+      if (n >= n_iter) break;
+    } else if (e <= tol || n >= max_iter) {
+      break;
+    }
+  }
+  memset(G, 0, sizeof(double) * 3 * N);
+  orc_spread(nx, ny, nz, kernel, np, x, du, G);
+  free(Un);
+  free(inc);
+  free(tmp);
+  free(un);
+  free(v);
+  return n;
+}
+
+/* Global sums of the populations: mass sum_X sum_i f_i and momentum
+ * sum_X sum_i e_i f_i.  out[0] = mass, out[1..3] = momentum. */
+void orc_sums(int nx, int ny, int nz, const double *f, double *out) {
+  long N = (long)nx * ny * nz;
+  double m = 0.0, p[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < Q; i++)
+    for (long n = 0; n < N; n++) {
+      double fi = f[i * N + n];
+      m += fi;
+      for (int c = 0; c < 3; c++) p[c] += E[i][c] * fi;
+    }
+  out[0] = m;
+  for (int c = 0; c < 3; c++) out[c + 1] = p[c];
+}
+
+/* One full time step in the order of the Sec. 2 summary:
+ *   1. rho, U from Eq. 1 (U0 below);
+ *   2. G = immersedBoundary(object, U) by orc_ibm (np > 0);
+ *      plus an optional uniform body force gbody (a test hook, not in the
+ *      paper);
+ *   3-5. U^G = U + tau G, equilibrium, BGK collision;
+ *   6. streaming.
+ * f holds the populations in and out; ftmp is scratch of the same size.
+ * rho, U0, G receive the step's fields (rho, G may be NULL).
+ * Returns the number of IBM iterations (0 without points). */
+int orc_step(int nx, int ny, int nz, double tau, int kernel, double *f,
+             double *ftmp, long np, const double *x, const double *ut,
+             const double *s, int n_iter, double tol, int max_iter,
+             int literal, const double *du_init, double *du,
+             const double *gbody, double *rho, double *U0, double *G,
+             double *eps, double *eps_pt) {
+  long N = (long)nx * ny * nz;
+  double *r = rho ? rho : malloc(sizeof(double) * N);
+  double *g = G ? G : malloc(sizeof(double) * 3 * N);
+  orc_moments(nx, ny, nz, f, r, U0);
+  int iters = 0;
+  if (np > 0)
+    iters = orc_ibm(nx, ny, nz, kernel, U0, np, x, ut, s, n_iter, tol,
+                    max_iter, literal, du_init, du, g, eps, eps_pt);
+  else
+    memset(g, 0, sizeof(double) * 3 * N);
+  if (gbody)
+    for (int c = 0; c < 3; c++)
+      for (long n = 0; n < N; n++) g[c * N + n] += gbody[c];
+  orc_collide(nx, ny, nz, tau, f, r, U0, g);
+  orc_stream(nx, ny, nz, f, ftmp);
+  memcpy(f, ftmp, sizeof(double) * Q * N);
+  if (!rho) free(r);
+  if (!G) free(g);
+  return iters;
+}
