@@ -1,0 +1,229 @@
+/*
+ * lbmibm.h -- C ABI of the GB300 (sm_103a) library for the coupled D3Q19 BGK
+ * lattice Boltzmann step with the Ota-Suzuki-Inamuro multi-direct-forcing
+ * immersed boundary loop (Beny & Latt, arXiv:1904.02108).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every function returning int returns LBM_OK (0) on success, a negative
+ *    LBM_E* code on error, or the positive warning LBM_WNOTCONVERGED.  On an
+ *    error, lbm_last_error(h) returns a static description (valid until the
+ *    next call on the same handle).  A NULL handle is LBM_EINVAL.
+ *  - Lattice coordinates are lattice units; cell (X, Y, Z) is centred on the
+ *    integer point.  The domain is periodic in all three directions.
+ *  - Eulerian fields passed in or out are component-major, x fastest:
+ *    rho[nz][ny][nx], U[3][nz][ny][nx] (FP32).  Lagrangian vectors are
+ *    point-major: v[n][3].
+ *  - Host pointers are read (inputs) or written (outputs) during the call;
+ *    the library copies inputs and keeps no reference to caller memory.
+ *    Functions whose name ends in _dev take device pointers instead and are
+ *    ordered on the handle's stream.
+ *  - All device work is enqueued on the handle's CUDA stream (lbm_set_stream;
+ *    default: the legacy default stream).  Calls that return host data
+ *    synchronise that stream.
+ *  - nx, ny, nz must be positive multiples of 4 (the 4x4x4 brick used to bin
+ *    Lagrangian points and to store forces).
+ *  - The library allocates its device memory with cudaMalloc at creation and
+ *    frees it in lbm_destroy.  One handle must not be used from two host
+ *    threads at once.
+ */
+#ifndef LBMIBM_H
+#define LBMIBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)       /* bad argument (dims, tau <= 1/2, n < 0, ...)  */
+#define LBM_ENOMEM (-2)       /* device or host allocation failed            */
+#define LBM_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed  */
+#define LBM_ENONFINITE (-4)   /* NaN/Inf found in inputs or in the FP64 sums  */
+#define LBM_ESTATE (-5)       /* state buffer of the wrong size or version    */
+#define LBM_WNOTCONVERGED 1   /* warning: IBM iteration cap reached; the step
+                                 still completed                             */
+
+/* Population storage: FP32, or 16-bit deviations f_i - t_i. */
+#define LBM_STORE_F32 0
+#define LBM_STORE_BF16 1
+#define LBM_STORE_F16 2
+
+/* Weighting function w(r) of Sec. 3, support |r| < 2. */
+#define LBM_DELTA_COSINE 0    /* (1 + cos(pi r / 2)) / 4                      */
+#define LBM_DELTA_PESKIN 1    /* Peskin's four-point kernel                   */
+
+/* Initial velocity correction du of each step's fixed point (Sec. 3). */
+#define LBM_WARM_ZERO 0       /* du = 0, as in the paper                      */
+#define LBM_WARM_PREVIOUS 1   /* du = previous step's final du                */
+
+typedef struct lbm lbm_t;
+
+typedef struct {
+  int nx, ny, nz;      /* lattice size, multiples of 4                        */
+  double tau;          /* BGK relaxation time (Eq. 2), > 1/2                  */
+  int storage;         /* LBM_STORE_*                                         */
+  int delta;           /* LBM_DELTA_*                                         */
+  int warm_start;      /* LBM_WARM_*                                          */
+  double ibm_tol;      /* residual target when lbm_step gets n_ibm_iter == 0  */
+  int ibm_max_iter;    /* iteration cap in that mode                          */
+  int stats;           /* 1: accumulate FP64 mass/momentum every step         */
+} lbm_opts;
+
+typedef struct {
+  double mass;           /* sum over cells and i of f_i (after the last step) */
+  double momentum[3];    /* sum of e_i f_i                                    */
+  int64_t step;          /* number of completed steps                         */
+  int last_ibm_iters;    /* fixed-point iterations of the last step           */
+  double last_residual;  /* eps of the last iteration (tolerance mode), else
+                            -1                                                */
+  int64_t not_converged; /* steps that hit the iteration cap                  */
+  int64_t active_bricks; /* 4x4x4 bricks in the support of the points         */
+  int64_t kernel_launches; /* kernels launched by this handle so far          */
+} lbm_stats;
+
+/* ---- lifetime -------------------------------------------------------- */
+
+/* Default options: tau 0.8, FP32 storage, cosine kernel, zero warm start,
+ * ibm_tol 1e-4, ibm_max_iter 500, stats on. */
+void lbm_default_opts(lbm_opts *o);
+
+/* Lattice at rest: f_i = t_i (rho = 1, U = 0) on every cell (Sec. 2).
+ * Errors: LBM_EINVAL (dims not positive multiples of 4, tau <= 1/2, out
+ * NULL), LBM_ENOMEM, LBM_ECUDA.  On error *out is set to NULL. */
+int lbm_create(int nx, int ny, int nz, double tau, lbm_t **out);
+int lbm_create_ex(const lbm_opts *o, lbm_t **out);
+
+/* Frees every device buffer of the handle.  NULL is a no-op. */
+void lbm_destroy(lbm_t *h);
+
+/* Description of the last error on h (h may be NULL: last creation error). */
+const char *lbm_last_error(const lbm_t *h);
+
+/* Stream for all further work of h (a cudaStream_t; NULL = legacy default). */
+int lbm_set_stream(lbm_t *h, void *stream);
+
+/* ---- the immersed object (Sec. 3, Alg. 1) ----------------------------- */
+
+/* Lagrangian points of the immersed surface.
+ *  X[n][3]        FP64 positions.  With bodies (ibm_set_bodies), the rest
+ *                 pose to which the rigid transform M(t) applies; without,
+ *                 fixed positions.
+ *  U_target[n][3] surface velocity u_k used when no bodies are set (NULL:
+ *                 zero).  Ignored when bodies are set (u_k = x(t) - x(t-1)).
+ *  area[n]        s(k), the surface area a point represents (NULL: 1).
+ *  body[n]        body index of each point (NULL: 0).
+ * n = 0 removes all points.  Replaces any previous set and resets the warm
+ * start.  Errors: LBM_EINVAL (n < 0, X NULL with n > 0, body index out of
+ * range of the bodies set), LBM_ENONFINITE (NaN/Inf in any input),
+ * LBM_ENOMEM, LBM_ECUDA. */
+int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
+                   const float *area, const int32_t *body);
+
+/* Rigid rotating bodies: M_b(t) rotates by phase[b] + omega[b] * t radians
+ * about the z axis through centre[b][3] (Alg. 1 applies M(t) at the first
+ * fixed-point iteration; u_k = x(t) - x(t-1)).  nb = 0 removes the bodies
+ * (points become fixed).  t counts completed steps. */
+int ibm_set_bodies(lbm_t *h, int nb, const double *centre, const double *omega,
+                   const double *phase);
+
+/* Uniform body force added to G on every cell (test hook for Poiseuille
+ * flow; not in the paper). */
+int lbm_set_body_force(lbm_t *h, double gx, double gy, double gz);
+
+/* ---- time stepping (Sec. 2 summary, Sec. 3 fixed point) --------------- */
+
+/* Advances n_steps coupled steps.  Each step: rho, U from the populations
+ * (Eq. 1) on the bricks around the points; the multi-direct-forcing fixed
+ * point (Sec. 3) for G; U^G = U + tau G; BGK collision (Eqs. 2-3) and
+ * streaming (Eq. 4) on every cell.  n_ibm_iter > 0: exactly that many
+ * fixed-point iterations (the paper uses 5).  n_ibm_iter == 0: iterate until
+ * the residual eps = ||S[s g_n]|| / ||S[s u_k]|| <= ibm_tol or ibm_max_iter
+ * iterations; returns LBM_WNOTCONVERGED if any step hit the cap.
+ * Errors: LBM_EINVAL (n_steps < 0, n_ibm_iter < 0), LBM_ECUDA,
+ * LBM_ENONFINITE (stats on and a NaN/Inf sum). */
+int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter);
+
+/* Current step counter t (completed steps); lbm_set_time overrides it. */
+int64_t lbm_time(const lbm_t *h);
+int lbm_set_time(lbm_t *h, int64_t t);
+
+/* ---- reading results ------------------------------------------------- */
+
+/* rho[N], U[3][N] of the current populations (Eq. 1) and G[3][N], the
+ * force field applied in the last step (zero away from the points).  Any
+ * output may be NULL.  Host buffers (lbm_read_fields) or device buffers
+ * (lbm_read_fields_dev). */
+int lbm_read_fields(lbm_t *h, float *rho, float *U, float *G);
+int lbm_read_fields_dev(lbm_t *h, float *rho, float *U, float *G);
+
+/* Per-point results of the last step, point order of ibm_set_points:
+ * x[n][3] positions x(t) (FP64), u_interp[n][3] velocity interpolated at the
+ * last iteration u_n(k), du[n][3] the velocity correction du(k) (Sec. 3).
+ * Any output may be NULL. */
+int ibm_read_points(lbm_t *h, double *x, float *u_interp, float *du);
+int ibm_read_points_dev(lbm_t *h, double *x, float *u_interp, float *du);
+
+/* Statistics; the FP64 sums are those of the last step with stats on. */
+int lbm_read_stats(lbm_t *h, lbm_stats *s);
+
+/* Full populations f[19][N] (FP32) of the current state, in the velocity
+ * order of lbm_velocity_set, and their replacement.  Host buffers. */
+int lbm_read_populations(lbm_t *h, float *f);
+int lbm_write_populations(lbm_t *h, const float *f);
+
+/* The stored deviations d_i = f_i - t_i (FP32 values of the storage type),
+ * same layout and pull offset as lbm_read_populations.  Host buffer. */
+int lbm_read_deviations(lbm_t *h, float *d);
+
+/* The D3Q19 velocity set e[19][3] and weights t[19] the library uses. */
+void lbm_velocity_set(int *e, double *t);
+
+/* ---- instrumentation -------------------------------------------------- */
+
+/* Stage timing with CUDA events recorded on the handle's stream around the
+ * stages of lbm_step selected by `mask` (bit i = stage i; LBM_TIME_ALL for
+ * every stage; 0 disables).  Each call clears the accumulated times.  Stage
+ * names: lbm_stage_name(i) for i < lbm_num_stages(); lbm_read_timing
+ * synchronises the stream, then ms[i] holds the accumulated event time and
+ * launches[i] the number of kernel launches timed in stage i. */
+#define LBM_TIME_ALL 0x7fffffff
+int lbm_enable_timing(lbm_t *h, int mask);
+int lbm_num_stages(void);
+const char *lbm_stage_name(int i);
+int lbm_read_timing(lbm_t *h, double *ms, int64_t *launches);
+
+/* ---- checkpoint / resume ---------------------------------------------- */
+
+/* Serialises populations, points, bodies, warm-start state and the step
+ * counter.  buf == NULL: *len receives the size.  Resume is bitwise exact. */
+int lbm_save_state(lbm_t *h, void *buf, size_t *len);
+int lbm_load_state(lbm_t *h, const void *buf, size_t len);
+
+/* ---- stateless operators on caller device memory --------------------- */
+
+/* Interpolation, fluid -> surface (Sec. 3, Alg. 1):
+ *   u(k) = sum_X U(X) w(x_k - X) w(y_k - Y) w(z_k - Z)
+ * U: device [3][nz][ny][nx] FP32; x: device [n][3] FP64; u: device [n][3]
+ * FP32 (written).  Enqueued on `stream`.  Errors: LBM_EINVAL, LBM_ECUDA. */
+int ibm_interpolate_dev(int nx, int ny, int nz, int delta, const float *U,
+                        int64_t n, const double *x, float *u, void *stream);
+
+/* Spreading, surface -> fluid (Sec. 3, Alg. 2), without atomics:
+ *   F(X) = sum_k v(k) w(x_k - X) w(y_k - Y) w(z_k - Z)
+ * F: device [3][nz][ny][nx] FP32, overwritten (zero away from the points).
+ * scratch: device memory of ibm_spread_scratch_bytes(nx,ny,nz,n) bytes, at
+ * least 256-byte aligned, owned by the caller; NULL makes the call allocate
+ * and free it itself.  Enqueued on `stream`. */
+size_t ibm_spread_scratch_bytes(int nx, int ny, int nz, int64_t n);
+int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n,
+                   const double *x, const float *v, float *F, void *scratch,
+                   void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMIBM_H */

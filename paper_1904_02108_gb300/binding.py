@@ -1,0 +1,318 @@
+"""Python binding of the C ABI in include/lbmibm.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``liblbmibm.so``; this
+module converts numpy arrays / torch tensors into pointers and status codes
+into exceptions.  There is no CPU fallback: if the library is missing,
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "liblbmibm.so")
+HEADER = os.path.join(ROOT, "include", "lbmibm.h")
+
+LBM_OK = 0
+LBM_EINVAL = -1
+LBM_ENOMEM = -2
+LBM_ECUDA = -3
+LBM_ENONFINITE = -4
+LBM_ESTATE = -5
+LBM_WNOTCONVERGED = 1
+
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+DELTA = {"cosine": 0, "peskin": 1}
+WARM = {"zero": 0, "previous": 1}
+
+_c = ctypes
+_p = _c.c_void_p
+_i = _c.c_int
+_d = _c.c_double
+_i64 = _c.c_int64
+
+
+class LbmOpts(_c.Structure):
+    _fields_ = [("nx", _i), ("ny", _i), ("nz", _i), ("tau", _d), ("storage", _i),
+                ("delta", _i), ("warm_start", _i), ("ibm_tol", _d), ("ibm_max_iter", _i),
+                ("stats", _i)]
+
+
+class LbmStats(_c.Structure):
+    _fields_ = [("mass", _d), ("momentum", _d * 3), ("step", _i64), ("last_ibm_iters", _i),
+                ("last_residual", _d), ("not_converged", _i64), ("active_bricks", _i64),
+                ("kernel_launches", _i64)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lbmibm error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+_SIGS = {
+    "lbm_default_opts": (None, [_p]),
+    "lbm_create": (_i, [_i, _i, _i, _d, _p]),
+    "lbm_create_ex": (_i, [_p, _p]),
+    "lbm_destroy": (None, [_p]),
+    "lbm_last_error": (_c.c_char_p, [_p]),
+    "lbm_set_stream": (_i, [_p, _p]),
+    "ibm_set_points": (_i, [_p, _i64, _p, _p, _p, _p]),
+    "ibm_set_bodies": (_i, [_p, _i, _p, _p, _p]),
+    "lbm_set_body_force": (_i, [_p, _d, _d, _d]),
+    "lbm_step": (_i, [_p, _i, _i]),
+    "lbm_time": (_i64, [_p]),
+    "lbm_set_time": (_i, [_p, _i64]),
+    "lbm_read_fields": (_i, [_p, _p, _p, _p]),
+    "lbm_read_fields_dev": (_i, [_p, _p, _p, _p]),
+    "ibm_read_points": (_i, [_p, _p, _p, _p]),
+    "ibm_read_points_dev": (_i, [_p, _p, _p, _p]),
+    "lbm_read_stats": (_i, [_p, _p]),
+    "lbm_read_populations": (_i, [_p, _p]),
+    "lbm_write_populations": (_i, [_p, _p]),
+    "lbm_read_deviations": (_i, [_p, _p]),
+    "lbm_velocity_set": (None, [_p, _p]),
+    "lbm_enable_timing": (_i, [_p, _i]),
+    "lbm_num_stages": (_i, []),
+    "lbm_stage_name": (_c.c_char_p, [_i]),
+    "lbm_read_timing": (_i, [_p, _p, _p]),
+    "lbm_save_state": (_i, [_p, _p, _p]),
+    "lbm_load_state": (_i, [_p, _p, _c.c_size_t]),
+    "ibm_interpolate_dev": (_i, [_i, _i, _i, _i, _p, _i64, _p, _p, _p]),
+    "ibm_spread_scratch_bytes": (_c.c_size_t, [_i, _i, _i, _i64]),
+    "ibm_spread_dev": (_i, [_i, _i, _i, _i, _i64, _p, _p, _p, _p, _p]),
+}
+
+
+def header_functions():
+    """Names of the functions declared in include/lbmibm.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z][a-z0-9_]*)\s*\(", txt)) - {"defined", "sizeof"})
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("liblbmibm.so is not built (run __graft_entry__.build()); "
+                           "there is no CPU fallback")
+    L = _c.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data_as(_p)
+    if hasattr(a, "data_ptr"):  # torch tensor
+        assert a.is_contiguous()
+        return _p(a.data_ptr())
+    if isinstance(a, int):
+        return _p(a)
+    raise TypeError(type(a))
+
+
+def _check(code, h=None):
+    if code < 0:
+        msg = load().lbm_last_error(h)
+        raise LbmError(code, msg.decode() if msg else "")
+    return code
+
+
+def velocity_set():
+    e = np.zeros((19, 3), dtype=np.int32)
+    t = np.zeros(19)
+    load().lbm_velocity_set(_ptr(e), _ptr(t))
+    return e, t
+
+
+def stage_names():
+    L = load()
+    return [L.lbm_stage_name(i).decode() for i in range(L.lbm_num_stages())]
+
+
+class Lattice:
+    """Owns one lbm_t handle."""
+
+    def __init__(self, shape, tau, storage="f32", delta="cosine", warm="zero",
+                 ibm_tol=1e-4, ibm_max_iter=500, stats=True, stream=None):
+        L = load()
+        nz, ny, nx = shape
+        o = LbmOpts()
+        L.lbm_default_opts(_c.byref(o))
+        o.nx, o.ny, o.nz, o.tau = nx, ny, nz, float(tau)
+        o.storage, o.delta, o.warm_start = STORAGE[storage], DELTA[delta], WARM[warm]
+        o.ibm_tol, o.ibm_max_iter, o.stats = float(ibm_tol), int(ibm_max_iter), int(stats)
+        h = _p()
+        _check(L.lbm_create_ex(_c.byref(o), _c.byref(h)))
+        self.h = h
+        self.shape = (nz, ny, nx)
+        self.np = 0
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, code):
+        return _check(code, self.h)
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        self._c(load().lbm_set_stream(self.h, _p(raw) if raw else None))
+
+    def set_points(self, X, U_target=None, area=None, body=None):
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        n = len(X)
+        ut = None if U_target is None else np.ascontiguousarray(U_target, np.float32).reshape(-1, 3)
+        ar = None if area is None else np.ascontiguousarray(area, np.float32).reshape(-1)
+        bd = None if body is None else np.ascontiguousarray(body, np.int32).reshape(-1)
+        self._c(load().ibm_set_points(self.h, n, _ptr(X), _ptr(ut), _ptr(ar), _ptr(bd)))
+        self.np = n
+
+    def set_bodies(self, centre, omega, phase):
+        c = np.ascontiguousarray(centre, np.float64).reshape(-1, 3)
+        om = np.ascontiguousarray(omega, np.float64).reshape(-1)
+        ph = np.ascontiguousarray(phase, np.float64).reshape(-1)
+        self._c(load().ibm_set_bodies(self.h, len(c), _ptr(c), _ptr(om), _ptr(ph)))
+
+    def set_propellers(self, props):
+        """props: workload.Propellers (rest pose + rigid rotating bodies)."""
+        self.set_bodies(props.centre, props.omega, props.phase)
+        self.set_points(props.xrest, None, props.area, props.body)
+
+    def set_body_force(self, g):
+        self._c(load().lbm_set_body_force(self.h, *[float(v) for v in g]))
+
+    def step(self, n_steps=1, n_ibm_iter=5):
+        return self._c(load().lbm_step(self.h, int(n_steps), int(n_ibm_iter)))
+
+    @property
+    def time(self):
+        return load().lbm_time(self.h)
+
+    def set_time(self, t):
+        self._c(load().lbm_set_time(self.h, int(t)))
+
+    def fields(self):
+        """rho [nz,ny,nx], U [3,nz,ny,nx], G [3,nz,ny,nx] (float32, host)."""
+        rho = np.empty(self.shape, np.float32)
+        U = np.empty((3,) + self.shape, np.float32)
+        G = np.empty((3,) + self.shape, np.float32)
+        self._c(load().lbm_read_fields(self.h, _ptr(rho), _ptr(U), _ptr(G)))
+        return rho, U, G
+
+    def fields_dev(self, rho=None, U=None, G=None):
+        self._c(load().lbm_read_fields_dev(self.h, _ptr(rho), _ptr(U), _ptr(G)))
+
+    def points(self):
+        x = np.empty((self.np, 3), np.float64)
+        u = np.empty((self.np, 3), np.float32)
+        du = np.empty((self.np, 3), np.float32)
+        self._c(load().ibm_read_points(self.h, _ptr(x), _ptr(u), _ptr(du)))
+        return x, u, du
+
+    def points_dev(self, x=None, u=None, du=None):
+        self._c(load().ibm_read_points_dev(self.h, _ptr(x), _ptr(u), _ptr(du)))
+
+    def stats(self):
+        s = LbmStats()
+        self._c(load().lbm_read_stats(self.h, _c.byref(s)))
+        return dict(mass=s.mass, momentum=tuple(s.momentum), step=s.step,
+                    last_ibm_iters=s.last_ibm_iters, last_residual=s.last_residual,
+                    not_converged=s.not_converged, active_bricks=s.active_bricks,
+                    kernel_launches=s.kernel_launches)
+
+    def populations(self):
+        f = np.empty((19,) + self.shape, np.float32)
+        self._c(load().lbm_read_populations(self.h, _ptr(f)))
+        return f
+
+    def deviations(self):
+        d = np.empty((19,) + self.shape, np.float32)
+        self._c(load().lbm_read_deviations(self.h, _ptr(d)))
+        return d
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, np.float32)
+        assert f.shape == (19,) + self.shape
+        self._c(load().lbm_write_populations(self.h, _ptr(f)))
+
+    def enable_timing(self, stages=True):
+        """stages: True (all), False (off) or an iterable of stage names."""
+        if stages is True:
+            mask = 0x7FFFFFFF
+        elif not stages:
+            mask = 0
+        else:
+            names = stage_names()
+            mask = sum(1 << names.index(s) for s in stages)
+        self._c(load().lbm_enable_timing(self.h, mask))
+
+    def timing(self):
+        L = load()
+        n = L.lbm_num_stages()
+        ms = np.zeros(n)
+        la = np.zeros(n, np.int64)
+        self._c(L.lbm_read_timing(self.h, _ptr(ms), _ptr(la)))
+        names = stage_names()
+        return {names[i]: (float(ms[i]), int(la[i])) for i in range(n)}
+
+    def save_state(self):
+        L = load()
+        n = _c.c_size_t(0)
+        self._c(L.lbm_save_state(self.h, None, _c.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        self._c(L.lbm_save_state(self.h, _ptr(buf), _c.byref(n)))
+        return buf
+
+    def load_state(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        self._c(load().lbm_load_state(self.h, _ptr(buf), buf.size))
+
+
+def interpolate_dev(U, x, u, delta="cosine", stream=None):
+    """U: cuda float32 [3,nz,ny,nx]; x: cuda float64 [n,3]; u: cuda float32 [n,3]."""
+    _, nz, ny, nx = U.shape
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load().ibm_interpolate_dev(nx, ny, nz, DELTA[delta], _ptr(U), x.shape[0], _ptr(x),
+                                      _ptr(u), _p(raw) if raw else None))
+
+
+def spread_scratch_bytes(shape, n):
+    nz, ny, nx = shape
+    return load().ibm_spread_scratch_bytes(nx, ny, nz, int(n))
+
+
+def spread_dev(x, v, F, delta="cosine", scratch=None, stream=None):
+    """x: cuda float64 [n,3]; v: cuda float32 [n,3]; F: cuda float32 [3,nz,ny,nx]."""
+    _, nz, ny, nx = F.shape
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load().ibm_spread_dev(nx, ny, nz, DELTA[delta], x.shape[0], _ptr(x), _ptr(v),
+                                 _ptr(F), _ptr(scratch), _p(raw) if raw else None))

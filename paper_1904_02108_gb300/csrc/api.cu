@@ -1,0 +1,931 @@
+// C ABI of the library (include/lbmibm.h): handle lifetime, argument checks,
+// device memory, and the host orchestration of one time step:
+//
+//   kinematics -> binning -> moments on active bricks -> n x (interpolation,
+//   spreading) -> fused collide-stream -> FP64 sums
+//
+// all enqueued on the handle's stream.  No CPU fallback exists: every step of
+// the method runs in the kernels of lbm.cu and ibm.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmibm.h"
+#include "kernels.h"
+
+using namespace lbmibm;
+
+namespace {
+
+const char *kStageNames[] = {"kinematics", "binning",        "moments", "interp",
+                             "spread",     "collide_stream", "stats"};
+constexpr int kNumStages = 7;
+enum Stage { ST_KIN, ST_BIN, ST_MOM, ST_INTERP, ST_SPREAD, ST_COLLIDE, ST_STATS };
+
+thread_local std::string g_create_error;
+
+size_t storage_bytes(int storage) { return storage == LBM_STORE_F32 ? 4 : 2; }
+
+}  // namespace
+
+struct lbm {
+  Geometry g{};
+  double tau = 0.8;
+  int storage = 0, delta = 0, warm = 0, max_iter = 500, stats_on = 1;
+  double tol = 1e-4;
+  cudaStream_t st = nullptr;
+
+  void *f[2] = {nullptr, nullptr};
+  int cur = 0;
+
+  // immersed points
+  int64_t np = 0, cap_np = 0;
+  int nb = 0, max_body = -1;
+  double *X = nullptr;
+  int *body = nullptr;
+  float *area = nullptr, *utarget = nullptr;
+  double *centre = nullptr, *omega = nullptr, *phase = nullptr, *trig = nullptr;
+  PointPrep pp{};
+  BrickMap m{};
+  float *U0s = nullptr, *Gs = nullptr, *res = nullptr;
+  float4 *du = nullptr, *uint = nullptr;
+  double *xpos = nullptr;
+  bool have_du = false;
+  double gbody[3] = {0, 0, 0};
+  int64_t t = 0;
+
+  // statistics
+  double *partial = nullptr, *red_scratch = nullptr, *sums = nullptr;
+  unsigned *ticket = nullptr;
+  int nparts = 0;
+  bool sums_valid = false;
+  int last_iters = 0;
+  int64_t not_converged = 0;
+  int64_t nlaunch = 0;
+
+  // timing
+  int timing = 0;  // stage mask
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+    int launches;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  double ms[kNumStages] = {0};
+  int64_t launches[kNumStages] = {0};
+
+  // read-out temporaries (allocated on first use)
+  float *tmp = nullptr;
+  size_t tmp_bytes = 0;
+
+  std::string err;
+};
+
+namespace {
+
+int fail(lbm_t *h, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(lbm_t *h, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h)
+    h->err = buf;
+  else
+    g_create_error = buf;
+  return code;
+}
+
+#define CK(h, call)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                        \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+cudaEvent_t get_event(lbm_t *h) {
+  if (!h->free_events.empty()) {
+    cudaEvent_t e = h->free_events.back();
+    h->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+struct StageTimer {
+  lbm_t *h;
+  int stage;
+  int n;
+  cudaEvent_t a = nullptr;
+  StageTimer(lbm_t *h_, int stage_, int n_ = 1) : h(h_), stage(stage_), n(n_) {
+    if (h->timing & (1 << stage)) {
+      a = get_event(h);
+      if (a) cudaEventRecord(a, h->st);
+    }
+    h->nlaunch += n;
+  }
+  ~StageTimer() {
+    if (a) {
+      cudaEvent_t b = get_event(h);
+      if (b) {
+        cudaEventRecord(b, h->st);
+        h->pending.push_back({stage, a, b, n});
+      }
+    }
+  }
+};
+
+int ensure_tmp(lbm_t *h, size_t bytes) {
+  if (h->tmp_bytes >= bytes) return LBM_OK;
+  dfree(h->tmp);
+  h->tmp_bytes = 0;
+  CK(h, cudaMalloc((void **)&h->tmp, bytes));
+  h->tmp_bytes = bytes;
+  return LBM_OK;
+}
+
+void free_points(lbm_t *h) {
+  dfree(h->X);
+  dfree(h->body);
+  dfree(h->area);
+  dfree(h->utarget);
+  dfree(h->pp.base);
+  dfree(h->pp.wts);
+  dfree(h->pp.ut);
+  dfree(h->pp.sorted);
+  dfree(h->du);
+  dfree(h->uint);
+  dfree(h->xpos);
+  dfree(h->m.slot_brick);
+  dfree(h->m.slot_count);
+  dfree(h->m.slot_start);
+  dfree(h->m.slot_cursor);
+  dfree(h->U0s);
+  dfree(h->Gs);
+  dfree(h->res);
+  h->cap_np = 0;
+  h->m.max_slots = 0;
+}
+
+bool all_finite(const double *a, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!isfinite(a[i])) return false;
+  return true;
+}
+bool all_finite(const float *a, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!isfinite(a[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_opts(lbm_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->tau = 0.8;
+  o->storage = LBM_STORE_F32;
+  o->delta = LBM_DELTA_COSINE;
+  o->warm_start = LBM_WARM_ZERO;
+  o->ibm_tol = 1e-4;
+  o->ibm_max_iter = 500;
+  o->stats = 1;
+}
+
+const char *lbm_last_error(const lbm_t *h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void lbm_velocity_set(int *e, double *t) {
+  for (int i = 0; i < Q; i++) {
+    if (e) {
+      e[3 * i] = ex(i);
+      e[3 * i + 1] = ey(i);
+      e[3 * i + 2] = ez(i);
+    }
+    if (t) t[i] = wtd(i);
+  }
+}
+
+void lbm_destroy(lbm_t *h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  dfree(h->f[0]);
+  dfree(h->f[1]);
+  free_points(h);
+  dfree(h->centre);
+  dfree(h->omega);
+  dfree(h->phase);
+  dfree(h->trig);
+  dfree(h->m.brick_flag);
+  dfree(h->m.brick_slot);
+  dfree(h->m.counters);
+  dfree(h->partial);
+  dfree(h->red_scratch);
+  dfree(h->sums);
+  dfree(h->ticket);
+  dfree(h->tmp);
+  for (auto &p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->free_events) cudaEventDestroy(e);
+  delete h;
+}
+
+int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!o) return fail(nullptr, LBM_EINVAL, "opts is NULL");
+  if (o->nx <= 0 || o->ny <= 0 || o->nz <= 0 || o->nx % 4 || o->ny % 4 || o->nz % 4)
+    return fail(nullptr, LBM_EINVAL, "dims %d x %d x %d must be positive multiples of 4",
+                o->nx, o->ny, o->nz);
+  const int64_t ncell = (int64_t)o->nx * o->ny * o->nz;
+  if (ncell >= (1LL << 31))
+    return fail(nullptr, LBM_EINVAL, "lattice of %lld cells is above 2^31",
+                (long long)ncell);
+  if (!(o->tau > 0.5) || !isfinite(o->tau))
+    return fail(nullptr, LBM_EINVAL, "tau = %g must be > 1/2", o->tau);
+  if (o->storage < 0 || o->storage > 2) return fail(nullptr, LBM_EINVAL, "bad storage");
+  if (o->delta < 0 || o->delta > 1) return fail(nullptr, LBM_EINVAL, "bad delta kernel");
+  if (o->warm_start < 0 || o->warm_start > 1) return fail(nullptr, LBM_EINVAL, "bad warm start");
+  if (o->ibm_max_iter <= 0 || !(o->ibm_tol >= 0))
+    return fail(nullptr, LBM_EINVAL, "bad ibm_tol/ibm_max_iter");
+  lbm_t *h = new lbm();
+  h->g.nx = o->nx;
+  h->g.ny = o->ny;
+  h->g.nz = o->nz;
+  h->g.nbx = o->nx / 4;
+  h->g.nby = o->ny / 4;
+  h->g.nbz = o->nz / 4;
+  h->g.ncell = ncell;
+  h->g.nbrick = h->g.nbx * h->g.nby * h->g.nbz;
+  h->tau = o->tau;
+  h->storage = o->storage;
+  h->delta = o->delta;
+  h->warm = o->warm_start;
+  h->tol = o->ibm_tol;
+  h->max_iter = o->ibm_max_iter;
+  h->stats_on = o->stats;
+  const size_t pop = (size_t)Q * ncell * storage_bytes(h->storage);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    e = cudaMalloc(&h->f[k], pop);
+    if (e == cudaSuccess) e = cudaMemset(h->f[k], 0, pop);  // deviations 0: rest
+  }
+  if (e == cudaSuccess) e = dalloc(&h->m.brick_flag, h->g.nbrick);
+  if (e == cudaSuccess) e = cudaMemset(h->m.brick_flag, 0, sizeof(int) * h->g.nbrick);
+  if (e == cudaSuccess) e = dalloc(&h->m.brick_slot, h->g.nbrick);
+  if (e == cudaSuccess) e = cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick);
+  if (e == cudaSuccess) e = dalloc(&h->m.counters, 4);
+  if (e == cudaSuccess) e = cudaMemset(h->m.counters, 0, 4 * sizeof(int));
+  h->nparts = collide_blocks(h->g);
+  if (e == cudaSuccess) e = dalloc(&h->partial, (size_t)h->nparts * 4);
+  if (e == cudaSuccess) e = dalloc(&h->red_scratch, 128 * 4);
+  if (e == cudaSuccess) e = dalloc(&h->sums, 4);
+  if (e == cudaSuccess) e = dalloc(&h->ticket, 1);
+  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    fail(nullptr, code, "allocation of a %d x %d x %d lattice: %s", o->nx, o->ny, o->nz,
+         cudaGetErrorString(e));
+    lbm_destroy(h);
+    return code;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_create(int nx, int ny, int nz, double tau, lbm_t **out) {
+  lbm_opts o;
+  lbm_default_opts(&o);
+  o.nx = nx;
+  o.ny = ny;
+  o.nz = nz;
+  o.tau = tau;
+  return lbm_create_ex(&o, out);
+}
+
+int lbm_set_stream(lbm_t *h, void *stream) {
+  if (!h) return LBM_EINVAL;
+  h->st = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
+                   const float *area, const int32_t *body) {
+  if (!h) return LBM_EINVAL;
+  if (n < 0) return fail(h, LBM_EINVAL, "n = %lld < 0", (long long)n);
+  if (n > 0 && !X) return fail(h, LBM_EINVAL, "X is NULL");
+  if (n > (1LL << 30)) return fail(h, LBM_EINVAL, "too many points");
+  if (n > 0) {
+    if (!all_finite(X, 3 * n)) return fail(h, LBM_ENONFINITE, "non-finite position");
+    if (U_target && !all_finite(U_target, 3 * n))
+      return fail(h, LBM_ENONFINITE, "non-finite target velocity");
+    if (area && !all_finite(area, n)) return fail(h, LBM_ENONFINITE, "non-finite area");
+  }
+  int maxb = -1;
+  if (body)
+    for (int64_t k = 0; k < n; k++) {
+      if (body[k] < 0) return fail(h, LBM_EINVAL, "negative body index at %lld", (long long)k);
+      if (body[k] > maxb) maxb = body[k];
+    }
+  if (n > 0 && !body) maxb = 0;
+  if (h->nb > 0 && maxb >= h->nb)
+    return fail(h, LBM_EINVAL, "body index %d out of range of %d bodies", maxb, h->nb);
+  CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
+  if (n > h->cap_np) {
+    free_points(h);
+    const int64_t ms = std::min<int64_t>(h->g.nbrick, 8 * n);
+    CK(h, dalloc(&h->X, 3 * n));
+    CK(h, dalloc(&h->body, n));
+    CK(h, dalloc(&h->area, n));
+    CK(h, dalloc(&h->utarget, 3 * n));
+    CK(h, dalloc(&h->pp.base, n));
+    CK(h, dalloc(&h->pp.wts, 12 * n));
+    CK(h, dalloc(&h->pp.ut, n));
+    CK(h, dalloc(&h->pp.sorted, n));
+    CK(h, dalloc(&h->du, n));
+    CK(h, dalloc(&h->uint, n));
+    CK(h, dalloc(&h->xpos, 3 * n));
+    CK(h, dalloc(&h->m.slot_brick, ms));
+    CK(h, dalloc(&h->m.slot_count, ms));
+    CK(h, dalloc(&h->m.slot_start, ms + 1));
+    CK(h, dalloc(&h->m.slot_cursor, ms));
+    CK(h, dalloc(&h->U0s, (size_t)ms * SLOT_FLOATS));
+    CK(h, dalloc(&h->Gs, (size_t)ms * SLOT_FLOATS));
+    CK(h, dalloc(&h->res, ms));
+    h->cap_np = n;
+    h->m.max_slots = (int)ms;
+  }
+  h->np = n;
+  h->max_body = maxb;
+  h->have_du = false;
+  if (n > 0) {
+    CK(h, cudaMemcpy(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
+    std::vector<float> a(n, 1.0f);
+    if (area) memcpy(a.data(), area, sizeof(float) * n);
+    CK(h, cudaMemcpy(h->area, a.data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+    std::vector<int> b(n, 0);
+    if (body) memcpy(b.data(), body, sizeof(int) * n);
+    CK(h, cudaMemcpy(h->body, b.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    std::vector<float> u(3 * n, 0.0f);
+    if (U_target) memcpy(u.data(), U_target, sizeof(float) * 3 * n);
+    CK(h, cudaMemcpy(h->utarget, u.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->du, 0, sizeof(float4) * n));
+    CK(h, cudaMemset(h->uint, 0, sizeof(float4) * n));
+  } else {
+    CK(h, cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick));
+    CK(h, cudaMemset(h->m.counters, 0, 4 * sizeof(int)));
+  }
+  return LBM_OK;
+}
+
+int ibm_set_bodies(lbm_t *h, int nb, const double *centre, const double *omega,
+                   const double *phase) {
+  if (!h) return LBM_EINVAL;
+  if (nb < 0) return fail(h, LBM_EINVAL, "nb = %d < 0", nb);
+  if (nb > 0 && (!centre || !omega || !phase))
+    return fail(h, LBM_EINVAL, "centre/omega/phase must be given");
+  if (nb > 0 && (!all_finite(centre, 3 * nb) || !all_finite(omega, nb) ||
+                 !all_finite(phase, nb)))
+    return fail(h, LBM_ENONFINITE, "non-finite body parameter");
+  if (nb > 0 && h->max_body >= nb)
+    return fail(h, LBM_EINVAL, "points refer to body %d, only %d bodies", h->max_body, nb);
+  CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
+  dfree(h->centre);
+  dfree(h->omega);
+  dfree(h->phase);
+  dfree(h->trig);
+  h->nb = nb;
+  if (nb > 0) {
+    CK(h, dalloc(&h->trig, 4 * nb));
+    CK(h, dalloc(&h->centre, 3 * nb));
+    CK(h, dalloc(&h->omega, nb));
+    CK(h, dalloc(&h->phase, nb));
+    CK(h, cudaMemcpy(h->centre, centre, sizeof(double) * 3 * nb, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->omega, omega, sizeof(double) * nb, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->phase, phase, sizeof(double) * nb, cudaMemcpyHostToDevice));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_body_force(lbm_t *h, double gx, double gy, double gz) {
+  if (!h) return LBM_EINVAL;
+  if (!isfinite(gx) || !isfinite(gy) || !isfinite(gz))
+    return fail(h, LBM_ENONFINITE, "non-finite body force");
+  h->gbody[0] = gx;
+  h->gbody[1] = gy;
+  h->gbody[2] = gz;
+  return LBM_OK;
+}
+
+int64_t lbm_time(const lbm_t *h) { return h ? h->t : -1; }
+int lbm_set_time(lbm_t *h, int64_t t) {
+  if (!h) return LBM_EINVAL;
+  h->t = t;
+  return LBM_OK;
+}
+
+static int step_once(lbm_t *h, int n_iter) {
+  cudaStream_t st = h->st;
+  const bool ibm = h->np > 0;
+  if (ibm) {
+    PointsIn p{h->np, h->X, h->body, h->area, h->utarget};
+    Bodies b{h->centre, h->omega, h->phase, h->nb, h->trig};
+    {
+      StageTimer T(h, ST_KIN, h->nb > 0 ? 2 : 1);
+      CK(h, launch_prepare_points(h->g, h->delta, p, b, h->t, h->pp, h->m, h->xpos, st));
+    }
+    {
+      int nl = 0;
+      StageTimer T(h, ST_BIN, 5);
+      CK(h, launch_build_bins(h->g, h->np, h->pp, h->m, st, &nl));
+    }
+    {
+      StageTimer T(h, ST_MOM);
+      CK(h, launch_moments_slots(h->storage, h->g, h->f[h->cur], h->m, h->U0s, h->Gs, st));
+    }
+    const bool warm = h->warm == LBM_WARM_PREVIOUS && h->have_du;
+    if (warm) {
+      StageTimer T(h, ST_SPREAD);
+      CK(h, launch_spread(h->g, h->pp, h->m, h->du, h->Gs, nullptr, st));
+    }
+    for (int it = 0; it < n_iter; it++) {
+      {
+        StageTimer T(h, ST_INTERP);
+        CK(h, launch_interp(h->g, h->np, h->pp, h->m, h->U0s, h->Gs, h->du, h->uint, it == 0,
+                            warm, st));
+      }
+      {
+        StageTimer T(h, ST_SPREAD);
+        CK(h, launch_spread(h->g, h->pp, h->m, h->du, h->Gs, nullptr, st));
+      }
+    }
+    h->have_du = true;
+    h->last_iters = n_iter;
+  } else {
+    h->last_iters = 0;
+  }
+  {
+    StageTimer T(h, ST_COLLIDE);
+    CollideArgs a{};
+    a.src = h->f[h->cur];
+    a.dst = h->f[h->cur ^ 1];
+    a.brick_slot = ibm ? h->m.brick_slot : nullptr;
+    a.Gs = h->Gs;
+    a.gbody[0] = (float)h->gbody[0];
+    a.gbody[1] = (float)h->gbody[1];
+    a.gbody[2] = (float)h->gbody[2];
+    a.tau = (float)h->tau;
+    a.partial = h->stats_on ? h->partial : nullptr;
+    CK(h, launch_collide_stream(h->storage, h->g, a, st));
+  }
+  if (h->stats_on) {
+    StageTimer T(h, ST_STATS);
+    CK(h, launch_stats_reduce(h->partial, h->nparts, h->red_scratch, h->ticket, h->sums,
+                              (double)h->g.ncell, st));
+    h->sums_valid = true;
+  }
+  h->cur ^= 1;
+  h->t++;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
+  if (!h) return LBM_EINVAL;
+  if (n_steps < 0 || n_ibm_iter < 0)
+    return fail(h, LBM_EINVAL, "n_steps = %d, n_ibm_iter = %d", n_steps, n_ibm_iter);
+  if (n_ibm_iter == 0 && h->np > 0)
+    return fail(h, LBM_EINVAL, "tolerance-driven iteration is not available in this build");
+  if (h->nb > 0 && h->max_body >= h->nb)
+    return fail(h, LBM_EINVAL, "points refer to body %d, only %d bodies", h->max_body, h->nb);
+  for (int s = 0; s < n_steps; s++) {
+    int r = step_once(h, n_ibm_iter);
+    if (r != LBM_OK) return r;
+  }
+  return LBM_OK;
+}
+
+int lbm_read_fields_dev(lbm_t *h, float *rho, float *U, float *G) {
+  if (!h) return LBM_EINVAL;
+  if (rho || U) CK(h, launch_moments_dense(h->storage, h->g, h->f[h->cur], rho, U, h->st));
+  if (G) {
+    const float gb[3] = {(float)h->gbody[0], (float)h->gbody[1], (float)h->gbody[2]};
+    CK(h, launch_force_dense(h->g, h->np > 0 ? h->m.brick_slot : nullptr, h->Gs, gb, G,
+                             h->st));
+  }
+  return LBM_OK;
+}
+
+int lbm_read_fields(lbm_t *h, float *rho, float *U, float *G) {
+  if (!h) return LBM_EINVAL;
+  const size_t N = (size_t)h->g.ncell;
+  int r = ensure_tmp(h, sizeof(float) * 7 * N);
+  if (r) return r;
+  float *drho = h->tmp, *dU = h->tmp + N, *dG = h->tmp + 4 * N;
+  r = lbm_read_fields_dev(h, rho ? drho : nullptr, U ? dU : nullptr, G ? dG : nullptr);
+  if (r) return r;
+  if (rho) CK(h, cudaMemcpyAsync(rho, drho, sizeof(float) * N, cudaMemcpyDeviceToHost, h->st));
+  if (U) CK(h, cudaMemcpyAsync(U, dU, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->st));
+  if (G) CK(h, cudaMemcpyAsync(G, dG, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+int ibm_read_points_dev(lbm_t *h, double *x, float *u_interp, float *du) {
+  if (!h) return LBM_EINVAL;
+  if (h->np == 0) return LBM_OK;
+  if (x)
+    CK(h, cudaMemcpyAsync(x, h->xpos, sizeof(double) * 3 * h->np, cudaMemcpyDeviceToDevice,
+                          h->st));
+  if (u_interp) CK(h, launch_pack_points(h->np, h->uint, u_interp, h->st));
+  if (du) CK(h, launch_pack_points(h->np, h->du, du, h->st));
+  return LBM_OK;
+}
+
+int ibm_read_points(lbm_t *h, double *x, float *u_interp, float *du) {
+  if (!h) return LBM_EINVAL;
+  const int64_t n = h->np;
+  if (n == 0) return LBM_OK;
+  int r = ensure_tmp(h, sizeof(double) * 3 * n + sizeof(float) * 6 * n);
+  if (r) return r;
+  double *dx = (double *)h->tmp;
+  float *du_ = (float *)(dx + 3 * n), *dd = du_ + 3 * n;
+  r = ibm_read_points_dev(h, x ? dx : nullptr, u_interp ? du_ : nullptr, du ? dd : nullptr);
+  if (r) return r;
+  if (x) CK(h, cudaMemcpyAsync(x, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->st));
+  if (u_interp)
+    CK(h, cudaMemcpyAsync(u_interp, du_, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->st));
+  if (du) CK(h, cudaMemcpyAsync(du, dd, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+int lbm_read_stats(lbm_t *h, lbm_stats *s) {
+  if (!h || !s) return LBM_EINVAL;
+  memset(s, 0, sizeof *s);
+  double sums[4] = {0, 0, 0, 0};
+  if (h->sums_valid) {
+    CK(h, cudaMemcpyAsync(sums, h->sums, sizeof sums, cudaMemcpyDeviceToHost, h->st));
+  }
+  CK(h, cudaStreamSynchronize(h->st));
+  s->mass = sums[0];
+  s->momentum[0] = sums[1];
+  s->momentum[1] = sums[2];
+  s->momentum[2] = sums[3];
+  s->step = h->t;
+  s->last_ibm_iters = h->last_iters;
+  s->last_residual = -1.0;
+  s->not_converged = h->not_converged;
+  s->kernel_launches = h->nlaunch;
+  if (h->np > 0) {
+    int c = 0;
+    CK(h, cudaMemcpy(&c, h->m.counters, sizeof(int), cudaMemcpyDeviceToHost));
+    s->active_bricks = c;
+  }
+  if (h->sums_valid && !(isfinite(sums[0]) && isfinite(sums[1]) && isfinite(sums[2]) &&
+                         isfinite(sums[3])))
+    return fail(h, LBM_ENONFINITE, "non-finite mass or momentum sum");
+  return LBM_OK;
+}
+
+static int read_pops(lbm_t *h, float *f, int deviations) {
+  if (!h || !f) return LBM_EINVAL;
+  const size_t n = (size_t)Q * h->g.ncell;
+  int r = ensure_tmp(h, sizeof(float) * n);
+  if (r) return r;
+  CK(h, launch_read_populations(h->storage, h->g, h->f[h->cur], h->tmp, deviations, h->st));
+  CK(h, cudaMemcpyAsync(f, h->tmp, sizeof(float) * n, cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+int lbm_read_populations(lbm_t *h, float *f) { return read_pops(h, f, 0); }
+int lbm_read_deviations(lbm_t *h, float *d) { return read_pops(h, d, 1); }
+
+int lbm_write_populations(lbm_t *h, const float *f) {
+  if (!h || !f) return LBM_EINVAL;
+  const size_t n = (size_t)Q * h->g.ncell;
+  if (!all_finite(f, n)) return fail(h, LBM_ENONFINITE, "non-finite population");
+  int r = ensure_tmp(h, sizeof(float) * n);
+  if (r) return r;
+  CK(h, cudaMemcpyAsync(h->tmp, f, sizeof(float) * n, cudaMemcpyHostToDevice, h->st));
+  CK(h, launch_write_populations(h->storage, h->g, h->tmp, h->f[h->cur], h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  h->have_du = false;
+  return LBM_OK;
+}
+
+int lbm_enable_timing(lbm_t *h, int mask) {
+  if (!h) return LBM_EINVAL;
+  CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
+  for (auto &p : h->pending) {
+    h->free_events.push_back(p.a);
+    h->free_events.push_back(p.b);
+  }
+  h->pending.clear();
+  memset(h->ms, 0, sizeof h->ms);
+  memset(h->launches, 0, sizeof h->launches);
+  h->timing = mask;
+  return LBM_OK;
+}
+
+int lbm_num_stages(void) { return kNumStages; }
+const char *lbm_stage_name(int i) { return i >= 0 && i < kNumStages ? kStageNames[i] : ""; }
+
+int lbm_read_timing(lbm_t *h, double *ms, int64_t *launches) {
+  if (!h) return LBM_EINVAL;
+  CK(h, cudaStreamSynchronize(h->st));
+  for (auto &p : h->pending) {
+    float e = 0.f;
+    CK(h, cudaEventElapsedTime(&e, p.a, p.b));
+    h->ms[p.stage] += e;
+    h->launches[p.stage] += p.launches;
+    h->free_events.push_back(p.a);
+    h->free_events.push_back(p.b);
+  }
+  h->pending.clear();
+  for (int i = 0; i < kNumStages; i++) {
+    if (ms) ms[i] = h->ms[i];
+    if (launches) launches[i] = h->launches[i];
+  }
+  return LBM_OK;
+}
+
+// ---- checkpoint ------------------------------------------------------------
+
+namespace {
+struct StateHeader {
+  char magic[8];
+  int32_t version, nx, ny, nz, storage, delta, warm, have_du, nb, pad;
+  int64_t np, t;
+  double tau, gbody[3];
+};
+const char kMagic[8] = {'L', 'B', 'M', 'I', 'B', 'M', '0', '1'};
+}  // namespace
+
+int lbm_save_state(lbm_t *h, void *buf, size_t *len) {
+  if (!h || !len) return LBM_EINVAL;
+  const size_t pop = (size_t)Q * h->g.ncell * storage_bytes(h->storage);
+  const size_t np = (size_t)h->np, nb = (size_t)h->nb;
+  const size_t need = sizeof(StateHeader) + pop + np * (3 * 8 + 4 + 4 + 12 + 16) +
+                      nb * (3 * 8 + 8 + 8);
+  if (!buf) {
+    *len = need;
+    return LBM_OK;
+  }
+  if (*len < need) return fail(h, LBM_ESTATE, "buffer of %zu bytes, need %zu", *len, need);
+  StateHeader hd{};
+  memcpy(hd.magic, kMagic, 8);
+  hd.version = 1;
+  hd.nx = h->g.nx;
+  hd.ny = h->g.ny;
+  hd.nz = h->g.nz;
+  hd.storage = h->storage;
+  hd.delta = h->delta;
+  hd.warm = h->warm;
+  hd.have_du = h->have_du;
+  hd.nb = h->nb;
+  hd.np = h->np;
+  hd.t = h->t;
+  hd.tau = h->tau;
+  memcpy(hd.gbody, h->gbody, sizeof hd.gbody);
+  char *p = (char *)buf;
+  memcpy(p, &hd, sizeof hd);
+  p += sizeof hd;
+  CK(h, cudaStreamSynchronize(h->st));
+  CK(h, cudaMemcpy(p, h->f[h->cur], pop, cudaMemcpyDeviceToHost));
+  p += pop;
+  if (np) {
+    CK(h, cudaMemcpy(p, h->X, 24 * np, cudaMemcpyDeviceToHost));
+    p += 24 * np;
+    CK(h, cudaMemcpy(p, h->body, 4 * np, cudaMemcpyDeviceToHost));
+    p += 4 * np;
+    CK(h, cudaMemcpy(p, h->area, 4 * np, cudaMemcpyDeviceToHost));
+    p += 4 * np;
+    CK(h, cudaMemcpy(p, h->utarget, 12 * np, cudaMemcpyDeviceToHost));
+    p += 12 * np;
+    CK(h, cudaMemcpy(p, h->du, 16 * np, cudaMemcpyDeviceToHost));
+    p += 16 * np;
+  }
+  if (nb) {
+    CK(h, cudaMemcpy(p, h->centre, 24 * nb, cudaMemcpyDeviceToHost));
+    p += 24 * nb;
+    CK(h, cudaMemcpy(p, h->omega, 8 * nb, cudaMemcpyDeviceToHost));
+    p += 8 * nb;
+    CK(h, cudaMemcpy(p, h->phase, 8 * nb, cudaMemcpyDeviceToHost));
+    p += 8 * nb;
+  }
+  *len = need;
+  return LBM_OK;
+}
+
+int lbm_load_state(lbm_t *h, const void *buf, size_t len) {
+  if (!h || !buf) return LBM_EINVAL;
+  if (len < sizeof(StateHeader)) return fail(h, LBM_ESTATE, "state buffer too short");
+  StateHeader hd;
+  memcpy(&hd, buf, sizeof hd);
+  if (memcmp(hd.magic, kMagic, 8) || hd.version != 1)
+    return fail(h, LBM_ESTATE, "not a state buffer of this library");
+  if (hd.nx != h->g.nx || hd.ny != h->g.ny || hd.nz != h->g.nz || hd.storage != h->storage)
+    return fail(h, LBM_ESTATE, "state of a %d x %d x %d lattice (storage %d)", hd.nx, hd.ny,
+                hd.nz, hd.storage);
+  const size_t pop = (size_t)Q * h->g.ncell * storage_bytes(h->storage);
+  const size_t np = (size_t)hd.np, nb = (size_t)hd.nb;
+  const size_t need = sizeof(StateHeader) + pop + np * (3 * 8 + 4 + 4 + 12 + 16) +
+                      nb * (3 * 8 + 8 + 8);
+  if (len < need) return fail(h, LBM_ESTATE, "state buffer of %zu bytes, need %zu", len, need);
+  const char *p = (const char *)buf + sizeof hd;
+  const char *pp = p + pop;
+  const double *X = (const double *)pp;
+  const int32_t *body = (const int32_t *)(pp + 24 * np);
+  const float *area = (const float *)(pp + 28 * np);
+  const float *ut = (const float *)(pp + 32 * np);
+  const float *du = (const float *)(pp + 44 * np);
+  const char *pb = pp + 60 * np;
+  // bodies first (points are validated against them)
+  int r = ibm_set_bodies(h, 0, nullptr, nullptr, nullptr);
+  if (r) return r;
+  r = ibm_set_points(h, (int64_t)np, np ? X : nullptr, np ? ut : nullptr, np ? area : nullptr,
+                     np ? body : nullptr);
+  if (r) return r;
+  if (nb) {
+    r = ibm_set_bodies(h, (int)nb, (const double *)pb, (const double *)(pb + 24 * nb),
+                       (const double *)(pb + 32 * nb));
+    if (r) return r;
+  }
+  CK(h, cudaMemcpy(h->f[h->cur], p, pop, cudaMemcpyHostToDevice));
+  if (np) CK(h, cudaMemcpy(h->du, du, 16 * np, cudaMemcpyHostToDevice));
+  h->have_du = hd.have_du != 0;
+  h->t = hd.t;
+  h->delta = hd.delta;
+  h->warm = hd.warm;
+  h->tau = hd.tau;
+  memcpy(h->gbody, hd.gbody, sizeof hd.gbody);
+  return LBM_OK;
+}
+
+// ---- stateless operators ----------------------------------------------------
+
+int ibm_interpolate_dev(int nx, int ny, int nz, int delta, const float *U, int64_t n,
+                        const double *x, float *u, void *stream) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || n < 0 || (delta != 0 && delta != 1))
+    return fail(nullptr, LBM_EINVAL, "bad arguments to ibm_interpolate_dev");
+  if (n > 0 && (!U || !x || !u)) return fail(nullptr, LBM_EINVAL, "NULL pointer");
+  Geometry g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.ncell = (int64_t)nx * ny * nz;
+  cudaError_t e = launch_interp_dense(g, delta, U, n, x, u, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "%s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct SpreadLayout {
+  size_t brick_flag, brick_slot, slot_brick, slot_count, slot_start, slot_cursor, counters,
+      sorted, base, wts, ut, vals, Gs, total;
+  int max_slots;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+SpreadLayout spread_layout(const Geometry &g, int64_t n) {
+  SpreadLayout L{};
+  const int64_t ms = std::max<int64_t>(1, std::min<int64_t>(g.nbrick, 8 * n));
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align256(o + bytes);
+    return r;
+  };
+  L.brick_flag = take(sizeof(int) * g.nbrick);
+  L.brick_slot = take(sizeof(int) * g.nbrick);
+  L.slot_brick = take(sizeof(int) * ms);
+  L.slot_count = take(sizeof(int) * ms);
+  L.slot_start = take(sizeof(int) * (ms + 1));
+  L.slot_cursor = take(sizeof(int) * ms);
+  L.counters = take(sizeof(int) * 4);
+  L.sorted = take(sizeof(int) * std::max<int64_t>(n, 1));
+  L.base = take(sizeof(int4) * std::max<int64_t>(n, 1));
+  L.wts = take(sizeof(float) * 12 * std::max<int64_t>(n, 1));
+  L.ut = take(sizeof(float4) * std::max<int64_t>(n, 1));
+  L.vals = take(sizeof(float4) * std::max<int64_t>(n, 1));
+  L.Gs = take(sizeof(float) * SLOT_FLOATS * ms);
+  L.total = o;
+  L.max_slots = (int)ms;
+  return L;
+}
+
+bool spread_geometry(int nx, int ny, int nz, Geometry &g) {
+  if (nx <= 0 || ny <= 0 || nz <= 0 || nx % 4 || ny % 4 || nz % 4) return false;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nbx = nx / 4;
+  g.nby = ny / 4;
+  g.nbz = nz / 4;
+  g.ncell = (int64_t)nx * ny * nz;
+  g.nbrick = g.nbx * g.nby * g.nbz;
+  return g.ncell < (1LL << 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ibm_spread_scratch_bytes(int nx, int ny, int nz, int64_t n) {
+  Geometry g{};
+  if (!spread_geometry(nx, ny, nz, g) || n < 0) return 0;
+  return spread_layout(g, n).total;
+}
+
+int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x,
+                   const float *v, float *F, void *scratch, void *stream) {
+  Geometry g{};
+  if (!spread_geometry(nx, ny, nz, g) || n < 0 || (delta != 0 && delta != 1))
+    return fail(nullptr, LBM_EINVAL, "bad arguments to ibm_spread_dev");
+  if (!F || (n > 0 && (!x || !v))) return fail(nullptr, LBM_EINVAL, "NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const SpreadLayout L = spread_layout(g, n);
+  char *base = (char *)scratch;
+  bool own = false;
+  cudaError_t e = cudaSuccess;
+  if (!base) {
+    e = cudaMallocAsync((void **)&base, L.total, st);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ENOMEM, "%s", cudaGetErrorString(e));
+    own = true;
+  } else if (((uintptr_t)base) & 255) {
+    return fail(nullptr, LBM_EINVAL, "scratch must be 256-byte aligned");
+  }
+  BrickMap m{};
+  m.brick_flag = (int *)(base + L.brick_flag);
+  m.brick_slot = (int *)(base + L.brick_slot);
+  m.slot_brick = (int *)(base + L.slot_brick);
+  m.slot_count = (int *)(base + L.slot_count);
+  m.slot_start = (int *)(base + L.slot_start);
+  m.slot_cursor = (int *)(base + L.slot_cursor);
+  m.counters = (int *)(base + L.counters);
+  m.max_slots = L.max_slots;
+  PointPrep pp{};
+  pp.sorted = (int *)(base + L.sorted);
+  pp.base = (int4 *)(base + L.base);
+  pp.wts = (float *)(base + L.wts);
+  pp.ut = (float4 *)(base + L.ut);
+  float4 *vals = (float4 *)(base + L.vals);
+  float *Gs = (float *)(base + L.Gs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, sizeof(float) * 3 * g.ncell, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.brick_flag, 0, sizeof(int) * g.nbrick, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.counters, 0, sizeof(int) * 4, st);
+  if (n > 0) {
+    PointsIn p{n, x, nullptr, nullptr, nullptr};
+    Bodies b{nullptr, nullptr, nullptr, 0, nullptr};
+    if (e == cudaSuccess) e = launch_prepare_points(g, delta, p, b, 0, pp, m, nullptr, st);
+    if (e == cudaSuccess) e = launch_build_bins(g, n, pp, m, st, nullptr);
+    if (e == cudaSuccess) e = launch_pack_vals(n, v, vals, st);
+    if (e == cudaSuccess) e = launch_spread(g, pp, m, vals, Gs, nullptr, st);
+    if (e == cudaSuccess) e = launch_slots_to_dense(g, m, Gs, F, st);
+  }
+  if (own) {
+    cudaError_t e2 = cudaFreeAsync(base, st);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e != cudaSuccess)
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s",
+                cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Shared definitions of the CUDA library: the D3Q19 velocity set, population
+// storage formats, the 4x4x4 brick geometry, and the device-side work
+// descriptors passed from the host orchestration (api.cu) to the kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmibm {
+
+// ---- D3Q19 (Sec. 2): index 0 rest, 1-6 axis, 7-18 face diagonals ---------
+// Order: +x -x +y -y +z -z, (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0),
+// (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1), (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1).
+__host__ __device__ constexpr int ex(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)    ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                               : 0;
+}
+__host__ __device__ constexpr int ey(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17)   ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18)  ? -1
+                                                               : 0;
+}
+__host__ __device__ constexpr int ez(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18)  ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1
+                                                                : 0;
+}
+// lattice weights t_i of Eq. 3
+__host__ __device__ constexpr float wt(int i) {
+  return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr double wtd(int i) {
+  return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+constexpr int Q = 19;
+
+// ---- population storage: deviations d_i = f_i - t_i ----------------------
+// Stored deviations keep the velocity moments well conditioned: rho - 1 and
+// rho U are sums of O(1e-3) numbers instead of O(0.1) ones.
+template <typename S>
+struct Store;
+template <>
+struct Store<float> {
+  static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+  }
+};
+template <>
+struct Store<__half> {
+  static __device__ __forceinline__ float ld(const __half *p) {
+    return __half2float(__ldg(p));
+  }
+  static __device__ __forceinline__ void st(__half *p, float v) {
+    *p = __float2half_rn(v);
+  }
+};
+
+// ---- bricks: 4x4x4 cells, the unit of point binning and force storage -----
+constexpr int BRICK = 4;
+constexpr int BRICK_CELLS = 64;
+constexpr int SLOT_FLOATS = 3 * BRICK_CELLS;  // [3][64] per active brick
+
+struct Geometry {
+  int nx, ny, nz;     // cells
+  int nbx, nby, nbz;  // bricks
+  int64_t ncell;      // nx*ny*nz
+  int nbrick;         // nbx*nby*nbz
+};
+
+__host__ __device__ __forceinline__ int brick_local(int x, int y, int z) {
+  return ((z & 3) * 4 + (y & 3)) * 4 + (x & 3);
+}
+
+__host__ __device__ __forceinline__ int wrapi(int a, int n) {
+  // a in (-n, 2n)
+  return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+// Sparse force storage over the active bricks (those inside the support of
+// some point).  brick_slot[b] = slot or -1; slot_brick[s] = b.  Per slot the
+// fields U0 and G are [3][64] floats (component-major, brick-local cell
+// order z,y,x).  Points are binned by the brick of their base cell floor(x):
+// bin of slot s = sorted[slot_start[s] .. slot_start[s] + slot_count[s]).
+struct BrickMap {
+  int *brick_flag;   // [nbrick] 1 = in some support (set per step, cleared
+                     //           by the compaction)
+  int *brick_slot;   // [nbrick]
+  int *slot_brick;   // [max_slots]
+  int *slot_count;   // [max_slots]
+  int *slot_start;   // [max_slots + 1]
+  int *slot_cursor;  // [max_slots]
+  int *counters;     // [4]: 0 = active slots
+  int max_slots;
+};
+
+// Per-point state prepared once per step (positions do not move within the
+// fixed point): base cell floor(x) (wrapped) with the bin brick in .w, the
+// four tap weights per axis for taps floor(x)-1 .. floor(x)+2, the surface
+// velocity u_k with the area s(k) in .w.
+struct PointPrep {
+  int4 *base;    // [np]
+  float *wts;    // [np][12]  wx[4] wy[4] wz[4]
+  float4 *ut;    // [np]      (u_k, s_k)
+  int *sorted;   // [np]      point indices grouped by bin
+};
+
+}  // namespace lbmibm

@@ -1,0 +1,374 @@
+// Lattice Boltzmann kernels (Sec. 2): the fused pull-stream + BGK collision
+// with the IBM force, moments on the active bricks, read-out kernels and the
+// FP64 reduction of the global sums.
+//
+// Populations are stored structure-of-arrays, f[i][z][y][x], as deviations
+// d_i = f_i - t_i in FP32, BF16 or FP16; all arithmetic is FP32.  Streaming
+// is a pull: the kernel for step t reads d_i(X - e_i) from the source lattice
+// (post-collision values of step t-1), which realises Eq. 4, and writes the
+// post-collision value at X into the destination lattice, so every write is
+// coalesced and each population is read and written exactly once per step.
+#include "kernels.h"
+
+namespace lbmibm {
+
+namespace {
+
+__device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &x, int &y,
+                                            int &z) {
+  uint32_t r = n / (uint32_t)g.nx;
+  x = (int)(n - r * (uint32_t)g.nx);
+  z = (int)(r / (uint32_t)g.ny);
+  y = (int)(r - (uint32_t)z * (uint32_t)g.ny);
+}
+
+// Pull of Eq. 4: d[i] = stored d_i at X - e_i (periodic).
+template <typename S>
+__device__ __forceinline__ void pull(const S *__restrict__ f, const Geometry &g, int x, int y,
+                                     int z, float d[Q]) {
+  const uint32_t nx = g.nx, ny = g.ny;
+  const uint32_t xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+  const uint32_t ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+  const uint32_t zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+  // source of population i is X - e_i: e = +1 reads the "minus" neighbour
+  const uint32_t X[3] = {xp, (uint32_t)x, xm};  // index by e + 1 -> X - e
+  const uint32_t Y[3] = {yp, (uint32_t)y, ym};
+  const uint32_t Z[3] = {zp, (uint32_t)z, zm};
+  const size_t N = (size_t)g.ncell;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const uint32_t src = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * nx + X[ex(i) + 1];
+    d[i] = Store<S>::ld(f + (size_t)i * N + src);
+  }
+}
+
+// Eq. 1 in deviation form: rho - 1 = sum d_i, rho U = sum e_i d_i.
+__device__ __forceinline__ void moments(const float d[Q], float &drho, float &jx, float &jy,
+                                        float &jz) {
+  drho = 0.f;
+  jx = jy = jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    drho += d[i];
+    if (ex(i)) jx += ex(i) > 0 ? d[i] : -d[i];
+    if (ey(i)) jy += ey(i) > 0 ? d[i] : -d[i];
+    if (ez(i)) jz += ez(i) > 0 ? d[i] : -d[i];
+  }
+}
+
+template <typename S, bool FORCE, bool STATS>
+__global__ void __launch_bounds__(256)
+    collide_stream_kernel(const S *__restrict__ src, S *__restrict__ dst, Geometry g,
+                          const int *__restrict__ brick_slot, const float *__restrict__ Gs,
+                          float gbx, float gby, float gbz, float tau,
+                          double *__restrict__ partial) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  float sm = 0.f, spx = 0.f, spy = 0.f, spz = 0.f;
+  if (n < (uint32_t)g.ncell) {
+    int x, y, z;
+    cell_coords(n, g, x, y, z);
+    float d[Q];
+    pull<S>(src, g, x, y, z, d);
+    float drho, jx, jy, jz;
+    moments(d, drho, jx, jy, jz);
+    const float rho = 1.f + drho;
+    const float inv = 1.f / rho;
+    // Sec. 2 step 3: U^G = U + tau G
+    float Gx = gbx, Gy = gby, Gz = gbz;
+    if (FORCE) {
+      const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
+      const int s = __ldg(brick_slot + b);
+      if (s >= 0) {
+        const float *p = Gs + (size_t)s * SLOT_FLOATS + brick_local(x, y, z);
+        Gx += __ldg(p);
+        Gy += __ldg(p + BRICK_CELLS);
+        Gz += __ldg(p + 2 * BRICK_CELLS);
+      }
+    }
+    const float ux = jx * inv + tau * Gx;
+    const float uy = jy * inv + tau * Gy;
+    const float uz = jz * inv + tau * Gz;
+    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float om = 1.f / tau;
+    const size_t N = (size_t)g.ncell;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      // Eq. 3 (with rho) minus t_i, then Eq. 2
+      const float eu = (float)ex(i) * ux + (float)ey(i) * uy + (float)ez(i) * uz;
+      const float eq = wt(i) * (drho + rho * (3.f * eu + 4.5f * eu * eu - uu));
+      const float dn = d[i] + om * (eq - d[i]);
+      Store<S>::st(dst + (size_t)i * N + n, dn);
+      if (STATS) {
+        sm += dn;
+        if (ex(i)) spx += ex(i) > 0 ? dn : -dn;
+        if (ey(i)) spy += ey(i) > 0 ? dn : -dn;
+        if (ez(i)) spz += ez(i) > 0 ? dn : -dn;
+      }
+    }
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sm += __shfl_xor_sync(0xffffffffu, sm, o);
+      spx += __shfl_xor_sync(0xffffffffu, spx, o);
+      spy += __shfl_xor_sync(0xffffffffu, spy, o);
+      spz += __shfl_xor_sync(0xffffffffu, spz, o);
+    }
+    __shared__ double red[8][4];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[w][0] = sm;
+      red[w][1] = spx;
+      red[w][2] = spy;
+      red[w][3] = spz;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      double a = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); k++) a += red[k][threadIdx.x];
+      partial[(size_t)blockIdx.x * 4 + threadIdx.x] = a;
+    }
+  }
+}
+
+// Deterministic two-level FP64 reduction: each block sums a fixed strided
+// subset, the last block to finish sums the block results in index order.
+__global__ void __launch_bounds__(256)
+    stats_reduce_kernel(const double *__restrict__ partial, int nparts,
+                        double *__restrict__ scratch, unsigned *ticket, double *out,
+                        double ncell) {
+  __shared__ double red[256][4];
+  double a[4] = {0, 0, 0, 0};
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nparts; p += gridDim.x * blockDim.x)
+    for (int c = 0; c < 4; c++) a[c] += partial[(size_t)p * 4 + c];
+  for (int c = 0; c < 4; c++) red[threadIdx.x][c] = a[c];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int c = 0; c < 4; c++) red[threadIdx.x][c] += red[threadIdx.x + s][c];
+    __syncthreads();
+  }
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 4; c++) scratch[blockIdx.x * 4 + c] = red[0][c];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x < 4) {
+    __threadfence();
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; b++)
+      s += ((volatile double *)scratch)[b * 4 + threadIdx.x];
+    out[threadIdx.x] = threadIdx.x == 0 ? ncell + s : s;
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128)
+    moments_slots_kernel(const S *__restrict__ f, Geometry g, BrickMap m,
+                         float *__restrict__ U0s, float *__restrict__ Gs) {
+  const int nslots = m.counters[0] < m.max_slots ? m.counters[0] : m.max_slots;
+  const int lane = threadIdx.x & 63;
+  for (int s = blockIdx.x * 2 + (threadIdx.x >> 6); s < nslots; s += gridDim.x * 2) {
+    const int b = m.slot_brick[s];
+    const int bx = b % g.nbx, r = b / g.nbx;
+    const int by = r % g.nby, bz = r / g.nby;
+    const int x = bx * 4 + (lane & 3), y = by * 4 + ((lane >> 2) & 3), z = bz * 4 + (lane >> 4);
+    float d[Q];
+    pull<S>(f, g, x, y, z, d);
+    float drho, jx, jy, jz;
+    moments(d, drho, jx, jy, jz);
+    const float inv = 1.f / (1.f + drho);
+    float *u = U0s + (size_t)s * SLOT_FLOATS + lane;
+    u[0] = jx * inv;
+    u[BRICK_CELLS] = jy * inv;
+    u[2 * BRICK_CELLS] = jz * inv;
+    float *G = Gs + (size_t)s * SLOT_FLOATS + lane;
+    G[0] = 0.f;
+    G[BRICK_CELLS] = 0.f;
+    G[2 * BRICK_CELLS] = 0.f;
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256)
+    moments_dense_kernel(const S *__restrict__ f, Geometry g, float *__restrict__ rho,
+                         float *__restrict__ U) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (uint32_t)g.ncell) return;
+  int x, y, z;
+  cell_coords(n, g, x, y, z);
+  float d[Q];
+  pull<S>(f, g, x, y, z, d);
+  float drho, jx, jy, jz;
+  moments(d, drho, jx, jy, jz);
+  const float r = 1.f + drho, inv = 1.f / r;
+  if (rho) rho[n] = r;
+  if (U) {
+    const size_t N = (size_t)g.ncell;
+    U[n] = jx * inv;
+    U[N + n] = jy * inv;
+    U[2 * N + n] = jz * inv;
+  }
+}
+
+template <typename S>
+__global__ void read_pop_kernel(const S *__restrict__ f, Geometry g, float *__restrict__ out,
+                                int deviations) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (uint32_t)g.ncell) return;
+  int x, y, z;
+  cell_coords(n, g, x, y, z);
+  float d[Q];
+  pull<S>(f, g, x, y, z, d);
+  const size_t N = (size_t)g.ncell;
+#pragma unroll
+  for (int i = 0; i < Q; i++) out[(size_t)i * N + n] = deviations ? d[i] : wt(i) + d[i];
+}
+
+// inverse of the pull: stored_i(X) = f_i(X + e_i) - t_i
+template <typename S>
+__global__ void write_pop_kernel(const float *__restrict__ in, Geometry g, S *__restrict__ f) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (uint32_t)g.ncell) return;
+  int x, y, z;
+  cell_coords(n, g, x, y, z);
+  const size_t N = (size_t)g.ncell;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const int xs = wrapi(x + ex(i), g.nx), ys = wrapi(y + ey(i), g.ny),
+              zs = wrapi(z + ez(i), g.nz);
+    const size_t src = ((size_t)zs * g.ny + ys) * g.nx + xs;
+    Store<S>::st(f + (size_t)i * N + n, in[(size_t)i * N + src] - wt(i));
+  }
+}
+
+__global__ void force_dense_kernel(Geometry g, const int *__restrict__ brick_slot,
+                                   const float *__restrict__ Gs, float gx, float gy, float gz,
+                                   float *__restrict__ G) {
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= (uint32_t)g.ncell) return;
+  int x, y, z;
+  cell_coords(n, g, x, y, z);
+  float a = gx, b = gy, c = gz;
+  if (brick_slot) {
+    const int s = brick_slot[((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2)];
+    if (s >= 0) {
+      const float *p = Gs + (size_t)s * SLOT_FLOATS + brick_local(x, y, z);
+      a += p[0];
+      b += p[BRICK_CELLS];
+      c += p[2 * BRICK_CELLS];
+    }
+  }
+  const size_t N = (size_t)g.ncell;
+  G[n] = a;
+  G[N + n] = b;
+  G[2 * N + n] = c;
+}
+
+inline unsigned cell_blocks(const Geometry &g, int threads) {
+  return (unsigned)((g.ncell + threads - 1) / threads);
+}
+
+template <typename S>
+cudaError_t collide_typed(const Geometry &g, const CollideArgs &a, cudaStream_t st) {
+  const unsigned nb = cell_blocks(g, 256);
+  const S *src = (const S *)a.src;
+  S *dst = (S *)a.dst;
+  const bool force = a.brick_slot != nullptr;
+  const bool stats = a.partial != nullptr;
+  if (force && stats)
+    collide_stream_kernel<S, true, true><<<nb, 256, 0, st>>>(
+        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
+  else if (force)
+    collide_stream_kernel<S, true, false><<<nb, 256, 0, st>>>(
+        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
+  else if (stats)
+    collide_stream_kernel<S, false, true><<<nb, 256, 0, st>>>(
+        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
+  else
+    collide_stream_kernel<S, false, false><<<nb, 256, 0, st>>>(
+        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int collide_blocks(const Geometry &g) { return (int)cell_blocks(g, 256); }
+
+#define DISPATCH_STORAGE(storage, FN, ...)                      \
+  switch (storage) {                                            \
+    case 0:                                                     \
+      return FN<float>(__VA_ARGS__);                            \
+    case 1:                                                     \
+      return FN<__nv_bfloat16>(__VA_ARGS__);                    \
+    case 2:                                                     \
+      return FN<__half>(__VA_ARGS__);                           \
+    default:                                                    \
+      return cudaErrorInvalidValue;                             \
+  }
+
+cudaError_t launch_collide_stream(int storage, const Geometry &g, const CollideArgs &a,
+                                  cudaStream_t st) {
+  DISPATCH_STORAGE(storage, collide_typed, g, a, st);
+}
+
+cudaError_t launch_stats_reduce(const double *partial, int nparts, double *scratch,
+                                unsigned *ticket, double *out, double ncell,
+                                cudaStream_t st) {
+  stats_reduce_kernel<<<128, 256, 0, st>>>(partial, nparts, scratch, ticket, out, ncell);
+  return cudaGetLastError();
+}
+
+namespace {
+template <typename S>
+cudaError_t moments_slots_typed(const Geometry &g, const void *f, const BrickMap &m,
+                                float *U0s, float *Gs, cudaStream_t st) {
+  moments_slots_kernel<S><<<152 * 8, 128, 0, st>>>((const S *)f, g, m, U0s, Gs);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t moments_dense_typed(const Geometry &g, const void *f, float *rho, float *U,
+                                cudaStream_t st) {
+  moments_dense_kernel<S><<<cell_blocks(g, 256), 256, 0, st>>>((const S *)f, g, rho, U);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t read_pop_typed(const Geometry &g, const void *f, float *out, int dev,
+                           cudaStream_t st) {
+  read_pop_kernel<S><<<cell_blocks(g, 256), 256, 0, st>>>((const S *)f, g, out, dev);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t write_pop_typed(const Geometry &g, const float *in, void *f, cudaStream_t st) {
+  write_pop_kernel<S><<<cell_blocks(g, 256), 256, 0, st>>>(in, g, (S *)f);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_moments_slots(int storage, const Geometry &g, const void *f,
+                                 const BrickMap &m, float *U0s, float *Gs, cudaStream_t st) {
+  DISPATCH_STORAGE(storage, moments_slots_typed, g, f, m, U0s, Gs, st);
+}
+cudaError_t launch_moments_dense(int storage, const Geometry &g, const void *f, float *rho,
+                                 float *U, cudaStream_t st) {
+  DISPATCH_STORAGE(storage, moments_dense_typed, g, f, rho, U, st);
+}
+cudaError_t launch_read_populations(int storage, const Geometry &g, const void *f,
+                                    float *out, int deviations, cudaStream_t st) {
+  DISPATCH_STORAGE(storage, read_pop_typed, g, f, out, deviations, st);
+}
+cudaError_t launch_write_populations(int storage, const Geometry &g, const float *in,
+                                     void *f, cudaStream_t st) {
+  DISPATCH_STORAGE(storage, write_pop_typed, g, in, f, st);
+}
+cudaError_t launch_force_dense(const Geometry &g, const int *brick_slot, const float *Gs,
+                               const float gbody[3], float *G, cudaStream_t st) {
+  force_dense_kernel<<<cell_blocks(g, 256), 256, 0, st>>>(g, brick_slot, Gs, gbody[0],
+                                                          gbody[1], gbody[2], G);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmibm
