@@ -222,6 +222,33 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n,
                    const double *x, const float *v, float *F, void *scratch,
                    void *stream);
 
+/* ---- spreading without any allocation ---------------------------------- */
+
+/* Size of the library's static scratch area on each device (16 MiB). */
+#define LBM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Same result as ibm_spread_dev, for callers that cannot allocate device
+ * memory: code embedded in a host application whose memory pool owns the
+ * whole device, or a time-critical loop that must not pay cudaMalloc's
+ * implicit device synchronisation.  The paper has no counterpart; this is a
+ * service of the library.
+ *
+ * Inputs and output are the caller's, exactly as for ibm_spread_dev.  The
+ * scratch space is a static device array of LBM_NOALLOC_SCRATCH_BYTES that
+ * every device which loads the library keeps until the process exits; the
+ * call allocates and frees nothing.  Problems whose
+ * ibm_spread_scratch_bytes(nx, ny, nz, n) exceeds that size are rejected with
+ * LBM_EINVAL (for example 64^3 with 12,000 points needs about 4.3 MiB).
+ *
+ * The first call on a device (the current device when it is made) looks up
+ * the array's device address; make that first call before any stream capture
+ * begins.  All calls on a device share the one array and it keeps the
+ * previous call's contents (the call clears what must start at zero), so
+ * calls that overlap on the GPU, on different streams or from different host
+ * threads, race: serialise them. */
+int ibm_spread_dev_noalloc(int nx, int ny, int nz, int delta, int64_t n,
+                           const double *x, const float *v, float *F, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,7 +88,10 @@ _SIGS = {
     "ibm_interpolate_dev": (_i, [_i, _i, _i, _i, _p, _i64, _p, _p, _p]),
     "ibm_spread_scratch_bytes": (_c.c_size_t, [_i, _i, _i, _i64]),
     "ibm_spread_dev": (_i, [_i, _i, _i, _i, _i64, _p, _p, _p, _p, _p]),
+    "ibm_spread_dev_noalloc": (_i, [_i, _i, _i, _i, _i64, _p, _p, _p, _p]),
 }
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 def header_functions():
@@ -316,3 +319,12 @@ def spread_dev(x, v, F, delta="cosine", scratch=None, stream=None):
     raw = getattr(stream, "cuda_stream", stream)
     _check(load().ibm_spread_dev(nx, ny, nz, DELTA[delta], x.shape[0], _ptr(x), _ptr(v),
                                  _ptr(F), _ptr(scratch), _p(raw) if raw else None))
+
+
+def spread_dev_noalloc(x, v, F, delta="cosine", stream=None):
+    """ibm_spread_dev_noalloc: spreading with the library's static scratch
+    (no device allocation).  Same arguments as spread_dev without scratch."""
+    _, nz, ny, nx = F.shape
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(load().ibm_spread_dev_noalloc(nx, ny, nz, DELTA[delta], x.shape[0], _ptr(x),
+                                         _ptr(v), _ptr(F), _p(raw) if raw else None))

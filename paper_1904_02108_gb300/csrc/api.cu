@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -929,3 +930,50 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
 }
 
 }  // extern "C"
+
+// ---- spreading without any allocation ---------------------------------------
+//
+// Scratch for ibm_spread_dev_noalloc: a static device array, so the call never
+// allocates.  Host code only knows the symbol; its device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LBM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" int ibm_spread_dev_noalloc(int nx, int ny, int nz, int delta, int64_t n,
+                                      const double *x, const float *v, float *F,
+                                      void *stream) {
+  const size_t need = ibm_spread_scratch_bytes(nx, ny, nz, n);
+  if (need == 0)
+    return fail(nullptr, LBM_EINVAL, "bad arguments to ibm_spread_dev_noalloc");
+  if (need > LBM_NOALLOC_SCRATCH_BYTES)
+    return fail(nullptr, LBM_EINVAL,
+                "ibm_spread_dev_noalloc: %d x %d x %d with %lld points needs %zu bytes of "
+                "scratch, the static area holds %zu",
+                nx, ny, nz, (long long)n, need, (size_t)LBM_NOALLOC_SCRATCH_BYTES);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(nullptr, LBM_EINVAL, "device ordinal %d out of range", dev);
+  void *ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      e = cudaGetSymbolAddress(&g_noalloc_addr[dev], g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_addr[dev] = nullptr;
+        return fail(nullptr, LBM_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      }
+    }
+    ptr = g_noalloc_addr[dev];
+  }
+  // the allocating entry point with caller scratch: it allocates nothing and
+  // clears the output and the binning state it needs at zero
+  return ibm_spread_dev(nx, ny, nz, delta, n, x, v, F, ptr, stream);
+}
