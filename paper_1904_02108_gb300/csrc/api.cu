@@ -23,10 +23,10 @@ using namespace lbmibm;
 
 namespace {
 
-const char *kStageNames[] = {"kinematics", "binning",        "moments", "interp",
-                             "spread",     "collide_stream", "stats"};
+const char *kStageNames[] = {"kinematics",   "pairs",          "brick_init", "point_update",
+                             "brick_spread", "collide_stream", "stats"};
 constexpr int kNumStages = 7;
-enum Stage { ST_KIN, ST_BIN, ST_MOM, ST_INTERP, ST_SPREAD, ST_COLLIDE, ST_STATS };
+enum Stage { ST_KIN, ST_PAIRS, ST_INIT, ST_UPDATE, ST_SPREAD, ST_COLLIDE, ST_STATS };
 
 thread_local std::string g_create_error;
 
@@ -53,6 +53,7 @@ struct lbm {
   double *centre = nullptr, *omega = nullptr, *phase = nullptr, *trig = nullptr;
   PointPrep pp{};
   BrickMap m{};
+  PairMap pm{};
   float *U0s = nullptr, *Gs = nullptr, *res = nullptr;
   float4 *du = nullptr, *uint = nullptr;
   double *xpos = nullptr;
@@ -176,14 +177,18 @@ void free_points(lbm_t *h) {
   dfree(h->pp.base);
   dfree(h->pp.wts);
   dfree(h->pp.ut);
-  dfree(h->pp.sorted);
   dfree(h->du);
   dfree(h->uint);
   dfree(h->xpos);
   dfree(h->m.slot_brick);
-  dfree(h->m.slot_count);
-  dfree(h->m.slot_start);
-  dfree(h->m.slot_cursor);
+  dfree(h->pm.count);
+  dfree(h->pm.start);
+  dfree(h->pm.cursor);
+  dfree(h->pm.k);
+  dfree(h->pm.w);
+  dfree(h->pm.part);
+  dfree(h->pm.point_pairs);
+  h->pm.max_pairs = 0;
   dfree(h->U0s);
   dfree(h->Gs);
   dfree(h->res);
@@ -372,14 +377,18 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->pp.base, n));
     CK(h, dalloc(&h->pp.wts, 12 * n));
     CK(h, dalloc(&h->pp.ut, n));
-    CK(h, dalloc(&h->pp.sorted, n));
     CK(h, dalloc(&h->du, n));
     CK(h, dalloc(&h->uint, n));
     CK(h, dalloc(&h->xpos, 3 * n));
     CK(h, dalloc(&h->m.slot_brick, ms));
-    CK(h, dalloc(&h->m.slot_count, ms));
-    CK(h, dalloc(&h->m.slot_start, ms + 1));
-    CK(h, dalloc(&h->m.slot_cursor, ms));
+    CK(h, dalloc(&h->pm.count, ms));
+    CK(h, dalloc(&h->pm.start, ms + 1));
+    CK(h, dalloc(&h->pm.cursor, ms));
+    CK(h, dalloc(&h->pm.k, 8 * n));
+    CK(h, dalloc(&h->pm.w, 3 * 8 * n));
+    CK(h, dalloc(&h->pm.part, 8 * n));
+    CK(h, dalloc(&h->pm.point_pairs, 8 * n));
+    h->pm.max_pairs = 8 * n;
     CK(h, dalloc(&h->U0s, (size_t)ms * SLOT_FLOATS));
     CK(h, dalloc(&h->Gs, (size_t)ms * SLOT_FLOATS));
     CK(h, dalloc(&h->res, ms));
@@ -463,31 +472,28 @@ static int step_once(lbm_t *h, int n_iter) {
     Bodies b{h->centre, h->omega, h->phase, h->nb, h->trig};
     {
       StageTimer T(h, ST_KIN, h->nb > 0 ? 2 : 1);
-      CK(h, launch_prepare_points(h->g, h->delta, p, b, h->t, h->pp, h->m, h->xpos, st));
+      CK(h, launch_prepare_points(h->g, h->delta, p, b, h->t, h->pp, h->m, h->pm, h->xpos,
+                                  st));
     }
     {
-      int nl = 0;
-      StageTimer T(h, ST_BIN, 5);
-      CK(h, launch_build_bins(h->g, h->np, h->pp, h->m, st, &nl));
-    }
-    {
-      StageTimer T(h, ST_MOM);
-      CK(h, launch_moments_slots(h->storage, h->g, h->f[h->cur], h->m, h->U0s, h->Gs, st));
+      StageTimer T(h, ST_PAIRS, 5);
+      CK(h, launch_build_pairs(h->g, h->np, h->pp, h->m, h->pm, st));
     }
     const bool warm = h->warm == LBM_WARM_PREVIOUS && h->have_du;
-    if (warm) {
-      StageTimer T(h, ST_SPREAD);
-      CK(h, launch_spread(h->g, h->pp, h->m, h->du, h->Gs, nullptr, st));
+    {
+      StageTimer T(h, ST_INIT);
+      CK(h, launch_brick_init(h->storage, h->g, h->f[h->cur], h->m, h->pm,
+                              warm ? h->du : nullptr, h->U0s, h->Gs, st));
     }
     for (int it = 0; it < n_iter; it++) {
       {
-        StageTimer T(h, ST_INTERP);
-        CK(h, launch_interp(h->g, h->np, h->pp, h->m, h->U0s, h->Gs, h->du, h->uint, it == 0,
-                            warm, st));
+        StageTimer T(h, ST_UPDATE);
+        CK(h, launch_point_update(h->np, h->pp, h->pm, h->du, h->uint, it == 0, warm, st));
       }
       {
         StageTimer T(h, ST_SPREAD);
-        CK(h, launch_spread(h->g, h->pp, h->m, h->du, h->Gs, nullptr, st));
+        CK(h, launch_brick_spread(h->m, h->pm, h->du, h->U0s, h->Gs, nullptr,
+                                  it + 1 < n_iter, st));
       }
     }
     h->have_du = true;
@@ -816,8 +822,8 @@ int ibm_interpolate_dev(int nx, int ny, int nz, int delta, const float *U, int64
 namespace {
 
 struct SpreadLayout {
-  size_t brick_flag, brick_slot, slot_brick, slot_count, slot_start, slot_cursor, counters,
-      sorted, base, wts, ut, vals, Gs, total;
+  size_t brick_flag, brick_slot, slot_brick, counters, count, start, cursor, pk, pw, ppart,
+      point_pairs, base, wts, ut, vals, Gs, total;
   int max_slots;
 };
 
@@ -826,6 +832,7 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 SpreadLayout spread_layout(const Geometry &g, int64_t n) {
   SpreadLayout L{};
   const int64_t ms = std::max<int64_t>(1, std::min<int64_t>(g.nbrick, 8 * n));
+  const int64_t n1 = std::max<int64_t>(n, 1);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t r = o;
@@ -835,15 +842,18 @@ SpreadLayout spread_layout(const Geometry &g, int64_t n) {
   L.brick_flag = take(sizeof(int) * g.nbrick);
   L.brick_slot = take(sizeof(int) * g.nbrick);
   L.slot_brick = take(sizeof(int) * ms);
-  L.slot_count = take(sizeof(int) * ms);
-  L.slot_start = take(sizeof(int) * (ms + 1));
-  L.slot_cursor = take(sizeof(int) * ms);
   L.counters = take(sizeof(int) * 4);
-  L.sorted = take(sizeof(int) * std::max<int64_t>(n, 1));
-  L.base = take(sizeof(int4) * std::max<int64_t>(n, 1));
-  L.wts = take(sizeof(float) * 12 * std::max<int64_t>(n, 1));
-  L.ut = take(sizeof(float4) * std::max<int64_t>(n, 1));
-  L.vals = take(sizeof(float4) * std::max<int64_t>(n, 1));
+  L.count = take(sizeof(int) * ms);
+  L.start = take(sizeof(int) * (ms + 1));
+  L.cursor = take(sizeof(int) * ms);
+  L.pk = take(sizeof(int) * 8 * n1);
+  L.pw = take(sizeof(float4) * 3 * 8 * n1);
+  L.ppart = take(sizeof(float4) * 8 * n1);
+  L.point_pairs = take(sizeof(int) * 8 * n1);
+  L.base = take(sizeof(int4) * n1);
+  L.wts = take(sizeof(float) * 12 * n1);
+  L.ut = take(sizeof(float4) * n1);
+  L.vals = take(sizeof(float4) * n1);
   L.Gs = take(sizeof(float) * SLOT_FLOATS * ms);
   L.total = o;
   L.max_slots = (int)ms;
@@ -895,13 +905,18 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   m.brick_flag = (int *)(base + L.brick_flag);
   m.brick_slot = (int *)(base + L.brick_slot);
   m.slot_brick = (int *)(base + L.slot_brick);
-  m.slot_count = (int *)(base + L.slot_count);
-  m.slot_start = (int *)(base + L.slot_start);
-  m.slot_cursor = (int *)(base + L.slot_cursor);
   m.counters = (int *)(base + L.counters);
   m.max_slots = L.max_slots;
+  PairMap pm{};
+  pm.count = (int *)(base + L.count);
+  pm.start = (int *)(base + L.start);
+  pm.cursor = (int *)(base + L.cursor);
+  pm.k = (int *)(base + L.pk);
+  pm.w = (float4 *)(base + L.pw);
+  pm.part = (float4 *)(base + L.ppart);
+  pm.point_pairs = (int *)(base + L.point_pairs);
+  pm.max_pairs = 8 * n;
   PointPrep pp{};
-  pp.sorted = (int *)(base + L.sorted);
   pp.base = (int4 *)(base + L.base);
   pp.wts = (float *)(base + L.wts);
   pp.ut = (float4 *)(base + L.ut);
@@ -913,10 +928,10 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   if (n > 0) {
     PointsIn p{n, x, nullptr, nullptr, nullptr};
     Bodies b{nullptr, nullptr, nullptr, 0, nullptr};
-    if (e == cudaSuccess) e = launch_prepare_points(g, delta, p, b, 0, pp, m, nullptr, st);
-    if (e == cudaSuccess) e = launch_build_bins(g, n, pp, m, st, nullptr);
+    if (e == cudaSuccess) e = launch_prepare_points(g, delta, p, b, 0, pp, m, pm, nullptr, st);
+    if (e == cudaSuccess) e = launch_build_pairs(g, n, pp, m, pm, st);
     if (e == cudaSuccess) e = launch_pack_vals(n, v, vals, st);
-    if (e == cudaSuccess) e = launch_spread(g, pp, m, vals, Gs, nullptr, st);
+    if (e == cudaSuccess) e = launch_brick_spread(m, pm, vals, nullptr, Gs, nullptr, 0, st);
     if (e == cudaSuccess) e = launch_slots_to_dense(g, m, Gs, F, st);
   }
   if (own) {

@@ -71,6 +71,10 @@ constexpr int BRICK = 4;
 constexpr int BRICK_CELLS = 64;
 constexpr int SLOT_FLOATS = 3 * BRICK_CELLS;  // [3][64] per active brick
 
+// Grid of the kernels that loop over the active bricks (grid-stride): 16
+// blocks per SM of the 152-SM GB300.
+constexpr int PERSISTENT_BLOCKS = 152 * 16;
+
 struct Geometry {
   int nx, ny, nz;     // cells
   int nbx, nby, nbz;  // bricks
@@ -87,32 +91,42 @@ __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   return a < 0 ? a + n : (a >= n ? a - n : a);
 }
 
-// Sparse force storage over the active bricks (those inside the support of
-// some point).  brick_slot[b] = slot or -1; slot_brick[s] = b.  Per slot the
-// fields U0 and G are [3][64] floats (component-major, brick-local cell
-// order z,y,x).  Points are binned by the brick of their base cell floor(x):
-// bin of slot s = sorted[slot_start[s] .. slot_start[s] + slot_count[s]).
+// Sparse storage over the active bricks (those inside the support of some
+// point).  brick_slot[b] = slot or -1; slot_brick[s] = b.  Per slot the fields
+// U0 and G are [3][64] floats (component-major, brick-local cell order z,y,x).
 struct BrickMap {
   int *brick_flag;   // [nbrick] 1 = in some support (set per step, cleared
                      //           by the compaction)
   int *brick_slot;   // [nbrick]
   int *slot_brick;   // [max_slots]
-  int *slot_count;   // [max_slots]
-  int *slot_start;   // [max_slots + 1]
-  int *slot_cursor;  // [max_slots]
-  int *counters;     // [4]: 0 = active slots
+  int *counters;     // [4]: 0 = active slots, 1 = overflow flag
   int max_slots;
 };
 
-// Per-point state prepared once per step (positions do not move within the
-// fixed point): base cell floor(x) (wrapped) with the bin brick in .w, the
-// four tap weights per axis for taps floor(x)-1 .. floor(x)+2, the surface
-// velocity u_k with the area s(k) in .w.
+// (brick, point) pairs: one per brick that a point's support overlaps (at most
+// eight per point).  Grouped by slot, ascending point index inside a slot (a
+// fixed summation order).  Built once per step; the points do not move inside
+// the fixed point.
+struct PairMap {
+  int *count;        // [max_slots] pairs of each slot
+  int *start;        // [max_slots + 1]
+  int *cursor;       // [max_slots]
+  int *k;            // [max_pairs] point of each pair
+  float4 *w;         // [max_pairs][3] weights of the brick's cells 0..3 along
+                     //                x, y, z (0 outside the support)
+  float4 *part;      // [max_pairs] brick's share of the interpolated velocity
+  int *point_pairs;  // [np][8] pair of each of the point's bricks, or -1;
+                     //         index = (z hi) << 2 | (y hi) << 1 | (x hi)
+  int64_t max_pairs;
+};
+
+// Per-point state prepared once per step: base cell floor(x) (wrapped) in
+// .xyz, the four tap weights per axis for taps floor(x)-1 .. floor(x)+2, the
+// surface velocity u_k with the area s(k) in .w.
 struct PointPrep {
   int4 *base;    // [np]
   float *wts;    // [np][12]  wx[4] wy[4] wz[4]
   float4 *ut;    // [np]      (u_k, s_k)
-  int *sorted;   // [np]      point indices grouped by bin
 };
 
 }  // namespace lbmibm

@@ -25,9 +25,6 @@ cudaError_t launch_collide_stream(int storage, const Geometry &g, const CollideA
 cudaError_t launch_stats_reduce(const double *partial, int nparts, double *scratch,
                                 unsigned *ticket, double *out, double ncell,
                                 cudaStream_t st);
-// rho, U0 on the cells of every active brick (pull of Eq. 4 + Eq. 1); G = 0.
-cudaError_t launch_moments_slots(int storage, const Geometry &g, const void *f,
-                                 const BrickMap &m, float *U0s, float *Gs, cudaStream_t st);
 // rho[N], U[3][N] on every cell (either may be NULL).
 cudaError_t launch_moments_dense(int storage, const Geometry &g, const void *f, float *rho,
                                  float *U, cudaStream_t st);
@@ -59,19 +56,26 @@ struct PointsIn {
 // Kinematics (Alg. 1, first iteration) + per-point weights + brick flags.
 cudaError_t launch_prepare_points(const Geometry &g, int delta, const PointsIn &p,
                                   const Bodies &b, int64_t t, PointPrep &pp,
-                                  const BrickMap &m, double *xpos, cudaStream_t st);
-// flags -> slots, bins of points by brick (deterministic order in each bin)
-cudaError_t launch_build_bins(const Geometry &g, int64_t np, const PointPrep &pp,
-                              const BrickMap &m, cudaStream_t st, int *nlaunch);
-// One fixed-point interpolation (Alg. 1): u = I[U0 + G]; g = u_k - u;
-// du += s g (du starts at 0 when first && !warm).
-cudaError_t launch_interp(const Geometry &g, int64_t np, const PointPrep &pp,
-                          const BrickMap &m, const float *U0s, const float *Gs, float4 *du,
-                          float4 *uint, int first, int warm, cudaStream_t st);
-// G = S[du] over every active brick, gathered from neighbouring bins
-// (Alg. 2 without atomics); res[slot] = sum (G_new - G_old)^2 (NULL: skip).
-cudaError_t launch_spread(const Geometry &g, const PointPrep &pp, const BrickMap &m,
-                          const float4 *vals, float *Gs, float *res, cudaStream_t st);
+                                  const BrickMap &m, const PairMap &pm, double *xpos,
+                                  cudaStream_t st);
+// flags -> slots; (brick, point) pairs grouped by brick in a fixed order, with
+// brick-local weights (5 launches when np > 0, else 1)
+cudaError_t launch_build_pairs(const Geometry &g, int64_t np, const PointPrep &pp,
+                               const BrickMap &m, const PairMap &pm, cudaStream_t st);
+// U0 on the active bricks (Eq. 1), G_0 = 0 or S[du_init], pair shares of
+// I[U0 + G_0]
+cudaError_t launch_brick_init(int storage, const Geometry &g, const void *f, const BrickMap &m,
+                              const PairMap &pm, const float4 *du_init, float *U0s, float *Gs,
+                              cudaStream_t st);
+// G = S[vals] on the active bricks (Alg. 2 as a gather); res[slot] = squared
+// change of G (NULL: skip); pair shares of I[U0 + G] if do_interp
+cudaError_t launch_brick_spread(const BrickMap &m, const PairMap &pm, const float4 *vals,
+                                const float *U0s, float *Gs, float *res, int do_interp,
+                                cudaStream_t st);
+// u_n(k) from the pair shares; g = u_k - u_n; du += s g (Alg. 1 loop body)
+cudaError_t launch_point_update(int64_t np, const PointPrep &pp, const PairMap &pm,
+                                float4 *du, float4 *uint, int first, int warm,
+                                cudaStream_t st);
 // stateless operators (caller memory)
 cudaError_t launch_interp_dense(const Geometry &g, int delta, const float *U, int64_t n,
                                 const double *x, float *u, cudaStream_t st);

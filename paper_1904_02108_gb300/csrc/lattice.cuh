@@ -1,0 +1,53 @@
+// Device helpers shared by the lattice kernels (lbm.cu) and the brick kernels
+// of the immersed boundary loop (ibm.cu): cell coordinates, the pull of Eq. 4
+// and the moments of Eq. 1 in deviation form.
+#pragma once
+
+#include "common.cuh"
+
+namespace lbmibm {
+
+__device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &x, int &y,
+                                            int &z) {
+  uint32_t r = n / (uint32_t)g.nx;
+  x = (int)(n - r * (uint32_t)g.nx);
+  z = (int)(r / (uint32_t)g.ny);
+  y = (int)(r - (uint32_t)z * (uint32_t)g.ny);
+}
+
+// Pull of Eq. 4: d[i] = stored d_i at X - e_i (periodic).
+template <typename S>
+__device__ __forceinline__ void pull(const S *__restrict__ f, const Geometry &g, int x, int y,
+                                     int z, float d[Q]) {
+  const uint32_t nx = g.nx, ny = g.ny;
+  const uint32_t xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
+  const uint32_t ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
+  const uint32_t zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+  // source of population i is X - e_i: e = +1 reads the "minus" neighbour
+  const uint32_t X[3] = {xp, (uint32_t)x, xm};  // index by e + 1 -> X - e
+  const uint32_t Y[3] = {yp, (uint32_t)y, ym};
+  const uint32_t Z[3] = {zp, (uint32_t)z, zm};
+  const size_t N = (size_t)g.ncell;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const uint32_t src = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * nx + X[ex(i) + 1];
+    d[i] = Store<S>::ld(f + (size_t)i * N + src);
+  }
+}
+
+// Eq. 1 in deviation form: rho - 1 = sum d_i, rho U = sum e_i d_i.
+__device__ __forceinline__ void moments(const float d[Q], float &drho, float &jx, float &jy,
+                                        float &jz) {
+  drho = 0.f;
+  jx = jy = jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    drho += d[i];
+    if (ex(i)) jx += ex(i) > 0 ? d[i] : -d[i];
+    if (ey(i)) jy += ey(i) > 0 ? d[i] : -d[i];
+    if (ez(i)) jz += ez(i) > 0 ? d[i] : -d[i];
+  }
+}
+
+
+}  // namespace lbmibm

@@ -9,52 +9,11 @@
 // post-collision value at X into the destination lattice, so every write is
 // coalesced and each population is read and written exactly once per step.
 #include "kernels.h"
+#include "lattice.cuh"
 
 namespace lbmibm {
 
 namespace {
-
-__device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &x, int &y,
-                                            int &z) {
-  uint32_t r = n / (uint32_t)g.nx;
-  x = (int)(n - r * (uint32_t)g.nx);
-  z = (int)(r / (uint32_t)g.ny);
-  y = (int)(r - (uint32_t)z * (uint32_t)g.ny);
-}
-
-// Pull of Eq. 4: d[i] = stored d_i at X - e_i (periodic).
-template <typename S>
-__device__ __forceinline__ void pull(const S *__restrict__ f, const Geometry &g, int x, int y,
-                                     int z, float d[Q]) {
-  const uint32_t nx = g.nx, ny = g.ny;
-  const uint32_t xm = x == 0 ? g.nx - 1 : x - 1, xp = x == g.nx - 1 ? 0 : x + 1;
-  const uint32_t ym = y == 0 ? g.ny - 1 : y - 1, yp = y == g.ny - 1 ? 0 : y + 1;
-  const uint32_t zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
-  // source of population i is X - e_i: e = +1 reads the "minus" neighbour
-  const uint32_t X[3] = {xp, (uint32_t)x, xm};  // index by e + 1 -> X - e
-  const uint32_t Y[3] = {yp, (uint32_t)y, ym};
-  const uint32_t Z[3] = {zp, (uint32_t)z, zm};
-  const size_t N = (size_t)g.ncell;
-#pragma unroll
-  for (int i = 0; i < Q; i++) {
-    const uint32_t src = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * nx + X[ex(i) + 1];
-    d[i] = Store<S>::ld(f + (size_t)i * N + src);
-  }
-}
-
-// Eq. 1 in deviation form: rho - 1 = sum d_i, rho U = sum e_i d_i.
-__device__ __forceinline__ void moments(const float d[Q], float &drho, float &jx, float &jy,
-                                        float &jz) {
-  drho = 0.f;
-  jx = jy = jz = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; i++) {
-    drho += d[i];
-    if (ex(i)) jx += ex(i) > 0 ? d[i] : -d[i];
-    if (ey(i)) jy += ey(i) > 0 ? d[i] : -d[i];
-    if (ez(i)) jz += ez(i) > 0 ? d[i] : -d[i];
-  }
-}
 
 template <typename S, bool FORCE, bool STATS>
 __global__ void __launch_bounds__(256)
@@ -162,33 +121,6 @@ __global__ void __launch_bounds__(256)
       s += ((volatile double *)scratch)[b * 4 + threadIdx.x];
     out[threadIdx.x] = threadIdx.x == 0 ? ncell + s : s;
     if (threadIdx.x == 0) *ticket = 0u;
-  }
-}
-
-template <typename S>
-__global__ void __launch_bounds__(128)
-    moments_slots_kernel(const S *__restrict__ f, Geometry g, BrickMap m,
-                         float *__restrict__ U0s, float *__restrict__ Gs) {
-  const int nslots = m.counters[0] < m.max_slots ? m.counters[0] : m.max_slots;
-  const int lane = threadIdx.x & 63;
-  for (int s = blockIdx.x * 2 + (threadIdx.x >> 6); s < nslots; s += gridDim.x * 2) {
-    const int b = m.slot_brick[s];
-    const int bx = b % g.nbx, r = b / g.nbx;
-    const int by = r % g.nby, bz = r / g.nby;
-    const int x = bx * 4 + (lane & 3), y = by * 4 + ((lane >> 2) & 3), z = bz * 4 + (lane >> 4);
-    float d[Q];
-    pull<S>(f, g, x, y, z, d);
-    float drho, jx, jy, jz;
-    moments(d, drho, jx, jy, jz);
-    const float inv = 1.f / (1.f + drho);
-    float *u = U0s + (size_t)s * SLOT_FLOATS + lane;
-    u[0] = jx * inv;
-    u[BRICK_CELLS] = jy * inv;
-    u[2 * BRICK_CELLS] = jz * inv;
-    float *G = Gs + (size_t)s * SLOT_FLOATS + lane;
-    G[0] = 0.f;
-    G[BRICK_CELLS] = 0.f;
-    G[2 * BRICK_CELLS] = 0.f;
   }
 }
 
@@ -324,12 +256,6 @@ cudaError_t launch_stats_reduce(const double *partial, int nparts, double *scrat
 
 namespace {
 template <typename S>
-cudaError_t moments_slots_typed(const Geometry &g, const void *f, const BrickMap &m,
-                                float *U0s, float *Gs, cudaStream_t st) {
-  moments_slots_kernel<S><<<152 * 8, 128, 0, st>>>((const S *)f, g, m, U0s, Gs);
-  return cudaGetLastError();
-}
-template <typename S>
 cudaError_t moments_dense_typed(const Geometry &g, const void *f, float *rho, float *U,
                                 cudaStream_t st) {
   moments_dense_kernel<S><<<cell_blocks(g, 256), 256, 0, st>>>((const S *)f, g, rho, U);
@@ -348,10 +274,6 @@ cudaError_t write_pop_typed(const Geometry &g, const float *in, void *f, cudaStr
 }
 }  // namespace
 
-cudaError_t launch_moments_slots(int storage, const Geometry &g, const void *f,
-                                 const BrickMap &m, float *U0s, float *Gs, cudaStream_t st) {
-  DISPATCH_STORAGE(storage, moments_slots_typed, g, f, m, U0s, Gs, st);
-}
 cudaError_t launch_moments_dense(int storage, const Geometry &g, const void *f, float *rho,
                                  float *U, cudaStream_t st) {
   DISPATCH_STORAGE(storage, moments_dense_typed, g, f, rho, U, st);

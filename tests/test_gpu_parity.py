@@ -273,9 +273,12 @@ def test_timing_and_launch_counters(gpu_lib, torch_cuda):
     lat.enable_timing(True)
     lat.step(3, 5)
     t = lat.timing()
-    assert t["collide_stream"][1] == 3 and t["interp"][1] == 15 and t["spread"][1] == 15
+    assert t["collide_stream"][1] == 3 and t["point_update"][1] == 15
+    assert t["brick_spread"][1] == 15 and t["brick_init"][1] == 3 and t["pairs"][1] == 15
     assert all(ms >= 0 for ms, _ in t.values()) and t["collide_stream"][0] > 0
-    assert lat.stats()["kernel_launches"] >= 3 * (1 + 5 + 1 + 10 + 1 + 1)
+    # per step: trig + points, 5 pair kernels, init, 5 x 2 iteration kernels,
+    # collide-stream, stats
+    assert lat.stats()["kernel_launches"] == 3 * (2 + 5 + 1 + 10 + 1 + 1)
     lat.close()
 
 
