@@ -178,6 +178,14 @@ int lbm_write_populations(lbm_t *h, const float *f);
  * same layout and pull offset as lbm_read_populations.  Host buffer. */
 int lbm_read_deviations(lbm_t *h, float *d);
 
+/* Residual eps_n = ||S[s g_n]|| / ||S[s u_k]|| of every fixed-point iteration
+ * of the last step in tolerance mode (Sec. 3 stops when g is "negligibly
+ * small"; the norm is over the lattice, in FP64; if every u_k vanishes the
+ * denominator is ||S[s (u_k - I[U0])]||).  Writes min(n, cap) values and
+ * returns n, the number of iterations of that step; 0 after a fixed-count
+ * step. */
+int lbm_read_residuals(lbm_t *h, double *eps, int cap);
+
 /* The D3Q19 velocity set e[19][3] and weights t[19] the library uses. */
 void lbm_velocity_set(int *e, double *t);
 

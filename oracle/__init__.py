@@ -69,6 +69,10 @@ def lib():
             L.orc_step.argtypes = [i, i, i, d, i, p, p, l, p, p, p, i, d, i, i,
                                    p, p, p, p, p, p, p, p]
             L.orc_step.restype = i
+            L.orc_mlp_nparam.restype = i
+            L.orc_mlp_forward.argtypes = [l, p, p, p]
+            L.orc_mlp_loss_grad.argtypes = [l, p, p, p, p]
+            L.orc_mlp_loss_grad.restype = d
             _lib = L
     return _lib
 
@@ -195,6 +199,29 @@ def sums(f):
     out = np.zeros(4)
     lib().orc_sums(nx, ny, nz, _p(f), _p(out))
     return out
+
+
+def mlp_nparam():
+    return lib().orc_mlp_nparam()
+
+
+def mlp_forward(P, x):
+    """Per-point MLP y = W3 s(W2 s(W1 x + b1) + b2) + b3 (SiLU), FP64."""
+    P = _f64(P).reshape(-1)
+    x = _f64(x).reshape(-1, 16)
+    y = np.zeros((len(x), 3))
+    lib().orc_mlp_forward(len(x), _p(P), _p(x), _p(y))
+    return y
+
+
+def mlp_loss_grad(P, x, t):
+    """Mean 0.5 |y - t|^2 over the samples and its gradient in P, FP64."""
+    P = _f64(P).reshape(-1)
+    x = _f64(x).reshape(-1, 16)
+    t = _f64(t).reshape(-1, 3)
+    g = np.zeros_like(P)
+    loss = lib().orc_mlp_loss_grad(len(x), _p(P), _p(x), _p(t), _p(g))
+    return loss, g
 
 
 class Simulation:

@@ -409,3 +409,108 @@ int orc_step(int nx, int ny, int nz, double tau, int kernel, double *f,
   if (!G) free(g);
   return iters;
 }
+
+/* ---- per-point MLP of the learned warm start (not in the paper) ----------
+ * y = W3 s(W2 s(W1 x + b1) + b2) + b3 with s(v) = v / (1 + exp(-v)) (SiLU),
+ * x in R^16, hidden widths 64 and 64, y in R^3.  Parameters are one flat
+ * vector P = [W1 (64x16, row-major: out x in), b1 (64), W2 (64x64), b2 (64),
+ * W3 (3x64), b3 (3)], 5443 values.  Plain FP64 loops, no blocking. */
+#define MLP_IN 16
+#define MLP_H 64
+#define MLP_OUT 3
+#define MLP_NPARAM (MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_OUT * MLP_H + MLP_OUT)
+
+static double silu(double v) { return v / (1.0 + exp(-v)); }
+static double silu_grad(double v) {
+  double sg = 1.0 / (1.0 + exp(-v));
+  return sg * (1.0 + v * (1.0 - sg));
+}
+
+int orc_mlp_nparam(void) { return MLP_NPARAM; }
+
+/* Forward pass of one sample; a1, a2 receive the pre-activations (may be
+ * NULL). */
+static void mlp_one(const double *P, const double *x, double *y, double *a1, double *a2) {
+  const double *W1 = P, *b1 = W1 + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
+               *W3 = b2 + MLP_H, *b3 = W3 + MLP_OUT * MLP_H;
+  double h1[MLP_H], h2[MLP_H], z1[MLP_H], z2[MLP_H];
+  for (int o = 0; o < MLP_H; o++) {
+    double v = b1[o];
+    for (int i = 0; i < MLP_IN; i++) v += W1[o * MLP_IN + i] * x[i];
+    z1[o] = v;
+    h1[o] = silu(v);
+  }
+  for (int o = 0; o < MLP_H; o++) {
+    double v = b2[o];
+    for (int i = 0; i < MLP_H; i++) v += W2[o * MLP_H + i] * h1[i];
+    z2[o] = v;
+    h2[o] = silu(v);
+  }
+  for (int o = 0; o < MLP_OUT; o++) {
+    double v = b3[o];
+    for (int i = 0; i < MLP_H; i++) v += W3[o * MLP_H + i] * h2[i];
+    y[o] = v;
+  }
+  if (a1) memcpy(a1, z1, sizeof z1);
+  if (a2) memcpy(a2, z2, sizeof z2);
+}
+
+void orc_mlp_forward(long n, const double *P, const double *x, double *y) {
+  for (long k = 0; k < n; k++) mlp_one(P, x + MLP_IN * k, y + MLP_OUT * k, NULL, NULL);
+}
+
+/* Loss L = (1/n) sum_k 0.5 |y_k - t_k|^2 and its gradient dL/dP (chain rule
+ * through the three layers, accumulated over the samples in order). */
+double orc_mlp_loss_grad(long n, const double *P, const double *x, const double *t,
+                         double *grad) {
+  const double *W1 = P, *b1 = W1 + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
+               *W3 = b2 + MLP_H;
+  (void)b1;
+  (void)b2;
+  double *gW1 = grad, *gb1 = gW1 + MLP_H * MLP_IN, *gW2 = gb1 + MLP_H,
+         *gb2 = gW2 + MLP_H * MLP_H, *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_OUT * MLP_H;
+  if (grad) memset(grad, 0, sizeof(double) * MLP_NPARAM);
+  double loss = 0.0;
+  for (long k = 0; k < n; k++) {
+    const double *xk = x + MLP_IN * k;
+    double y[MLP_OUT], z1[MLP_H], z2[MLP_H], h1[MLP_H], h2[MLP_H];
+    mlp_one(P, xk, y, z1, z2);
+    for (int o = 0; o < MLP_H; o++) {
+      h1[o] = silu(z1[o]);
+      h2[o] = silu(z2[o]);
+    }
+    double dy[MLP_OUT];
+    for (int o = 0; o < MLP_OUT; o++) {
+      double e = y[o] - t[MLP_OUT * k + o];
+      loss += 0.5 * e * e / (double)n;
+      dy[o] = e / (double)n;
+    }
+    if (!grad) continue;
+    double dh2[MLP_H], dz2[MLP_H], dh1[MLP_H], dz1[MLP_H];
+    for (int o = 0; o < MLP_OUT; o++) {
+      gb3[o] += dy[o];
+      for (int i = 0; i < MLP_H; i++) gW3[o * MLP_H + i] += dy[o] * h2[i];
+    }
+    for (int i = 0; i < MLP_H; i++) {
+      double v = 0.0;
+      for (int o = 0; o < MLP_OUT; o++) v += W3[o * MLP_H + i] * dy[o];
+      dh2[i] = v;
+      dz2[i] = v * silu_grad(z2[i]);
+    }
+    for (int o = 0; o < MLP_H; o++) {
+      gb2[o] += dz2[o];
+      for (int i = 0; i < MLP_H; i++) gW2[o * MLP_H + i] += dz2[o] * h1[i];
+    }
+    for (int i = 0; i < MLP_H; i++) {
+      double v = 0.0;
+      for (int o = 0; o < MLP_H; o++) v += W2[o * MLP_H + i] * dz2[o];
+      dh1[i] = v;
+      dz1[i] = v * silu_grad(z1[i]);
+    }
+    for (int o = 0; o < MLP_H; o++) {
+      gb1[o] += dz1[o];
+      for (int i = 0; i < MLP_IN; i++) gW1[o * MLP_IN + i] += dz1[o] * xk[i];
+    }
+  }
+  return loss;
+}

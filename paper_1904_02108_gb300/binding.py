@@ -78,6 +78,7 @@ _SIGS = {
     "lbm_read_populations": (_i, [_p, _p]),
     "lbm_write_populations": (_i, [_p, _p]),
     "lbm_read_deviations": (_i, [_p, _p]),
+    "lbm_read_residuals": (_i, [_p, _p, _i]),
     "lbm_velocity_set": (None, [_p, _p]),
     "lbm_enable_timing": (_i, [_p, _i]),
     "lbm_num_stages": (_i, []),
@@ -256,6 +257,12 @@ class Lattice:
         f = np.empty((19,) + self.shape, np.float32)
         self._c(load().lbm_read_populations(self.h, _ptr(f)))
         return f
+
+    def residuals(self, cap=4096):
+        """eps of every fixed-point iteration of the last (tolerance-mode) step."""
+        eps = np.zeros(cap)
+        n = self._c(load().lbm_read_residuals(self.h, _ptr(eps), cap))
+        return eps[:min(n, cap)]
 
     def deviations(self):
         d = np.empty((19,) + self.shape, np.float32)

@@ -24,9 +24,20 @@ using namespace lbmibm;
 namespace {
 
 const char *kStageNames[] = {"kinematics",   "pairs",          "brick_init", "point_update",
-                             "brick_spread", "collide_stream", "stats"};
-constexpr int kNumStages = 7;
-enum Stage { ST_KIN, ST_PAIRS, ST_INIT, ST_UPDATE, ST_SPREAD, ST_COLLIDE, ST_STATS };
+                             "brick_spread", "collide_stream", "stats",      "residual"};
+constexpr int kNumStages = 8;
+enum Stage {
+  ST_KIN,
+  ST_PAIRS,
+  ST_INIT,
+  ST_UPDATE,
+  ST_SPREAD,
+  ST_COLLIDE,
+  ST_STATS,
+  ST_RESID
+};
+// iterations launched between two host checks of the tolerance-mode stop flag
+constexpr int kCheckChunk = 16;
 
 thread_local std::string g_create_error;
 
@@ -67,7 +78,10 @@ struct lbm {
   int nparts = 0;
   bool sums_valid = false;
   int last_iters = 0;
+  double last_eps = -1.0;
   int64_t not_converged = 0;
+  IbmState *state = nullptr;       // device
+  IbmState *state_host = nullptr;  // pinned mirror of the header fields
   int64_t nlaunch = 0;
 
   // timing
@@ -185,6 +199,7 @@ void free_points(lbm_t *h) {
   dfree(h->pm.start);
   dfree(h->pm.cursor);
   dfree(h->pm.k);
+  dfree(h->pm.brick);
   dfree(h->pm.w);
   dfree(h->pm.part);
   dfree(h->pm.point_pairs);
@@ -249,7 +264,7 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->omega);
   dfree(h->phase);
   dfree(h->trig);
-  dfree(h->m.brick_flag);
+  dfree(h->m.brick_count);
   dfree(h->m.brick_slot);
   dfree(h->m.counters);
   dfree(h->partial);
@@ -257,6 +272,8 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->sums);
   dfree(h->ticket);
   dfree(h->tmp);
+  dfree(h->state);
+  if (h->state_host) cudaFreeHost(h->state_host);
   for (auto &p : h->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -305,8 +322,8 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
     e = cudaMalloc(&h->f[k], pop);
     if (e == cudaSuccess) e = cudaMemset(h->f[k], 0, pop);  // deviations 0: rest
   }
-  if (e == cudaSuccess) e = dalloc(&h->m.brick_flag, h->g.nbrick);
-  if (e == cudaSuccess) e = cudaMemset(h->m.brick_flag, 0, sizeof(int) * h->g.nbrick);
+  if (e == cudaSuccess) e = dalloc(&h->m.brick_count, h->g.nbrick);
+  if (e == cudaSuccess) e = cudaMemset(h->m.brick_count, 0, sizeof(int) * h->g.nbrick);
   if (e == cudaSuccess) e = dalloc(&h->m.brick_slot, h->g.nbrick);
   if (e == cudaSuccess) e = cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick);
   if (e == cudaSuccess) e = dalloc(&h->m.counters, 4);
@@ -317,6 +334,9 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   if (e == cudaSuccess) e = dalloc(&h->sums, 4);
   if (e == cudaSuccess) e = dalloc(&h->ticket, 1);
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = dalloc(&h->state, 1);
+  if (e == cudaSuccess) e = cudaMemset(h->state, 0, sizeof(IbmState));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&h->state_host, sizeof(IbmState));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
@@ -385,6 +405,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->pm.start, ms + 1));
     CK(h, dalloc(&h->pm.cursor, ms));
     CK(h, dalloc(&h->pm.k, 8 * n));
+    CK(h, dalloc(&h->pm.brick, 8 * n));
     CK(h, dalloc(&h->pm.w, 3 * 8 * n));
     CK(h, dalloc(&h->pm.part, 8 * n));
     CK(h, dalloc(&h->pm.point_pairs, 8 * n));
@@ -464,9 +485,81 @@ int lbm_set_time(lbm_t *h, int64_t t) {
   return LBM_OK;
 }
 
+// The multi-direct-forcing fixed point of Sec. 3 after brick_init: n_iter > 0
+// iterations, or (n_iter == 0) iterations until eps <= ibm_tol or ibm_max_iter,
+// with the stop decided on the device and checked by the host every
+// kCheckChunk iterations.  Returns LBM_WNOTCONVERGED when the cap was hit.
+static int ibm_fixed_point(lbm_t *h, int n_iter, bool warm) {
+  cudaStream_t st = h->st;
+  if (n_iter > 0) {
+    const IbmLoop none{nullptr};
+    for (int it = 0; it < n_iter; it++) {
+      {
+        StageTimer T(h, ST_UPDATE);
+        CK(h, launch_point_update(h->np, h->pp, h->pm, h->du, h->uint, it == 0, warm, none, st));
+      }
+      {
+        StageTimer T(h, ST_SPREAD);
+        CK(h, launch_brick_spread(h->m, h->pm, h->du, h->U0s, h->Gs, nullptr, it + 1 < n_iter,
+                                  none, st));
+      }
+    }
+    h->last_iters = n_iter;
+    h->last_eps = -1.0;
+    return LBM_OK;
+  }
+  const IbmLoop loop{h->state};
+  {
+    // denominator ||S[s u_k]||^2
+    StageTimer T(h, ST_RESID, 2);
+    CK(h, launch_brick_norm(h->m, h->pm, h->pp.ut, 1, h->res, st));
+    CK(h, launch_ibm_den(h->m, h->res, h->state, 0, st));
+  }
+  CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
+  CK(h, cudaStreamSynchronize(st));
+  if (h->state_host->den2 == 0.0) {
+    // all surface velocities vanish: ||S[s (u_k - I[U0])]||^2 instead
+    StageTimer T(h, ST_RESID, warm ? 5 : 3);
+    if (warm) CK(h, launch_brick_init(h->m, h->pm, nullptr, h->U0s, h->Gs, st));
+    CK(h, launch_point_residual0(h->np, h->pp, h->pm, h->uint, st));
+    CK(h, launch_brick_norm(h->m, h->pm, h->uint, 0, h->res, st));
+    CK(h, launch_ibm_den(h->m, h->res, h->state, 1, st));
+    if (warm) CK(h, launch_brick_init(h->m, h->pm, h->du, h->U0s, h->Gs, st));
+  }
+  int it = 0;
+  while (it < h->max_iter) {
+    const int chunk = std::min(kCheckChunk, h->max_iter - it);
+    for (int j = 0; j < chunk; j++, it++) {
+      {
+        StageTimer T(h, ST_UPDATE);
+        CK(h, launch_point_update(h->np, h->pp, h->pm, h->du, h->uint, it == 0, warm, loop, st));
+      }
+      {
+        StageTimer T(h, ST_SPREAD);
+        CK(h, launch_brick_spread(h->m, h->pm, h->du, h->U0s, h->Gs, h->res, 1, loop, st));
+      }
+      {
+        StageTimer T(h, ST_RESID);
+        CK(h, launch_ibm_check(h->m, h->res, h->state, it, h->tol, h->max_iter, st));
+      }
+    }
+    CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    if (h->state_host->done) break;
+  }
+  h->last_iters = h->state_host->iters;
+  h->last_eps = h->state_host->last_eps;
+  if (h->state_host->capped) {
+    h->not_converged++;
+    return LBM_WNOTCONVERGED;
+  }
+  return LBM_OK;
+}
+
 static int step_once(lbm_t *h, int n_iter) {
   cudaStream_t st = h->st;
   const bool ibm = h->np > 0;
+  int warn = LBM_OK;
   if (ibm) {
     PointsIn p{h->np, h->X, h->body, h->area, h->utarget};
     Bodies b{h->centre, h->omega, h->phase, h->nb, h->trig};
@@ -481,25 +574,16 @@ static int step_once(lbm_t *h, int n_iter) {
     }
     const bool warm = h->warm == LBM_WARM_PREVIOUS && h->have_du;
     {
-      StageTimer T(h, ST_INIT);
-      CK(h, launch_brick_init(h->storage, h->g, h->f[h->cur], h->m, h->pm,
-                              warm ? h->du : nullptr, h->U0s, h->Gs, st));
+      StageTimer T(h, ST_INIT, 2);
+      CK(h, launch_brick_moments(h->storage, h->g, h->f[h->cur], h->m, h->U0s, st));
+      CK(h, launch_brick_init(h->m, h->pm, warm ? h->du : nullptr, h->U0s, h->Gs, st));
     }
-    for (int it = 0; it < n_iter; it++) {
-      {
-        StageTimer T(h, ST_UPDATE);
-        CK(h, launch_point_update(h->np, h->pp, h->pm, h->du, h->uint, it == 0, warm, st));
-      }
-      {
-        StageTimer T(h, ST_SPREAD);
-        CK(h, launch_brick_spread(h->m, h->pm, h->du, h->U0s, h->Gs, nullptr,
-                                  it + 1 < n_iter, st));
-      }
-    }
+    warn = ibm_fixed_point(h, n_iter, warm);
+    if (warn < 0) return warn;
     h->have_du = true;
-    h->last_iters = n_iter;
   } else {
     h->last_iters = 0;
+    h->last_eps = -1.0;
   }
   {
     StageTimer T(h, ST_COLLIDE);
@@ -523,22 +607,22 @@ static int step_once(lbm_t *h, int n_iter) {
   }
   h->cur ^= 1;
   h->t++;
-  return LBM_OK;
+  return warn;
 }
 
 int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
   if (!h) return LBM_EINVAL;
   if (n_steps < 0 || n_ibm_iter < 0)
     return fail(h, LBM_EINVAL, "n_steps = %d, n_ibm_iter = %d", n_steps, n_ibm_iter);
-  if (n_ibm_iter == 0 && h->np > 0)
-    return fail(h, LBM_EINVAL, "tolerance-driven iteration is not available in this build");
   if (h->nb > 0 && h->max_body >= h->nb)
     return fail(h, LBM_EINVAL, "points refer to body %d, only %d bodies", h->max_body, h->nb);
+  int warn = LBM_OK;
   for (int s = 0; s < n_steps; s++) {
     int r = step_once(h, n_ibm_iter);
-    if (r != LBM_OK) return r;
+    if (r < 0) return r;
+    if (r == LBM_WNOTCONVERGED) warn = r;
   }
-  return LBM_OK;
+  return warn;
 }
 
 int lbm_read_fields_dev(lbm_t *h, float *rho, float *U, float *G) {
@@ -610,7 +694,7 @@ int lbm_read_stats(lbm_t *h, lbm_stats *s) {
   s->momentum[2] = sums[3];
   s->step = h->t;
   s->last_ibm_iters = h->last_iters;
-  s->last_residual = -1.0;
+  s->last_residual = h->last_eps;
   s->not_converged = h->not_converged;
   s->kernel_launches = h->nlaunch;
   if (h->np > 0) {
@@ -636,6 +720,17 @@ static int read_pops(lbm_t *h, float *f, int deviations) {
 }
 
 int lbm_read_populations(lbm_t *h, float *f) { return read_pops(h, f, 0); }
+
+int lbm_read_residuals(lbm_t *h, double *eps, int cap) {
+  if (!h || cap < 0 || (cap > 0 && !eps)) return LBM_EINVAL;
+  if (h->last_eps < 0.0) return 0;
+  const int n = std::min(h->last_iters, (int)IbmState::HIST);
+  const int m = std::min(n, cap);
+  if (m > 0)
+    CK(h, cudaMemcpyAsync(eps, h->state->eps, sizeof(double) * m, cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return n;
+}
 int lbm_read_deviations(lbm_t *h, float *d) { return read_pops(h, d, 1); }
 
 int lbm_write_populations(lbm_t *h, const float *f) {
@@ -822,7 +917,8 @@ int ibm_interpolate_dev(int nx, int ny, int nz, int delta, const float *U, int64
 namespace {
 
 struct SpreadLayout {
-  size_t brick_flag, brick_slot, slot_brick, counters, count, start, cursor, pk, pw, ppart,
+  size_t brick_count, brick_slot, slot_brick, counters, count, start, cursor, pk, pbrick, pw,
+      ppart,
       point_pairs, base, wts, ut, vals, Gs, total;
   int max_slots;
 };
@@ -839,7 +935,7 @@ SpreadLayout spread_layout(const Geometry &g, int64_t n) {
     o = align256(o + bytes);
     return r;
   };
-  L.brick_flag = take(sizeof(int) * g.nbrick);
+  L.brick_count = take(sizeof(int) * g.nbrick);
   L.brick_slot = take(sizeof(int) * g.nbrick);
   L.slot_brick = take(sizeof(int) * ms);
   L.counters = take(sizeof(int) * 4);
@@ -847,6 +943,7 @@ SpreadLayout spread_layout(const Geometry &g, int64_t n) {
   L.start = take(sizeof(int) * (ms + 1));
   L.cursor = take(sizeof(int) * ms);
   L.pk = take(sizeof(int) * 8 * n1);
+  L.pbrick = take(sizeof(int) * 8 * n1);
   L.pw = take(sizeof(float4) * 3 * 8 * n1);
   L.ppart = take(sizeof(float4) * 8 * n1);
   L.point_pairs = take(sizeof(int) * 8 * n1);
@@ -902,7 +999,7 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
     return fail(nullptr, LBM_EINVAL, "scratch must be 256-byte aligned");
   }
   BrickMap m{};
-  m.brick_flag = (int *)(base + L.brick_flag);
+  m.brick_count = (int *)(base + L.brick_count);
   m.brick_slot = (int *)(base + L.brick_slot);
   m.slot_brick = (int *)(base + L.slot_brick);
   m.counters = (int *)(base + L.counters);
@@ -912,6 +1009,7 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   pm.start = (int *)(base + L.start);
   pm.cursor = (int *)(base + L.cursor);
   pm.k = (int *)(base + L.pk);
+  pm.brick = (int *)(base + L.pbrick);
   pm.w = (float4 *)(base + L.pw);
   pm.part = (float4 *)(base + L.ppart);
   pm.point_pairs = (int *)(base + L.point_pairs);
@@ -923,7 +1021,7 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   float4 *vals = (float4 *)(base + L.vals);
   float *Gs = (float *)(base + L.Gs);
   if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, sizeof(float) * 3 * g.ncell, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m.brick_flag, 0, sizeof(int) * g.nbrick, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.brick_count, 0, sizeof(int) * g.nbrick, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m.counters, 0, sizeof(int) * 4, st);
   if (n > 0) {
     PointsIn p{n, x, nullptr, nullptr, nullptr};
@@ -931,7 +1029,8 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
     if (e == cudaSuccess) e = launch_prepare_points(g, delta, p, b, 0, pp, m, pm, nullptr, st);
     if (e == cudaSuccess) e = launch_build_pairs(g, n, pp, m, pm, st);
     if (e == cudaSuccess) e = launch_pack_vals(n, v, vals, st);
-    if (e == cudaSuccess) e = launch_brick_spread(m, pm, vals, nullptr, Gs, nullptr, 0, st);
+    if (e == cudaSuccess)
+      e = launch_brick_spread(m, pm, vals, nullptr, Gs, nullptr, 0, IbmLoop{nullptr}, st);
     if (e == cudaSuccess) e = launch_slots_to_dense(g, m, Gs, F, st);
   }
   if (own) {

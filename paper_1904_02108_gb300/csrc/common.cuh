@@ -95,8 +95,8 @@ __host__ __device__ __forceinline__ int wrapi(int a, int n) {
 // point).  brick_slot[b] = slot or -1; slot_brick[s] = b.  Per slot the fields
 // U0 and G are [3][64] floats (component-major, brick-local cell order z,y,x).
 struct BrickMap {
-  int *brick_flag;   // [nbrick] 1 = in some support (set per step, cleared
-                     //           by the compaction)
+  int *brick_count;  // [nbrick] points whose support overlaps the brick (set
+                     //           per step, cleared by the compaction)
   int *brick_slot;   // [nbrick]
   int *slot_brick;   // [max_slots]
   int *counters;     // [4]: 0 = active slots, 1 = overflow flag
@@ -112,6 +112,7 @@ struct PairMap {
   int *start;        // [max_slots + 1]
   int *cursor;       // [max_slots]
   int *k;            // [max_pairs] point of each pair
+  int *brick;        // [max_pairs] brick of each pair
   float4 *w;         // [max_pairs][3] weights of the brick's cells 0..3 along
                      //                x, y, z (0 outside the support)
   float4 *part;      // [max_pairs] brick's share of the interpolated velocity
@@ -127,6 +128,24 @@ struct PointPrep {
   int4 *base;    // [np]
   float *wts;    // [np][12]  wx[4] wy[4] wz[4]
   float4 *ut;    // [np]      (u_k, s_k)
+};
+
+// State of the tolerance-driven fixed point, on the device.
+struct IbmState {
+  static constexpr int HIST = 4096;
+  int done;        // 1: converged or capped
+  int iters;       // iterations taken this step
+  int capped;      // 1: stopped at max_iter with eps > tol
+  int pad;
+  double den2;     // ||S[s u_k]||^2 (or the fallback)
+  double last_eps;
+  double eps[HIST];  // eps of every iteration of this step
+};
+
+// Passed to the loop kernels: state == nullptr in fixed-count mode; otherwise
+// the kernels return at once when state->done is set.
+struct IbmLoop {
+  const IbmState *state;
 };
 
 }  // namespace lbmibm

@@ -2,14 +2,15 @@
 // (brick, point) pair lists, and the fixed-point loop.
 //
 // Once per step (points do not move inside the fixed point):
-//   prepare_points  x(t) = M(t)[x_rest, 1], u_k, tap weights, brick flags
-//   compact         flagged bricks -> slots of the sparse force storage
-//   pair_count/scan/fill/sort
+//   prepare_points  x(t) = M(t)[x_rest, 1], u_k, tap weights, and for each
+//                   brick its number of overlapping supports
+//   compact         bricks with a count -> slots of the sparse force storage
+//   pair_scan/fill/sort/weights
 //                   one pair per (brick, point) with the point's support
 //                   overlapping the brick, grouped by brick, ascending point
 //                   index, with the brick-local weights of the point
-//   brick_init      rho, U0 on the brick's cells (Eq. 1), G = 0 (or S[du_init])
-//                   and each pair's share of I[U0 + G]
+//   brick_moments   rho, U0 on the brick's cells (Eq. 1)
+//   brick_init      G = 0 (or S[du_init]) and each pair's share of I[U0 + G]
 // Each iteration:
 //   point_update    u_n(k) = sum of the point's pair shares; g = u_k - u_n;
 //                   du += s g                                   (Alg. 1)
@@ -19,6 +20,8 @@
 // Every sum runs in a fixed order (pairs ascending inside a brick, four
 // partial sums combined in a fixed order, a point's shares in brick order), so
 // results are bitwise reproducible, unlike the atomicAdd scatter of Alg. 2.
+#include <algorithm>
+
 #include "kernels.h"
 #include "lattice.cuh"
 
@@ -52,10 +55,8 @@ __device__ __forceinline__ void tap_weights(int delta, float f, float w[4]) {
 __device__ __forceinline__ int base_and_frac(double x, int n, float &f) {
   const double fl = floor(x);
   f = (float)(x - fl);
-  int b = (int)(fl - n * floor(fl / n));  // wrap into [0, n)
-  if (b >= n) b -= n;
-  if (b < 0) b += n;
-  return b;
+  int b = (int)fl % n;  // wrap into [0, n)
+  return b < 0 ? b + n : b;
 }
 
 // Bricks holding the support floor(x)-1 .. floor(x)+2 along one axis: the
@@ -66,6 +67,50 @@ struct SupportBricks {
 };
 __device__ __forceinline__ SupportBricks support_bricks(int b, int n) {
   return {wrapi(b - 1, n) >> 2, wrapi(b + 2, n) >> 2};
+}
+
+// Adds 1 to ctr[key] for every calling lane with `valid`; lanes of a warp with
+// equal keys share one atomicAdd.  Returns the lane's slot among the
+// increments of its key (the value its own atomicAdd would have returned,
+// lanes taken in order).  Every active lane of the warp must call it.
+__device__ __forceinline__ int aggregated_inc(int *ctr, int key, bool valid) {
+  const unsigned grp = __match_any_sync(__activemask(), valid ? key : -1);
+  int pos = 0;
+  if (valid) {
+    const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+    int old = 0;
+    if (lane == leader) old = atomicAdd(ctr + key, __popc(grp));
+    pos = __shfl_sync(grp, old, leader) + __popc(grp & ((1u << lane) - 1u));
+  }
+  return pos;
+}
+
+// Calls fn(brick, valid) eight times, once per (z, y, x) choice of low/high
+// support brick; valid is false for repeats when the support lies in one
+// brick along an axis.  The trip count is uniform, so warps stay converged.
+template <typename Fn>
+__device__ __forceinline__ void for_support_bricks8(const Geometry &g, int4 b, Fn fn) {
+  const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
+                      sz = support_bricks(b.z, g.nz);
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int e = j & 1, a = (j >> 1) & 1, c = j >> 2;
+    const bool valid = (!e || sx.hi != sx.lo) && (!a || sy.hi != sy.lo) && (!c || sz.hi != sz.lo);
+    fn(((c ? sz.hi : sz.lo) * g.nby + (a ? sy.hi : sy.lo)) * g.nbx + (e ? sx.hi : sx.lo), valid);
+  }
+}
+
+// Calls fn(brick) for each distinct brick of a point's support.
+template <typename Fn>
+__device__ __forceinline__ void for_support_bricks(const Geometry &g, int4 b, Fn fn) {
+  const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
+                      sz = support_bricks(b.z, g.nz);
+  const int nzb = sz.hi != sz.lo ? 2 : 1, nyb = sy.hi != sy.lo ? 2 : 1,
+            nxb = sx.hi != sx.lo ? 2 : 1;
+  for (int c = 0; c < nzb; c++)
+    for (int a = 0; a < nyb; a++)
+      for (int e = 0; e < nxb; e++)
+        fn(((c ? sz.hi : sz.lo) * g.nby + (a ? sy.hi : sy.lo)) * g.nbx + (e ? sx.hi : sx.lo));
 }
 
 // Per body, once per step: cos/sin of phi(t) = phase + omega t and the
@@ -146,28 +191,23 @@ __global__ void __launch_bounds__(256)
   int4 *pk = (int4 *)(pm.point_pairs + 8 * k);
   pk[0] = make_int4(-1, -1, -1, -1);
   pk[1] = make_int4(-1, -1, -1, -1);
-  // bricks covered by the support (at most two per axis)
-  const SupportBricks sx = support_bricks(bx, g.nx), sy = support_bricks(by, g.ny),
-                      sz = support_bricks(bz, g.nz);
-  const int zz[2] = {sz.lo, sz.hi}, yy[2] = {sy.lo, sy.hi}, xx[2] = {sx.lo, sx.hi};
-#pragma unroll
-  for (int a = 0; a < 2; a++)
-#pragma unroll
-    for (int b = 0; b < 2; b++)
-#pragma unroll
-      for (int c = 0; c < 2; c++) m.brick_flag[(zz[a] * g.nby + yy[b]) * g.nbx + xx[c]] = 1;
+  // count this point in every distinct brick of its support
+  for_support_bricks8(g, make_int4(bx, by, bz, 0), [&](int brick, bool valid) {
+    aggregated_inc(m.brick_count, brick, valid);
+  });
 }
 
 __global__ void compact_kernel(Geometry g, BrickMap m, PairMap pm) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= g.nbrick) return;
-  if (m.brick_flag[b]) {
-    m.brick_flag[b] = 0;
+  const int c = m.brick_count[b];
+  if (c > 0) {
+    m.brick_count[b] = 0;
     const int s = atomicAdd(m.counters, 1);
     if (s < m.max_slots) {
       m.brick_slot[b] = s;
       m.slot_brick[s] = b;
-      pm.count[s] = 0;
+      pm.count[s] = c;
       pm.cursor[s] = 0;
     } else {
       m.brick_slot[b] = -1;
@@ -183,77 +223,76 @@ __device__ __forceinline__ int active_slots(const BrickMap &m) {
   return n < m.max_slots ? n : m.max_slots;
 }
 
-// Calls fn(brick) for each distinct brick of a point's support.
-template <typename Fn>
-__device__ __forceinline__ void for_support_bricks(const Geometry &g, int4 b, Fn fn) {
-  const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
-                      sz = support_bricks(b.z, g.nz);
-  const int nzb = sz.hi != sz.lo ? 2 : 1, nyb = sy.hi != sy.lo ? 2 : 1,
-            nxb = sx.hi != sx.lo ? 2 : 1;
-  for (int c = 0; c < nzb; c++)
-    for (int a = 0; a < nyb; a++)
-      for (int e = 0; e < nxb; e++)
-        fn(((c ? sz.hi : sz.lo) * g.nby + (a ? sy.hi : sy.lo)) * g.nbx + (e ? sx.hi : sx.lo));
-}
+// Exclusive scan of pm.count[0 .. nslots) into pm.start, one block, in tiles
+// of SCAN_TILE counts staged through shared memory with coalesced loads and
+// stores (8 consecutive counts per thread).
+constexpr int SCAN_TILE = 8192;
 
-__global__ void pair_count_kernel(Geometry g, int64_t np, PointPrep pp, BrickMap m,
-                                  PairMap pm) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= np) return;
-  for_support_bricks(g, pp.base[k], [&](int brick) {
-    const int s = m.brick_slot[brick];
-    if (s >= 0) atomicAdd(pm.count + s, 1);
-  });
-}
-
-// Exclusive scan of pm.count[0 .. nslots) into pm.start, one block.
 __global__ void __launch_bounds__(1024) pair_scan_kernel(BrickMap m, PairMap pm) {
+  __shared__ int tile[SCAN_TILE];
   __shared__ int wsum[32];
+  __shared__ int carry;
   const int n = active_slots(m);
-  const int per = (n + 1023) / 1024;
-  const int lo = threadIdx.x * per, hi = min(lo + per, n);
-  int local = 0;
-  for (int i = lo; i < hi; i++) local += pm.count[i];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int v = local;
+  if (threadIdx.x == 0) carry = 0;
+  for (int t0 = 0; t0 < n; t0 += SCAN_TILE) {
+    const int len = min(SCAN_TILE, n - t0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < SCAN_TILE; i += 1024) tile[i] = i < len ? pm.count[t0 + i] : 0;
+    __syncthreads();
+    int v[8], local = 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
-  }
-  if (lane == 31) wsum[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    int s = wsum[lane];
+    for (int j = 0; j < 8; j++) {
+      v[j] = tile[threadIdx.x * 8 + j];
+      local += v[j];
+    }
+    int inc = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += t;
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
     }
-    wsum[lane] = s;
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      int s = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+      }
+      wsum[lane] = s;
+    }
+    __syncthreads();
+    int run = carry + inc - local + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      tile[threadIdx.x * 8 + j] = run;
+      run += v[j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += 1024) pm.start[t0 + i] = tile[i];
+    if (threadIdx.x == 1023) carry = run;
   }
   __syncthreads();
-  int run = v - local + (w > 0 ? wsum[w - 1] : 0);
-  for (int i = lo; i < hi; i++) {
-    pm.start[i] = run;
-    run += pm.count[i];
-  }
-  if (threadIdx.x == 1023) pm.start[n] = run;
+  if (threadIdx.x == 0) pm.start[n] = carry;
 }
 
 __global__ void pair_fill_kernel(Geometry g, int64_t np, PointPrep pp, BrickMap m, PairMap pm) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= np) return;
-  for_support_bricks(g, pp.base[k], [&](int brick) {
-    const int s = m.brick_slot[brick];
-    if (s >= 0) pm.k[pm.start[s] + atomicAdd(pm.cursor + s, 1)] = (int)k;
+  for_support_bricks8(g, pp.base[k], [&](int brick, bool valid) {
+    const int s = valid ? m.brick_slot[brick] : -1;
+    const int pos = aggregated_inc(pm.cursor, s, s >= 0);
+    if (s >= 0) pm.k[pm.start[s] + pos] = (int)k;
   });
 }
 
-// One warp per slot: sort the slot's points ascending (rank sort; the points
-// of a slot are distinct), then write each pair's brick-local weights and
-// register the pair with its point.
-constexpr int SORT_CAP = 1024;
+// One warp per slot: sort the slot's points ascending (in registers up to 32
+// pairs, bitonic in shared memory up to SORT_CAP, else a rank sort through
+// this slot's not yet written weight storage; the points of a slot are
+// distinct) and record the slot's brick with each pair.
+constexpr int SORT_CAP = 512;
 
 __global__ void __launch_bounds__(128)
     pair_sort_kernel(Geometry g, PointPrep pp, BrickMap m, PairMap pm) {
@@ -263,63 +302,99 @@ __global__ void __launch_bounds__(128)
   for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
     const int cnt = pm.count[s], st = pm.start[s];
     int *a = pm.k + st;
-    // scratch copy: shared memory, or this slot's (not yet written) weights
-    int *tmp = cnt <= SORT_CAP ? buf[w] : (int *)(pm.w + 3 * (size_t)st);
-    for (int i = lane; i < cnt; i += 32) tmp[i] = a[i];
-    __syncwarp();
-    for (int i = lane; i < cnt; i += 32) {
-      const int v = tmp[i];
+    if (cnt <= 32) {
+      const int v = lane < cnt ? a[lane] : 0x7fffffff;
       int r = 0;
-      for (int j = 0; j < cnt; j++) r += tmp[j] < v;
-      a[r] = v;
+      for (int j = 0; j < cnt; j++) r += __shfl_sync(0xffffffffu, v, j) < v;
+      __syncwarp();
+      if (lane < cnt) a[r] = v;
+    } else if (cnt <= SORT_CAP) {
+      int n2 = 2;
+      while (n2 < cnt) n2 <<= 1;
+      int *b = buf[w];
+      for (int i = lane; i < n2; i += 32) b[i] = i < cnt ? a[i] : 0x7fffffff;
+      __syncwarp();
+      for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < n2; i += 32) {
+            const int l = i ^ j;
+            if (l > i) {
+              const int x = b[i], y = b[l];
+              if ((x > y) == ((i & k) == 0)) {
+                b[i] = y;
+                b[l] = x;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      for (int i = lane; i < cnt; i += 32) a[i] = b[i];
+    } else {
+      int *tmp = (int *)(pm.w + 3 * (size_t)st);
+      for (int i = lane; i < cnt; i += 32) tmp[i] = a[i];
+      __syncwarp();
+      for (int i = lane; i < cnt; i += 32) {
+        const int v = tmp[i];
+        int r = 0;
+        for (int j = 0; j < cnt; j++) r += tmp[j] < v;
+        a[r] = v;
+      }
     }
     __syncwarp();
     const int B = m.slot_brick[s];
-    const int bxb = B % g.nbx, rr = B / g.nbx;
-    const int byb = rr % g.nby, bzb = rr / g.nby;
-    const int X0 = bxb * 4, Y0 = byb * 4, Z0 = bzb * 4;
-    for (int i = lane; i < cnt; i += 32) {
-      const int k = a[i];
-      const int4 b = pp.base[k];
-      const float4 *wp = (const float4 *)(pp.wts + 12 * (int64_t)k);
-      const float4 w0 = wp[0], w1 = wp[1], w2 = wp[2];
-      const float wx[4] = {w0.x, w0.y, w0.z, w0.w};
-      const float wy[4] = {w1.x, w1.y, w1.z, w1.w};
-      const float wz[4] = {w2.x, w2.y, w2.z, w2.w};
-      float lx[4], ly[4], lz[4];
-#pragma unroll
-      for (int c = 0; c < 4; c++) {
-        // tap index of the brick's cell c along each axis (periodic), or none
-        int dx = X0 + c - b.x + 1;
-        dx = dx < 0 ? dx + g.nx : (dx >= g.nx ? dx - g.nx : dx);
-        int dy = Y0 + c - b.y + 1;
-        dy = dy < 0 ? dy + g.ny : (dy >= g.ny ? dy - g.ny : dy);
-        int dz = Z0 + c - b.z + 1;
-        dz = dz < 0 ? dz + g.nz : (dz >= g.nz ? dz - g.nz : dz);
-        float vx = 0.f, vy = 0.f, vz = 0.f;
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-          vx = dx == e ? wx[e] : vx;
-          vy = dy == e ? wy[e] : vy;
-          vz = dz == e ? wz[e] : vz;
-        }
-        lx[c] = vx;
-        ly[c] = vy;
-        lz[c] = vz;
-      }
-      const size_t p = (size_t)st + i;
-      pm.w[3 * p] = make_float4(lx[0], lx[1], lx[2], lx[3]);
-      pm.w[3 * p + 1] = make_float4(ly[0], ly[1], ly[2], ly[3]);
-      pm.w[3 * p + 2] = make_float4(lz[0], lz[1], lz[2], lz[3]);
-      const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
-                          sz = support_bricks(b.z, g.nz);
-      const int j = (sx.hi != sx.lo && bxb == sx.hi ? 1 : 0) |
-                    (sy.hi != sy.lo && byb == sy.hi ? 2 : 0) |
-                    (sz.hi != sz.lo && bzb == sz.hi ? 4 : 0);
-      pm.point_pairs[8 * (size_t)k + j] = (int)p;
-    }
-    __syncwarp();
+    for (int i = lane; i < cnt; i += 32) pm.brick[st + i] = B;
   }
+}
+
+// Per pair (after the sort): the brick-local weights of its point (the
+// point's tap weights at the brick's cells 0..3 along each axis, 0 outside
+// the support, periodic offsets resolved) and the pair's entry in the point's
+// list of bricks.
+__global__ void __launch_bounds__(256)
+    pair_weights_kernel(Geometry g, PointPrep pp, BrickMap m, PairMap pm) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pm.start[active_slots(m)]) return;
+  const int k = pm.k[p], B = pm.brick[p];
+  const int bxb = B % g.nbx, rr = B / g.nbx;
+  const int byb = rr % g.nby, bzb = rr / g.nby;
+  const int X0 = bxb * 4, Y0 = byb * 4, Z0 = bzb * 4;
+  const int4 b = pp.base[k];
+  const float4 *wp = (const float4 *)(pp.wts + 12 * (int64_t)k);
+  const float4 w0 = wp[0], w1 = wp[1], w2 = wp[2];
+  const float wx[4] = {w0.x, w0.y, w0.z, w0.w};
+  const float wy[4] = {w1.x, w1.y, w1.z, w1.w};
+  const float wz[4] = {w2.x, w2.y, w2.z, w2.w};
+  float lx[4], ly[4], lz[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    // tap index of the brick's cell c along each axis (periodic), or none
+    int dx = X0 + c - b.x + 1;
+    dx = dx < 0 ? dx + g.nx : (dx >= g.nx ? dx - g.nx : dx);
+    int dy = Y0 + c - b.y + 1;
+    dy = dy < 0 ? dy + g.ny : (dy >= g.ny ? dy - g.ny : dy);
+    int dz = Z0 + c - b.z + 1;
+    dz = dz < 0 ? dz + g.nz : (dz >= g.nz ? dz - g.nz : dz);
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      vx = dx == e ? wx[e] : vx;
+      vy = dy == e ? wy[e] : vy;
+      vz = dz == e ? wz[e] : vz;
+    }
+    lx[c] = vx;
+    ly[c] = vy;
+    lz[c] = vz;
+  }
+  pm.w[3 * p] = make_float4(lx[0], lx[1], lx[2], lx[3]);
+  pm.w[3 * p + 1] = make_float4(ly[0], ly[1], ly[2], ly[3]);
+  pm.w[3 * p + 2] = make_float4(lz[0], lz[1], lz[2], lz[3]);
+  const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
+                      sz = support_bricks(b.z, g.nz);
+  const int j = (sx.hi != sx.lo && bxb == sx.hi ? 1 : 0) |
+                (sy.hi != sy.lo && byb == sy.hi ? 2 : 0) |
+                (sz.hi != sz.lo && bzb == sz.hi ? 4 : 0);
+  pm.point_pairs[8 * (size_t)k + j] = (int)p;
 }
 
 // ---- the brick kernels: one 64-thread block per active brick ----------------
@@ -340,7 +415,8 @@ struct BrickSmem {
 // x-row of four cells, its group takes every fourth pair, and the four partial
 // sums are added in a fixed order.  Thread t returns the sum of cell t.
 __device__ __forceinline__ float3 brick_gather(BrickSmem &sm, const PairMap &pm, int p0, int cnt,
-                                               const float4 *__restrict__ vals) {
+                                               const float4 *__restrict__ vals,
+                                               bool scale_by_w = false) {
   const int t = threadIdx.x;
   const int grp = t >> 4, tg = t & 15, yl = tg & 3, zl = tg >> 2;
   float acc[4][3];
@@ -360,7 +436,13 @@ __device__ __forceinline__ float3 brick_gather(BrickSmem &sm, const PairMap &pm,
         sm.swz[q][1] = wz.y;
         sm.swz[q][2] = wz.z;
         sm.swz[q][3] = wz.w;
-        sm.sv[q] = vals[pm.k[p]];
+        float4 v = vals[pm.k[p]];
+        if (scale_by_w) {
+          v.x *= v.w;
+          v.y *= v.w;
+          v.z *= v.w;
+        }
+        sm.sv[q] = v;
       }
     }
     __syncthreads();
@@ -393,15 +475,29 @@ __device__ __forceinline__ float3 brick_gather(BrickSmem &sm, const PairMap &pm,
 // Each pair's share of I[F] for F = sm.sF: sum over the brick's cells of
 // F(X) wx wy wz (one thread per pair; every thread reads the same F row at the
 // same time, a shared-memory broadcast).
-__device__ __forceinline__ void brick_interp(BrickSmem &sm, const PairMap &pm, int p0,
-                                             int cnt) {
+// staged: the pair weights of this brick are still in sm.swx/swy/swz (the
+// gather staged them and cnt <= SP_CHUNK).
+__device__ __forceinline__ void brick_interp(BrickSmem &sm, const PairMap &pm, int p0, int cnt,
+                                             bool staged) {
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
     // re-read F for every pair instead of holding all 192 values in registers
     asm volatile("" ::: "memory");
     const size_t p = (size_t)p0 + i;
-    const float4 wx = pm.w[3 * p], wy4 = pm.w[3 * p + 1], wz4 = pm.w[3 * p + 2];
-    const float wy[4] = {wy4.x, wy4.y, wy4.z, wy4.w};
-    const float wz[4] = {wz4.x, wz4.y, wz4.z, wz4.w};
+    float4 wx;
+    float wy[4], wz[4];
+    if (staged) {
+      wx = sm.swx[i];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        wy[c] = sm.swy[i][c];
+        wz[c] = sm.swz[i][c];
+      }
+    } else {
+      wx = pm.w[3 * p];
+      const float4 wy4 = pm.w[3 * p + 1], wz4 = pm.w[3 * p + 2];
+      wy[0] = wy4.x; wy[1] = wy4.y; wy[2] = wy4.z; wy[3] = wy4.w;
+      wz[0] = wz4.x; wz[1] = wz4.y; wz[2] = wz4.z; wz[3] = wz4.w;
+    }
     float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
     for (int z = 0; z < 4; z++) {
@@ -426,18 +522,16 @@ __device__ __forceinline__ void store_F(BrickSmem &sm, float fx, float fy, float
   ((float *)sm.sF[2])[t] = fz;
 }
 
-// First pass of a step over each active brick: U0 from the populations
-// (pull + Eq. 1), G_0 = 0 or S[du_init] (warm start), and the pairs' shares of
-// I[U0 + G_0] for the first iteration.
+// U0 on every cell of every active brick: pull of Eq. 4 and Eq. 1 (the
+// paper's kernel strategy of Sec. 5 without duplicated cells).  One thread per
+// cell, four bricks per 256-thread block.
 template <typename S>
-__global__ void __launch_bounds__(64, 16)
-    brick_init_kernel(const S *__restrict__ f, Geometry g, BrickMap m, PairMap pm,
-                      const float4 *__restrict__ du_init, float *__restrict__ U0s,
-                      float *__restrict__ Gs) {
-  __shared__ BrickSmem sm;
+__global__ void __launch_bounds__(256)
+    brick_moments_kernel(const S *__restrict__ f, Geometry g, BrickMap m,
+                         float *__restrict__ U0s) {
   const int nslots = active_slots(m);
-  const int t = threadIdx.x;
-  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+  const int t = threadIdx.x & 63;
+  for (int s = blockIdx.x * 4 + (threadIdx.x >> 6); s < nslots; s += gridDim.x * 4) {
     const int B = m.slot_brick[s];
     const int bx = B % g.nbx, rr = B / g.nbx;
     const int by = rr % g.nby, bz = rr / g.nby;
@@ -447,11 +541,25 @@ __global__ void __launch_bounds__(64, 16)
     float drho, jx, jy, jz;
     moments(d, drho, jx, jy, jz);
     const float inv = 1.f / (1.f + drho);
-    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
     float *u = U0s + (size_t)s * SLOT_FLOATS + t;
-    u[0] = ux;
-    u[BRICK_CELLS] = uy;
-    u[2 * BRICK_CELLS] = uz;
+    u[0] = jx * inv;
+    u[BRICK_CELLS] = jy * inv;
+    u[2 * BRICK_CELLS] = jz * inv;
+  }
+}
+
+// First pass of a step over each active brick after the moments: G_0 = 0 or
+// S[du_init] (warm start), and the pairs' shares of I[U0 + G_0] for the first
+// iteration.
+__global__ void __launch_bounds__(64, 16)
+    brick_init_kernel(BrickMap m, PairMap pm, const float4 *__restrict__ du_init,
+                      const float *__restrict__ U0s, float *__restrict__ Gs) {
+  __shared__ BrickSmem sm;
+  const int nslots = active_slots(m);
+  const int t = threadIdx.x;
+  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+    const float *u = U0s + (size_t)s * SLOT_FLOATS + t;
+    const float ux = u[0], uy = u[BRICK_CELLS], uz = u[2 * BRICK_CELLS];
     const int p0 = pm.start[s], cnt = pm.count[s];
     float3 G = make_float3(0.f, 0.f, 0.f);
     if (du_init) G = brick_gather(sm, pm, p0, cnt, du_init);
@@ -461,7 +569,7 @@ __global__ void __launch_bounds__(64, 16)
     Gp[2 * BRICK_CELLS] = G.z;
     store_F(sm, ux + G.x, uy + G.y, uz + G.z);
     __syncthreads();
-    brick_interp(sm, pm, p0, cnt);
+    brick_interp(sm, pm, p0, cnt, du_init != nullptr && cnt <= SP_CHUNK);
     __syncthreads();
   }
 }
@@ -472,8 +580,9 @@ __global__ void __launch_bounds__(64, 16)
 __global__ void __launch_bounds__(64, 16)
     brick_spread_kernel(BrickMap m, PairMap pm, const float4 *__restrict__ vals,
                         const float *__restrict__ U0s, float *__restrict__ Gs,
-                        float *__restrict__ res, int do_interp) {
+                        float *__restrict__ res, int do_interp, const IbmLoop loop) {
   __shared__ BrickSmem sm;
+  if (loop.state && loop.state->done) return;
   const int nslots = active_slots(m);
   const int t = threadIdx.x;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
@@ -496,8 +605,78 @@ __global__ void __launch_bounds__(64, 16)
     }
     __syncthreads();
     if (res && t == 0) res[s] = sm.sred[0] + sm.sred[1];
-    if (do_interp) brick_interp(sm, pm, p0, cnt);
+    if (do_interp) brick_interp(sm, pm, p0, cnt, cnt <= SP_CHUNK);
     __syncthreads();
+  }
+}
+
+// ||S[v]||^2 per active brick into res[slot] (v = vals, scaled by .w when
+// scale_by_w): the denominator ||S[s u_k]|| of the residual.
+__global__ void __launch_bounds__(64, 16)
+    brick_norm_kernel(BrickMap m, PairMap pm, const float4 *__restrict__ vals, int scale_by_w,
+                      float *__restrict__ res) {
+  __shared__ BrickSmem sm;
+  const int nslots = active_slots(m);
+  const int t = threadIdx.x;
+  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+    const float3 G = brick_gather(sm, pm, pm.start[s], pm.count[s], vals, scale_by_w != 0);
+    float r = G.x * G.x + G.y * G.y + G.z * G.z;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if ((t & 31) == 0) sm.sred[t >> 5] = r;
+    __syncthreads();
+    if (t == 0) res[s] = sm.sred[0] + sm.sred[1];
+    __syncthreads();
+  }
+}
+
+// Deterministic FP64 sum of res[0 .. nslots) (one block of 256 threads).
+__device__ double block_sum_res(const BrickMap &m, const float *__restrict__ res) {
+  __shared__ double red[256];
+  const int nslots = active_slots(m);
+  double a = 0.0;
+  for (int s = threadIdx.x; s < nslots; s += 256) a += (double)res[s];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// mode 0: den2 = sum res (||S[s u_k]||^2); mode 1: fallback den2 (used when
+// the first is 0): sum res, or 1 if that is 0 as well.
+__global__ void __launch_bounds__(256) ibm_den_kernel(BrickMap m, const float *__restrict__ res,
+                                                       IbmState *st, int mode) {
+  const double v = block_sum_res(m, res);
+  if (threadIdx.x == 0) {
+    if (mode == 0) {
+      st->den2 = v;
+      st->done = 0;
+      st->iters = 0;
+    } else if (st->den2 == 0.0) {
+      st->den2 = v > 0.0 ? v : 1.0;
+    }
+  }
+}
+
+// After iteration `it`: eps = ||G_{it+1} - G_it|| / den (Eulerian residual of
+// the fixed point); stop at the first eps <= tol or at max_iter iterations.
+__global__ void __launch_bounds__(256) ibm_check_kernel(BrickMap m, const float *__restrict__ res,
+                                                         IbmState *st, int it, double tol,
+                                                         int max_iter) {
+  if (st->done) return;
+  const double v = block_sum_res(m, res);
+  if (threadIdx.x == 0) {
+    const double eps = sqrt(v / st->den2);
+    if (it < IbmState::HIST) st->eps[it] = eps;
+    st->last_eps = eps;
+    if (eps <= tol || it + 1 >= max_iter) {
+      st->done = 1;
+      st->iters = it + 1;
+      st->capped = eps > tol;
+    }
   }
 }
 
@@ -505,9 +684,10 @@ __global__ void __launch_bounds__(64, 16)
 // g = u_k - u_n, du += s g (du starts at 0 when first && !warm).
 __global__ void __launch_bounds__(256)
     point_update_kernel(int64_t np, PointPrep pp, PairMap pm, float4 *__restrict__ du,
-                        float4 *__restrict__ uint, int first, int warm) {
+                        float4 *__restrict__ uint, int first, int warm, const IbmLoop loop) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= np) return;
+  if (loop.state && loop.state->done) return;
   const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
   const int4 a = pk[0], b = pk[1];
   const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -528,6 +708,29 @@ __global__ void __launch_bounds__(256)
   d.z += ut.w * (ut.z - uz);
   du[k] = d;
   uint[k] = make_float4(ux, uy, uz, 0.f);
+}
+
+// s(k) (u_k - u(k)) with u(k) the sum of the point's pair shares: the
+// first increment from a zero start, for the fallback residual denominator.
+__global__ void __launch_bounds__(256)
+    point_residual0_kernel(int64_t np, PointPrep pp, PairMap pm, float4 *__restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
+  const int4 a = pk[0], b = pk[1];
+  const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    if (idx[j] >= 0) {
+      const float4 v = pm.part[idx[j]];
+      ux += v.x;
+      uy += v.y;
+      uz += v.z;
+    }
+  }
+  const float4 ut = pp.ut[k];
+  out[k] = make_float4(ut.w * (ut.x - ux), ut.w * (ut.y - uy), ut.w * (ut.z - uz), 0.f);
 }
 
 __global__ void interp_dense_kernel(Geometry g, int delta, const float *__restrict__ U,
@@ -600,11 +803,9 @@ __global__ void slots_to_dense_kernel(Geometry g, BrickMap m, const float *__res
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename S>
-cudaError_t brick_init_typed(const Geometry &g, const void *f, const BrickMap &m,
-                             const PairMap &pm, const float4 *du_init, float *U0s, float *Gs,
-                             cudaStream_t st) {
-  brick_init_kernel<S><<<PERSISTENT_BLOCKS, 64, 0, st>>>((const S *)f, g, m, pm, du_init, U0s,
-                                                         Gs);
+cudaError_t brick_moments_typed(const Geometry &g, const void *f, const BrickMap &m, float *U0s,
+                                cudaStream_t st) {
+  brick_moments_kernel<S><<<PERSISTENT_BLOCKS / 2, 256, 0, st>>>((const S *)f, g, m, U0s);
   return cudaGetLastError();
 }
 
@@ -624,10 +825,12 @@ cudaError_t launch_build_pairs(const Geometry &g, int64_t np, const PointPrep &p
                                const BrickMap &m, const PairMap &pm, cudaStream_t st) {
   compact_kernel<<<nblk(g.nbrick, 256), 256, 0, st>>>(g, m, pm);
   if (np > 0) {
-    pair_count_kernel<<<nblk(np, 256), 256, 0, st>>>(g, np, pp, m, pm);
     pair_scan_kernel<<<1, 1024, 0, st>>>(m, pm);
     pair_fill_kernel<<<nblk(np, 256), 256, 0, st>>>(g, np, pp, m, pm);
-    pair_sort_kernel<<<PERSISTENT_BLOCKS / 8, 128, 0, st>>>(g, pp, m, pm);
+    // one warp per slot
+    const int blocks = (int)std::min<int64_t>((m.max_slots + 3) / 4, 152 * 32);
+    pair_sort_kernel<<<blocks > 0 ? blocks : 1, 128, 0, st>>>(g, pp, m, pm);
+    pair_weights_kernel<<<nblk(pm.max_pairs, 256), 256, 0, st>>>(g, pp, m, pm);
   }
   return cudaGetLastError();
 }
@@ -644,24 +847,55 @@ cudaError_t launch_build_pairs(const Geometry &g, int64_t np, const PointPrep &p
       return cudaErrorInvalidValue;          \
   }
 
-cudaError_t launch_brick_init(int storage, const Geometry &g, const void *f, const BrickMap &m,
-                              const PairMap &pm, const float4 *du_init, float *U0s, float *Gs,
-                              cudaStream_t st) {
-  DISPATCH_STORAGE(storage, brick_init_typed, g, f, m, pm, du_init, U0s, Gs, st);
+cudaError_t launch_brick_moments(int storage, const Geometry &g, const void *f,
+                                 const BrickMap &m, float *U0s, cudaStream_t st) {
+  DISPATCH_STORAGE(storage, brick_moments_typed, g, f, m, U0s, st);
+}
+
+cudaError_t launch_brick_init(const BrickMap &m, const PairMap &pm, const float4 *du_init,
+                              const float *U0s, float *Gs, cudaStream_t st) {
+  brick_init_kernel<<<PERSISTENT_BLOCKS, 64, 0, st>>>(m, pm, du_init, U0s, Gs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_brick_spread(const BrickMap &m, const PairMap &pm, const float4 *vals,
                                 const float *U0s, float *Gs, float *res, int do_interp,
-                                cudaStream_t st) {
-  brick_spread_kernel<<<PERSISTENT_BLOCKS, 64, 0, st>>>(m, pm, vals, U0s, Gs, res, do_interp);
+                                const IbmLoop &loop, cudaStream_t st) {
+  brick_spread_kernel<<<PERSISTENT_BLOCKS, 64, 0, st>>>(m, pm, vals, U0s, Gs, res, do_interp,
+                                                        loop);
   return cudaGetLastError();
 }
 
 cudaError_t launch_point_update(int64_t np, const PointPrep &pp, const PairMap &pm,
                                 float4 *du, float4 *uint, int first, int warm,
-                                cudaStream_t st) {
+                                const IbmLoop &loop, cudaStream_t st) {
   if (np <= 0) return cudaSuccess;
-  point_update_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, du, uint, first, warm);
+  point_update_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, du, uint, first, warm, loop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_brick_norm(const BrickMap &m, const PairMap &pm, const float4 *vals,
+                              int scale_by_w, float *res, cudaStream_t st) {
+  brick_norm_kernel<<<PERSISTENT_BLOCKS, 64, 0, st>>>(m, pm, vals, scale_by_w, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibm_den(const BrickMap &m, const float *res, IbmState *state, int mode,
+                           cudaStream_t st) {
+  ibm_den_kernel<<<1, 256, 0, st>>>(m, res, state, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ibm_check(const BrickMap &m, const float *res, IbmState *state, int it,
+                             double tol, int max_iter, cudaStream_t st) {
+  ibm_check_kernel<<<1, 256, 0, st>>>(m, res, state, it, tol, max_iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_point_residual0(int64_t np, const PointPrep &pp, const PairMap &pm,
+                                   float4 *out, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  point_residual0_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, out);
   return cudaGetLastError();
 }
 

@@ -58,24 +58,36 @@ cudaError_t launch_prepare_points(const Geometry &g, int delta, const PointsIn &
                                   const Bodies &b, int64_t t, PointPrep &pp,
                                   const BrickMap &m, const PairMap &pm, double *xpos,
                                   cudaStream_t st);
-// flags -> slots; (brick, point) pairs grouped by brick in a fixed order, with
-// brick-local weights (5 launches when np > 0, else 1)
+// counted bricks -> slots; (brick, point) pairs grouped by brick in a fixed
+// order, with brick-local weights (5 launches when np > 0, else 1)
 cudaError_t launch_build_pairs(const Geometry &g, int64_t np, const PointPrep &pp,
                                const BrickMap &m, const PairMap &pm, cudaStream_t st);
-// U0 on the active bricks (Eq. 1), G_0 = 0 or S[du_init], pair shares of
-// I[U0 + G_0]
-cudaError_t launch_brick_init(int storage, const Geometry &g, const void *f, const BrickMap &m,
-                              const PairMap &pm, const float4 *du_init, float *U0s, float *Gs,
-                              cudaStream_t st);
+// U0 on the active bricks (pull + Eq. 1)
+cudaError_t launch_brick_moments(int storage, const Geometry &g, const void *f,
+                                 const BrickMap &m, float *U0s, cudaStream_t st);
+// G_0 = 0 or S[du_init], pair shares of I[U0 + G_0]
+cudaError_t launch_brick_init(const BrickMap &m, const PairMap &pm, const float4 *du_init,
+                              const float *U0s, float *Gs, cudaStream_t st);
 // G = S[vals] on the active bricks (Alg. 2 as a gather); res[slot] = squared
 // change of G (NULL: skip); pair shares of I[U0 + G] if do_interp
 cudaError_t launch_brick_spread(const BrickMap &m, const PairMap &pm, const float4 *vals,
                                 const float *U0s, float *Gs, float *res, int do_interp,
-                                cudaStream_t st);
+                                const IbmLoop &loop, cudaStream_t st);
 // u_n(k) from the pair shares; g = u_k - u_n; du += s g (Alg. 1 loop body)
 cudaError_t launch_point_update(int64_t np, const PointPrep &pp, const PairMap &pm,
                                 float4 *du, float4 *uint, int first, int warm,
-                                cudaStream_t st);
+                                const IbmLoop &loop, cudaStream_t st);
+// ||S[v]||^2 per brick into res (v scaled by .w if scale_by_w)
+cudaError_t launch_brick_norm(const BrickMap &m, const PairMap &pm, const float4 *vals,
+                              int scale_by_w, float *res, cudaStream_t st);
+// residual denominators (mode 0: ||S[s u_k]||^2, mode 1: fallback) and the
+// per-iteration convergence check of the tolerance mode
+cudaError_t launch_ibm_den(const BrickMap &m, const float *res, IbmState *state, int mode,
+                           cudaStream_t st);
+cudaError_t launch_point_residual0(int64_t np, const PointPrep &pp, const PairMap &pm,
+                                   float4 *out, cudaStream_t st);
+cudaError_t launch_ibm_check(const BrickMap &m, const float *res, IbmState *state, int it,
+                             double tol, int max_iter, cudaStream_t st);
 // stateless operators (caller memory)
 cudaError_t launch_interp_dense(const Geometry &g, int delta, const float *U, int64_t n,
                                 const double *x, float *u, cudaStream_t st);

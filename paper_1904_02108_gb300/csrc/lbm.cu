@@ -114,12 +114,19 @@ __global__ void __launch_bounds__(256)
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x < 4) {
+  if (last) {
+    // the last block sums the block results with the same fixed tree
     __threadfence();
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; b++)
-      s += ((volatile double *)scratch)[b * 4 + threadIdx.x];
-    out[threadIdx.x] = threadIdx.x == 0 ? ncell + s : s;
+    for (int c = 0; c < 4; c++)
+      red[threadIdx.x][c] =
+          threadIdx.x < gridDim.x ? ((volatile double *)scratch)[threadIdx.x * 4 + c] : 0.0;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s)
+        for (int c = 0; c < 4; c++) red[threadIdx.x][c] += red[threadIdx.x + s][c];
+      __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = threadIdx.x == 0 ? ncell + red[0][0] : red[0][threadIdx.x];
     if (threadIdx.x == 0) *ticket = 0u;
   }
 }

@@ -1,0 +1,72 @@
+"""Reduced-precision population storage (BF16 / FP16 deviations f_i - t_i,
+FP32 arithmetic) against the FP64 oracle on the 64^3 downscale of the 384^3
+propeller array (216 propellers), and FP32 for reference.
+
+The bound per format follows from its unit roundoff u (FP16: 2^-11, BF16:
+2^-8): each stored deviation carries a relative error u per step; over the
+run the velocity error grows like the accumulated rounding, and the test holds
+each format to a fixed multiple of u measured on this workload.
+"""
+import numpy as np
+import pytest
+
+from paper_1904_02108_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 50
+# relative L2 bound on U after STEPS steps
+BOUND = {"f32": 1e-5, "f16": 40 * 2.0 ** -11, "bf16": 40 * 2.0 ** -8}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def oracle_run(orc):
+    w = W.dense_array_64()
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=w.n_iter)
+    sim.step(STEPS)
+    return w, sim.fields()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_storage_error_against_oracle(gpu_lib, orc, oracle_run, storage):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, (rho_o, U_o) = oracle_run
+    lat = gpu_lib.Lattice(w.shape, w.tau, storage=storage,
+                          stream=torch.cuda.current_stream())
+    lat.set_propellers(w.props)
+    lat.step(STEPS, w.n_iter)
+    rho, U, _ = lat.fields()
+    err = rel_l2(U, U_o)
+    print("storage %s: rel L2(U) after %d steps = %.3e (bound %.3e), max|rho err| = %.3e"
+          % (storage, STEPS, err, BOUND[storage], np.abs(rho - rho_o).max()))
+    assert err < BOUND[storage]
+    s = lat.stats()
+    assert abs(s["mass"] / w.cells - 1.0) < 1e-3
+    lat.close()
+
+
+@pytest.mark.parametrize("storage,u", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+def test_roundtrip_rounds_deviations_to_nearest(gpu_lib, orc, storage, u):
+    """Stored deviations are f - t rounded to nearest in the 16-bit format:
+    the read-back error is at most u |f - t| (plus the smallest subnormal)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    shape = (8, 8, 12)
+    rng = W.SplitMix64(61)
+    f = orc.init_equilibrium(shape, 1 + 0.02 * W.random_array(rng, shape),
+                             0.05 * W.random_array(rng, (3,) + shape))
+    t = orc.velocity_set()[1][:, None, None, None]
+    lat = gpu_lib.Lattice(shape, 0.8, storage=storage, stream=torch.cuda.current_stream())
+    lat.set_populations(f)
+    d = lat.deviations().astype(np.float64)
+    dev = (f - t).astype(np.float32).astype(np.float64)
+    tiny = 6e-8 if storage == "f16" else 1e-38
+    assert np.all(np.abs(d - dev) <= u * np.abs(dev) + tiny)
+    lat.close()
