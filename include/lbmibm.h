@@ -58,6 +58,8 @@ extern "C" {
 /* Initial velocity correction du of each step's fixed point (Sec. 3). */
 #define LBM_WARM_ZERO 0       /* du = 0, as in the paper                      */
 #define LBM_WARM_PREVIOUS 1   /* du = previous step's final du                */
+#define LBM_WARM_MLP 2        /* du = previous du + V * MLP(features), the
+                                 learned warm start (mlp_set_weights)        */
 
 typedef struct lbm lbm_t;
 
@@ -229,6 +231,51 @@ size_t ibm_spread_scratch_bytes(int nx, int ny, int nz, int64_t n);
 int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n,
                    const double *x, const float *v, float *F, void *scratch,
                    void *stream);
+
+/* ---- learned warm start (not in the paper) ------------------------------ */
+
+/* Per-point MLP y = W3 s(W2 s(W1 x + b1) + b2) + b3, s(v) = v / (1 + e^-v),
+ * x in R^16, two hidden layers of 64, y in R^3.  Parameters P: FP32 vector of
+ * LBM_MLP_NPARAM values [W1 (64x16, row-major out x in), b1, W2 (64x64), b2,
+ * W3 (3x64), b3].  The kernels run on BF16 tensor cores with FP32
+ * accumulation from a packed BF16 copy of P (mlp_pack_dev).
+ *
+ * Features of point k (velocities / LBM_MLP_VSCALE, lengths /
+ * LBM_MLP_LSCALE): u_i = I[U0 + S[du_prev]](k), the velocity interpolated
+ * with the previous step's force applied (3), u_k (3), the previous step's
+ * du (3), local point density (pairs of its bricks per brick cell) (1),
+ * radius and axial offset from its body's axis and omega r (3), u_k - u_i
+ * (3).  In LBM_WARM_MLP mode the fixed point starts from
+ * du_prev + V * MLP(x). */
+#define LBM_MLP_NPARAM 5443
+#define LBM_MLP_VSCALE 0.05
+#define LBM_MLP_LSCALE 16.0
+
+size_t mlp_packed_bytes(void);
+int mlp_pack_dev(const float *P, void *packed, void *stream);
+/* Y[n][3] = MLP(X[n][16]); device pointers. */
+int mlp_forward_dev(int64_t n, const float *X, const void *packed, float *Y, void *stream);
+/* grad (device, LBM_MLP_NPARAM floats) and *loss (device float, may be
+ * NULL) of the mean 0.5 |MLP(x) - t|^2 over X[n][16], T[n][3];
+ * P is the FP32 parameter vector packed as `packed`; scratch: device memory
+ * of mlp_grad_scratch_bytes(n) bytes. */
+size_t mlp_grad_scratch_bytes(int64_t n);
+int mlp_loss_grad_dev(int64_t n, const float *X, const float *T, const float *P,
+                      const void *packed, float *grad, float *loss, void *scratch,
+                      void *stream);
+/* One Adam step (bias-corrected, step >= 1) on P with moments m, v (device,
+ * LBM_MLP_NPARAM floats each); repacks into `packed` if not NULL. */
+int mlp_adam_dev(float *P, float *m, float *v, const float *grad, int64_t step, double lr,
+                 double beta1, double beta2, double eps, void *packed, void *stream);
+/* Weights of the learned warm start of h (host or device FP32 vector). */
+int mlp_set_weights(lbm_t *h, const float *P);
+int mlp_set_weights_dev(lbm_t *h, const float *P);
+/* Compute the features every step even without the learned start (for
+ * generating training data). */
+int lbm_set_features(lbm_t *h, int on);
+/* Training sample of the last step: X[n][16] its features, T[n][3] =
+ * (final du - previous du) / LBM_MLP_VSCALE; device buffers. */
+int ibm_read_mlp_sample_dev(lbm_t *h, float *X, float *T);
 
 /* ---- spreading without any allocation ---------------------------------- */
 

@@ -28,7 +28,10 @@ LBM_WNOTCONVERGED = 1
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 DELTA = {"cosine": 0, "peskin": 1}
-WARM = {"zero": 0, "previous": 1}
+WARM = {"zero": 0, "previous": 1, "mlp": 2}
+MLP_NPARAM = 5443
+MLP_VSCALE = 0.05
+MLP_LSCALE = 16.0
 
 _c = ctypes
 _p = _c.c_void_p
@@ -90,6 +93,16 @@ _SIGS = {
     "ibm_spread_scratch_bytes": (_c.c_size_t, [_i, _i, _i, _i64]),
     "ibm_spread_dev": (_i, [_i, _i, _i, _i, _i64, _p, _p, _p, _p, _p]),
     "ibm_spread_dev_noalloc": (_i, [_i, _i, _i, _i, _i64, _p, _p, _p, _p]),
+    "mlp_packed_bytes": (_c.c_size_t, []),
+    "mlp_pack_dev": (_i, [_p, _p, _p]),
+    "mlp_forward_dev": (_i, [_i64, _p, _p, _p, _p]),
+    "mlp_grad_scratch_bytes": (_c.c_size_t, [_i64]),
+    "mlp_loss_grad_dev": (_i, [_i64, _p, _p, _p, _p, _p, _p, _p, _p]),
+    "mlp_adam_dev": (_i, [_p, _p, _p, _p, _i64, _d, _d, _d, _d, _p, _p]),
+    "mlp_set_weights": (_i, [_p, _p]),
+    "mlp_set_weights_dev": (_i, [_p, _p]),
+    "lbm_set_features": (_i, [_p, _i]),
+    "ibm_read_mlp_sample_dev": (_i, [_p, _p, _p]),
 }
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -294,6 +307,22 @@ class Lattice:
         names = stage_names()
         return {names[i]: (float(ms[i]), int(la[i])) for i in range(n)}
 
+    def set_mlp_weights(self, P):
+        """P: FP32 parameter vector (numpy on the host or a CUDA tensor)."""
+        if hasattr(P, "is_cuda") and P.is_cuda:
+            self._c(load().mlp_set_weights_dev(self.h, _ptr(P)))
+        else:
+            P = np.ascontiguousarray(P, np.float32).reshape(-1)
+            assert P.size == MLP_NPARAM
+            self._c(load().mlp_set_weights(self.h, _ptr(P)))
+
+    def set_features(self, on=True):
+        self._c(load().lbm_set_features(self.h, int(on)))
+
+    def mlp_sample_dev(self, X=None, T=None):
+        """Writes the last step's features X[n,16] and targets T[n,3] (CUDA)."""
+        self._c(load().ibm_read_mlp_sample_dev(self.h, _ptr(X), _ptr(T)))
+
     def save_state(self):
         L = load()
         n = _c.c_size_t(0)
@@ -335,3 +364,36 @@ def spread_dev_noalloc(x, v, F, delta="cosine", stream=None):
     raw = getattr(stream, "cuda_stream", stream)
     _check(load().ibm_spread_dev_noalloc(nx, ny, nz, DELTA[delta], x.shape[0], _ptr(x),
                                          _ptr(v), _ptr(F), _p(raw) if raw else None))
+
+
+def _raw(stream):
+    raw = getattr(stream, "cuda_stream", stream)
+    return _p(raw) if raw else None
+
+
+def mlp_packed_bytes():
+    return load().mlp_packed_bytes()
+
+
+def mlp_pack_dev(P, packed, stream=None):
+    _check(load().mlp_pack_dev(_ptr(P), _ptr(packed), _raw(stream)))
+
+
+def mlp_forward_dev(X, packed, Y, stream=None):
+    _check(load().mlp_forward_dev(X.shape[0], _ptr(X), _ptr(packed), _ptr(Y), _raw(stream)))
+
+
+def mlp_grad_scratch_bytes(n):
+    return load().mlp_grad_scratch_bytes(int(n))
+
+
+def mlp_loss_grad_dev(X, T, P, packed, grad, loss, scratch, stream=None):
+    _check(load().mlp_loss_grad_dev(X.shape[0], _ptr(X), _ptr(T), _ptr(P), _ptr(packed),
+                                    _ptr(grad), _ptr(loss), _ptr(scratch), _raw(stream)))
+
+
+def mlp_adam_dev(P, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, packed=None,
+                 stream=None):
+    _check(load().mlp_adam_dev(_ptr(P), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps), _ptr(packed),
+                               _raw(stream)))

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbmibm.so")
-SOURCES = ["lbm.cu", "ibm.cu", "api.cu"]
+SOURCES = ["lbm.cu", "ibm.cu", "mlp.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

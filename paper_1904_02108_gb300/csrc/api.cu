@@ -24,8 +24,9 @@ using namespace lbmibm;
 namespace {
 
 const char *kStageNames[] = {"kinematics",   "pairs",          "brick_init", "point_update",
-                             "brick_spread", "collide_stream", "stats",      "residual"};
-constexpr int kNumStages = 8;
+                             "brick_spread", "collide_stream", "stats",      "residual",
+                             "mlp"};
+constexpr int kNumStages = 9;
 enum Stage {
   ST_KIN,
   ST_PAIRS,
@@ -34,7 +35,8 @@ enum Stage {
   ST_SPREAD,
   ST_COLLIDE,
   ST_STATS,
-  ST_RESID
+  ST_RESID,
+  ST_MLP
 };
 // iterations launched between two host checks of the tolerance-mode stop flag
 constexpr int kCheckChunk = 16;
@@ -82,6 +84,12 @@ struct lbm {
   int64_t not_converged = 0;
   IbmState *state = nullptr;       // device
   IbmState *state_host = nullptr;  // pinned mirror of the header fields
+
+  // learned warm start
+  bool features_on = false;
+  float *feat = nullptr;           // [np][16] features of the last step
+  float *mlp_P = nullptr;          // [MLP_NPARAM] FP32 weights
+  void *mlp_packed = nullptr;      // BF16 packed copy
   int64_t nlaunch = 0;
 
   // timing
@@ -204,6 +212,7 @@ void free_points(lbm_t *h) {
   dfree(h->pm.part);
   dfree(h->pm.point_pairs);
   h->pm.max_pairs = 0;
+  dfree(h->feat);
   dfree(h->U0s);
   dfree(h->Gs);
   dfree(h->res);
@@ -274,6 +283,8 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->tmp);
   dfree(h->state);
   if (h->state_host) cudaFreeHost(h->state_host);
+  dfree(h->mlp_P);
+  if (h->mlp_packed) cudaFree(h->mlp_packed);
   for (auto &p : h->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -297,7 +308,7 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
     return fail(nullptr, LBM_EINVAL, "tau = %g must be > 1/2", o->tau);
   if (o->storage < 0 || o->storage > 2) return fail(nullptr, LBM_EINVAL, "bad storage");
   if (o->delta < 0 || o->delta > 1) return fail(nullptr, LBM_EINVAL, "bad delta kernel");
-  if (o->warm_start < 0 || o->warm_start > 1) return fail(nullptr, LBM_EINVAL, "bad warm start");
+  if (o->warm_start < 0 || o->warm_start > 2) return fail(nullptr, LBM_EINVAL, "bad warm start");
   if (o->ibm_max_iter <= 0 || !(o->ibm_tol >= 0))
     return fail(nullptr, LBM_EINVAL, "bad ibm_tol/ibm_max_iter");
   lbm_t *h = new lbm();
@@ -404,6 +415,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->pm.count, ms));
     CK(h, dalloc(&h->pm.start, ms + 1));
     CK(h, dalloc(&h->pm.cursor, ms));
+    CK(h, dalloc(&h->feat, (size_t)MLP_IN * n));
     CK(h, dalloc(&h->pm.k, 8 * n));
     CK(h, dalloc(&h->pm.brick, 8 * n));
     CK(h, dalloc(&h->pm.w, 3 * 8 * n));
@@ -572,10 +584,30 @@ static int step_once(lbm_t *h, int n_iter) {
       StageTimer T(h, ST_PAIRS, 5);
       CK(h, launch_build_pairs(h->g, h->np, h->pp, h->m, h->pm, st));
     }
-    const bool warm = h->warm == LBM_WARM_PREVIOUS && h->have_du;
+    const bool mlp = h->warm == LBM_WARM_MLP;
+    const bool feat = mlp || h->features_on;
+    const bool warm = (h->warm == LBM_WARM_PREVIOUS && h->have_du) || mlp;
     {
-      StageTimer T(h, ST_INIT, 2);
+      StageTimer T(h, ST_INIT, 1);
       CK(h, launch_brick_moments(h->storage, h->g, h->f[h->cur], h->m, h->U0s, st));
+    }
+    if (feat) {
+      // features from the shares of I[U0 + S[du_prev]] (the previous step's
+      // force applied); the learned start du = du_prev + V MLP(x)
+      StageTimer T(h, ST_MLP, mlp ? 3 : 2);
+      if (mlp && !h->have_du) CK(h, cudaMemsetAsync(h->du, 0, sizeof(float4) * h->np, st));
+      CK(h, launch_brick_init(h->m, h->pm, h->have_du ? h->du : nullptr, h->U0s, h->Gs, st));
+      CK(h, launch_mlp_features(h->g, h->np, h->pp, h->pm, h->m, h->have_du ? h->du : nullptr, p,
+                                b, h->feat, st));
+      if (mlp)
+        CK(h, launch_mlp_forward(h->np, h->feat, h->mlp_packed, nullptr, h->du, MLP_VSCALE, 1,
+                                 st));
+    }
+    // G_0 = S[du_init] and the shares of I[U0 + G_0], unless the feature pass
+    // above already left exactly these
+    const bool init_done = feat && !mlp && (warm == h->have_du);
+    if (!init_done) {
+      StageTimer T(h, ST_INIT, 1);
       CK(h, launch_brick_init(h->m, h->pm, warm ? h->du : nullptr, h->U0s, h->Gs, st));
     }
     warn = ibm_fixed_point(h, n_iter, warm);
@@ -616,6 +648,8 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
     return fail(h, LBM_EINVAL, "n_steps = %d, n_ibm_iter = %d", n_steps, n_ibm_iter);
   if (h->nb > 0 && h->max_body >= h->nb)
     return fail(h, LBM_EINVAL, "points refer to body %d, only %d bodies", h->max_body, h->nb);
+  if (h->warm == LBM_WARM_MLP && !h->mlp_packed && h->np > 0)
+    return fail(h, LBM_EINVAL, "learned warm start without weights (mlp_set_weights)");
   int warn = LBM_OK;
   for (int s = 0; s < n_steps; s++) {
     int r = step_once(h, n_ibm_iter);
@@ -1091,3 +1125,85 @@ extern "C" int ibm_spread_dev_noalloc(int nx, int ny, int nz, int delta, int64_t
   // clears the output and the binning state it needs at zero
   return ibm_spread_dev(nx, ny, nz, delta, n, x, v, F, ptr, stream);
 }
+
+// ---- learned warm start -------------------------------------------------------
+
+extern "C" {
+
+size_t mlp_packed_bytes(void) { return lbmibm::mlp_packed_bytes(); }
+
+int mlp_pack_dev(const float *P, void *packed, void *stream) {
+  if (!P || !packed) return fail(nullptr, LBM_EINVAL, "NULL pointer");
+  cudaError_t e = launch_mlp_pack(P, packed, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "%s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int mlp_forward_dev(int64_t n, const float *X, const void *packed, float *Y, void *stream) {
+  if (n < 0 || (n > 0 && (!X || !packed || !Y))) return fail(nullptr, LBM_EINVAL, "bad arguments");
+  cudaError_t e = launch_mlp_forward(n, X, packed, Y, nullptr, 0.f, 0, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "%s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+size_t mlp_grad_scratch_bytes(int64_t n) {
+  return n > 0 ? sizeof(float) * mlp_grad_scratch_floats(n) : 0;
+}
+
+int mlp_loss_grad_dev(int64_t n, const float *X, const float *T, const float *P,
+                      const void *packed, float *grad, float *loss, void *scratch, void *stream) {
+  if (n <= 0 || !X || !T || !P || !packed || !grad || !scratch)
+    return fail(nullptr, LBM_EINVAL, "bad arguments to mlp_loss_grad_dev");
+  cudaError_t e = launch_mlp_loss_grad(n, X, T, packed, P, grad, loss, (float *)scratch,
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "%s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int mlp_adam_dev(float *P, float *m, float *v, const float *grad, int64_t step, double lr,
+                 double beta1, double beta2, double eps, void *packed, void *stream) {
+  if (!P || !m || !v || !grad || step < 1 || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) ||
+      !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return fail(nullptr, LBM_EINVAL, "bad arguments to mlp_adam_dev");
+  cudaError_t e = launch_mlp_adam(P, m, v, grad, step, (float)lr, (float)beta1, (float)beta2,
+                                  (float)eps, packed, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "%s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+static int set_weights(lbm_t *h, const float *P, cudaMemcpyKind kind) {
+  if (!h || !P) return LBM_EINVAL;
+  if (kind == cudaMemcpyHostToDevice && !all_finite(P, MLP_NPARAM))
+    return fail(h, LBM_ENONFINITE, "non-finite MLP weight");
+  if (!h->mlp_P) CK(h, dalloc(&h->mlp_P, MLP_NPARAM));
+  if (!h->mlp_packed) CK(h, cudaMalloc(&h->mlp_packed, lbmibm::mlp_packed_bytes()));
+  CK(h, cudaMemcpyAsync(h->mlp_P, P, sizeof(float) * MLP_NPARAM, kind, h->st));
+  CK(h, launch_mlp_pack(h->mlp_P, h->mlp_packed, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+int mlp_set_weights(lbm_t *h, const float *P) { return set_weights(h, P, cudaMemcpyHostToDevice); }
+int mlp_set_weights_dev(lbm_t *h, const float *P) {
+  return set_weights(h, P, cudaMemcpyDeviceToDevice);
+}
+
+int lbm_set_features(lbm_t *h, int on) {
+  if (!h) return LBM_EINVAL;
+  h->features_on = on != 0;
+  return LBM_OK;
+}
+
+int ibm_read_mlp_sample_dev(lbm_t *h, float *X, float *T) {
+  if (!h) return LBM_EINVAL;
+  if (h->np == 0) return LBM_OK;
+  if (!(h->features_on || h->warm == LBM_WARM_MLP))
+    return fail(h, LBM_EINVAL, "features are not computed (lbm_set_features)");
+  if (X)
+    CK(h, cudaMemcpyAsync(X, h->feat, sizeof(float) * MLP_IN * h->np, cudaMemcpyDeviceToDevice,
+                          h->st));
+  if (T) CK(h, launch_mlp_targets(h->np, h->feat, h->du, T, h->st));
+  return LBM_OK;
+}
+
+}  // extern "C"

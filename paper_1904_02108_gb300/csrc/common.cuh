@@ -130,6 +130,13 @@ struct PointPrep {
   float4 *ut;    // [np]      (u_k, s_k)
 };
 
+// Per-point MLP of the learned warm start: 16 features -> 64 -> 64 -> 3.
+constexpr int MLP_IN = 16, MLP_HIDDEN = 64, MLP_OUT = 3;
+constexpr int MLP_NPARAM = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN +
+                           MLP_HIDDEN + MLP_OUT * MLP_HIDDEN + MLP_OUT;
+// feature scales: velocities in units of MLP_VSCALE, lengths of MLP_LSCALE
+constexpr float MLP_VSCALE = 0.05f, MLP_LSCALE = 16.f;
+
 // State of the tolerance-driven fixed point, on the device.
 struct IbmState {
   static constexpr int HIST = 4096;

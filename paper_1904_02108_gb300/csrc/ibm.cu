@@ -733,6 +733,81 @@ __global__ void __launch_bounds__(256)
   out[k] = make_float4(ut.w * (ut.x - ux), ut.w * (ut.y - uy), ut.w * (ut.z - uz), 0.f);
 }
 
+// Features of the learned warm start, per point (velocities in units of
+// MLP_VSCALE, lengths of MLP_LSCALE), from the pair shares of
+// I[U0 + S[du_prev]] left by brick_init:
+//   0-2  u_i = I[U0 + S[du_prev]](k), the fluid velocity interpolated at the
+//        point with the previous step's force applied
+//   3-5  u_k, the surface velocity
+//   6-8  du_prev, the previous step's final velocity correction
+//   9    local point density: pairs of the point's bricks per brick cell
+//   10-12 body-relative rest position: radius and axial offset from the
+//        body's axis, and the speed omega r (0 without bodies)
+//   13-15 u_k - u_i, the slip left by the previous force
+__global__ void __launch_bounds__(256)
+    mlp_features_kernel(int64_t np, PointPrep pp, PairMap pm, BrickMap m,
+                        const float4 *__restrict__ du_prev, PointsIn p, Bodies bd,
+                        float *__restrict__ X) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
+  const int4 a = pk[0], b = pk[1];
+  const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  float ux = 0.f, uy = 0.f, uz = 0.f, dens = 0.f;
+  int nb = 0;
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    if (idx[j] >= 0) {
+      const float4 v = pm.part[idx[j]];
+      ux += v.x;
+      uy += v.y;
+      uz += v.z;
+      dens += (float)pm.count[m.brick_slot[pm.brick[idx[j]]]];
+      nb++;
+    }
+  }
+  const float iv = 1.f / MLP_VSCALE;
+  const float4 ut = pp.ut[k];
+  const float4 dp = du_prev ? du_prev[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float r = 0.f, zr = 0.f, sp = 0.f;
+  if (bd.nb > 0) {
+    const int bi = p.body ? p.body[k] : 0;
+    const double *c = bd.centre + 3 * bi;
+    const double dx = p.X[3 * k] - c[0], dy = p.X[3 * k + 1] - c[1], dz = p.X[3 * k + 2] - c[2];
+    r = (float)sqrt(dx * dx + dy * dy);
+    zr = (float)dz;
+    sp = (float)fabs(bd.omega[bi]) * r;
+  }
+  float *o = X + MLP_IN * k;
+  o[0] = ux * iv;
+  o[1] = uy * iv;
+  o[2] = uz * iv;
+  o[3] = ut.x * iv;
+  o[4] = ut.y * iv;
+  o[5] = ut.z * iv;
+  o[6] = dp.x * iv;
+  o[7] = dp.y * iv;
+  o[8] = dp.z * iv;
+  o[9] = nb > 0 ? dens / (64.f * nb) : 0.f;
+  o[10] = r / MLP_LSCALE;
+  o[11] = zr / MLP_LSCALE;
+  o[12] = sp * iv;
+  o[13] = (ut.x - ux) * iv;
+  o[14] = (ut.y - uy) * iv;
+  o[15] = (ut.z - uz) * iv;
+}
+
+__global__ void mlp_targets_kernel(int64_t np, const float *__restrict__ X,
+                                   const float4 *__restrict__ du, float *__restrict__ T) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const float iv = 1.f / MLP_VSCALE;
+  const float4 d = du[k];
+  T[3 * k] = d.x * iv - X[MLP_IN * k + 6];
+  T[3 * k + 1] = d.y * iv - X[MLP_IN * k + 7];
+  T[3 * k + 2] = d.z * iv - X[MLP_IN * k + 8];
+}
+
 __global__ void interp_dense_kernel(Geometry g, int delta, const float *__restrict__ U,
                                     int64_t n, const double *__restrict__ x,
                                     float *__restrict__ u) {
@@ -896,6 +971,21 @@ cudaError_t launch_point_residual0(int64_t np, const PointPrep &pp, const PairMa
                                    float4 *out, cudaStream_t st) {
   if (np <= 0) return cudaSuccess;
   point_residual0_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_features(const Geometry &g, int64_t np, const PointPrep &pp,
+                                const PairMap &pm, const BrickMap &m, const float4 *du_prev,
+                                const PointsIn &p, const Bodies &b, float *X, cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  mlp_features_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, m, du_prev, p, b, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_targets(int64_t np, const float *X, const float4 *du, float *T,
+                               cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  mlp_targets_kernel<<<nblk(np, 256), 256, 0, st>>>(np, X, du, T);
   return cudaGetLastError();
 }
 

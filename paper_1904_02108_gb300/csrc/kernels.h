@@ -88,6 +88,31 @@ cudaError_t launch_point_residual0(int64_t np, const PointPrep &pp, const PairMa
                                    float4 *out, cudaStream_t st);
 cudaError_t launch_ibm_check(const BrickMap &m, const float *res, IbmState *state, int it,
                              double tol, int max_iter, cudaStream_t st);
+// Per-point MLP features (16) of the learned warm start from the pair shares
+// of I[U0] (brick_init without du_init), u_k, du_prev and the body-relative
+// rest position; see api.cu for the list.
+cudaError_t launch_mlp_features(const Geometry &g, int64_t np, const PointPrep &pp,
+                                const PairMap &pm, const BrickMap &m, const float4 *du_prev,
+                                const PointsIn &p, const Bodies &b, float *X, cudaStream_t st);
+// training sample target T = (du - du_prev) / MLP_VSCALE, du_prev from X
+cudaError_t launch_mlp_targets(int64_t np, const float *X, const float4 *du, float *T,
+                               cudaStream_t st);
+
+// ----------------------------------------------------------------- mlp.cu
+size_t mlp_packed_bytes();
+size_t mlp_train_smem_bytes();
+size_t mlp_grad_scratch_floats(int64_t n);
+cudaError_t launch_mlp_pack(const float *P, void *packed, cudaStream_t st);
+// mode 0: Y[n][3] = MLP(X); mode 1: du[k] += scale * MLP(X)[k]
+cudaError_t launch_mlp_forward(int64_t n, const float *X, const void *packed, float *Y,
+                               float4 *du, float scale, int mode, cudaStream_t st);
+cudaError_t launch_mlp_loss_grad(int64_t n, const float *X, const float *T, const void *packed,
+                                 const float *P, float *grad, float *loss, float *part,
+                                 cudaStream_t st);
+cudaError_t launch_mlp_adam(float *P, float *m, float *v, const float *grad, int64_t step,
+                            float lr, float b1, float b2, float eps, void *packed,
+                            cudaStream_t st);
+
 // stateless operators (caller memory)
 cudaError_t launch_interp_dense(const Geometry &g, int delta, const float *U, int64_t n,
                                 const double *x, float *u, cudaStream_t st);
