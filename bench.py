@@ -105,6 +105,18 @@ def _captured_traffic(name):
         return None
 
 
+def combine_ranks(ms, cells, steps, ws, device="cpu"):
+    """Replicas only: every rank advances its own copy of the workload.  The
+    job's time is the slowest rank's; the value counts every rank's cells."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, ws * cells * steps / (ms / 1e3) / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -201,10 +213,7 @@ def run_ours(args):
     stage = lat.timing()
     s = lat.stats()
     launches = s["kernel_launches"] - launches0
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = combine_ranks(ms, w.cells, args.steps, ws, device="cuda")
     lat.enable_timing(False)
 
     # ---- per-stage breakdown (separate pass, every stage bracketed)
@@ -237,8 +246,7 @@ def run_ours(args):
     h2d = npnt * (24 + 4 + 4 + 12)
     d2h = npnt * 12 + 32
 
-    value = ws * w.cells * args.steps / (ms / 1e3) / 1e6
-    e2e = ws * w.cells * e2e_steps / e2e_s / 1e6
+    _, e2e = combine_ranks(e2e_s * 1e3, w.cells, e2e_steps, ws, device="cuda")
 
     # ---- roofline of the dominant kernel (collide-stream, HBM-bound)
     coll_ms, coll_n = stage["collide_stream"]
@@ -268,18 +276,130 @@ def run_ours(args):
         "stage_ms_per_step": {k: round(v, 5) for k, v in breakdown.items()},
         "clocks": clk.summary(),
     }
+    lat.close()
+    if not args.no_extras and ws == 1:
+        line["batched"] = bench_batched()
+        line["precision"] = bench_precision()
+        line["tolerance"] = bench_tolerance()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         wcpu = W.dense_array_256()
         dt, cores = cpu_oracle_run(wcpu, 2)
         line["cpu_baseline"] = {"value": wcpu.cells * 2 / dt / 1e6, "unit": UNIT,
                                 "cores": cores, "kind": "oracle",
                                 "sample": "2 full steps of the workload from rest, FP64"}
-    lat.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+WEIGHTS = os.path.join(ROOT, "paper_1904_02108_gb300", "data", "warm_start_256.npy")
+
+
+def _device_ms(fn, st):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def bench_batched(steps=100, warmup=4):
+    """48 uneven periodic cubes (side U{48,64,80,96}) with 1-8 propellers
+    each, one launch per stage for all of them, replayed as a CUDA graph."""
+    import torch
+    from paper_1904_02108_gb300 import binding, workload as W
+    doms, dropped = W.batched_domains()
+    st = torch.cuda.current_stream()
+    lats = []
+    for w in doms:
+        lat = binding.Lattice(w.shape, w.tau, stream=st)
+        lat.set_propellers(w.props)
+        lats.append(lat)
+    batch = binding.Batch(lats)
+    batch.set_graph(True)
+    batch.step(warmup, 5)
+    l0 = lats[0].stats()["kernel_launches"]
+    ms = _device_ms(lambda: batch.step(steps, 5), st)
+    launches = lats[0].stats()["kernel_launches"] - l0
+    cells = sum(w.cells for w in doms)
+    out = {"workload": "batched_domains_48", "value": cells * steps / (ms / 1e3) / 1e6,
+           "unit": "MLUPS", "domains": len(doms), "cells": cells,
+           "points": sum(w.props.n_points for w in doms), "propellers_dropped": dropped,
+           "steps": steps, "ms_per_step": ms / steps, "graph": True,
+           "launches_per_step": launches / steps}
+    batch.close()
+    for lat in lats:
+        lat.close()
+    return out
+
+
+def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
+    """ms per step when every step iterates the fixed point to eps <= tol,
+    on the 256^3 propeller array: zero start, previous-force start, the
+    learned start, and the previous-force start on 16-bit storage."""
+    import numpy as np
+    import torch
+    from paper_1904_02108_gb300 import binding, workload as W
+    w = W.dense_array_256()
+    st = torch.cuda.current_stream()
+    variants = [("zero_f32", "zero", "f32"), ("previous_f32", "previous", "f32")]
+    P = None
+    if os.path.exists(WEIGHTS):
+        P = np.load(WEIGHTS)
+        variants.append(("learned_f32", "mlp", "f32"))
+    variants += [("previous_bf16", "previous", "bf16"), ("previous_f16", "previous", "f16")]
+    out = {"tol": tol, "max_iter": max_iter, "workload": w.name, "steps": steps}
+    for name, warm, storage in variants:
+        lat = binding.Lattice(w.shape, w.tau, storage=storage, warm=warm, ibm_tol=tol,
+                              ibm_max_iter=max_iter, stream=st)
+        lat.set_propellers(w.props)
+        if warm == "mlp":
+            lat.set_mlp_weights(P)
+        lat.step(warmup, 0)
+        iters, capped = 0, 0
+        t_ms = 0.0
+        for _ in range(steps):
+            t_ms += _device_ms(lambda: lat.step(1, 0), st)
+            s = lat.stats()
+            iters += s["last_ibm_iters"]
+            capped += int(s["last_residual"] > tol)
+        out[name] = {"ms_per_step": t_ms / steps, "iters_per_step": iters / steps,
+                     "capped_steps": capped}
+        lat.close()
+    return out
+
+
+def bench_precision(steps=100, warmup=5):
+    """384^3 array of 216 propellers (5 iterations per step) with 16-bit
+    deviation storage: MLUPS and the collide-stream kernel's HBM roofline."""
+    import torch
+    from paper_1904_02108_gb300 import binding, workload as W
+    w = W.dense_array_384()
+    st = torch.cuda.current_stream()
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    out = {"workload": w.name, "cells": w.cells, "points": w.props.n_points, "steps": steps}
+    for storage in ("bf16", "f16"):
+        lat = binding.Lattice(w.shape, w.tau, storage=storage, stream=st)
+        lat.set_propellers(w.props)
+        lat.step(warmup, w.n_iter)
+        lat.enable_timing(["collide_stream"])
+        ms = _device_ms(lambda: lat.step(steps, w.n_iter), st)
+        cms, cn = lat.timing()["collide_stream"]
+        s = lat.stats()
+        alg = w.cells * 19 * 2 * 2 + s["active_bricks"] * 64 * 12
+        ach = alg / (cms / 1e3 / cn) / 1e9
+        out[storage] = {"value": w.cells * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
+                        "ms_per_step": ms / steps,
+                        "collide_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s",
+                                             "frac": ach / peak, "alg_bytes_per_launch": alg}}
+        lat.close()
+    return out
 
 
 def main():
@@ -289,6 +409,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, 16-bit and tolerance-mode measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

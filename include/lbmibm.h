@@ -191,6 +191,28 @@ int lbm_read_residuals(lbm_t *h, double *eps, int cap);
 /* The D3Q19 velocity set e[19][3] and weights t[19] the library uses. */
 void lbm_velocity_set(int *e, double *t);
 
+/* ---- captured steps and batches of lattices ------------------------------ */
+
+/* on != 0: lbm_step with n_ibm_iter > 0 captures two consecutive steps into
+ * a CUDA graph once the warm-start history is steady, and replays it for
+ * every further pair of steps (a new capture follows any change of points,
+ * bodies, options or iteration count).  Stage timing is not recorded inside
+ * replayed steps.  Work is ordered on the handle's stream through events. */
+int lbm_set_graph(lbm_t *h, int on);
+
+/* A batch advances several lattices (different sizes, points and bodies)
+ * together: each stage of the step is one kernel launch over all of them.
+ * The handles stay owned by the caller and must not be destroyed before the
+ * batch; they must share the storage format, the stats option, the warm-start
+ * mode and history, the stream, and be at the same lattice parity (created
+ * together or stepped together).  lbm_batch_step needs n_ibm_iter > 0;
+ * results are read through the individual handles. */
+typedef struct lbm_batch lbm_batch_t;
+int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out);
+int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter);
+int lbm_batch_set_graph(lbm_batch_t *b, int on);
+void lbm_batch_destroy(lbm_batch_t *b);
+
 /* ---- instrumentation -------------------------------------------------- */
 
 /* Stage timing with CUDA events recorded on the handle's stream around the

@@ -82,6 +82,11 @@ _SIGS = {
     "lbm_write_populations": (_i, [_p, _p]),
     "lbm_read_deviations": (_i, [_p, _p]),
     "lbm_read_residuals": (_i, [_p, _p, _i]),
+    "lbm_set_graph": (_i, [_p, _i]),
+    "lbm_batch_create": (_i, [_i, _p, _p]),
+    "lbm_batch_step": (_i, [_p, _i, _i]),
+    "lbm_batch_set_graph": (_i, [_p, _i]),
+    "lbm_batch_destroy": (None, [_p]),
     "lbm_velocity_set": (None, [_p, _p]),
     "lbm_enable_timing": (_i, [_p, _i]),
     "lbm_num_stages": (_i, []),
@@ -316,6 +321,10 @@ class Lattice:
             assert P.size == MLP_NPARAM
             self._c(load().mlp_set_weights(self.h, _ptr(P)))
 
+    def set_graph(self, on=True):
+        """Replay captured pairs of steps (fixed iteration counts)."""
+        self._c(load().lbm_set_graph(self.h, int(on)))
+
     def set_features(self, on=True):
         self._c(load().lbm_set_features(self.h, int(on)))
 
@@ -397,3 +406,35 @@ def mlp_adam_dev(P, m, v, grad, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
     _check(load().mlp_adam_dev(_ptr(P), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr),
                                float(beta1), float(beta2), float(eps), _ptr(packed),
                                _raw(stream)))
+
+
+class Batch:
+    """Several lattices advanced together, one launch per stage."""
+
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        arr = (_p * len(self.lattices))(*[l.h for l in self.lattices])
+        self._arr = arr
+        b = _p()
+        _check(load().lbm_batch_create(len(self.lattices), arr, _c.byref(b)))
+        self.b = b
+
+    def step(self, n_steps=1, n_ibm_iter=5):
+        code = load().lbm_batch_step(self.b, int(n_steps), int(n_ibm_iter))
+        if code < 0:
+            _check(code, self.lattices[0].h)
+        return code
+
+    def set_graph(self, on=True):
+        _check(load().lbm_batch_set_graph(self.b, int(on)))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

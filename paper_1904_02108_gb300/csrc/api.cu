@@ -75,7 +75,7 @@ struct lbm {
   int64_t t = 0;
 
   // statistics
-  double *partial = nullptr, *red_scratch = nullptr, *sums = nullptr;
+  double *partial = nullptr, *sums = nullptr, *red_scratch = nullptr;
   unsigned *ticket = nullptr;
   int nparts = 0;
   bool sums_valid = false;
@@ -84,6 +84,22 @@ struct lbm {
   int64_t not_converged = 0;
   IbmState *state = nullptr;       // device
   IbmState *state_host = nullptr;  // pinned mirror of the header fields
+
+  // device descriptor of this lattice (a batch of one) and the step counter
+  DomainDesc *desc = nullptr;
+  DomainDesc desc_host{};
+  int64_t *t_dev = nullptr;
+  bool desc_dirty = true;
+  uint64_t version = 1;  // changes whenever a pointer in the descriptor does
+
+  // captured steps (fixed iteration count)
+  bool graph_on = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_iters = -1, g_cur = -1;
+  uint64_t g_version = 0;
+  int64_t g_launches = 0;
 
   // learned warm start
   bool features_on = false;
@@ -277,12 +293,18 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->m.brick_slot);
   dfree(h->m.counters);
   dfree(h->partial);
-  dfree(h->red_scratch);
   dfree(h->sums);
+  dfree(h->red_scratch);
   dfree(h->ticket);
   dfree(h->tmp);
   dfree(h->state);
   if (h->state_host) cudaFreeHost(h->state_host);
+  dfree(h->desc);
+  dfree(h->t_dev);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   dfree(h->mlp_P);
   if (h->mlp_packed) cudaFree(h->mlp_packed);
   for (auto &p : h->pending) {
@@ -341,10 +363,13 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   if (e == cudaSuccess) e = cudaMemset(h->m.counters, 0, 4 * sizeof(int));
   h->nparts = collide_blocks(h->g);
   if (e == cudaSuccess) e = dalloc(&h->partial, (size_t)h->nparts * 4);
-  if (e == cudaSuccess) e = dalloc(&h->red_scratch, 128 * 4);
   if (e == cudaSuccess) e = dalloc(&h->sums, 4);
+  if (e == cudaSuccess) e = dalloc(&h->red_scratch, 128 * 4);
   if (e == cudaSuccess) e = dalloc(&h->ticket, 1);
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = dalloc(&h->desc, 1);
+  if (e == cudaSuccess) e = dalloc(&h->t_dev, 1);
+  if (e == cudaSuccess) e = cudaMemset(h->t_dev, 0, sizeof(int64_t));
   if (e == cudaSuccess) e = dalloc(&h->state, 1);
   if (e == cudaSuccess) e = cudaMemset(h->state, 0, sizeof(IbmState));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->state_host, sizeof(IbmState));
@@ -381,7 +406,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
   if (!h) return LBM_EINVAL;
   if (n < 0) return fail(h, LBM_EINVAL, "n = %lld < 0", (long long)n);
   if (n > 0 && !X) return fail(h, LBM_EINVAL, "X is NULL");
-  if (n > (1LL << 30)) return fail(h, LBM_EINVAL, "too many points");
+  if (n > (1LL << 28)) return fail(h, LBM_EINVAL, "too many points");
   if (n > 0) {
     if (!all_finite(X, 3 * n)) return fail(h, LBM_ENONFINITE, "non-finite position");
     if (U_target && !all_finite(U_target, 3 * n))
@@ -431,6 +456,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
   h->np = n;
   h->max_body = maxb;
   h->have_du = false;
+  h->desc_dirty = true;
   if (n > 0) {
     CK(h, cudaMemcpy(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
     std::vector<float> a(n, 1.0f);
@@ -468,6 +494,7 @@ int ibm_set_bodies(lbm_t *h, int nb, const double *centre, const double *omega,
   dfree(h->phase);
   dfree(h->trig);
   h->nb = nb;
+  h->desc_dirty = true;
   if (nb > 0) {
     CK(h, dalloc(&h->trig, 4 * nb));
     CK(h, dalloc(&h->centre, 3 * nb));
@@ -487,56 +514,197 @@ int lbm_set_body_force(lbm_t *h, double gx, double gy, double gz) {
   h->gbody[0] = gx;
   h->gbody[1] = gy;
   h->gbody[2] = gz;
+  h->desc_dirty = true;
   return LBM_OK;
 }
 
 int64_t lbm_time(const lbm_t *h) { return h ? h->t : -1; }
 int lbm_set_time(lbm_t *h, int64_t t) {
   if (!h) return LBM_EINVAL;
+  CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
+  CK(h, cudaMemcpy(h->t_dev, &t, sizeof t, cudaMemcpyHostToDevice));
   h->t = t;
   return LBM_OK;
 }
 
-// The multi-direct-forcing fixed point of Sec. 3 after brick_init: n_iter > 0
-// iterations, or (n_iter == 0) iterations until eps <= ibm_tol or ibm_max_iter,
-// with the stop decided on the device and checked by the host every
-// kCheckChunk iterations.  Returns LBM_WNOTCONVERGED when the cap was hit.
-static int ibm_fixed_point(lbm_t *h, int n_iter, bool warm) {
-  cudaStream_t st = h->st;
-  if (n_iter > 0) {
-    const IbmLoop none{nullptr};
-    for (int it = 0; it < n_iter; it++) {
-      {
-        StageTimer T(h, ST_UPDATE);
-        CK(h, launch_point_update(h->np, h->pp, h->pm, h->du, h->uint, it == 0, warm, none, st));
-      }
-      {
-        StageTimer T(h, ST_SPREAD);
-        CK(h, launch_brick_spread(h->m, h->pm, h->du, h->U0s, h->Gs, nullptr, it + 1 < n_iter,
-                                  none, st));
-      }
-    }
-    h->last_iters = n_iter;
-    h->last_eps = -1.0;
-    return LBM_OK;
+// ---- one time step --------------------------------------------------------
+
+// The descriptor of h (pointers of its arrays and per-domain parameters).
+static DomainDesc host_desc(const lbm_t *h) {
+  DomainDesc d{};
+  d.g = h->g;
+  d.delta = h->delta;
+  d.np = (int)h->np;
+  d.tau = (float)h->tau;
+  for (int c = 0; c < 3; c++) d.gbody[c] = (float)h->gbody[c];
+  d.f[0] = h->f[0];
+  d.f[1] = h->f[1];
+  d.t = h->t_dev;
+  d.X = h->X;
+  d.body = h->body;
+  d.area = h->area;
+  d.utarget = h->utarget;
+  d.centre = h->centre;
+  d.omega = h->omega;
+  d.phase = h->phase;
+  d.trig = h->trig;
+  d.nb = h->nb;
+  d.cblocks = h->nparts;
+  d.pp = h->pp;
+  d.m = h->m;
+  d.pm = h->pm;
+  d.U0s = h->U0s;
+  d.Gs = h->Gs;
+  d.res = h->res;
+  d.du = h->du;
+  d.uint = h->uint;
+  d.xpos = h->xpos;
+  d.partial = h->partial;
+  d.sums = h->sums;
+  d.red_scratch = h->red_scratch;
+  d.ticket = h->ticket;
+  d.state = h->state;
+  d.feat = h->feat;
+  d.mlp_packed = h->mlp_packed;
+  return d;
+}
+
+static int sync_desc(lbm_t *h) {
+  if (!h->desc_dirty) return LBM_OK;
+  const DomainDesc d = host_desc(h);
+  CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
+  CK(h, cudaMemcpy(h->desc, &d, sizeof d, cudaMemcpyHostToDevice));
+  h->desc_host = d;
+  h->desc_dirty = false;
+  h->version++;
+  return LBM_OK;
+}
+
+static BatchDims dims_of(const lbm_t *h) {
+  BatchDims b{};
+  b.nd = 1;
+  b.max_cells = h->g.ncell;
+  b.max_points = (int)h->np;
+  b.max_bodies = h->nb;
+  b.max_bricks = h->g.nbrick;
+  b.max_slots = h->np > 0 ? h->m.max_slots : 0;
+  return b;
+}
+
+// What one step launches, for one lattice or a batch (uniform host-side
+// decisions; per-domain differences live in the descriptors).
+struct StepCtx {
+  lbm_t *acct;          // launch counting, timing, errors
+  const DomainDesc *D;  // device descriptors
+  const DomainDesc *Dhost;  // host copy for a single lattice, else NULL
+  BatchDims dims;
+  int storage, stats, cur;
+  int warm_mode;
+  bool have_du, features;
+  cudaStream_t st;
+};
+
+// Kinematics, pairs, moments, learned start / features, and the first
+// brick pass.  Returns the warm flag of the fixed point.
+static int enqueue_prefix(StepCtx &c, bool *warm_out) {
+  lbm_t *h = c.acct;
+  const bool mlp = c.warm_mode == LBM_WARM_MLP;
+  const bool feat = mlp || c.features;
+  const bool warm = (c.warm_mode == LBM_WARM_PREVIOUS && c.have_du) || mlp;
+  *warm_out = warm;
+  {
+    StageTimer T(h, ST_KIN, c.dims.max_bodies > 0 ? 2 : 1);
+    CK(h, launch_prepare_points(c.D, c.dims, c.st));
   }
-  const IbmLoop loop{h->state};
+  {
+    StageTimer T(h, ST_PAIRS, 5);
+    CK(h, launch_build_pairs(c.D, c.dims, c.st));
+  }
+  {
+    StageTimer T(h, ST_INIT, 1);
+    CK(h, launch_brick_moments(c.storage, c.D, c.dims, c.cur, c.st));
+  }
+  if (feat) {
+    // features from the shares of I[U0 + S[du_prev]] (the previous step's
+    // force applied); the learned start du = du_prev + V MLP(x)
+    StageTimer T(h, ST_MLP, mlp ? 3 : 2);
+    CK(h, launch_brick_init(c.D, c.dims, c.have_du, c.st));
+    CK(h, launch_mlp_features(c.D, c.dims, c.have_du, c.st));
+    if (mlp) CK(h, launch_mlp_warm(c.D, c.dims, c.have_du, c.st));
+  }
+  // G_0 = S[du_init] and the shares of I[U0 + G_0], unless the feature pass
+  // above already left exactly these
+  const bool init_done = feat && !mlp && (warm == c.have_du);
+  if (!init_done) {
+    StageTimer T(h, ST_INIT, 1);
+    CK(h, launch_brick_init(c.D, c.dims, warm, c.st));
+  }
+  return LBM_OK;
+}
+
+static int enqueue_fixed_loop(StepCtx &c, int n_iter, bool warm) {
+  lbm_t *h = c.acct;
+  for (int it = 0; it < n_iter; it++) {
+    {
+      StageTimer T(h, ST_UPDATE);
+      CK(h, launch_point_update(c.D, c.dims, it == 0, warm, 0, c.st));
+    }
+    {
+      StageTimer T(h, ST_SPREAD);
+      CK(h, launch_brick_spread(c.D, c.dims, it + 1 < n_iter, 0, c.st));
+    }
+  }
+  return LBM_OK;
+}
+
+static int enqueue_suffix(StepCtx &c) {
+  lbm_t *h = c.acct;
+  {
+    StageTimer T(h, ST_COLLIDE);
+    CK(h, launch_collide_stream(c.storage, c.D, c.Dhost, c.dims, c.cur, c.stats, c.st));
+  }
+  {
+    StageTimer T(h, ST_STATS);
+    CK(h, launch_finish_step(c.D, c.dims, c.stats, c.st));
+  }
+  return LBM_OK;
+}
+
+// One full step with a fixed iteration count (n_iter > 0, or no points).
+static int enqueue_step(StepCtx &c, int n_iter) {
+  if (c.dims.max_points > 0) {
+    bool warm = false;
+    int r = enqueue_prefix(c, &warm);
+    if (r) return r;
+    r = enqueue_fixed_loop(c, n_iter, warm);
+    if (r) return r;
+  }
+  return enqueue_suffix(c);
+}
+
+// The tolerance-driven fixed point of Sec. 3 for one lattice: iterations
+// until eps <= ibm_tol or ibm_max_iter, the stop decided on the device and
+// read by the host every kCheckChunk iterations.  Returns LBM_WNOTCONVERGED
+// when the cap was hit.
+static int tolerance_loop(StepCtx &c, bool warm) {
+  lbm_t *h = c.acct;
+  cudaStream_t st = c.st;
   {
     // denominator ||S[s u_k]||^2
     StageTimer T(h, ST_RESID, 2);
-    CK(h, launch_brick_norm(h->m, h->pm, h->pp.ut, 1, h->res, st));
-    CK(h, launch_ibm_den(h->m, h->res, h->state, 0, st));
+    CK(h, launch_brick_norm(c.D, c.dims, 0, st));
+    CK(h, launch_ibm_den(c.D, c.dims, 0, st));
   }
   CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
   CK(h, cudaStreamSynchronize(st));
   if (h->state_host->den2 == 0.0) {
     // all surface velocities vanish: ||S[s (u_k - I[U0])]||^2 instead
     StageTimer T(h, ST_RESID, warm ? 5 : 3);
-    if (warm) CK(h, launch_brick_init(h->m, h->pm, nullptr, h->U0s, h->Gs, st));
-    CK(h, launch_point_residual0(h->np, h->pp, h->pm, h->uint, st));
-    CK(h, launch_brick_norm(h->m, h->pm, h->uint, 0, h->res, st));
-    CK(h, launch_ibm_den(h->m, h->res, h->state, 1, st));
-    if (warm) CK(h, launch_brick_init(h->m, h->pm, h->du, h->U0s, h->Gs, st));
+    if (warm) CK(h, launch_brick_init(c.D, c.dims, 0, st));
+    CK(h, launch_point_residual0(c.D, c.dims, st));
+    CK(h, launch_brick_norm(c.D, c.dims, 1, st));
+    CK(h, launch_ibm_den(c.D, c.dims, 1, st));
+    if (warm) CK(h, launch_brick_init(c.D, c.dims, 1, st));
   }
   int it = 0;
   while (it < h->max_iter) {
@@ -544,15 +712,15 @@ static int ibm_fixed_point(lbm_t *h, int n_iter, bool warm) {
     for (int j = 0; j < chunk; j++, it++) {
       {
         StageTimer T(h, ST_UPDATE);
-        CK(h, launch_point_update(h->np, h->pp, h->pm, h->du, h->uint, it == 0, warm, loop, st));
+        CK(h, launch_point_update(c.D, c.dims, it == 0, warm, 1, st));
       }
       {
         StageTimer T(h, ST_SPREAD);
-        CK(h, launch_brick_spread(h->m, h->pm, h->du, h->U0s, h->Gs, h->res, 1, loop, st));
+        CK(h, launch_brick_spread(c.D, c.dims, 1, 1, st));
       }
       {
         StageTimer T(h, ST_RESID);
-        CK(h, launch_ibm_check(h->m, h->res, h->state, it, h->tol, h->max_iter, st));
+        CK(h, launch_ibm_check(c.D, c.dims, it, h->tol, h->max_iter, st));
       }
     }
     CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
@@ -568,78 +736,123 @@ static int ibm_fixed_point(lbm_t *h, int n_iter, bool warm) {
   return LBM_OK;
 }
 
-static int step_once(lbm_t *h, int n_iter) {
-  cudaStream_t st = h->st;
-  const bool ibm = h->np > 0;
-  int warn = LBM_OK;
-  if (ibm) {
-    PointsIn p{h->np, h->X, h->body, h->area, h->utarget};
-    Bodies b{h->centre, h->omega, h->phase, h->nb, h->trig};
-    {
-      StageTimer T(h, ST_KIN, h->nb > 0 ? 2 : 1);
-      CK(h, launch_prepare_points(h->g, h->delta, p, b, h->t, h->pp, h->m, h->pm, h->xpos,
-                                  st));
-    }
-    {
-      StageTimer T(h, ST_PAIRS, 5);
-      CK(h, launch_build_pairs(h->g, h->np, h->pp, h->m, h->pm, st));
-    }
-    const bool mlp = h->warm == LBM_WARM_MLP;
-    const bool feat = mlp || h->features_on;
-    const bool warm = (h->warm == LBM_WARM_PREVIOUS && h->have_du) || mlp;
-    {
-      StageTimer T(h, ST_INIT, 1);
-      CK(h, launch_brick_moments(h->storage, h->g, h->f[h->cur], h->m, h->U0s, st));
-    }
-    if (feat) {
-      // features from the shares of I[U0 + S[du_prev]] (the previous step's
-      // force applied); the learned start du = du_prev + V MLP(x)
-      StageTimer T(h, ST_MLP, mlp ? 3 : 2);
-      if (mlp && !h->have_du) CK(h, cudaMemsetAsync(h->du, 0, sizeof(float4) * h->np, st));
-      CK(h, launch_brick_init(h->m, h->pm, h->have_du ? h->du : nullptr, h->U0s, h->Gs, st));
-      CK(h, launch_mlp_features(h->g, h->np, h->pp, h->pm, h->m, h->have_du ? h->du : nullptr, p,
-                                b, h->feat, st));
-      if (mlp)
-        CK(h, launch_mlp_forward(h->np, h->feat, h->mlp_packed, nullptr, h->du, MLP_VSCALE, 1,
-                                 st));
-    }
-    // G_0 = S[du_init] and the shares of I[U0 + G_0], unless the feature pass
-    // above already left exactly these
-    const bool init_done = feat && !mlp && (warm == h->have_du);
-    if (!init_done) {
-      StageTimer T(h, ST_INIT, 1);
-      CK(h, launch_brick_init(h->m, h->pm, warm ? h->du : nullptr, h->U0s, h->Gs, st));
-    }
-    warn = ibm_fixed_point(h, n_iter, warm);
-    if (warn < 0) return warn;
+static StepCtx ctx_of(lbm_t *h, cudaStream_t st) {
+  StepCtx c{};
+  c.acct = h;
+  c.D = h->desc;
+  c.Dhost = &h->desc_host;
+  c.dims = dims_of(h);
+  c.storage = h->storage;
+  c.stats = h->stats_on;
+  c.cur = h->cur;
+  c.warm_mode = h->warm;
+  c.have_du = h->have_du;
+  c.features = h->features_on;
+  c.st = st;
+  return c;
+}
+
+// host-side bookkeeping after a step was enqueued
+static void after_step(lbm_t *h, int n_iter) {
+  if (h->np > 0) {
     h->have_du = true;
+    if (n_iter > 0) {
+      h->last_iters = n_iter;
+      h->last_eps = -1.0;
+    }
   } else {
     h->last_iters = 0;
     h->last_eps = -1.0;
   }
-  {
-    StageTimer T(h, ST_COLLIDE);
-    CollideArgs a{};
-    a.src = h->f[h->cur];
-    a.dst = h->f[h->cur ^ 1];
-    a.brick_slot = ibm ? h->m.brick_slot : nullptr;
-    a.Gs = h->Gs;
-    a.gbody[0] = (float)h->gbody[0];
-    a.gbody[1] = (float)h->gbody[1];
-    a.gbody[2] = (float)h->gbody[2];
-    a.tau = (float)h->tau;
-    a.partial = h->stats_on ? h->partial : nullptr;
-    CK(h, launch_collide_stream(h->storage, h->g, a, st));
-  }
-  if (h->stats_on) {
-    StageTimer T(h, ST_STATS);
-    CK(h, launch_stats_reduce(h->partial, h->nparts, h->red_scratch, h->ticket, h->sums,
-                              (double)h->g.ncell, st));
-    h->sums_valid = true;
-  }
+  if (h->stats_on) h->sums_valid = true;
   h->cur ^= 1;
   h->t++;
+}
+
+static int step_once(lbm_t *h, int n_iter) {
+  StepCtx c = ctx_of(h, h->st);
+  int warn = LBM_OK;
+  if (h->np > 0 && n_iter == 0) {
+    bool warm = false;
+    int r = enqueue_prefix(c, &warm);
+    if (r) return r;
+    warn = tolerance_loop(c, warm);
+    if (warn < 0) return warn;
+    r = enqueue_suffix(c);
+    if (r) return r;
+  } else {
+    int r = enqueue_step(c, n_iter);
+    if (r) return r;
+  }
+  after_step(h, n_iter);
   return warn;
+}
+
+// ---- captured steps ------------------------------------------------------------
+//
+// Two consecutive steps (the lattices swap each step, so two steps bring the
+// pointers back) are captured once into a CUDA graph and replayed; the step
+// counter and every other changing quantity live on the device.  Captured on a
+// private stream ordered after and before the handle's stream with events.
+
+struct GraphSlot {
+  cudaStream_t *cap_stream;
+  cudaEvent_t *ev_in, *ev_out;
+  cudaGraphExec_t *exec;
+};
+
+static int ensure_capture_stream(lbm_t *acct, cudaStream_t *cs, cudaEvent_t *a, cudaEvent_t *b) {
+  if (!*cs) CK(acct, cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking));
+  if (!*a) CK(acct, cudaEventCreateWithFlags(a, cudaEventDisableTiming));
+  if (!*b) CK(acct, cudaEventCreateWithFlags(b, cudaEventDisableTiming));
+  return LBM_OK;
+}
+
+// Captures two steps of `c` (c.st is replaced by the capture stream) into
+// *exec; *launches receives the kernels per replay.
+static int capture_two_steps(StepCtx c, int n_iter, cudaStream_t cs, cudaGraphExec_t *exec,
+                             int64_t *launches) {
+  lbm_t *h = c.acct;
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  const int saved_timing = h->timing;
+  const int64_t l0 = h->nlaunch;
+  h->timing = 0;
+  c.st = cs;
+  CK(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int r = enqueue_step(c, n_iter);
+  if (r == LBM_OK) {
+    c.cur ^= 1;
+    c.have_du = c.have_du || c.dims.max_points > 0;
+    r = enqueue_step(c, n_iter);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  h->timing = saved_timing;
+  *launches = h->nlaunch - l0;
+  h->nlaunch = l0;
+  if (r != LBM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (e != cudaSuccess) return fail(h, LBM_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return fail(h, LBM_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+static int replay(lbm_t *acct, cudaStream_t user, cudaStream_t cs, cudaEvent_t a, cudaEvent_t b,
+                  cudaGraphExec_t exec) {
+  CK(acct, cudaEventRecord(a, user));
+  CK(acct, cudaStreamWaitEvent(cs, a, 0));
+  CK(acct, cudaGraphLaunch(exec, cs));
+  CK(acct, cudaEventRecord(b, cs));
+  CK(acct, cudaStreamWaitEvent(user, b, 0));
+  return LBM_OK;
 }
 
 int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
@@ -650,14 +863,191 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
     return fail(h, LBM_EINVAL, "points refer to body %d, only %d bodies", h->max_body, h->nb);
   if (h->warm == LBM_WARM_MLP && !h->mlp_packed && h->np > 0)
     return fail(h, LBM_EINVAL, "learned warm start without weights (mlp_set_weights)");
+  int r = sync_desc(h);
+  if (r) return r;
   int warn = LBM_OK;
-  for (int s = 0; s < n_steps; s++) {
-    int r = step_once(h, n_ibm_iter);
+  int s = 0;
+  const bool graphable = h->graph_on && (n_ibm_iter > 0 || h->np == 0);
+  while (s < n_steps) {
+    // replay captured pairs of steps once the host-side decisions are steady
+    const bool steady = h->have_du || h->np == 0;
+    if (graphable && steady && n_steps - s >= 2) {
+      if (!h->gexec || h->g_iters != n_ibm_iter || h->g_cur != h->cur ||
+          h->g_version != h->version) {
+        r = ensure_capture_stream(h, &h->cap_stream, &h->ev_in, &h->ev_out);
+        if (r) return r;
+        r = capture_two_steps(ctx_of(h, h->st), n_ibm_iter, h->cap_stream, &h->gexec,
+                              &h->g_launches);
+        if (r) return r;
+        h->g_iters = n_ibm_iter;
+        h->g_cur = h->cur;
+        h->g_version = h->version;
+      }
+      r = replay(h, h->st, h->cap_stream, h->ev_in, h->ev_out, h->gexec);
+      if (r) return r;
+      h->nlaunch += h->g_launches;
+      after_step(h, n_ibm_iter);
+      after_step(h, n_ibm_iter);
+      s += 2;
+      continue;
+    }
+    r = step_once(h, n_ibm_iter);
     if (r < 0) return r;
     if (r == LBM_WNOTCONVERGED) warn = r;
+    s++;
   }
   return warn;
 }
+
+int lbm_set_graph(lbm_t *h, int on) {
+  if (!h) return LBM_EINVAL;
+  h->graph_on = on != 0;
+  return LBM_OK;
+}
+
+// ---- batches ----------------------------------------------------------------------
+
+struct lbm_batch {
+  std::vector<lbm_t *> hs;
+  DomainDesc *D = nullptr;
+  uint64_t built_for = 0;  // sum of the handles' versions at the last build
+  bool graph_on = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_iters = -1, g_cur = -1;
+  uint64_t g_version = 0;
+  int64_t g_launches = 0;
+  std::string err;
+};
+
+extern "C" {
+
+int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || !handles) return fail(nullptr, LBM_EINVAL, "empty batch");
+  if (n > 65535) return fail(nullptr, LBM_EINVAL, "too many domains");
+  for (int i = 0; i < n; i++) {
+    if (!handles[i]) return fail(nullptr, LBM_EINVAL, "NULL handle %d", i);
+    for (int j = 0; j < i; j++)
+      if (handles[j] == handles[i]) return fail(nullptr, LBM_EINVAL, "handle %d twice", i);
+    if (handles[i]->storage != handles[0]->storage)
+      return fail(nullptr, LBM_EINVAL, "storage of handle %d differs", i);
+  }
+  lbm_batch_t *b = new lbm_batch();
+  b->hs.assign(handles, handles + n);
+  if (cudaMalloc(&b->D, sizeof(DomainDesc) * n) != cudaSuccess) {
+    delete b;
+    return fail(nullptr, LBM_ENOMEM, "batch descriptors");
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch_t *b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->D) cudaFree(b->D);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  delete b;
+}
+
+int lbm_batch_set_graph(lbm_batch_t *b, int on) {
+  if (!b) return LBM_EINVAL;
+  b->graph_on = on != 0;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
+  if (!b) return LBM_EINVAL;
+  lbm_t *h0 = b->hs[0];
+  if (n_steps < 0 || n_ibm_iter <= 0)
+    return fail(h0, LBM_EINVAL, "batch steps need n_steps >= 0 and n_ibm_iter > 0");
+  // uniform host-side decisions
+  for (lbm_t *h : b->hs) {
+    if (h->stats_on != h0->stats_on || h->warm != h0->warm ||
+        h->features_on != h0->features_on || h->cur != h0->cur || h->st != h0->st)
+      return fail(h0, LBM_EINVAL, "batch handles differ in stats, warm start, features, stream "
+                                  "or lattice parity");
+    if ((h->np > 0 && h->have_du) != (h0->np > 0 && h0->have_du) && h->np > 0 && h0->np > 0)
+      return fail(h0, LBM_EINVAL, "batch handles differ in warm-start history");
+    if (h->nb > 0 && h->max_body >= h->nb)
+      return fail(h0, LBM_EINVAL, "points refer to a missing body");
+    if (h->warm == LBM_WARM_MLP && !h->mlp_packed && h->np > 0)
+      return fail(h0, LBM_EINVAL, "learned warm start without weights");
+    int r = sync_desc(h);
+    if (r) return r;
+  }
+  uint64_t ver = 0;
+  BatchDims dims{};
+  dims.nd = (int)b->hs.size();
+  bool have_du = false;
+  for (lbm_t *h : b->hs) {
+    ver = ver * 1000003u + h->version;
+    dims.max_cells = std::max<int64_t>(dims.max_cells, h->g.ncell);
+    dims.max_points = std::max<int>(dims.max_points, (int)h->np);
+    dims.max_bodies = std::max(dims.max_bodies, h->nb);
+    dims.max_bricks = std::max(dims.max_bricks, h->g.nbrick);
+    if (h->np > 0) {
+      dims.max_slots = std::max(dims.max_slots, h->m.max_slots);
+      have_du = h->have_du;
+    }
+  }
+  if (ver != b->built_for) {
+    std::vector<DomainDesc> hd;
+    for (lbm_t *h : b->hs) hd.push_back(host_desc(h));
+    CK(h0, cudaMemcpy(b->D, hd.data(), sizeof(DomainDesc) * hd.size(), cudaMemcpyHostToDevice));
+    b->built_for = ver;
+  }
+  StepCtx c{};
+  c.acct = h0;
+  c.D = b->D;
+  c.dims = dims;
+  c.storage = h0->storage;
+  c.stats = h0->stats_on;
+  c.warm_mode = h0->warm;
+  c.have_du = have_du;
+  c.features = h0->features_on;
+  int s = 0;
+  while (s < n_steps) {
+    c.cur = h0->cur;
+    const bool steady = have_du || dims.max_points == 0;
+    if (b->graph_on && steady && n_steps - s >= 2) {
+      if (!b->gexec || b->g_iters != n_ibm_iter || b->g_cur != c.cur || b->g_version != ver) {
+        int r = ensure_capture_stream(h0, &b->cap_stream, &b->ev_in, &b->ev_out);
+        if (r) return r;
+        r = capture_two_steps(c, n_ibm_iter, b->cap_stream, &b->gexec, &b->g_launches);
+        if (r) return r;
+        b->g_iters = n_ibm_iter;
+        b->g_cur = c.cur;
+        b->g_version = ver;
+      }
+      int r = replay(h0, h0->st, b->cap_stream, b->ev_in, b->ev_out, b->gexec);
+      if (r) return r;
+      h0->nlaunch += b->g_launches;
+      for (lbm_t *h : b->hs) {
+        after_step(h, n_ibm_iter);
+        after_step(h, n_ibm_iter);
+      }
+      s += 2;
+      continue;
+    }
+    c.st = h0->st;
+    int r = enqueue_step(c, n_ibm_iter);
+    if (r) return r;
+    for (lbm_t *h : b->hs) after_step(h, n_ibm_iter);
+    have_du = have_du || dims.max_points > 0;
+    c.have_du = have_du;
+    s++;
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"
 
 int lbm_read_fields_dev(lbm_t *h, float *rho, float *U, float *G) {
   if (!h) return LBM_EINVAL;
@@ -921,10 +1311,12 @@ int lbm_load_state(lbm_t *h, const void *buf, size_t len) {
   CK(h, cudaMemcpy(h->f[h->cur], p, pop, cudaMemcpyHostToDevice));
   if (np) CK(h, cudaMemcpy(h->du, du, 16 * np, cudaMemcpyHostToDevice));
   h->have_du = hd.have_du != 0;
+  CK(h, cudaMemcpy(h->t_dev, &hd.t, sizeof hd.t, cudaMemcpyHostToDevice));
   h->t = hd.t;
   h->delta = hd.delta;
   h->warm = hd.warm;
   h->tau = hd.tau;
+  h->desc_dirty = true;
   memcpy(h->gbody, hd.gbody, sizeof hd.gbody);
   return LBM_OK;
 }
@@ -951,7 +1343,7 @@ int ibm_interpolate_dev(int nx, int ny, int nz, int delta, const float *U, int64
 namespace {
 
 struct SpreadLayout {
-  size_t brick_count, brick_slot, slot_brick, counters, count, start, cursor, pk, pbrick, pw,
+  size_t desc, brick_count, brick_slot, slot_brick, counters, count, start, cursor, pk, pbrick, pw,
       ppart,
       point_pairs, base, wts, ut, vals, Gs, total;
   int max_slots;
@@ -969,6 +1361,7 @@ SpreadLayout spread_layout(const Geometry &g, int64_t n) {
     o = align256(o + bytes);
     return r;
   };
+  L.desc = take(sizeof(DomainDesc));
   L.brick_count = take(sizeof(int) * g.nbrick);
   L.brick_slot = take(sizeof(int) * g.nbrick);
   L.slot_brick = take(sizeof(int) * ms);
@@ -1058,13 +1451,29 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   if (e == cudaSuccess) e = cudaMemsetAsync(m.brick_count, 0, sizeof(int) * g.nbrick, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m.counters, 0, sizeof(int) * 4, st);
   if (n > 0) {
-    PointsIn p{n, x, nullptr, nullptr, nullptr};
-    Bodies b{nullptr, nullptr, nullptr, 0, nullptr};
-    if (e == cudaSuccess) e = launch_prepare_points(g, delta, p, b, 0, pp, m, pm, nullptr, st);
-    if (e == cudaSuccess) e = launch_build_pairs(g, n, pp, m, pm, st);
+    // a batch of one domain whose descriptor lives in the scratch
+    DomainDesc dd{};
+    dd.g = g;
+    dd.delta = delta;
+    dd.np = (int)n;
+    dd.X = x;
+    dd.pp = pp;
+    dd.m = m;
+    dd.pm = pm;
+    dd.du = vals;
+    dd.Gs = Gs;
+    DomainDesc *D = (DomainDesc *)(base + L.desc);
+    BatchDims dims{};
+    dims.nd = 1;
+    dims.max_cells = g.ncell;
+    dims.max_points = (int)n;
+    dims.max_bricks = g.nbrick;
+    dims.max_slots = m.max_slots;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(D, &dd, sizeof dd, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_prepare_points(D, dims, st);
+    if (e == cudaSuccess) e = launch_build_pairs(D, dims, st);
     if (e == cudaSuccess) e = launch_pack_vals(n, v, vals, st);
-    if (e == cudaSuccess)
-      e = launch_brick_spread(m, pm, vals, nullptr, Gs, nullptr, 0, IbmLoop{nullptr}, st);
+    if (e == cudaSuccess) e = launch_brick_spread(D, dims, 0, 0, st);
     if (e == cudaSuccess) e = launch_slots_to_dense(g, m, Gs, F, st);
   }
   if (own) {
@@ -1141,7 +1550,7 @@ int mlp_pack_dev(const float *P, void *packed, void *stream) {
 
 int mlp_forward_dev(int64_t n, const float *X, const void *packed, float *Y, void *stream) {
   if (n < 0 || (n > 0 && (!X || !packed || !Y))) return fail(nullptr, LBM_EINVAL, "bad arguments");
-  cudaError_t e = launch_mlp_forward(n, X, packed, Y, nullptr, 0.f, 0, (cudaStream_t)stream);
+  cudaError_t e = launch_mlp_forward(n, X, packed, Y, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "%s", cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -1180,6 +1589,7 @@ static int set_weights(lbm_t *h, const float *P, cudaMemcpyKind kind) {
   CK(h, cudaMemcpyAsync(h->mlp_P, P, sizeof(float) * MLP_NPARAM, kind, h->st));
   CK(h, launch_mlp_pack(h->mlp_P, h->mlp_packed, h->st));
   CK(h, cudaStreamSynchronize(h->st));
+  h->desc_dirty = true;
   return LBM_OK;
 }
 

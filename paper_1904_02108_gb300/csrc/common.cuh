@@ -155,4 +155,51 @@ struct IbmLoop {
   const IbmState *state;
 };
 
+// Everything a step kernel needs about one domain (lattice, points, force
+// storage).  The step kernels read D[blockIdx.y]: one launch advances every
+// domain of a batch, and a single lattice is a batch of one.  Pointers are
+// fixed between steps (which keeps a captured step replayable); the step
+// counter t lives on the device and is advanced by the last kernel of a step.
+struct DomainDesc {
+  Geometry g;
+  int delta;          // weighting function
+  int np;             // Lagrangian points
+  float tau;
+  float gbody[3];
+  void *f[2];         // the two population lattices
+  int64_t *t;         // device step counter
+  const double *X;    // [np][3] rest or fixed positions
+  const int *body;    // [np]
+  const float *area;  // [np]
+  const float *utarget;  // [np][3]
+  const double *centre, *omega, *phase;
+  double *trig;       // [nb][4]
+  int nb;
+  int cblocks;        // blocks of the collide kernel for this domain, one
+                      // per 256 cells (one FP64 partial each)
+  PointPrep pp;
+  BrickMap m;
+  PairMap pm;
+  float *U0s, *Gs, *res;
+  float4 *du, *uint;
+  double *xpos;
+  double *partial, *sums;  // collide partials [cblocks][4], FP64 sums [4]
+  double *red_scratch;     // [128][4] block sums of the final reduction
+  unsigned *ticket;        // blocks of the final reduction done (reset by
+                           // the last one)
+  IbmState *state;
+  float *feat;
+  const void *mlp_packed;
+};
+
+// Grid extents of a batch: the largest domain along each work dimension.
+struct BatchDims {
+  int nd;              // domains (gridDim.y)
+  int64_t max_cells;
+  int max_points;
+  int max_bodies;
+  int max_bricks;
+  int max_slots;
+};
+
 }  // namespace lbmibm

@@ -117,9 +117,12 @@ __device__ __forceinline__ void for_support_bricks(const Geometry &g, int4 b, Fn
 // differences cos phi(t) - cos phi(t-1), sin phi(t) - sin phi(t-1), the latter
 // without cancellation as -2 sin(phi - omega/2) sin(omega/2) and
 // 2 cos(phi - omega/2) sin(omega/2).
-__global__ void body_trig_kernel(Bodies bd, int64_t t) {
+__global__ void body_trig_kernel(const DomainDesc *__restrict__ D) {
+  const DomainDesc &d = D[blockIdx.y];
+  const Bodies bd{d.centre, d.omega, d.phase, d.nb, d.trig};
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= bd.nb) return;
+  const int64_t t = *d.t;
   const double om = bd.omega[b];
   const double phi = bd.phase[b] + om * (double)t;
   double sn, cs, sh, ch;
@@ -135,8 +138,16 @@ __global__ void body_trig_kernel(Bodies bd, int64_t t) {
 }
 
 __global__ void __launch_bounds__(256)
-    prepare_points_kernel(Geometry g, int delta, PointsIn p, Bodies bd, int64_t t,
-                          PointPrep pp, BrickMap m, PairMap pm, double *__restrict__ xpos) {
+    prepare_points_kernel(const DomainDesc *__restrict__ D) {
+  const DomainDesc &d = D[blockIdx.y];
+  const Geometry g = d.g;
+  const int delta = d.delta;
+  const PointsIn p{d.np, d.X, d.body, d.area, d.utarget};
+  const Bodies bd{d.centre, d.omega, d.phase, d.nb, d.trig};
+  const PointPrep pp = d.pp;
+  const BrickMap m = d.m;
+  const PairMap pm = d.pm;
+  double *__restrict__ xpos = d.xpos;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k == 0) {
     m.counters[0] = 0;
@@ -197,7 +208,11 @@ __global__ void __launch_bounds__(256)
   });
 }
 
-__global__ void compact_kernel(Geometry g, BrickMap m, PairMap pm) {
+__global__ void compact_kernel(const DomainDesc *__restrict__ D) {
+  const DomainDesc &d = D[blockIdx.y];
+  const Geometry g = d.g;
+  const BrickMap m = d.m;
+  const PairMap pm = d.pm;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= g.nbrick) return;
   const int c = m.brick_count[b];
@@ -228,7 +243,10 @@ __device__ __forceinline__ int active_slots(const BrickMap &m) {
 // stores (8 consecutive counts per thread).
 constexpr int SCAN_TILE = 8192;
 
-__global__ void __launch_bounds__(1024) pair_scan_kernel(BrickMap m, PairMap pm) {
+__global__ void __launch_bounds__(1024) pair_scan_kernel(const DomainDesc *__restrict__ D) {
+  if (D[blockIdx.y].np == 0) return;  // no pair storage in a domain without points
+  const BrickMap m = D[blockIdx.y].m;
+  const PairMap pm = D[blockIdx.y].pm;
   __shared__ int tile[SCAN_TILE];
   __shared__ int wsum[32];
   __shared__ int carry;
@@ -278,7 +296,13 @@ __global__ void __launch_bounds__(1024) pair_scan_kernel(BrickMap m, PairMap pm)
   if (threadIdx.x == 0) pm.start[n] = carry;
 }
 
-__global__ void pair_fill_kernel(Geometry g, int64_t np, PointPrep pp, BrickMap m, PairMap pm) {
+__global__ void pair_fill_kernel(const DomainDesc *__restrict__ D) {
+  const DomainDesc &d = D[blockIdx.y];
+  const Geometry g = d.g;
+  const int64_t np = d.np;
+  const PointPrep pp = d.pp;
+  const BrickMap m = d.m;
+  const PairMap pm = d.pm;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= np) return;
   for_support_bricks8(g, pp.base[k], [&](int brick, bool valid) {
@@ -295,8 +319,10 @@ __global__ void pair_fill_kernel(Geometry g, int64_t np, PointPrep pp, BrickMap 
 constexpr int SORT_CAP = 512;
 
 __global__ void __launch_bounds__(128)
-    pair_sort_kernel(Geometry g, PointPrep pp, BrickMap m, PairMap pm) {
+    pair_sort_kernel(const DomainDesc *__restrict__ D) {
   __shared__ int buf[4][SORT_CAP];
+  const BrickMap m = D[blockIdx.y].m;
+  const PairMap pm = D[blockIdx.y].pm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nslots = active_slots(m);
   for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
@@ -352,7 +378,13 @@ __global__ void __launch_bounds__(128)
 // the support, periodic offsets resolved) and the pair's entry in the point's
 // list of bricks.
 __global__ void __launch_bounds__(256)
-    pair_weights_kernel(Geometry g, PointPrep pp, BrickMap m, PairMap pm) {
+    pair_weights_kernel(const DomainDesc *__restrict__ D) {
+  const DomainDesc &d = D[blockIdx.y];
+  if (d.np == 0) return;
+  const Geometry g = d.g;
+  const PointPrep pp = d.pp;
+  const BrickMap m = d.m;
+  const PairMap pm = d.pm;
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= pm.start[active_slots(m)]) return;
   const int k = pm.k[p], B = pm.brick[p];
@@ -527,8 +559,12 @@ __device__ __forceinline__ void store_F(BrickSmem &sm, float fx, float fy, float
 // cell, four bricks per 256-thread block.
 template <typename S>
 __global__ void __launch_bounds__(256)
-    brick_moments_kernel(const S *__restrict__ f, Geometry g, BrickMap m,
-                         float *__restrict__ U0s) {
+    brick_moments_kernel(const DomainDesc *__restrict__ D, int cur) {
+  const DomainDesc &d = D[blockIdx.y];
+  const S *__restrict__ f = (const S *)d.f[cur];
+  const Geometry g = d.g;
+  const BrickMap m = d.m;
+  float *__restrict__ U0s = d.U0s;
   const int nslots = active_slots(m);
   const int t = threadIdx.x & 63;
   for (int s = blockIdx.x * 4 + (threadIdx.x >> 6); s < nslots; s += gridDim.x * 4) {
@@ -552,9 +588,14 @@ __global__ void __launch_bounds__(256)
 // S[du_init] (warm start), and the pairs' shares of I[U0 + G_0] for the first
 // iteration.
 __global__ void __launch_bounds__(64, 16)
-    brick_init_kernel(BrickMap m, PairMap pm, const float4 *__restrict__ du_init,
-                      const float *__restrict__ U0s, float *__restrict__ Gs) {
+    brick_init_kernel(const DomainDesc *__restrict__ D, int use_du) {
   __shared__ BrickSmem sm;
+  const DomainDesc &d = D[blockIdx.y];
+  const BrickMap m = d.m;
+  const PairMap pm = d.pm;
+  const float4 *__restrict__ du_init = use_du ? d.du : nullptr;
+  const float *__restrict__ U0s = d.U0s;
+  float *__restrict__ Gs = d.Gs;
   const int nslots = active_slots(m);
   const int t = threadIdx.x;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
@@ -578,11 +619,16 @@ __global__ void __launch_bounds__(64, 16)
 // gather), the squared change of G into res[slot] (if res), and, unless this
 // is the last iteration, the pairs' shares of I[U0 + G] for the next one.
 __global__ void __launch_bounds__(64, 16)
-    brick_spread_kernel(BrickMap m, PairMap pm, const float4 *__restrict__ vals,
-                        const float *__restrict__ U0s, float *__restrict__ Gs,
-                        float *__restrict__ res, int do_interp, const IbmLoop loop) {
+    brick_spread_kernel(const DomainDesc *__restrict__ D, int do_interp, int tol_mode) {
   __shared__ BrickSmem sm;
-  if (loop.state && loop.state->done) return;
+  const DomainDesc &d = D[blockIdx.y];
+  if (tol_mode && d.state->done) return;
+  const BrickMap m = d.m;
+  const PairMap pm = d.pm;
+  const float4 *__restrict__ vals = d.du;
+  const float *__restrict__ U0s = d.U0s;
+  float *__restrict__ Gs = d.Gs;
+  float *__restrict__ res = tol_mode ? d.res : nullptr;
   const int nslots = active_slots(m);
   const int t = threadIdx.x;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
@@ -613,9 +659,15 @@ __global__ void __launch_bounds__(64, 16)
 // ||S[v]||^2 per active brick into res[slot] (v = vals, scaled by .w when
 // scale_by_w): the denominator ||S[s u_k]|| of the residual.
 __global__ void __launch_bounds__(64, 16)
-    brick_norm_kernel(BrickMap m, PairMap pm, const float4 *__restrict__ vals, int scale_by_w,
-                      float *__restrict__ res) {
+    brick_norm_kernel(const DomainDesc *__restrict__ D, int which) {
   __shared__ BrickSmem sm;
+  const DomainDesc &d = D[blockIdx.y];
+  const BrickMap m = d.m;
+  const PairMap pm = d.pm;
+  // which 0: s(k) u_k (u_k with s(k) in .w); 1: the vectors left in uint
+  const float4 *__restrict__ vals = which == 0 ? d.pp.ut : d.uint;
+  const int scale_by_w = which == 0;
+  float *__restrict__ res = d.res;
   const int nslots = active_slots(m);
   const int t = threadIdx.x;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
@@ -647,9 +699,11 @@ __device__ double block_sum_res(const BrickMap &m, const float *__restrict__ res
 
 // mode 0: den2 = sum res (||S[s u_k]||^2); mode 1: fallback den2 (used when
 // the first is 0): sum res, or 1 if that is 0 as well.
-__global__ void __launch_bounds__(256) ibm_den_kernel(BrickMap m, const float *__restrict__ res,
-                                                       IbmState *st, int mode) {
-  const double v = block_sum_res(m, res);
+__global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restrict__ D,
+                                                       int mode) {
+  const DomainDesc &d = D[blockIdx.y];
+  IbmState *st = d.state;
+  const double v = block_sum_res(d.m, d.res);
   if (threadIdx.x == 0) {
     if (mode == 0) {
       st->den2 = v;
@@ -663,11 +717,12 @@ __global__ void __launch_bounds__(256) ibm_den_kernel(BrickMap m, const float *_
 
 // After iteration `it`: eps = ||G_{it+1} - G_it|| / den (Eulerian residual of
 // the fixed point); stop at the first eps <= tol or at max_iter iterations.
-__global__ void __launch_bounds__(256) ibm_check_kernel(BrickMap m, const float *__restrict__ res,
-                                                         IbmState *st, int it, double tol,
-                                                         int max_iter) {
+__global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__restrict__ D, int it,
+                                                         double tol, int max_iter) {
+  const DomainDesc &d = D[blockIdx.y];
+  IbmState *st = d.state;
   if (st->done) return;
-  const double v = block_sum_res(m, res);
+  const double v = block_sum_res(d.m, d.res);
   if (threadIdx.x == 0) {
     const double eps = sqrt(v / st->den2);
     if (it < IbmState::HIST) st->eps[it] = eps;
@@ -683,11 +738,15 @@ __global__ void __launch_bounds__(256) ibm_check_kernel(BrickMap m, const float 
 // Alg. 1 loop body per point: u_n(k) = sum of its bricks' shares (brick order),
 // g = u_k - u_n, du += s g (du starts at 0 when first && !warm).
 __global__ void __launch_bounds__(256)
-    point_update_kernel(int64_t np, PointPrep pp, PairMap pm, float4 *__restrict__ du,
-                        float4 *__restrict__ uint, int first, int warm, const IbmLoop loop) {
+    point_update_kernel(const DomainDesc *__restrict__ D, int first, int warm, int tol_mode) {
+  const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= np) return;
-  if (loop.state && loop.state->done) return;
+  if (k >= d.np) return;
+  if (tol_mode && d.state->done) return;
+  const PointPrep pp = d.pp;
+  const PairMap pm = d.pm;
+  float4 *__restrict__ du = d.du;
+  float4 *__restrict__ uint = d.uint;
   const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
   const int4 a = pk[0], b = pk[1];
   const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -702,20 +761,24 @@ __global__ void __launch_bounds__(256)
     }
   }
   const float4 ut = pp.ut[k];
-  float4 d = (first && !warm) ? make_float4(0.f, 0.f, 0.f, 0.f) : du[k];
-  d.x += ut.w * (ut.x - ux);
-  d.y += ut.w * (ut.y - uy);
-  d.z += ut.w * (ut.z - uz);
-  du[k] = d;
+  float4 dk = (first && !warm) ? make_float4(0.f, 0.f, 0.f, 0.f) : du[k];
+  dk.x += ut.w * (ut.x - ux);
+  dk.y += ut.w * (ut.y - uy);
+  dk.z += ut.w * (ut.z - uz);
+  du[k] = dk;
   uint[k] = make_float4(ux, uy, uz, 0.f);
 }
 
 // s(k) (u_k - u(k)) with u(k) the sum of the point's pair shares: the
 // first increment from a zero start, for the fallback residual denominator.
 __global__ void __launch_bounds__(256)
-    point_residual0_kernel(int64_t np, PointPrep pp, PairMap pm, float4 *__restrict__ out) {
+    point_residual0_kernel(const DomainDesc *__restrict__ D) {
+  const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= np) return;
+  if (k >= d.np) return;
+  const PointPrep pp = d.pp;
+  const PairMap pm = d.pm;
+  float4 *__restrict__ out = d.uint;
   const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
   const int4 a = pk[0], b = pk[1];
   const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -745,11 +808,17 @@ __global__ void __launch_bounds__(256)
 //        body's axis, and the speed omega r (0 without bodies)
 //   13-15 u_k - u_i, the slip left by the previous force
 __global__ void __launch_bounds__(256)
-    mlp_features_kernel(int64_t np, PointPrep pp, PairMap pm, BrickMap m,
-                        const float4 *__restrict__ du_prev, PointsIn p, Bodies bd,
-                        float *__restrict__ X) {
+    mlp_features_kernel(const DomainDesc *__restrict__ D, int use_prev) {
+  const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= np) return;
+  if (k >= d.np) return;
+  const PointPrep pp = d.pp;
+  const PairMap pm = d.pm;
+  const BrickMap m = d.m;
+  const float4 *__restrict__ du_prev = use_prev ? d.du : nullptr;
+  const PointsIn p{d.np, d.X, d.body, d.area, d.utarget};
+  const Bodies bd{d.centre, d.omega, d.phase, d.nb, d.trig};
+  float *__restrict__ X = d.feat;
   const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
   const int4 a = pk[0], b = pk[1];
   const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -877,35 +946,39 @@ __global__ void slots_to_dense_kernel(Geometry g, BrickMap m, const float *__res
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+inline unsigned xblocks(int64_t want, int nd, int cap) {
+  int64_t b = std::min<int64_t>(want, std::max<int64_t>(1, cap / std::max(1, nd)));
+  return (unsigned)std::max<int64_t>(1, b);
+}
+
 template <typename S>
-cudaError_t brick_moments_typed(const Geometry &g, const void *f, const BrickMap &m, float *U0s,
+cudaError_t brick_moments_typed(const DomainDesc *D, const BatchDims &dims, int cur,
                                 cudaStream_t st) {
-  brick_moments_kernel<S><<<PERSISTENT_BLOCKS / 2, 256, 0, st>>>((const S *)f, g, m, U0s);
+  const dim3 grid(xblocks((dims.max_slots + 3) / 4, dims.nd, PERSISTENT_BLOCKS / 2), dims.nd);
+  brick_moments_kernel<S><<<grid, 256, 0, st>>>(D, cur);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_prepare_points(const Geometry &g, int delta, const PointsIn &p,
-                                  const Bodies &b, int64_t t, PointPrep &pp,
-                                  const BrickMap &m, const PairMap &pm, double *xpos,
-                                  cudaStream_t st) {
-  if (p.np <= 0) return cudaSuccess;
-  if (b.nb > 0) body_trig_kernel<<<nblk(b.nb, 128), 128, 0, st>>>(b, t);
-  prepare_points_kernel<<<nblk(p.np, 256), 256, 0, st>>>(g, delta, p, b, t, pp, m, pm, xpos);
+cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  if (dims.max_bodies > 0)
+    body_trig_kernel<<<dim3(nblk(dims.max_bodies, 128), dims.nd), 128, 0, st>>>(D);
+  prepare_points_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D);
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_pairs(const Geometry &g, int64_t np, const PointPrep &pp,
-                               const BrickMap &m, const PairMap &pm, cudaStream_t st) {
-  compact_kernel<<<nblk(g.nbrick, 256), 256, 0, st>>>(g, m, pm);
-  if (np > 0) {
-    pair_scan_kernel<<<1, 1024, 0, st>>>(m, pm);
-    pair_fill_kernel<<<nblk(np, 256), 256, 0, st>>>(g, np, pp, m, pm);
+cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+  compact_kernel<<<dim3(nblk(dims.max_bricks, 256), dims.nd), 256, 0, st>>>(D);
+  if (dims.max_points > 0) {
+    pair_scan_kernel<<<dim3(1, dims.nd), 1024, 0, st>>>(D);
+    pair_fill_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D);
     // one warp per slot
-    const int blocks = (int)std::min<int64_t>((m.max_slots + 3) / 4, 152 * 32);
-    pair_sort_kernel<<<blocks > 0 ? blocks : 1, 128, 0, st>>>(g, pp, m, pm);
-    pair_weights_kernel<<<nblk(pm.max_pairs, 256), 256, 0, st>>>(g, pp, m, pm);
+    pair_sort_kernel<<<dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, 152 * 32), dims.nd), 128, 0,
+                       st>>>(D);
+    pair_weights_kernel<<<dim3(nblk(8 * (int64_t)dims.max_points, 256), dims.nd), 256, 0, st>>>(
+        D);
   }
   return cudaGetLastError();
 }
@@ -922,63 +995,62 @@ cudaError_t launch_build_pairs(const Geometry &g, int64_t np, const PointPrep &p
       return cudaErrorInvalidValue;          \
   }
 
-cudaError_t launch_brick_moments(int storage, const Geometry &g, const void *f,
-                                 const BrickMap &m, float *U0s, cudaStream_t st) {
-  DISPATCH_STORAGE(storage, brick_moments_typed, g, f, m, U0s, st);
+cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDims &dims, int cur,
+                                 cudaStream_t st) {
+  DISPATCH_STORAGE(storage, brick_moments_typed, D, dims, cur, st);
 }
 
-cudaError_t launch_brick_init(const BrickMap &m, const PairMap &pm, const float4 *du_init,
-                              const float *U0s, float *Gs, cudaStream_t st) {
-  brick_init_kernel<<<PERSISTENT_BLOCKS, 64, 0, st>>>(m, pm, du_init, U0s, Gs);
+static dim3 brick_grid(const BatchDims &dims) {
+  return dim3(xblocks(dims.max_slots, dims.nd, PERSISTENT_BLOCKS), dims.nd);
+}
+
+cudaError_t launch_brick_init(const DomainDesc *D, const BatchDims &dims, int use_du,
+                              cudaStream_t st) {
+  brick_init_kernel<<<brick_grid(dims), 64, 0, st>>>(D, use_du);
   return cudaGetLastError();
 }
 
-cudaError_t launch_brick_spread(const BrickMap &m, const PairMap &pm, const float4 *vals,
-                                const float *U0s, float *Gs, float *res, int do_interp,
-                                const IbmLoop &loop, cudaStream_t st) {
-  brick_spread_kernel<<<PERSISTENT_BLOCKS, 64, 0, st>>>(m, pm, vals, U0s, Gs, res, do_interp,
-                                                        loop);
+cudaError_t launch_brick_spread(const DomainDesc *D, const BatchDims &dims, int do_interp,
+                                int tol_mode, cudaStream_t st) {
+  brick_spread_kernel<<<brick_grid(dims), 64, 0, st>>>(D, do_interp, tol_mode);
   return cudaGetLastError();
 }
 
-cudaError_t launch_point_update(int64_t np, const PointPrep &pp, const PairMap &pm,
-                                float4 *du, float4 *uint, int first, int warm,
-                                const IbmLoop &loop, cudaStream_t st) {
-  if (np <= 0) return cudaSuccess;
-  point_update_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, du, uint, first, warm, loop);
+cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int first, int warm,
+                                int tol_mode, cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  point_update_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D, first, warm,
+                                                                                 tol_mode);
   return cudaGetLastError();
 }
 
-cudaError_t launch_brick_norm(const BrickMap &m, const PairMap &pm, const float4 *vals,
-                              int scale_by_w, float *res, cudaStream_t st) {
-  brick_norm_kernel<<<PERSISTENT_BLOCKS, 64, 0, st>>>(m, pm, vals, scale_by_w, res);
+cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,
+                              cudaStream_t st) {
+  brick_norm_kernel<<<brick_grid(dims), 64, 0, st>>>(D, which);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ibm_den(const BrickMap &m, const float *res, IbmState *state, int mode,
-                           cudaStream_t st) {
-  ibm_den_kernel<<<1, 256, 0, st>>>(m, res, state, mode);
+cudaError_t launch_ibm_den(const DomainDesc *D, const BatchDims &dims, int mode, cudaStream_t st) {
+  ibm_den_kernel<<<dim3(1, dims.nd), 256, 0, st>>>(D, mode);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ibm_check(const BrickMap &m, const float *res, IbmState *state, int it,
-                             double tol, int max_iter, cudaStream_t st) {
-  ibm_check_kernel<<<1, 256, 0, st>>>(m, res, state, it, tol, max_iter);
+cudaError_t launch_ibm_check(const DomainDesc *D, const BatchDims &dims, int it, double tol,
+                             int max_iter, cudaStream_t st) {
+  ibm_check_kernel<<<dim3(1, dims.nd), 256, 0, st>>>(D, it, tol, max_iter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_point_residual0(int64_t np, const PointPrep &pp, const PairMap &pm,
-                                   float4 *out, cudaStream_t st) {
-  if (np <= 0) return cudaSuccess;
-  point_residual0_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, out);
+cudaError_t launch_point_residual0(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  point_residual0_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_features(const Geometry &g, int64_t np, const PointPrep &pp,
-                                const PairMap &pm, const BrickMap &m, const float4 *du_prev,
-                                const PointsIn &p, const Bodies &b, float *X, cudaStream_t st) {
-  if (np <= 0) return cudaSuccess;
-  mlp_features_kernel<<<nblk(np, 256), 256, 0, st>>>(np, pp, pm, m, du_prev, p, b, X);
+cudaError_t launch_mlp_features(const DomainDesc *D, const BatchDims &dims, int use_prev,
+                                cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  mlp_features_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D, use_prev);
   return cudaGetLastError();
 }
 

@@ -8,23 +8,18 @@
 namespace lbmibm {
 
 // ----------------------------------------------------------------- lbm.cu
-struct CollideArgs {
-  const void *src;      // populations (storage type), [19][ncell]
-  void *dst;
-  const int *brick_slot;  // NULL: no IBM force
-  const float *Gs;        // slot force storage
-  float gbody[3];
-  float tau;
-  double *partial;        // per-block FP64 sums (4 per block) or NULL
-};
+// Fused pull-stream + collision f[cur] -> f[1 - cur] of every domain, with
+// the IBM force of its active bricks and its body force; per-block FP64
+// partial sums when stats.
+// Dhost: host copy of D when dims.nd == 1 (passed as a kernel parameter), or
+// NULL.
+cudaError_t launch_collide_stream(int storage, const DomainDesc *D, const DomainDesc *Dhost,
+                                  const BatchDims &dims, int cur, int stats, cudaStream_t st);
+// End of a step: FP64 reduction of the collide partials into sums (if
+// stats) and t += 1 of every domain (one block per domain).
+cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats,
+                               cudaStream_t st);
 int collide_blocks(const Geometry &g);
-cudaError_t launch_collide_stream(int storage, const Geometry &g, const CollideArgs &a,
-                                  cudaStream_t st);
-// FP64 reduction of the collide partials into out[4] (mass dev, momentum);
-// `scratch` holds nblocks_reduce*4 doubles, `ticket` one zeroed uint.
-cudaError_t launch_stats_reduce(const double *partial, int nparts, double *scratch,
-                                unsigned *ticket, double *out, double ncell,
-                                cudaStream_t st);
 // rho[N], U[3][N] on every cell (either may be NULL).
 cudaError_t launch_moments_dense(int storage, const Geometry &g, const void *f, float *rho,
                                  float *U, cudaStream_t st);
@@ -53,47 +48,39 @@ struct PointsIn {
   const float *area;      // [np] or NULL (1)
   const float *utarget;   // [np][3] or NULL (0)
 };
-// Kinematics (Alg. 1, first iteration) + per-point weights + brick flags.
-cudaError_t launch_prepare_points(const Geometry &g, int delta, const PointsIn &p,
-                                  const Bodies &b, int64_t t, PointPrep &pp,
-                                  const BrickMap &m, const PairMap &pm, double *xpos,
-                                  cudaStream_t st);
+// ---- step kernels over a batch of domains (D: device array of dims.nd) ----
+// Kinematics (Alg. 1, first iteration) + per-point weights + brick counts.
+cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // counted bricks -> slots; (brick, point) pairs grouped by brick in a fixed
-// order, with brick-local weights (5 launches when np > 0, else 1)
-cudaError_t launch_build_pairs(const Geometry &g, int64_t np, const PointPrep &pp,
-                               const BrickMap &m, const PairMap &pm, cudaStream_t st);
-// U0 on the active bricks (pull + Eq. 1)
-cudaError_t launch_brick_moments(int storage, const Geometry &g, const void *f,
-                                 const BrickMap &m, float *U0s, cudaStream_t st);
-// G_0 = 0 or S[du_init], pair shares of I[U0 + G_0]
-cudaError_t launch_brick_init(const BrickMap &m, const PairMap &pm, const float4 *du_init,
-                              const float *U0s, float *Gs, cudaStream_t st);
-// G = S[vals] on the active bricks (Alg. 2 as a gather); res[slot] = squared
-// change of G (NULL: skip); pair shares of I[U0 + G] if do_interp
-cudaError_t launch_brick_spread(const BrickMap &m, const PairMap &pm, const float4 *vals,
-                                const float *U0s, float *Gs, float *res, int do_interp,
-                                const IbmLoop &loop, cudaStream_t st);
+// order, with brick-local weights (5 launches when points exist, else 1)
+cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
+// U0 on the active bricks (pull + Eq. 1) from lattice f[cur]
+cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDims &dims, int cur,
+                                 cudaStream_t st);
+// G_0 = 0 or S[du] (use_du), pair shares of I[U0 + G_0]
+cudaError_t launch_brick_init(const DomainDesc *D, const BatchDims &dims, int use_du,
+                              cudaStream_t st);
+// G = S[du] on the active bricks (Alg. 2 as a gather); in tolerance mode the
+// squared change of G per brick into res and an early exit once converged;
+// pair shares of I[U0 + G] if do_interp
+cudaError_t launch_brick_spread(const DomainDesc *D, const BatchDims &dims, int do_interp,
+                                int tol_mode, cudaStream_t st);
 // u_n(k) from the pair shares; g = u_k - u_n; du += s g (Alg. 1 loop body)
-cudaError_t launch_point_update(int64_t np, const PointPrep &pp, const PairMap &pm,
-                                float4 *du, float4 *uint, int first, int warm,
-                                const IbmLoop &loop, cudaStream_t st);
-// ||S[v]||^2 per brick into res (v scaled by .w if scale_by_w)
-cudaError_t launch_brick_norm(const BrickMap &m, const PairMap &pm, const float4 *vals,
-                              int scale_by_w, float *res, cudaStream_t st);
+cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int first, int warm,
+                                int tol_mode, cudaStream_t st);
+// ||S[v]||^2 per brick into res; which 0: v = s u_k, 1: v = uint
+cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,
+                              cudaStream_t st);
 // residual denominators (mode 0: ||S[s u_k]||^2, mode 1: fallback) and the
 // per-iteration convergence check of the tolerance mode
-cudaError_t launch_ibm_den(const BrickMap &m, const float *res, IbmState *state, int mode,
-                           cudaStream_t st);
-cudaError_t launch_point_residual0(int64_t np, const PointPrep &pp, const PairMap &pm,
-                                   float4 *out, cudaStream_t st);
-cudaError_t launch_ibm_check(const BrickMap &m, const float *res, IbmState *state, int it,
-                             double tol, int max_iter, cudaStream_t st);
-// Per-point MLP features (16) of the learned warm start from the pair shares
-// of I[U0] (brick_init without du_init), u_k, du_prev and the body-relative
-// rest position; see api.cu for the list.
-cudaError_t launch_mlp_features(const Geometry &g, int64_t np, const PointPrep &pp,
-                                const PairMap &pm, const BrickMap &m, const float4 *du_prev,
-                                const PointsIn &p, const Bodies &b, float *X, cudaStream_t st);
+cudaError_t launch_ibm_den(const DomainDesc *D, const BatchDims &dims, int mode, cudaStream_t st);
+cudaError_t launch_ibm_check(const DomainDesc *D, const BatchDims &dims, int it, double tol,
+                             int max_iter, cudaStream_t st);
+// uint = s (u_k - u) from the pair shares (fallback denominator)
+cudaError_t launch_point_residual0(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
+// features of the learned warm start from the pair shares (see ibm.cu)
+cudaError_t launch_mlp_features(const DomainDesc *D, const BatchDims &dims, int use_prev,
+                                cudaStream_t st);
 // training sample target T = (du - du_prev) / MLP_VSCALE, du_prev from X
 cudaError_t launch_mlp_targets(int64_t np, const float *X, const float4 *du, float *T,
                                cudaStream_t st);
@@ -103,9 +90,12 @@ size_t mlp_packed_bytes();
 size_t mlp_train_smem_bytes();
 size_t mlp_grad_scratch_floats(int64_t n);
 cudaError_t launch_mlp_pack(const float *P, void *packed, cudaStream_t st);
-// mode 0: Y[n][3] = MLP(X); mode 1: du[k] += scale * MLP(X)[k]
+// Y[n][3] = MLP(X)
 cudaError_t launch_mlp_forward(int64_t n, const float *X, const void *packed, float *Y,
-                               float4 *du, float scale, int mode, cudaStream_t st);
+                               cudaStream_t st);
+// learned start of every domain: du = (use_prev ? du : 0) + MLP_VSCALE MLP(feat)
+cudaError_t launch_mlp_warm(const DomainDesc *D, const BatchDims &dims, int use_prev,
+                            cudaStream_t st);
 cudaError_t launch_mlp_loss_grad(int64_t n, const float *X, const float *T, const void *packed,
                                  const float *P, float *grad, float *loss, float *part,
                                  cudaStream_t st);

@@ -8,6 +8,8 @@
 // (post-collision values of step t-1), which realises Eq. 4, and writes the
 // post-collision value at X into the destination lattice, so every write is
 // coalesced and each population is read and written exactly once per step.
+#include <algorithm>
+
 #include "kernels.h"
 #include "lattice.cuh"
 
@@ -15,14 +17,22 @@ namespace lbmibm {
 
 namespace {
 
-template <typename S, bool FORCE, bool STATS>
-__global__ void __launch_bounds__(256)
-    collide_stream_kernel(const S *__restrict__ src, S *__restrict__ dst, Geometry g,
-                          const int *__restrict__ brick_slot, const float *__restrict__ Gs,
-                          float gbx, float gby, float gbz, float tau,
-                          double *__restrict__ partial) {
-  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+// One thread per cell.  dd is the domain of this block: a kernel parameter
+// for a single lattice (constant bank, no dependent loads before the first
+// population load), or D[blockIdx.y] of a batch.
+template <typename S, bool STATS>
+__device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int cur) {
+  const Geometry g = dd.g;
+  // blocks past this domain's cells (batches of unequal domains) leave at once
+  if ((int64_t)blockIdx.x * blockDim.x >= g.ncell) return;
+  const S *__restrict__ src = (const S *)dd.f[cur];
+  S *__restrict__ dst = (S *)dd.f[cur ^ 1];
+  const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
+  const float *__restrict__ Gs = dd.Gs;
+  const float gbx = dd.gbody[0], gby = dd.gbody[1], gbz = dd.gbody[2], tau = dd.tau;
+  double *__restrict__ partial = dd.partial;
   float sm = 0.f, spx = 0.f, spy = 0.f, spz = 0.f;
+  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < (uint32_t)g.ncell) {
     int x, y, z;
     cell_coords(n, g, x, y, z);
@@ -34,7 +44,7 @@ __global__ void __launch_bounds__(256)
     const float inv = 1.f / rho;
     // Sec. 2 step 3: U^G = U + tau G
     float Gx = gbx, Gy = gby, Gz = gbz;
-    if (FORCE) {
+    if (brick_slot) {
       const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
       const int s = __ldg(brick_slot + b);
       if (s >= 0) {
@@ -92,13 +102,36 @@ __global__ void __launch_bounds__(256)
 
 // Deterministic two-level FP64 reduction: each block sums a fixed strided
 // subset, the last block to finish sums the block results in index order.
+template <typename S, bool STATS>
 __global__ void __launch_bounds__(256)
-    stats_reduce_kernel(const double *__restrict__ partial, int nparts,
-                        double *__restrict__ scratch, unsigned *ticket, double *out,
-                        double ncell) {
+    collide_stream_kernel(const __grid_constant__ DomainDesc dd, int cur) {
+  collide_stream_cells<S, STATS>(dd, cur);
+}
+
+template <typename S, bool STATS>
+__global__ void __launch_bounds__(256)
+    collide_stream_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
+  collide_stream_cells<S, STATS>(D[blockIdx.y], cur);
+}
+
+// End of a step: the FP64 sum of the collide blocks' partials in a fixed
+// order (FINISH_BLOCKS blocks per domain each sum a strided subset with a
+// tree; the last of them to finish sums the block results the same way), and
+// t += 1.  With stats off only the step counter advances.
+constexpr int FINISH_BLOCKS = 128;
+
+__global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__restrict__ D,
+                                                          int stats) {
+  const DomainDesc &dd = D[blockIdx.y];
+  if (!stats) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dd.t += 1;
+    return;
+  }
   __shared__ double red[256][4];
+  __shared__ bool last;
+  const double *__restrict__ partial = dd.partial;
   double a[4] = {0, 0, 0, 0};
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nparts; p += gridDim.x * blockDim.x)
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < dd.cblocks; p += gridDim.x * blockDim.x)
     for (int c = 0; c < 4; c++) a[c] += partial[(size_t)p * 4 + c];
   for (int c = 0; c < 4; c++) red[threadIdx.x][c] = a[c];
   __syncthreads();
@@ -107,27 +140,28 @@ __global__ void __launch_bounds__(256)
       for (int c = 0; c < 4; c++) red[threadIdx.x][c] += red[threadIdx.x + s][c];
     __syncthreads();
   }
-  __shared__ bool last;
   if (threadIdx.x == 0) {
-    for (int c = 0; c < 4; c++) scratch[blockIdx.x * 4 + c] = red[0][c];
+    for (int c = 0; c < 4; c++) dd.red_scratch[blockIdx.x * 4 + c] = red[0][c];
     __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    last = atomicAdd(dd.ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last) {
-    // the last block sums the block results with the same fixed tree
-    __threadfence();
-    for (int c = 0; c < 4; c++)
-      red[threadIdx.x][c] =
-          threadIdx.x < gridDim.x ? ((volatile double *)scratch)[threadIdx.x * 4 + c] : 0.0;
+  if (!last) return;
+  __threadfence();
+  for (int c = 0; c < 4; c++)
+    red[threadIdx.x][c] =
+        threadIdx.x < gridDim.x ? ((volatile double *)dd.red_scratch)[threadIdx.x * 4 + c] : 0.0;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int c = 0; c < 4; c++) red[threadIdx.x][c] += red[threadIdx.x + s][c];
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s)
-        for (int c = 0; c < 4; c++) red[threadIdx.x][c] += red[threadIdx.x + s][c];
-      __syncthreads();
-    }
-    if (threadIdx.x < 4) out[threadIdx.x] = threadIdx.x == 0 ? ncell + red[0][0] : red[0][threadIdx.x];
-    if (threadIdx.x == 0) *ticket = 0u;
+  }
+  if (threadIdx.x < 4)
+    dd.sums[threadIdx.x] = threadIdx.x == 0 ? (double)dd.g.ncell + red[0][0] : red[0][threadIdx.x];
+  if (threadIdx.x == 0) {
+    *dd.ticket = 0u;
+    *dd.t += 1;
   }
 }
 
@@ -212,24 +246,20 @@ inline unsigned cell_blocks(const Geometry &g, int threads) {
 }
 
 template <typename S>
-cudaError_t collide_typed(const Geometry &g, const CollideArgs &a, cudaStream_t st) {
-  const unsigned nb = cell_blocks(g, 256);
-  const S *src = (const S *)a.src;
-  S *dst = (S *)a.dst;
-  const bool force = a.brick_slot != nullptr;
-  const bool stats = a.partial != nullptr;
-  if (force && stats)
-    collide_stream_kernel<S, true, true><<<nb, 256, 0, st>>>(
-        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
-  else if (force)
-    collide_stream_kernel<S, true, false><<<nb, 256, 0, st>>>(
-        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
-  else if (stats)
-    collide_stream_kernel<S, false, true><<<nb, 256, 0, st>>>(
-        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
-  else
-    collide_stream_kernel<S, false, false><<<nb, 256, 0, st>>>(
-        src, dst, g, a.brick_slot, a.Gs, a.gbody[0], a.gbody[1], a.gbody[2], a.tau, a.partial);
+cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const BatchDims &dims,
+                          int cur, int stats, cudaStream_t st) {
+  const dim3 grid((unsigned)((dims.max_cells + 255) / 256), dims.nd);
+  if (dims.nd == 1 && Dhost) {
+    if (stats)
+      collide_stream_kernel<S, true><<<grid, 256, 0, st>>>(*Dhost, cur);
+    else
+      collide_stream_kernel<S, false><<<grid, 256, 0, st>>>(*Dhost, cur);
+  } else {
+    if (stats)
+      collide_stream_batch_kernel<S, true><<<grid, 256, 0, st>>>(D, cur);
+    else
+      collide_stream_batch_kernel<S, false><<<grid, 256, 0, st>>>(D, cur);
+  }
   return cudaGetLastError();
 }
 
@@ -249,15 +279,14 @@ int collide_blocks(const Geometry &g) { return (int)cell_blocks(g, 256); }
       return cudaErrorInvalidValue;                             \
   }
 
-cudaError_t launch_collide_stream(int storage, const Geometry &g, const CollideArgs &a,
-                                  cudaStream_t st) {
-  DISPATCH_STORAGE(storage, collide_typed, g, a, st);
+cudaError_t launch_collide_stream(int storage, const DomainDesc *D, const DomainDesc *Dhost,
+                                  const BatchDims &dims, int cur, int stats, cudaStream_t st) {
+  DISPATCH_STORAGE(storage, collide_typed, D, Dhost, dims, cur, stats, st);
 }
 
-cudaError_t launch_stats_reduce(const double *partial, int nparts, double *scratch,
-                                unsigned *ticket, double *out, double ncell,
-                                cudaStream_t st) {
-  stats_reduce_kernel<<<128, 256, 0, st>>>(partial, nparts, scratch, ticket, out, ncell);
+cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats,
+                               cudaStream_t st) {
+  finish_step_kernel<<<dim3(stats ? FINISH_BLOCKS : 1, dims.nd), 256, 0, st>>>(D, stats);
   return cudaGetLastError();
 }
 

@@ -168,11 +168,12 @@ __device__ __forceinline__ void load_x(const float *__restrict__ X, int64_t row0
 }
 
 // Inference.  mode 0: Y[n][3] = y.  mode 1 (warm start of the fixed point):
-// du[k] = du_prev[k] + scale * y, with du_prev read from du itself.
-__global__ void __launch_bounds__(256)
-    mlp_forward_kernel(int64_t n, const float *__restrict__ X, const void *packed,
-                       float *__restrict__ Y, float4 *__restrict__ du, float scale, int mode) {
-  __shared__ MlpSmem sm;
+// du[k] = du_prev[k] + scale * y, with du_prev read from du itself (zero when
+// !use_prev).  The domain variant takes n, X, the weights and du from
+// D[blockIdx.y].
+__device__ void mlp_forward_rows(int64_t n, const float *__restrict__ X, const void *packed,
+                                 float *__restrict__ Y, float4 *__restrict__ du, float scale,
+                                 int mode, int use_prev, MlpSmem &sm) {
   load_weights(sm, packed);
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(256)
           Y[3 * r[q] + 1] = v[q][1];
           Y[3 * r[q] + 2] = v[q][2];
         } else {
-          float4 d = du[r[q]];
+          float4 d = use_prev ? du[r[q]] : make_float4(0.f, 0.f, 0.f, 0.f);
           d.x += scale * v[q][0];
           d.y += scale * v[q][1];
           d.z += scale * v[q][2];
@@ -208,6 +209,21 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(256)
+    mlp_forward_kernel(int64_t n, const float *__restrict__ X, const void *packed,
+                       float *__restrict__ Y) {
+  __shared__ MlpSmem sm;
+  mlp_forward_rows(n, X, packed, Y, nullptr, 0.f, 0, 0, sm);
+}
+
+__global__ void __launch_bounds__(256)
+    mlp_warm_kernel(const DomainDesc *__restrict__ D, int use_prev) {
+  __shared__ MlpSmem sm;
+  const DomainDesc &d = D[blockIdx.y];
+  if (d.np == 0 || !d.mlp_packed) return;
+  mlp_forward_rows(d.np, d.feat, d.mlp_packed, nullptr, d.du, MLP_VSCALE, 1, use_prev, sm);
 }
 
 // Shared memory of the training kernel: weights plus the block's 128 samples
@@ -491,10 +507,20 @@ cudaError_t launch_mlp_pack(const float *P, void *packed, cudaStream_t st) {
 }
 
 cudaError_t launch_mlp_forward(int64_t n, const float *X, const void *packed, float *Y,
-                               float4 *du, float scale, int mode, cudaStream_t st) {
+                               cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = std::min<int64_t>((n + 127) / 128, 152 * 8);
-  mlp_forward_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, X, packed, Y, du, scale, mode);
+  mlp_forward_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, X, packed, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_warm(const DomainDesc *D, const BatchDims &dims, int use_prev,
+                            cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  const int64_t want = (dims.max_points + 127) / 128;
+  const int64_t cap = std::max<int64_t>(1, 152 * 8 / std::max(1, dims.nd));
+  const unsigned bx = (unsigned)std::max<int64_t>(1, std::min(want, cap));
+  mlp_warm_kernel<<<dim3(bx, dims.nd), 256, 0, st>>>(D, use_prev);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,57 @@
+"""Trains the learned warm start on trajectories the solver itself generates.
+
+    python -m paper_1904_02108_gb300.train_warm_start --out weights.npy \
+        [--seeds 4] [--steps 500] [--samples 8192] [--epochs 8]
+
+Data: the 256^3 array of 64 propellers with fresh seeds (5000, 5001, ...),
+each advanced `steps` steps in tolerance mode (eps <= 1e-4, previous-force
+start); every step contributes `samples` random points (features and the
+target (final du - previous du) / V).  Training: Adam on the library's BF16
+tensor-core kernels.  Writes the FP32 weights (.npy) and a JSON log beside
+them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--seeds", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--samples", type=int, default=8192)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--max-iter", type=int, default=1000)
+    a = ap.parse_args(argv)
+    import torch
+    from . import binding, learned
+    from . import workload as W
+    binding.load()
+    t0 = time.time()
+    ws = [W.dense_array_256(5000 + i) for i in range(a.seeds)]
+    X, T = learned.generate(ws, a.steps, tol=a.tol, max_iter=a.max_iter,
+                            samples_per_step=a.samples)
+    t1 = time.time()
+    P, losses = learned.train(X, T, epochs=a.epochs, batch=a.batch, lr=a.lr,
+                              log=lambda m: print(m, flush=True))
+    torch.cuda.synchronize()
+    t2 = time.time()
+    np.save(a.out, P.cpu().numpy())
+    log = {"samples": int(X.shape[0]), "seeds": [5000 + i for i in range(a.seeds)],
+           "steps_per_seed": a.steps, "tol": a.tol, "epochs": a.epochs, "batch": a.batch,
+           "lr": a.lr, "losses": losses, "generate_s": t1 - t0, "train_s": t2 - t1}
+    with open(a.out.rsplit(".", 1)[0] + ".json", "w") as f:
+        json.dump(log, f, indent=1)
+    print(json.dumps({k: v for k, v in log.items() if k != "losses"}))
+
+
+if __name__ == "__main__":
+    main()

@@ -151,10 +151,11 @@ def propeller_array(n_side: int, box: int, L: float, W: float, pitch: float,
     return propellers(centres, L, W, np.asarray(vt), np.asarray(ph))
 
 
-def dense_array_256() -> Workload:
+def dense_array_256(seed: int = 1235) -> Workload:
     """256^3, tau 0.6: 4x4x4 propellers (centres 32 + 64 i), blades 24 x 6,
-    tip speed U[0.02, 0.06], phase U[0, 2pi); 5 iterations, 1000 steps."""
-    p = propeller_array(4, 256, 24.0, 6.0, 64.0, 1235)
+    tip speed U[0.02, 0.06], phase U[0, 2pi); 5 iterations, 1000 steps.
+    Other seeds give the same geometry with fresh speeds and phases."""
+    p = propeller_array(4, 256, 24.0, 6.0, 64.0, seed)
     return Workload("propeller_array_256", (256, 256, 256), 0.6, p, 5, 1000)
 
 
