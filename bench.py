@@ -50,6 +50,12 @@ class Clocks:
         self.p = None
 
     def __enter__(self):
+        """Starts the sampler and waits for its first sample, so that the
+        tool's start-up (which can hold the driver for seconds on a fresh
+        machine) falls before the timed region rather than inside it."""
+        import threading
+        self.lines = []
+        first = threading.Event()
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
@@ -57,18 +63,30 @@ class Clocks:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+            return self
+
+        def reader():
+            for l in self.p.stdout:
+                if l.strip():
+                    self.lines.append(l)
+                    first.set()
+            first.set()
+
+        self.t = threading.Thread(target=reader, daemon=True)
+        self.t.start()
+        first.wait(timeout=30)
+        self.skip = len(self.lines)  # samples taken before the timed region
         return self
 
     def __exit__(self, *a):
-        self.lines = []
         if self.p is not None:
             self.p.terminate()
             try:
-                out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
-                out = ""
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.t.join(timeout=5)
+            self.lines = self.lines[self.skip:]
 
     def summary(self):
         sm, mx, reasons = [], None, set()
