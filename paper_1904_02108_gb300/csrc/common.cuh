@@ -66,6 +66,37 @@ struct Store<__half> {
   }
 };
 
+// ---- programmatic dependent launch --------------------------------------
+// The step kernels are launched with programmatic stream serialization: a
+// kernel may be scheduled while its predecessor in the stream drains.  Every
+// step kernel calls pdl_wait() (which returns once the predecessor grid has
+// completed and its writes are visible) before it touches anything the
+// predecessor wrote, and pdl_wait() precedes every exit, so completion still
+// chains through the stream; pdl_launch_dependents() right after lets the
+// next kernel be scheduled early.  Both are no-ops for a plain launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches kern<<<grid, block, smem, st>>>(args...) with programmatic stream
+// serialization allowed.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---- bricks: 4x4x4 cells, the unit of point binning and force storage -----
 constexpr int BRICK = 4;
 constexpr int BRICK_CELLS = 64;

@@ -118,6 +118,8 @@ __device__ __forceinline__ void for_support_bricks(const Geometry &g, int4 b, Fn
 // without cancellation as -2 sin(phi - omega/2) sin(omega/2) and
 // 2 cos(phi - omega/2) sin(omega/2).
 __global__ void body_trig_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Bodies bd{d.centre, d.omega, d.phase, d.nb, d.trig};
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,6 +141,8 @@ __global__ void body_trig_kernel(const DomainDesc *__restrict__ D) {
 
 __global__ void __launch_bounds__(256)
     prepare_points_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
   const int delta = d.delta;
@@ -209,6 +213,8 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void compact_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
   const BrickMap m = d.m;
@@ -244,6 +250,8 @@ __device__ __forceinline__ int active_slots(const BrickMap &m) {
 constexpr int SCAN_TILE = 8192;
 
 __global__ void __launch_bounds__(1024) pair_scan_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   if (D[blockIdx.y].np == 0) return;  // no pair storage in a domain without points
   const BrickMap m = D[blockIdx.y].m;
   const PairMap pm = D[blockIdx.y].pm;
@@ -297,6 +305,8 @@ __global__ void __launch_bounds__(1024) pair_scan_kernel(const DomainDesc *__res
 }
 
 __global__ void pair_fill_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
   const int64_t np = d.np;
@@ -312,7 +322,7 @@ __global__ void pair_fill_kernel(const DomainDesc *__restrict__ D) {
   });
 }
 
-// One warp per slot: sort the slot's points ascending (in registers up to 32
+// One warp per slot: sort the slot's points ascending (in registers up to 128
 // pairs, bitonic in shared memory up to SORT_CAP, else a rank sort through
 // this slot's not yet written weight storage; the points of a slot are
 // distinct) and record the slot's brick with each pair.
@@ -320,6 +330,8 @@ constexpr int SORT_CAP = 512;
 
 __global__ void __launch_bounds__(128)
     pair_sort_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ int buf[4][SORT_CAP];
   const BrickMap m = D[blockIdx.y].m;
   const PairMap pm = D[blockIdx.y].pm;
@@ -328,12 +340,28 @@ __global__ void __launch_bounds__(128)
   for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
     const int cnt = pm.count[s], st = pm.start[s];
     int *a = pm.k + st;
-    if (cnt <= 32) {
-      const int v = lane < cnt ? a[lane] : 0x7fffffff;
-      int r = 0;
-      for (int j = 0; j < cnt; j++) r += __shfl_sync(0xffffffffu, v, j) < v;
+    if (cnt <= 128) {
+      // rank sort in registers: lane holds entries lane + 32 i, i < nr; the
+      // rank of a value is the number of smaller ones (the points differ)
+      const int nr = (cnt + 31) >> 5;
+      int v[4], r[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        v[i] = (i < nr && lane + 32 * i < cnt) ? a[lane + 32 * i] : 0x7fffffff;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        if (i < nr) {
+          for (int j = 0; j < 32; j++) {
+            const int x = __shfl_sync(0xffffffffu, v[i], j);
+#pragma unroll
+            for (int q = 0; q < 4; q++) r[q] += x < v[q];
+          }
+        }
+      }
       __syncwarp();
-      if (lane < cnt) a[r] = v;
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        if (lane + 32 * i < cnt) a[r[i]] = v[i];
     } else if (cnt <= SORT_CAP) {
       int n2 = 2;
       while (n2 < cnt) n2 <<= 1;
@@ -379,6 +407,8 @@ __global__ void __launch_bounds__(128)
 // list of bricks.
 __global__ void __launch_bounds__(256)
     pair_weights_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   if (d.np == 0) return;
   const Geometry g = d.g;
@@ -560,6 +590,8 @@ __device__ __forceinline__ void store_F(BrickSmem &sm, float fx, float fy, float
 template <typename S>
 __global__ void __launch_bounds__(256)
     brick_moments_kernel(const DomainDesc *__restrict__ D, int cur) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const S *__restrict__ f = (const S *)d.f[cur];
   const Geometry g = d.g;
@@ -589,6 +621,8 @@ __global__ void __launch_bounds__(256)
 // iteration.
 __global__ void __launch_bounds__(64, 16)
     brick_init_kernel(const DomainDesc *__restrict__ D, int use_du) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ BrickSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   const BrickMap m = d.m;
@@ -620,6 +654,8 @@ __global__ void __launch_bounds__(64, 16)
 // is the last iteration, the pairs' shares of I[U0 + G] for the next one.
 __global__ void __launch_bounds__(64, 16)
     brick_spread_kernel(const DomainDesc *__restrict__ D, int do_interp, int tol_mode) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ BrickSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   if (tol_mode && d.state->done) return;
@@ -660,6 +696,8 @@ __global__ void __launch_bounds__(64, 16)
 // scale_by_w): the denominator ||S[s u_k]|| of the residual.
 __global__ void __launch_bounds__(64, 16)
     brick_norm_kernel(const DomainDesc *__restrict__ D, int which) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ BrickSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   const BrickMap m = d.m;
@@ -701,6 +739,8 @@ __device__ double block_sum_res(const BrickMap &m, const float *__restrict__ res
 // the first is 0): sum res, or 1 if that is 0 as well.
 __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restrict__ D,
                                                        int mode) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
   const double v = block_sum_res(d.m, d.res);
@@ -719,6 +759,8 @@ __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restri
 // the fixed point); stop at the first eps <= tol or at max_iter iterations.
 __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__restrict__ D, int it,
                                                          double tol, int max_iter) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
   if (st->done) return;
@@ -739,6 +781,8 @@ __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__rest
 // g = u_k - u_n, du += s g (du starts at 0 when first && !warm).
 __global__ void __launch_bounds__(256)
     point_update_kernel(const DomainDesc *__restrict__ D, int first, int warm, int tol_mode) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.np) return;
@@ -773,6 +817,8 @@ __global__ void __launch_bounds__(256)
 // first increment from a zero start, for the fallback residual denominator.
 __global__ void __launch_bounds__(256)
     point_residual0_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.np) return;
@@ -809,6 +855,8 @@ __global__ void __launch_bounds__(256)
 //   13-15 u_k - u_i, the slip left by the previous force
 __global__ void __launch_bounds__(256)
     mlp_features_kernel(const DomainDesc *__restrict__ D, int use_prev) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.np) return;
@@ -955,32 +1003,40 @@ template <typename S>
 cudaError_t brick_moments_typed(const DomainDesc *D, const BatchDims &dims, int cur,
                                 cudaStream_t st) {
   const dim3 grid(xblocks((dims.max_slots + 3) / 4, dims.nd, PERSISTENT_BLOCKS / 2), dims.nd);
-  brick_moments_kernel<S><<<grid, 256, 0, st>>>(D, cur);
-  return cudaGetLastError();
+  return launch_pdl(brick_moments_kernel<S>, grid, dim3(256), 0, st, D, cur);
 }
 
 }  // namespace
 
 cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
   if (dims.max_bodies > 0)
-    body_trig_kernel<<<dim3(nblk(dims.max_bodies, 128), dims.nd), 128, 0, st>>>(D);
-  prepare_points_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D);
-  return cudaGetLastError();
+    e = launch_pdl(body_trig_kernel, dim3(nblk(dims.max_bodies, 128), dims.nd), dim3(128), 0, st,
+                   D);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(prepare_points_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0,
+                    st, D);
 }
 
 cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
-  compact_kernel<<<dim3(nblk(dims.max_bricks, 256), dims.nd), 256, 0, st>>>(D);
-  if (dims.max_points > 0) {
-    pair_scan_kernel<<<dim3(1, dims.nd), 1024, 0, st>>>(D);
-    pair_fill_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D);
+  cudaError_t e =
+      launch_pdl(compact_kernel, dim3(nblk(dims.max_bricks, 256), dims.nd), dim3(256), 0, st, D);
+  if (e == cudaSuccess && dims.max_points > 0) {
+    e = launch_pdl(pair_scan_kernel, dim3(1, dims.nd), dim3(1024), 0, st, D);
+    if (e == cudaSuccess)
+      e = launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0, st,
+                     D);
     // one warp per slot
-    pair_sort_kernel<<<dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, 152 * 32), dims.nd), 128, 0,
-                       st>>>(D);
-    pair_weights_kernel<<<dim3(nblk(8 * (int64_t)dims.max_points, 256), dims.nd), 256, 0, st>>>(
-        D);
+    if (e == cudaSuccess)
+      e = launch_pdl(pair_sort_kernel,
+                     dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, 152 * 32), dims.nd), dim3(128),
+                     0, st, D);
+    if (e == cudaSuccess)
+      e = launch_pdl(pair_weights_kernel, dim3(nblk(8 * (int64_t)dims.max_points, 256), dims.nd),
+                     dim3(256), 0, st, D);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 #define DISPATCH_STORAGE(storage, FN, ...)   \
@@ -1006,52 +1062,46 @@ static dim3 brick_grid(const BatchDims &dims) {
 
 cudaError_t launch_brick_init(const DomainDesc *D, const BatchDims &dims, int use_du,
                               cudaStream_t st) {
-  brick_init_kernel<<<brick_grid(dims), 64, 0, st>>>(D, use_du);
-  return cudaGetLastError();
+  return launch_pdl(brick_init_kernel, brick_grid(dims), dim3(64), 0, st, D, use_du);
 }
 
 cudaError_t launch_brick_spread(const DomainDesc *D, const BatchDims &dims, int do_interp,
                                 int tol_mode, cudaStream_t st) {
-  brick_spread_kernel<<<brick_grid(dims), 64, 0, st>>>(D, do_interp, tol_mode);
-  return cudaGetLastError();
+  return launch_pdl(brick_spread_kernel, brick_grid(dims), dim3(64), 0, st, D, do_interp, tol_mode);
 }
 
 cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int first, int warm,
                                 int tol_mode, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
-  point_update_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D, first, warm,
-                                                                                 tol_mode);
-  return cudaGetLastError();
+  return launch_pdl(point_update_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0,
+                    st, D, first, warm, tol_mode);
 }
 
 cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,
                               cudaStream_t st) {
-  brick_norm_kernel<<<brick_grid(dims), 64, 0, st>>>(D, which);
-  return cudaGetLastError();
+  return launch_pdl(brick_norm_kernel, brick_grid(dims), dim3(64), 0, st, D, which);
 }
 
 cudaError_t launch_ibm_den(const DomainDesc *D, const BatchDims &dims, int mode, cudaStream_t st) {
-  ibm_den_kernel<<<dim3(1, dims.nd), 256, 0, st>>>(D, mode);
-  return cudaGetLastError();
+  return launch_pdl(ibm_den_kernel, dim3(1, dims.nd), dim3(256), 0, st, D, mode);
 }
 
 cudaError_t launch_ibm_check(const DomainDesc *D, const BatchDims &dims, int it, double tol,
                              int max_iter, cudaStream_t st) {
-  ibm_check_kernel<<<dim3(1, dims.nd), 256, 0, st>>>(D, it, tol, max_iter);
-  return cudaGetLastError();
+  return launch_pdl(ibm_check_kernel, dim3(1, dims.nd), dim3(256), 0, st, D, it, tol, max_iter);
 }
 
 cudaError_t launch_point_residual0(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
-  point_residual0_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D);
-  return cudaGetLastError();
+  return launch_pdl(point_residual0_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256),
+                    0, st, D);
 }
 
 cudaError_t launch_mlp_features(const DomainDesc *D, const BatchDims &dims, int use_prev,
                                 cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
-  mlp_features_kernel<<<dim3(nblk(dims.max_points, 256), dims.nd), 256, 0, st>>>(D, use_prev);
-  return cudaGetLastError();
+  return launch_pdl(mlp_features_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0,
+                    st, D, use_prev);
 }
 
 cudaError_t launch_mlp_targets(int64_t np, const float *X, const float4 *du, float *T,

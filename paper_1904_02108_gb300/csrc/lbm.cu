@@ -105,12 +105,16 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
 template <typename S, bool STATS>
 __global__ void __launch_bounds__(256)
     collide_stream_kernel(const __grid_constant__ DomainDesc dd, int cur) {
+  pdl_wait();
+  pdl_launch_dependents();
   collide_stream_cells<S, STATS>(dd, cur);
 }
 
 template <typename S, bool STATS>
 __global__ void __launch_bounds__(256)
     collide_stream_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
+  pdl_wait();
+  pdl_launch_dependents();
   collide_stream_cells<S, STATS>(D[blockIdx.y], cur);
 }
 
@@ -122,6 +126,8 @@ constexpr int FINISH_BLOCKS = 128;
 
 __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__restrict__ D,
                                                           int stats) {
+  pdl_wait();
+  pdl_launch_dependents();
   const DomainDesc &dd = D[blockIdx.y];
   if (!stats) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *dd.t += 1;
@@ -249,18 +255,11 @@ template <typename S>
 cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const BatchDims &dims,
                           int cur, int stats, cudaStream_t st) {
   const dim3 grid((unsigned)((dims.max_cells + 255) / 256), dims.nd);
-  if (dims.nd == 1 && Dhost) {
-    if (stats)
-      collide_stream_kernel<S, true><<<grid, 256, 0, st>>>(*Dhost, cur);
-    else
-      collide_stream_kernel<S, false><<<grid, 256, 0, st>>>(*Dhost, cur);
-  } else {
-    if (stats)
-      collide_stream_batch_kernel<S, true><<<grid, 256, 0, st>>>(D, cur);
-    else
-      collide_stream_batch_kernel<S, false><<<grid, 256, 0, st>>>(D, cur);
-  }
-  return cudaGetLastError();
+  if (dims.nd == 1 && Dhost)
+    return stats ? launch_pdl(collide_stream_kernel<S, true>, grid, dim3(256), 0, st, *Dhost, cur)
+                 : launch_pdl(collide_stream_kernel<S, false>, grid, dim3(256), 0, st, *Dhost, cur);
+  return stats ? launch_pdl(collide_stream_batch_kernel<S, true>, grid, dim3(256), 0, st, D, cur)
+               : launch_pdl(collide_stream_batch_kernel<S, false>, grid, dim3(256), 0, st, D, cur);
 }
 
 }  // namespace
@@ -286,8 +285,8 @@ cudaError_t launch_collide_stream(int storage, const DomainDesc *D, const Domain
 
 cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats,
                                cudaStream_t st) {
-  finish_step_kernel<<<dim3(stats ? FINISH_BLOCKS : 1, dims.nd), 256, 0, st>>>(D, stats);
-  return cudaGetLastError();
+  return launch_pdl(finish_step_kernel, dim3(stats ? FINISH_BLOCKS : 1, dims.nd), dim3(256), 0, st,
+                    D, stats);
 }
 
 namespace {

@@ -220,6 +220,8 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(256)
     mlp_warm_kernel(const DomainDesc *__restrict__ D, int use_prev) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ MlpSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   if (d.np == 0 || !d.mlp_packed) return;
@@ -520,8 +522,7 @@ cudaError_t launch_mlp_warm(const DomainDesc *D, const BatchDims &dims, int use_
   const int64_t want = (dims.max_points + 127) / 128;
   const int64_t cap = std::max<int64_t>(1, 152 * 8 / std::max(1, dims.nd));
   const unsigned bx = (unsigned)std::max<int64_t>(1, std::min(want, cap));
-  mlp_warm_kernel<<<dim3(bx, dims.nd), 256, 0, st>>>(D, use_prev);
-  return cudaGetLastError();
+  return launch_pdl(mlp_warm_kernel, dim3(bx, dims.nd), dim3(256), 0, st, D, use_prev);
 }
 
 cudaError_t launch_mlp_loss_grad(int64_t n, const float *X, const float *T, const void *packed,
