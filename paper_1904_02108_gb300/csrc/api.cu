@@ -292,6 +292,7 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->m.brick_count);
   dfree(h->m.brick_slot);
   dfree(h->m.counters);
+  dfree(h->m.tiles);
   dfree(h->partial);
   dfree(h->sums);
   dfree(h->red_scratch);
@@ -359,8 +360,13 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   if (e == cudaSuccess) e = cudaMemset(h->m.brick_count, 0, sizeof(int) * h->g.nbrick);
   if (e == cudaSuccess) e = dalloc(&h->m.brick_slot, h->g.nbrick);
   if (e == cudaSuccess) e = cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick);
-  if (e == cudaSuccess) e = dalloc(&h->m.counters, 4);
-  if (e == cudaSuccess) e = cudaMemset(h->m.counters, 0, 4 * sizeof(int));
+  if (e == cudaSuccess) e = dalloc(&h->m.counters, 8);
+  if (e == cudaSuccess) e = cudaMemset(h->m.counters, 0, 8 * sizeof(int));
+  {
+    const size_t nt = (h->g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE;
+    if (e == cudaSuccess) e = dalloc(&h->m.tiles, nt);
+    if (e == cudaSuccess) e = cudaMemset(h->m.tiles, 0, nt * sizeof(unsigned long long));
+  }
   h->nparts = collide_blocks(h->g);
   if (e == cudaSuccess) e = dalloc(&h->partial, (size_t)h->nparts * 4);
   if (e == cudaSuccess) e = dalloc(&h->sums, 4);
@@ -472,7 +478,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, cudaMemset(h->uint, 0, sizeof(float4) * n));
   } else {
     CK(h, cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick));
-    CK(h, cudaMemset(h->m.counters, 0, 4 * sizeof(int)));
+    CK(h, cudaMemset(h->m.counters, 0, 2 * sizeof(int)));
   }
   return LBM_OK;
 }
@@ -617,7 +623,7 @@ static int enqueue_prefix(StepCtx &c, bool *warm_out) {
     CK(h, launch_prepare_points(c.D, c.dims, c.st));
   }
   {
-    StageTimer T(h, ST_PAIRS, 5);
+    StageTimer T(h, ST_PAIRS, 4);
     CK(h, launch_build_pairs(c.D, c.dims, c.st));
   }
   {
@@ -1122,9 +1128,13 @@ int lbm_read_stats(lbm_t *h, lbm_stats *s) {
   s->not_converged = h->not_converged;
   s->kernel_launches = h->nlaunch;
   if (h->np > 0) {
-    int c = 0;
-    CK(h, cudaMemcpy(&c, h->m.counters, sizeof(int), cudaMemcpyDeviceToHost));
-    s->active_bricks = c;
+    int c[8] = {0};
+    CK(h, cudaMemcpy(c, h->m.counters, sizeof c, cudaMemcpyDeviceToHost));
+    s->active_bricks = c[0];
+    if (c[5] & 4) {
+      CK(h, cudaMemset(h->m.counters + 5, 0, sizeof(int)));
+      return fail(h, LBM_ECUDA, "brick compaction scan timed out");
+    }
   }
   if (h->sums_valid && !(isfinite(sums[0]) && isfinite(sums[1]) && isfinite(sums[2]) &&
                          isfinite(sums[3])))
@@ -1343,7 +1353,8 @@ int ibm_interpolate_dev(int nx, int ny, int nz, int delta, const float *U, int64
 namespace {
 
 struct SpreadLayout {
-  size_t desc, brick_count, brick_slot, slot_brick, counters, count, start, cursor, pk, pbrick, pw,
+  size_t desc, brick_count, brick_slot, slot_brick, counters, tiles, count, start, cursor, pk,
+      pbrick, pw,
       ppart,
       point_pairs, base, wts, ut, vals, Gs, total;
   int max_slots;
@@ -1365,7 +1376,8 @@ SpreadLayout spread_layout(const Geometry &g, int64_t n) {
   L.brick_count = take(sizeof(int) * g.nbrick);
   L.brick_slot = take(sizeof(int) * g.nbrick);
   L.slot_brick = take(sizeof(int) * ms);
-  L.counters = take(sizeof(int) * 4);
+  L.counters = take(sizeof(int) * 8);
+  L.tiles = take(sizeof(unsigned long long) * ((g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE));
   L.count = take(sizeof(int) * ms);
   L.start = take(sizeof(int) * (ms + 1));
   L.cursor = take(sizeof(int) * ms);
@@ -1430,6 +1442,7 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   m.brick_slot = (int *)(base + L.brick_slot);
   m.slot_brick = (int *)(base + L.slot_brick);
   m.counters = (int *)(base + L.counters);
+  m.tiles = (unsigned long long *)(base + L.tiles);
   m.max_slots = L.max_slots;
   PairMap pm{};
   pm.count = (int *)(base + L.count);
@@ -1449,7 +1462,12 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   float *Gs = (float *)(base + L.Gs);
   if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, sizeof(float) * 3 * g.ncell, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m.brick_count, 0, sizeof(int) * g.nbrick, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m.counters, 0, sizeof(int) * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.counters, 0, sizeof(int) * 8, st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(m.tiles, 0,
+                        sizeof(unsigned long long) *
+                            ((g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE),
+                        st);
   if (n > 0) {
     // a batch of one domain whose descriptor lives in the scratch
     DomainDesc dd{};

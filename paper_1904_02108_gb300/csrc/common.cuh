@@ -102,6 +102,9 @@ constexpr int BRICK = 4;
 constexpr int BRICK_CELLS = 64;
 constexpr int SLOT_FLOATS = 3 * BRICK_CELLS;  // [3][64] per active brick
 
+// Bricks per block of the compaction scan (256 threads x 4).
+constexpr int COMPACT_TILE = 1024;
+
 // Grid of the kernels that loop over the active bricks (grid-stride): 16
 // blocks per SM of the 152-SM GB300.
 constexpr int PERSISTENT_BLOCKS = 152 * 16;
@@ -130,7 +133,12 @@ struct BrickMap {
                      //           per step, cleared by the compaction)
   int *brick_slot;   // [nbrick]
   int *slot_brick;   // [max_slots]
-  int *counters;     // [4]: 0 = active slots, 1 = overflow flag
+  int *counters;     // [8]: 0 = active slots, 1 = error flags of the step
+                     //      (1: slot overflow, 4: compaction scan timed
+                     //      out), 3 = tile ticket, 4 = scan epoch, 5 = error
+                     //      flags kept until the host reads them
+  unsigned long long *tiles;  // [compact tiles] look-back words of the
+                              // compaction scan
   int max_slots;
 };
 

@@ -4,8 +4,9 @@
 // Once per step (points do not move inside the fixed point):
 //   prepare_points  x(t) = M(t)[x_rest, 1], u_k, tap weights, and for each
 //                   brick its number of overlapping supports
-//   compact         bricks with a count -> slots of the sparse force storage
-//   pair_scan/fill/sort/weights
+//   compact         bricks with a count -> slots of the sparse force storage,
+//                   in brick order, and each slot's first pair (one scan)
+//   pair_fill/sort/weights
 //                   one pair per (brick, point) with the point's support
 //                   overlapping the brick, grouped by brick, ascending point
 //                   index, with the brick-local weights of the point
@@ -212,96 +213,153 @@ __global__ void __launch_bounds__(256)
   });
 }
 
-__global__ void compact_kernel(const DomainDesc *__restrict__ D) {
+// Look-back word of a compaction tile: epoch (6 bits, never 0), status (2
+// bits: 1 = the tile's own totals, 2 = inclusive prefix), active bricks (25
+// bits), pairs (31 bits).
+__device__ __forceinline__ unsigned long long tile_word(unsigned epoch, unsigned status,
+                                                       unsigned long long a,
+                                                       unsigned long long c) {
+  return ((unsigned long long)epoch << 58) | ((unsigned long long)status << 56) | (a << 31) | c;
+}
+
+constexpr unsigned SCAN_SPIN_LIMIT = 1u << 22;
+
+// Bricks with a count -> slots in brick order, and each slot's first pair:
+// one pass over the bricks in tiles of COMPACT_TILE with a single-pass scan.
+// A tile takes its index from a ticket, so it only waits on tiles already
+// running; it publishes its totals, then adds up its predecessors' words
+// (stopping at the first inclusive prefix) and publishes its own prefix.
+// Every wait is bounded: past SCAN_SPIN_LIMIT polls the tile sets error flag 4
+// and the step's slots are left empty.
+__global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
   pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
   const BrickMap m = d.m;
   const PairMap pm = d.pm;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= g.nbrick) return;
-  const int c = m.brick_count[b];
-  if (c > 0) {
-    m.brick_count[b] = 0;
-    const int s = atomicAdd(m.counters, 1);
-    if (s < m.max_slots) {
-      m.brick_slot[b] = s;
-      m.slot_brick[s] = b;
-      pm.count[s] = c;
-      pm.cursor[s] = 0;
+  const int ntiles = (g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE;
+  if ((int)blockIdx.x >= ntiles) return;
+  __shared__ int tile_s, wa[8], wc[8];
+  __shared__ unsigned epoch_s;
+  __shared__ long long pre_a, pre_c;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) {
+    tile_s = atomicAdd(m.counters + 3, 1);
+    epoch_s = (unsigned)(*(volatile int *)(m.counters + 4)) % 63u + 1u;
+  }
+  __syncthreads();
+  const int tile = tile_s;
+  const unsigned epoch = epoch_s;
+  const int b0 = tile * COMPACT_TILE + 4 * t;
+  int c[4], na = 0, nc = 0;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    c[i] = b0 + i < g.nbrick ? m.brick_count[b0 + i] : 0;
+    na += c[i] > 0;
+    nc += c[i];
+  }
+  // block-exclusive scan of (na, nc)
+  int ia = na, ic = nc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int ta = __shfl_up_sync(0xffffffffu, ia, o), tc = __shfl_up_sync(0xffffffffu, ic, o);
+    if (lane >= o) {
+      ia += ta;
+      ic += tc;
+    }
+  }
+  if (lane == 31) {
+    wa[w] = ia;
+    wc[w] = ic;
+  }
+  __syncthreads();
+  int ba = 0, bc = 0, ta = 0, tc = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    if (k < w) {
+      ba += wa[k];
+      bc += wc[k];
+    }
+    ta += wa[k];
+    tc += wc[k];
+  }
+  ia += ba - na;  // exclusive within the tile
+  ic += bc - nc;
+  if (t == 0) {
+    unsigned long long *tw = m.tiles;
+    long long pa = 0, pc = 0;
+    if (tile == 0) {
+      atomicExch(tw + 0, tile_word(epoch, 2, (unsigned)ta, (unsigned)tc));
+    } else {
+      atomicExch(tw + tile, tile_word(epoch, 1, (unsigned)ta, (unsigned)tc));
+      bool ok = true;
+      for (int j = tile - 1; j >= 0 && ok; j--) {
+        unsigned long long v = 0;
+        unsigned spins = 0;
+        for (;;) {
+          v = *(volatile unsigned long long *)(tw + j);
+          if ((unsigned)(v >> 58) == epoch && ((v >> 56) & 3u) != 0) break;
+          if (++spins >= SCAN_SPIN_LIMIT) {
+            ok = false;
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (!ok) break;
+        pa += (long long)((v >> 31) & 0x1ffffffull);
+        pc += (long long)(v & 0x7fffffffull);
+        if (((v >> 56) & 3u) == 2) break;
+      }
+      if (!ok) {
+        atomicOr(m.counters + 1, 4);
+        atomicOr(m.counters + 5, 4);  // kept until the host reads it
+        pa = 0;
+        pc = 0;
+      }
+      atomicExch(tw + tile, tile_word(epoch, 2, (unsigned)(pa + ta), (unsigned)(pc + tc)));
+    }
+    pre_a = pa;
+    pre_c = pc;
+  }
+  __syncthreads();
+  int slot = (int)pre_a + ia, first = (int)pre_c + ic;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const int b = b0 + i;
+    if (b >= g.nbrick) break;
+    if (c[i] > 0) {
+      m.brick_count[b] = 0;
+      if (slot < m.max_slots) {
+        m.brick_slot[b] = slot;
+        m.slot_brick[slot] = b;
+        pm.count[slot] = c[i];
+        pm.start[slot] = first;
+        pm.cursor[slot] = 0;
+      } else {
+        m.brick_slot[b] = -1;
+        atomicOr(m.counters + 1, 1);
+      }
+      slot++;
+      first += c[i];
     } else {
       m.brick_slot[b] = -1;
-      atomicOr(m.counters + 1, 1);
     }
-  } else {
-    m.brick_slot[b] = -1;
+  }
+  if (tile == ntiles - 1 && t == 0) {
+    const int total = (int)(pre_a + ta);
+    m.counters[0] = total;
+    // (a domain without points has no pair storage)
+    if (d.np > 0 && total <= m.max_slots) pm.start[total] = (int)(pre_c + tc);
+    m.counters[3] = 0;
+    m.counters[4] = (int)(epoch % 63u);  // the next launch's epoch is this + 1
   }
 }
 
 __device__ __forceinline__ int active_slots(const BrickMap &m) {
+  if (m.counters[1] & 4) return 0;  // the compaction did not complete
   const int n = m.counters[0];
   return n < m.max_slots ? n : m.max_slots;
-}
-
-// Exclusive scan of pm.count[0 .. nslots) into pm.start, one block, in tiles
-// of SCAN_TILE counts staged through shared memory with coalesced loads and
-// stores (8 consecutive counts per thread).
-constexpr int SCAN_TILE = 8192;
-
-__global__ void __launch_bounds__(1024) pair_scan_kernel(const DomainDesc *__restrict__ D) {
-  pdl_wait();
-  pdl_launch_dependents();
-  if (D[blockIdx.y].np == 0) return;  // no pair storage in a domain without points
-  const BrickMap m = D[blockIdx.y].m;
-  const PairMap pm = D[blockIdx.y].pm;
-  __shared__ int tile[SCAN_TILE];
-  __shared__ int wsum[32];
-  __shared__ int carry;
-  const int n = active_slots(m);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  for (int t0 = 0; t0 < n; t0 += SCAN_TILE) {
-    const int len = min(SCAN_TILE, n - t0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < SCAN_TILE; i += 1024) tile[i] = i < len ? pm.count[t0 + i] : 0;
-    __syncthreads();
-    int v[8], local = 0;
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      v[j] = tile[threadIdx.x * 8 + j];
-      local += v[j];
-    }
-    int inc = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    if (lane == 31) wsum[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-      int s = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += t;
-      }
-      wsum[lane] = s;
-    }
-    __syncthreads();
-    int run = carry + inc - local + (w > 0 ? wsum[w - 1] : 0);
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      tile[threadIdx.x * 8 + j] = run;
-      run += v[j];
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < len; i += 1024) pm.start[t0 + i] = tile[i];
-    if (threadIdx.x == 1023) carry = run;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) pm.start[n] = carry;
 }
 
 __global__ void pair_fill_kernel(const DomainDesc *__restrict__ D) {
@@ -314,7 +372,7 @@ __global__ void pair_fill_kernel(const DomainDesc *__restrict__ D) {
   const BrickMap m = d.m;
   const PairMap pm = d.pm;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= np) return;
+  if (k >= np || (m.counters[1] & 4)) return;
   for_support_bricks8(g, pp.base[k], [&](int brick, bool valid) {
     const int s = valid ? m.brick_slot[brick] : -1;
     const int pos = aggregated_inc(pm.cursor, s, s >= 0);
@@ -1020,12 +1078,10 @@ cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cu
 }
 
 cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
-  cudaError_t e =
-      launch_pdl(compact_kernel, dim3(nblk(dims.max_bricks, 256), dims.nd), dim3(256), 0, st, D);
+  cudaError_t e = launch_pdl(compact_kernel, dim3(nblk(dims.max_bricks, COMPACT_TILE), dims.nd),
+                             dim3(256), 0, st, D);
   if (e == cudaSuccess && dims.max_points > 0) {
-    e = launch_pdl(pair_scan_kernel, dim3(1, dims.nd), dim3(1024), 0, st, D);
-    if (e == cudaSuccess)
-      e = launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0, st,
+    e = launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0, st,
                      D);
     // one warp per slot
     if (e == cudaSuccess)
