@@ -206,6 +206,9 @@ def run_ours(args):
     st = torch.cuda.current_stream()
     lat = binding.Lattice(w.shape, w.tau, storage="f32", stream=st)
     lat.set_propellers(w.props)
+    # launch shapes from the project's autotuner (results do not depend on
+    # them; the lattice is left where it was)
+    shape = lat.autotune(w.n_iter, 6) if not args.no_autotune else lat.launch_shape()
 
     def barrier():
         if ws > 1:
@@ -240,6 +243,13 @@ def run_ours(args):
     lat.step(nb_steps, w.n_iter)
     breakdown = {k: v[0] / nb_steps for k, v in lat.timing().items()}
     lat.enable_timing(False)
+
+    # ---- the same steps replayed from captured CUDA graphs (two steps each)
+    lat.set_graph(True)
+    lat.step(2, w.n_iter)  # capture
+    barrier()
+    graph_ms = _device_ms(lambda: lat.step(args.steps, w.n_iter), st) / args.steps
+    lat.set_graph(False)
 
     # ---- end to end through the C ABI with host buffers: per step the point
     # set is uploaded from pinned memory and du + the FP64 sums read back
@@ -292,6 +302,8 @@ def run_ours(args):
                      "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": per_launch_s * 1e3},
         "stage_ms_per_step": {k: round(v, 5) for k, v in breakdown.items()},
+        "launch_shape": shape,
+        "graph_ms_per_step": graph_ms,
         "clocks": clk.summary(),
     }
     lat.close()
@@ -339,6 +351,7 @@ def bench_batched(steps=100, warmup=4):
         lat.set_propellers(w.props)
         lats.append(lat)
     batch = binding.Batch(lats)
+    shape = batch.autotune(5, 2)
     batch.set_graph(True)
     batch.step(warmup, 5)
     l0 = lats[0].stats()["kernel_launches"]
@@ -348,7 +361,7 @@ def bench_batched(steps=100, warmup=4):
     out = {"workload": "batched_domains_48", "value": cells * steps / (ms / 1e3) / 1e6,
            "unit": "MLUPS", "domains": len(doms), "cells": cells,
            "points": sum(w.props.n_points for w in doms), "propellers_dropped": dropped,
-           "steps": steps, "ms_per_step": ms / steps, "graph": True,
+           "steps": steps, "ms_per_step": ms / steps, "graph": True, "launch_shape": shape,
            "launches_per_step": launches / steps}
     batch.close()
     for lat in lats:
@@ -427,6 +440,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, 16-bit and tolerance-mode measurements")
     args = ap.parse_args()

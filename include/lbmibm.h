@@ -191,6 +191,41 @@ int lbm_read_residuals(lbm_t *h, double *eps, int cap);
 /* The D3Q19 velocity set e[19][3] and weights t[19] the library uses. */
 void lbm_velocity_set(int *e, double *t);
 
+/* ---- launch shapes and the autotuner ----------------------------------- */
+
+/* How the step kernels spread their work over the GPU.  No field depends on
+ * it: every launch shape gives bitwise the same populations, forces, point
+ * values and FP64 sums (the paper fixes the kernels' work, not their launch
+ * geometry; this is a GB300 tuning knob with no counterpart there). */
+typedef struct {
+  int collide_block; /* threads per block of the collide-stream kernel:
+                        128 or 256                                         */
+  int brick_blocks;  /* blocks of the brick kernels (64 threads each,
+                        grid-stride over the active bricks), >= 1          */
+  int point_block;   /* threads per block of the per-point kernels:
+                        128, 256 or 512                                    */
+  int moments_spb;   /* bricks per block of the moments kernel: 1, 2 or 4   */
+  int sort_blocks;   /* blocks of the pair sort (a warp per brick), >= 1   */
+} lbm_launch_shape;
+
+/* The handle's launch shape (defaults: 256, 2432, 256, 4, 4864).  Set
+ * returns LBM_EINVAL for a value outside the ranges above. */
+int lbm_get_launch_shape(lbm_t *h, lbm_launch_shape *out);
+int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s);
+
+/* Picks the launch shape by timing trial steps on this handle's own lattice
+ * and points: one parameter at a time (collide block, brick grid, point
+ * block, moments bricks per block, sort grid), each candidate timed with CUDA
+ * events over the stages it affects for steps_per_trial steps (>= 1) after
+ * one untimed step, in two interleaved rounds (the faster kept), with
+ * n_ibm_iter (> 0) fixed iterations; a candidate replaces the current value
+ * only when more than 1 % faster.  The lattice is
+ * restored afterwards (populations, corrections, step counter, sums), so the
+ * call does not advance the simulation; it allocates a copy of one
+ * population lattice for that.  The chosen shape is set on the handle and
+ * written to *chosen (may be NULL).  Stage timing is off on return. */
+int lbm_autotune(lbm_t *h, int n_ibm_iter, int steps_per_trial, lbm_launch_shape *chosen);
+
 /* ---- captured steps and batches of lattices ------------------------------ */
 
 /* on != 0: lbm_step with n_ibm_iter > 0 captures two consecutive steps into
@@ -212,6 +247,13 @@ int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out);
 int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter);
 int lbm_batch_set_graph(lbm_batch_t *b, int on);
 void lbm_batch_destroy(lbm_batch_t *b);
+/* A batch launches with its own shape: the first handle's at creation, or
+ * the one lbm_batch_set_launch_shape / lbm_batch_autotune set (the autotuner
+ * times whole batch steps, n_ibm_iter > 0, and restores every lattice). */
+int lbm_batch_get_launch_shape(lbm_batch_t *b, lbm_launch_shape *out);
+int lbm_batch_set_launch_shape(lbm_batch_t *b, const lbm_launch_shape *s);
+int lbm_batch_autotune(lbm_batch_t *b, int n_ibm_iter, int steps_per_trial,
+                       lbm_launch_shape *chosen);
 
 /* ---- instrumentation -------------------------------------------------- */
 

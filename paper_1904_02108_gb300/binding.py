@@ -52,6 +52,14 @@ class LbmStats(_c.Structure):
                 ("kernel_launches", _i64)]
 
 
+class LaunchShape(_c.Structure):
+    _fields_ = [("collide_block", _i), ("brick_blocks", _i), ("point_block", _i),
+                ("moments_spb", _i), ("sort_blocks", _i)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class LbmError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("lbmibm error %d: %s" % (code, msg))
@@ -83,6 +91,12 @@ _SIGS = {
     "lbm_read_deviations": (_i, [_p, _p]),
     "lbm_read_residuals": (_i, [_p, _p, _i]),
     "lbm_set_graph": (_i, [_p, _i]),
+    "lbm_get_launch_shape": (_i, [_p, _p]),
+    "lbm_set_launch_shape": (_i, [_p, _p]),
+    "lbm_autotune": (_i, [_p, _i, _i, _p]),
+    "lbm_batch_get_launch_shape": (_i, [_p, _p]),
+    "lbm_batch_set_launch_shape": (_i, [_p, _p]),
+    "lbm_batch_autotune": (_i, [_p, _i, _i, _p]),
     "lbm_batch_create": (_i, [_i, _p, _p]),
     "lbm_batch_step": (_i, [_p, _i, _i]),
     "lbm_batch_set_graph": (_i, [_p, _i]),
@@ -325,6 +339,24 @@ class Lattice:
         """Replay captured pairs of steps (fixed iteration counts)."""
         self._c(load().lbm_set_graph(self.h, int(on)))
 
+    def launch_shape(self):
+        s = LaunchShape()
+        self._c(load().lbm_get_launch_shape(self.h, _c.byref(s)))
+        return s.as_dict()
+
+    def set_launch_shape(self, **kw):
+        """Changes fields of the launch shape (results do not depend on it)."""
+        s = LaunchShape(**{**self.launch_shape(), **kw})
+        self._c(load().lbm_set_launch_shape(self.h, _c.byref(s)))
+
+    def autotune(self, n_ibm_iter=5, steps_per_trial=4):
+        """Times candidate launch shapes on this lattice and keeps the fastest;
+        the lattice is left as it was.  Returns the chosen shape."""
+        s = LaunchShape()
+        self._c(load().lbm_autotune(self.h, int(n_ibm_iter), int(steps_per_trial),
+                                    _c.byref(s)))
+        return s.as_dict()
+
     def set_features(self, on=True):
         self._c(load().lbm_set_features(self.h, int(on)))
 
@@ -427,6 +459,21 @@ class Batch:
 
     def set_graph(self, on=True):
         _check(load().lbm_batch_set_graph(self.b, int(on)))
+
+    def launch_shape(self):
+        s = LaunchShape()
+        _check(load().lbm_batch_get_launch_shape(self.b, _c.byref(s)))
+        return s.as_dict()
+
+    def set_launch_shape(self, **kw):
+        s = LaunchShape(**{**self.launch_shape(), **kw})
+        _check(load().lbm_batch_set_launch_shape(self.b, _c.byref(s)), self.lattices[0].h)
+
+    def autotune(self, n_ibm_iter=5, steps_per_trial=3):
+        s = LaunchShape()
+        _check(load().lbm_batch_autotune(self.b, int(n_ibm_iter), int(steps_per_trial),
+                                         _c.byref(s)), self.lattices[0].h)
+        return s.as_dict()
 
     def close(self):
         if getattr(self, "b", None):

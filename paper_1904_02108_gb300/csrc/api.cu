@@ -120,6 +120,9 @@ struct lbm {
   double ms[kNumStages] = {0};
   int64_t launches[kNumStages] = {0};
 
+  // launch shapes of the step kernels (lbm_autotune)
+  LaunchShape shape;
+
   // read-out temporaries (allocated on first use)
   float *tmp = nullptr;
   size_t tmp_bytes = 0;
@@ -367,7 +370,7 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
     if (e == cudaSuccess) e = dalloc(&h->m.tiles, nt);
     if (e == cudaSuccess) e = cudaMemset(h->m.tiles, 0, nt * sizeof(unsigned long long));
   }
-  h->nparts = collide_blocks(h->g);
+  h->nparts = collide_partials(h->g);
   if (e == cudaSuccess) e = dalloc(&h->partial, (size_t)h->nparts * 4);
   if (e == cudaSuccess) e = dalloc(&h->sums, 4);
   if (e == cudaSuccess) e = dalloc(&h->red_scratch, 128 * 4);
@@ -594,6 +597,7 @@ static BatchDims dims_of(const lbm_t *h) {
   b.max_bodies = h->nb;
   b.max_bricks = h->g.nbrick;
   b.max_slots = h->np > 0 ? h->m.max_slots : 0;
+  b.ls = h->shape;
   return b;
 }
 
@@ -924,6 +928,8 @@ struct lbm_batch {
   int g_iters = -1, g_cur = -1;
   uint64_t g_version = 0;
   int64_t g_launches = 0;
+  LaunchShape shape;
+  uint64_t shape_version = 0;  // changes with the shape (a new capture)
   std::string err;
 };
 
@@ -943,6 +949,7 @@ int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out) {
   }
   lbm_batch_t *b = new lbm_batch();
   b->hs.assign(handles, handles + n);
+  b->shape = handles[0]->shape;
   if (cudaMalloc(&b->D, sizeof(DomainDesc) * n) != cudaSuccess) {
     delete b;
     return fail(nullptr, LBM_ENOMEM, "batch descriptors");
@@ -988,9 +995,10 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
     int r = sync_desc(h);
     if (r) return r;
   }
-  uint64_t ver = 0;
+  uint64_t ver = b->shape_version;
   BatchDims dims{};
   dims.nd = (int)b->hs.size();
+  dims.ls = b->shape;
   bool have_du = false;
   for (lbm_t *h : b->hs) {
     ver = ver * 1000003u + h->version;
@@ -1054,6 +1062,308 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
 }
 
 }  // extern "C"
+
+}  // extern "C"
+
+// ---- launch shapes and the autotuner ---------------------------------------
+
+namespace {
+
+bool shape_ok(const lbm_launch_shape &s) {
+  return (s.collide_block == 128 || s.collide_block == 256) &&
+         (s.point_block == 128 || s.point_block == 256 || s.point_block == 512) &&
+         s.brick_blocks >= 1 && s.brick_blocks <= (1 << 20) && s.sort_blocks >= 1 &&
+         s.sort_blocks <= (1 << 20) &&
+         (s.moments_spb == 1 || s.moments_spb == 2 || s.moments_spb == 4);
+}
+
+lbm_launch_shape to_c(const LaunchShape &l) {
+  return {l.collide_block, l.brick_blocks, l.point_block, l.moments_spb, l.sort_blocks};
+}
+
+LaunchShape from_c(const lbm_launch_shape &c) {
+  LaunchShape l;
+  l.collide_block = c.collide_block;
+  l.brick_blocks = c.brick_blocks;
+  l.point_block = c.point_block;
+  l.moments_spb = c.moments_spb;
+  l.sort_blocks = c.sort_blocks;
+  return l;
+}
+
+// What a trial step changes and the autotuner puts back: the current
+// population lattice, the per-point corrections, the step counter, the FP64
+// sums and the host-side step bookkeeping.
+struct Snapshot {
+  void *f = nullptr;
+  float4 *du = nullptr, *uint = nullptr;
+  double sums[4] = {0, 0, 0, 0};
+  int cur = 0, last_iters = 0;
+  int64_t t = 0, not_converged = 0, nlaunch = 0;
+  bool have_du = false, sums_valid = false;
+  double last_eps = -1.0;
+};
+
+int snapshot_take(lbm_t *h, Snapshot &sn) {
+  CK(h, cudaStreamSynchronize(h->st));
+  const size_t pop = (size_t)Q * h->g.ncell * storage_bytes(h->storage);
+  CK(h, cudaMalloc(&sn.f, pop));
+  CK(h, cudaMemcpy(sn.f, h->f[h->cur], pop, cudaMemcpyDeviceToDevice));
+  if (h->np > 0) {
+    CK(h, dalloc(&sn.du, h->np));
+    CK(h, dalloc(&sn.uint, h->np));
+    CK(h, cudaMemcpy(sn.du, h->du, sizeof(float4) * h->np, cudaMemcpyDeviceToDevice));
+    CK(h, cudaMemcpy(sn.uint, h->uint, sizeof(float4) * h->np, cudaMemcpyDeviceToDevice));
+  }
+  CK(h, cudaMemcpy(sn.sums, h->sums, sizeof sn.sums, cudaMemcpyDeviceToHost));
+  sn.cur = h->cur;
+  sn.t = h->t;
+  sn.have_du = h->have_du;
+  sn.sums_valid = h->sums_valid;
+  sn.last_iters = h->last_iters;
+  sn.last_eps = h->last_eps;
+  sn.not_converged = h->not_converged;
+  sn.nlaunch = h->nlaunch;
+  return LBM_OK;
+}
+
+int snapshot_restore(lbm_t *h, Snapshot &sn) {
+  CK(h, cudaStreamSynchronize(h->st));
+  const size_t pop = (size_t)Q * h->g.ncell * storage_bytes(h->storage);
+  CK(h, cudaMemcpy(h->f[sn.cur], sn.f, pop, cudaMemcpyDeviceToDevice));
+  if (h->np > 0 && sn.du) {
+    CK(h, cudaMemcpy(h->du, sn.du, sizeof(float4) * h->np, cudaMemcpyDeviceToDevice));
+    CK(h, cudaMemcpy(h->uint, sn.uint, sizeof(float4) * h->np, cudaMemcpyDeviceToDevice));
+  }
+  CK(h, cudaMemcpy(h->sums, sn.sums, sizeof sn.sums, cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->t_dev, &sn.t, sizeof sn.t, cudaMemcpyHostToDevice));
+  h->cur = sn.cur;
+  h->t = sn.t;
+  h->have_du = sn.have_du;
+  h->sums_valid = sn.sums_valid;
+  h->last_iters = sn.last_iters;
+  h->last_eps = sn.last_eps;
+  h->not_converged = sn.not_converged;
+  h->nlaunch = sn.nlaunch;
+  return LBM_OK;
+}
+
+void snapshot_free(Snapshot &sn) {
+  if (sn.f) cudaFree(sn.f);
+  dfree(sn.du);
+  dfree(sn.uint);
+  sn.f = nullptr;
+}
+
+// The autotuner's candidates, one parameter after another, and the stages
+// each one is timed on.
+struct TuneParam {
+  int LaunchShape::*field;
+  std::vector<int> values;
+  int stage_mask;
+};
+
+std::vector<TuneParam> tune_params(bool points) {
+  std::vector<TuneParam> ps;
+  ps.push_back({&LaunchShape::collide_block, {128, 256}, 1 << ST_COLLIDE});
+  if (points) {
+    ps.push_back({&LaunchShape::brick_blocks,
+                  {152 * 8, 152 * 16, 152 * 24, 152 * 32},
+                  (1 << ST_SPREAD) | (1 << ST_INIT)});
+    ps.push_back({&LaunchShape::point_block,
+                  {128, 256, 512},
+                  (1 << ST_KIN) | (1 << ST_PAIRS) | (1 << ST_UPDATE)});
+    ps.push_back({&LaunchShape::moments_spb, {1, 2, 4}, 1 << ST_INIT});
+    ps.push_back({&LaunchShape::sort_blocks, {152 * 8, 152 * 16, 152 * 32, 152 * 64},
+                  1 << ST_PAIRS});
+  }
+  return ps;
+}
+
+// Coordinate search over tune_params: step(k) advances the lattices k steps
+// with the current shape, stage_ms(mask) reads the time of the stages in mask
+// since the last clear(mask).  Each candidate is timed in kRounds interleaved
+// rounds and keeps its fastest; a candidate replaces the current value only
+// when it is more than kMargin faster (timing noise does not move the shape).
+constexpr int kRounds = 2;
+constexpr double kMargin = 0.01;
+
+template <typename SetShape, typename Step, typename Clear, typename StageMs>
+int coordinate_search(LaunchShape &shape, bool points, int steps_per_trial, SetShape set_shape,
+                      Step step, Clear clear, StageMs stage_ms) {
+  for (const TuneParam &p : tune_params(points)) {
+    const int incumbent = shape.*p.field;
+    std::vector<double> best_ms(p.values.size(), 1e300);
+    for (int round = 0; round < kRounds; round++) {
+      for (size_t i = 0; i < p.values.size(); i++) {
+        LaunchShape trial = shape;
+        trial.*p.field = p.values[i];
+        int r = set_shape(trial);
+        if (r) return r;
+        r = clear(0);
+        if (r) return r;
+        r = step(1);  // untimed
+        if (r < 0) return r;
+        r = clear(p.stage_mask);
+        if (r) return r;
+        r = step(steps_per_trial);
+        if (r < 0) return r;
+        double ms = 0.0;
+        r = stage_ms(p.stage_mask, &ms);
+        if (r) return r;
+        best_ms[i] = std::min(best_ms[i], ms);
+      }
+    }
+    double inc_ms = 1e300;
+    size_t arg = 0;
+    for (size_t i = 0; i < p.values.size(); i++) {
+      if (p.values[i] == incumbent) inc_ms = best_ms[i];
+      if (best_ms[i] < best_ms[arg]) arg = i;
+    }
+    shape.*p.field = best_ms[arg] < inc_ms * (1.0 - kMargin) ? p.values[arg] : incumbent;
+    int r = set_shape(shape);
+    if (r) return r;
+  }
+  return clear(0);
+}
+
+int read_stage_ms(lbm_t *h, int mask, double *out) {
+  double ms[kNumStages];
+  int r = lbm_read_timing(h, ms, nullptr);
+  if (r) return r;
+  double a = 0.0;
+  for (int i = 0; i < kNumStages; i++)
+    if (mask & (1 << i)) a += ms[i];
+  *out = a;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_get_launch_shape(lbm_t *h, lbm_launch_shape *out) {
+  if (!h || !out) return LBM_EINVAL;
+  *out = to_c(h->shape);
+  return LBM_OK;
+}
+
+int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s) {
+  if (!h || !s) return LBM_EINVAL;
+  if (!shape_ok(*s)) return fail(h, LBM_EINVAL, "launch shape out of range");
+  h->shape = from_c(*s);
+  h->version++;  // a captured step holds the old shape
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_t *h, int n_ibm_iter, int steps_per_trial, lbm_launch_shape *chosen) {
+  if (!h) return LBM_EINVAL;
+  if (n_ibm_iter <= 0 || steps_per_trial < 1)
+    return fail(h, LBM_EINVAL, "autotune needs n_ibm_iter > 0 and steps_per_trial >= 1");
+  Snapshot sn;
+  int r = snapshot_take(h, sn);
+  if (r) {
+    snapshot_free(sn);
+    return r;
+  }
+  const bool graph = h->graph_on;
+  h->graph_on = false;  // stage timing is not recorded in replayed steps
+  LaunchShape shape = h->shape;
+  r = coordinate_search(
+      shape, h->np > 0, steps_per_trial,
+      [&](const LaunchShape &l) {
+        lbm_launch_shape c = to_c(l);
+        return lbm_set_launch_shape(h, &c);
+      },
+      [&](int k) { return lbm_step(h, k, n_ibm_iter); },
+      [&](int mask) { return lbm_enable_timing(h, mask); },
+      [&](int mask, double *ms) { return read_stage_ms(h, mask, ms); });
+  h->graph_on = graph;
+  const int r2 = snapshot_restore(h, sn);
+  snapshot_free(sn);
+  if (r) return r;
+  if (r2) return r2;
+  if (chosen) *chosen = to_c(h->shape);
+  return LBM_OK;
+}
+
+int lbm_batch_get_launch_shape(lbm_batch_t *b, lbm_launch_shape *out) {
+  if (!b || !out) return LBM_EINVAL;
+  *out = to_c(b->shape);
+  return LBM_OK;
+}
+
+int lbm_batch_set_launch_shape(lbm_batch_t *b, const lbm_launch_shape *s) {
+  if (!b || !s) return LBM_EINVAL;
+  if (!shape_ok(*s)) return fail(b->hs[0], LBM_EINVAL, "launch shape out of range");
+  b->shape = from_c(*s);
+  b->shape_version++;
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch_t *b, int n_ibm_iter, int steps_per_trial,
+                       lbm_launch_shape *chosen) {
+  if (!b) return LBM_EINVAL;
+  lbm_t *h0 = b->hs[0];
+  if (n_ibm_iter <= 0 || steps_per_trial < 1)
+    return fail(h0, LBM_EINVAL, "autotune needs n_ibm_iter > 0 and steps_per_trial >= 1");
+  std::vector<Snapshot> sn(b->hs.size());
+  int r = LBM_OK;
+  for (size_t i = 0; i < b->hs.size() && r == LBM_OK; i++) r = snapshot_take(b->hs[i], sn[i]);
+  bool points = false;
+  for (lbm_t *h : b->hs) points = points || h->np > 0;
+  const bool graph = b->graph_on;
+  b->graph_on = false;
+  LaunchShape shape = b->shape;
+  // whole batch steps, timed with events on the first handle's stream
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float last_ms = 0.f;
+  if (r == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    r = fail(h0, LBM_ECUDA, "event creation");
+  bool timing = false;
+  if (r == LBM_OK)
+    r = coordinate_search(
+        shape, points, steps_per_trial,
+        [&](const LaunchShape &l) {
+          lbm_launch_shape c = to_c(l);
+          return lbm_batch_set_launch_shape(b, &c);
+        },
+        [&](int k) {
+          if (timing) cudaEventRecord(e0, h0->st);
+          const int rr = lbm_batch_step(b, k, n_ibm_iter);
+          if (timing) cudaEventRecord(e1, h0->st);
+          return rr;
+        },
+        [&](int mask) {
+          timing = mask != 0;
+          return LBM_OK;
+        },
+        [&](int, double *ms) {
+          CK(h0, cudaEventSynchronize(e1));
+          CK(h0, cudaEventElapsedTime(&last_ms, e0, e1));
+          *ms = last_ms;
+          return LBM_OK;
+        });
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->graph_on = graph;
+  int r2 = LBM_OK;
+  for (size_t i = 0; i < b->hs.size(); i++) {
+    if (sn[i].f) {
+      const int ri = snapshot_restore(b->hs[i], sn[i]);
+      if (ri && !r2) r2 = ri;
+    }
+    snapshot_free(sn[i]);
+  }
+  if (r) return r;
+  if (r2) return r2;
+  if (chosen) *chosen = to_c(b->shape);
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 int lbm_read_fields_dev(lbm_t *h, float *rho, float *U, float *G) {
   if (!h) return LBM_EINVAL;

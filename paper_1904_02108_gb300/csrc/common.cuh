@@ -214,8 +214,8 @@ struct DomainDesc {
   const double *centre, *omega, *phase;
   double *trig;       // [nb][4]
   int nb;
-  int cblocks;        // blocks of the collide kernel for this domain, one
-                      // per 256 cells (one FP64 partial each)
+  int cblocks;        // FP64 partial sums of the collide kernel, one per
+                      // PARTIAL_CELLS cells
   PointPrep pp;
   BrickMap m;
   PairMap pm;
@@ -231,6 +231,26 @@ struct DomainDesc {
   const void *mlp_packed;
 };
 
+// Launch shapes of the step kernels, picked by the autotuner (lbm_autotune).
+// None changes a result: they only spread the same work over the GPU
+// differently (the collide kernel's FP64 partial sums stay one per 128 cells
+// whatever its block size).
+struct LaunchShape {
+  int collide_block = 256;       // threads per block of the collide-stream
+                                 // kernel: 128 or 256
+  int brick_blocks = 152 * 16;   // grid of the brick kernels (grid-stride
+                                 // over the active bricks, 64 threads each)
+  int point_block = 256;         // threads per block of the per-point
+                                 // kernels: 128, 256 or 512
+  int moments_spb = 4;           // bricks per block of the moments kernel
+                                 // (64 threads each): 1, 2 or 4
+  int sort_blocks = 152 * 32;    // grid of the sort kernel (a warp per slot,
+                                 // four per block)
+};
+
+// Cells per FP64 partial sum of the collide kernel.
+constexpr int PARTIAL_CELLS = 128;
+
 // Grid extents of a batch: the largest domain along each work dimension.
 struct BatchDims {
   int nd;              // domains (gridDim.y)
@@ -239,6 +259,7 @@ struct BatchDims {
   int max_bodies;
   int max_bricks;
   int max_slots;
+  LaunchShape ls;
 };
 
 }  // namespace lbmibm

@@ -140,7 +140,7 @@ __global__ void body_trig_kernel(const DomainDesc *__restrict__ D) {
   o[3] = 2.0 * cm * sh;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512, 2)
     prepare_points_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
   pdl_launch_dependents();
@@ -362,7 +362,7 @@ __device__ __forceinline__ int active_slots(const BrickMap &m) {
   return n < m.max_slots ? n : m.max_slots;
 }
 
-__global__ void pair_fill_kernel(const DomainDesc *__restrict__ D) {
+__global__ void __launch_bounds__(512) pair_fill_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
   pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(128)
 // point's tap weights at the brick's cells 0..3 along each axis, 0 outside
 // the support, periodic offsets resolved) and the pair's entry in the point's
 // list of bricks.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     pair_weights_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
   pdl_launch_dependents();
@@ -644,7 +644,7 @@ __device__ __forceinline__ void store_F(BrickSmem &sm, float fx, float fy, float
 
 // U0 on every cell of every active brick: pull of Eq. 4 and Eq. 1 (the
 // paper's kernel strategy of Sec. 5 without duplicated cells).  One thread per
-// cell, four bricks per 256-thread block.
+// cell, 64 threads per brick, blockDim.x / 64 bricks per block.
 template <typename S>
 __global__ void __launch_bounds__(256)
     brick_moments_kernel(const DomainDesc *__restrict__ D, int cur) {
@@ -656,8 +656,8 @@ __global__ void __launch_bounds__(256)
   const BrickMap m = d.m;
   float *__restrict__ U0s = d.U0s;
   const int nslots = active_slots(m);
-  const int t = threadIdx.x & 63;
-  for (int s = blockIdx.x * 4 + (threadIdx.x >> 6); s < nslots; s += gridDim.x * 4) {
+  const int t = threadIdx.x & 63, spb = blockDim.x >> 6;
+  for (int s = blockIdx.x * spb + (threadIdx.x >> 6); s < nslots; s += gridDim.x * spb) {
     const int B = m.slot_brick[s];
     const int bx = B % g.nbx, rr = B / g.nbx;
     const int by = rr % g.nby, bz = rr / g.nby;
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__rest
 
 // Alg. 1 loop body per point: u_n(k) = sum of its bricks' shares (brick order),
 // g = u_k - u_n, du += s g (du starts at 0 when first && !warm).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     point_update_kernel(const DomainDesc *__restrict__ D, int first, int warm, int tol_mode) {
   pdl_wait();
   pdl_launch_dependents();
@@ -873,7 +873,7 @@ __global__ void __launch_bounds__(256)
 
 // s(k) (u_k - u(k)) with u(k) the sum of the point's pair shares: the
 // first increment from a zero start, for the fallback residual denominator.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     point_residual0_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
   pdl_launch_dependents();
@@ -911,7 +911,7 @@ __global__ void __launch_bounds__(256)
 //   10-12 body-relative rest position: radius and axial offset from the
 //        body's axis, and the speed omega r (0 without bodies)
 //   13-15 u_k - u_i, the slip left by the previous force
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
     mlp_features_kernel(const DomainDesc *__restrict__ D, int use_prev) {
   pdl_wait();
   pdl_launch_dependents();
@@ -1060,20 +1060,24 @@ inline unsigned xblocks(int64_t want, int nd, int cap) {
 template <typename S>
 cudaError_t brick_moments_typed(const DomainDesc *D, const BatchDims &dims, int cur,
                                 cudaStream_t st) {
-  const dim3 grid(xblocks((dims.max_slots + 3) / 4, dims.nd, PERSISTENT_BLOCKS / 2), dims.nd);
-  return launch_pdl(brick_moments_kernel<S>, grid, dim3(256), 0, st, D, cur);
+  const int spb = dims.ls.moments_spb;
+  if (spb != 1 && spb != 2 && spb != 4) return cudaErrorInvalidValue;
+  const dim3 grid(xblocks((dims.max_slots + spb - 1) / spb, dims.nd, 152 * 64 / spb), dims.nd);
+  return launch_pdl(brick_moments_kernel<S>, grid, dim3(64 * spb), 0, st, D, cur);
 }
 
 }  // namespace
 
 cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
+  const int pb = dims.ls.point_block;
+  if (pb != 128 && pb != 256 && pb != 512) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (dims.max_bodies > 0)
     e = launch_pdl(body_trig_kernel, dim3(nblk(dims.max_bodies, 128), dims.nd), dim3(128), 0, st,
                    D);
   if (e != cudaSuccess) return e;
-  return launch_pdl(prepare_points_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0,
+  return launch_pdl(prepare_points_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0,
                     st, D);
 }
 
@@ -1081,16 +1085,17 @@ cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaS
   cudaError_t e = launch_pdl(compact_kernel, dim3(nblk(dims.max_bricks, COMPACT_TILE), dims.nd),
                              dim3(256), 0, st, D);
   if (e == cudaSuccess && dims.max_points > 0) {
-    e = launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0, st,
-                     D);
+    const int pb = dims.ls.point_block;
+    e = launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0, st, D);
     // one warp per slot
     if (e == cudaSuccess)
       e = launch_pdl(pair_sort_kernel,
-                     dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, 152 * 32), dims.nd), dim3(128),
-                     0, st, D);
+                     dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, dims.ls.sort_blocks),
+                          dims.nd),
+                     dim3(128), 0, st, D);
     if (e == cudaSuccess)
-      e = launch_pdl(pair_weights_kernel, dim3(nblk(8 * (int64_t)dims.max_points, 256), dims.nd),
-                     dim3(256), 0, st, D);
+      e = launch_pdl(pair_weights_kernel, dim3(nblk(8 * (int64_t)dims.max_points, pb), dims.nd),
+                     dim3(pb), 0, st, D);
   }
   return e;
 }
@@ -1113,7 +1118,7 @@ cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDi
 }
 
 static dim3 brick_grid(const BatchDims &dims) {
-  return dim3(xblocks(dims.max_slots, dims.nd, PERSISTENT_BLOCKS), dims.nd);
+  return dim3(xblocks(dims.max_slots, dims.nd, dims.ls.brick_blocks), dims.nd);
 }
 
 cudaError_t launch_brick_init(const DomainDesc *D, const BatchDims &dims, int use_du,
@@ -1129,8 +1134,9 @@ cudaError_t launch_brick_spread(const DomainDesc *D, const BatchDims &dims, int 
 cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int first, int warm,
                                 int tol_mode, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
-  return launch_pdl(point_update_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0,
-                    st, D, first, warm, tol_mode);
+  const int pb = dims.ls.point_block;
+  return launch_pdl(point_update_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0, st,
+                    D, first, warm, tol_mode);
 }
 
 cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,
@@ -1149,15 +1155,17 @@ cudaError_t launch_ibm_check(const DomainDesc *D, const BatchDims &dims, int it,
 
 cudaError_t launch_point_residual0(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
-  return launch_pdl(point_residual0_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256),
-                    0, st, D);
+  const int pb = dims.ls.point_block;
+  return launch_pdl(point_residual0_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0,
+                    st, D);
 }
 
 cudaError_t launch_mlp_features(const DomainDesc *D, const BatchDims &dims, int use_prev,
                                 cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
-  return launch_pdl(mlp_features_kernel, dim3(nblk(dims.max_points, 256), dims.nd), dim3(256), 0,
-                    st, D, use_prev);
+  const int pb = dims.ls.point_block;
+  return launch_pdl(mlp_features_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0, st,
+                    D, use_prev);
 }
 
 cudaError_t launch_mlp_targets(int64_t np, const float *X, const float4 *du, float *T,

@@ -19,7 +19,8 @@ cudaError_t launch_collide_stream(int storage, const DomainDesc *D, const Domain
 // stats) and t += 1 of every domain (one block per domain).
 cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats,
                                cudaStream_t st);
-int collide_blocks(const Geometry &g);
+// FP64 partial sums per step of a lattice (one per PARTIAL_CELLS cells)
+int collide_partials(const Geometry &g);
 // rho[N], U[3][N] on every cell (either may be NULL).
 cudaError_t launch_moments_dense(int storage, const Geometry &g, const void *f, float *rho,
                                  float *U, cudaStream_t st);

@@ -83,6 +83,8 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
       spy += __shfl_xor_sync(0xffffffffu, spy, o);
       spz += __shfl_xor_sync(0xffffffffu, spz, o);
     }
+    // one partial per PARTIAL_CELLS cells (four warps), whatever the block
+    // size: the sums do not depend on the launch shape
     __shared__ double red[8][4];
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
@@ -92,16 +94,17 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
       red[w][3] = spz;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
-      double a = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); k++) a += red[k][threadIdx.x];
-      partial[(size_t)blockIdx.x * 4 + threadIdx.x] = a;
+    const int groups = blockDim.x / PARTIAL_CELLS;
+    if ((int)threadIdx.x < 4 * groups) {
+      const int gi = threadIdx.x >> 2, c = threadIdx.x & 3;
+      const double a = ((red[4 * gi][c] + red[4 * gi + 1][c]) + red[4 * gi + 2][c]) +
+                       red[4 * gi + 3][c];
+      const int64_t pidx = (int64_t)blockIdx.x * groups + gi;
+      if (pidx < dd.cblocks) partial[(size_t)pidx * 4 + c] = a;
     }
   }
 }
 
-// Deterministic two-level FP64 reduction: each block sums a fixed strided
-// subset, the last block to finish sums the block results in index order.
 template <typename S, bool STATS>
 __global__ void __launch_bounds__(256)
     collide_stream_kernel(const __grid_constant__ DomainDesc dd, int cur) {
@@ -254,17 +257,19 @@ inline unsigned cell_blocks(const Geometry &g, int threads) {
 template <typename S>
 cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const BatchDims &dims,
                           int cur, int stats, cudaStream_t st) {
-  const dim3 grid((unsigned)((dims.max_cells + 255) / 256), dims.nd);
+  const int bs = dims.ls.collide_block;
+  if (bs != 128 && bs != 256) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((dims.max_cells + bs - 1) / bs), dims.nd), block(bs);
   if (dims.nd == 1 && Dhost)
-    return stats ? launch_pdl(collide_stream_kernel<S, true>, grid, dim3(256), 0, st, *Dhost, cur)
-                 : launch_pdl(collide_stream_kernel<S, false>, grid, dim3(256), 0, st, *Dhost, cur);
-  return stats ? launch_pdl(collide_stream_batch_kernel<S, true>, grid, dim3(256), 0, st, D, cur)
-               : launch_pdl(collide_stream_batch_kernel<S, false>, grid, dim3(256), 0, st, D, cur);
+    return stats ? launch_pdl(collide_stream_kernel<S, true>, grid, block, 0, st, *Dhost, cur)
+                 : launch_pdl(collide_stream_kernel<S, false>, grid, block, 0, st, *Dhost, cur);
+  return stats ? launch_pdl(collide_stream_batch_kernel<S, true>, grid, block, 0, st, D, cur)
+               : launch_pdl(collide_stream_batch_kernel<S, false>, grid, block, 0, st, D, cur);
 }
 
 }  // namespace
 
-int collide_blocks(const Geometry &g) { return (int)cell_blocks(g, 256); }
+int collide_partials(const Geometry &g) { return (int)cell_blocks(g, PARTIAL_CELLS); }
 
 #define DISPATCH_STORAGE(storage, FN, ...)                      \
   switch (storage) {                                            \

@@ -1,0 +1,100 @@
+"""Launch shapes and the autotuner: no result depends on the launch shape
+(populations, point corrections and FP64 sums are bitwise equal under any
+shape), and autotuning leaves the lattice exactly where it was."""
+import numpy as np
+import pytest
+
+from paper_1904_02108_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+OTHER = dict(collide_block=128, brick_blocks=152 * 8, point_block=512, moments_spb=1,
+             sort_blocks=152 * 8)
+WIDE = dict(collide_block=256, brick_blocks=152 * 32, point_block=128, moments_spb=2,
+            sort_blocks=152 * 64)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _pair_lattice(gpu_lib, torch, **kw):
+    w = W.propellers([(12.0, 20.0, 14.0), (34.0, 20.0, 30.0)], 8.0, 2.0, 0.04, [0.3, 1.9])
+    lat = gpu_lib.Lattice((44, 40, 48), 0.7, stream=torch.cuda.current_stream(), **kw)
+    lat.set_propellers(w)
+    return lat
+
+
+def _same(a, b):
+    assert np.array_equal(a.populations(), b.populations())
+    sa, sb = a.stats(), b.stats()
+    assert sa["step"] == sb["step"]
+    assert sa["mass"] == sb["mass"] and sa["momentum"] == sb["momentum"]
+    assert np.array_equal(a.points()[2], b.points()[2])
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("shape", [OTHER, WIDE])
+def test_results_do_not_depend_on_the_launch_shape(gpu_lib, torch_cuda, storage, shape):
+    a = _pair_lattice(gpu_lib, torch_cuda, storage=storage, warm="previous")
+    b = _pair_lattice(gpu_lib, torch_cuda, storage=storage, warm="previous")
+    b.set_launch_shape(**shape)
+    assert b.launch_shape() == {**a.launch_shape(), **shape}
+    a.step(7, 5)
+    b.step(7, 5)
+    _same(a, b)
+    for lat in (a, b):
+        lat.close()
+
+
+def test_autotune_leaves_the_lattice_unchanged(gpu_lib, torch_cuda):
+    a = _pair_lattice(gpu_lib, torch_cuda, warm="previous")
+    b = _pair_lattice(gpu_lib, torch_cuda, warm="previous")
+    a.step(3, 5)
+    b.step(3, 5)
+    chosen = a.autotune(n_ibm_iter=5, steps_per_trial=2)
+    assert a.launch_shape() == chosen
+    assert chosen["collide_block"] in (128, 256)
+    assert chosen["moments_spb"] in (1, 2, 4)
+    assert a.stats()["step"] == 3
+    a.step(4, 5)
+    b.step(4, 5)
+    _same(a, b)
+    for lat in (a, b):
+        lat.close()
+
+
+def test_launch_shape_rejects_values_out_of_range(gpu_lib, torch_cuda):
+    lat = _pair_lattice(gpu_lib, torch_cuda)
+    for bad in (dict(collide_block=512), dict(point_block=1024), dict(moments_spb=8),
+                dict(brick_blocks=0), dict(sort_blocks=-1)):
+        with pytest.raises(gpu_lib.LbmError):
+            lat.set_launch_shape(**bad)
+    lat.close()
+
+
+def test_batch_autotune_keeps_batch_equal_to_single_stepping(gpu_lib, torch_cuda):
+    torch = torch_cuda
+    specs = [W.single_propeller(7), W.single_propeller(8)]
+    mk = lambda w: gpu_lib.Lattice(w.shape, w.tau, warm="previous",
+                                   stream=torch.cuda.current_stream())
+    single = [mk(w) for w in specs]
+    batched = [mk(w) for w in specs]
+    for lat, w in zip(single + batched, specs + specs):
+        lat.set_propellers(w.props)
+    for lat in single:
+        lat.step(5, 5)
+    batch = gpu_lib.Batch(batched)
+    batch.step(2, 5)
+    chosen = batch.autotune(n_ibm_iter=5, steps_per_trial=2)
+    assert batch.launch_shape() == chosen
+    batch.step(3, 5)
+    for s, b in zip(single, batched):
+        _same(s, b)
+    batch.close()
+    for lat in single + batched:
+        lat.close()
