@@ -63,7 +63,7 @@ struct lbm {
   double *X = nullptr;
   int *body = nullptr;
   float *area = nullptr, *utarget = nullptr;
-  double *centre = nullptr, *omega = nullptr, *phase = nullptr, *trig = nullptr;
+  double *centre = nullptr, *omega = nullptr, *phase = nullptr;
   PointPrep pp{};
   BrickMap m{};
   PairMap pm{};
@@ -80,6 +80,7 @@ struct lbm {
   int nparts = 0;
   bool sums_valid = false;
   int last_iters = 0;
+  int tol_hint = 0;  // iterations of the last tolerance-mode step
   double last_eps = -1.0;
   int64_t not_converged = 0;
   IbmState *state = nullptr;       // device
@@ -291,7 +292,6 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->centre);
   dfree(h->omega);
   dfree(h->phase);
-  dfree(h->trig);
   dfree(h->m.brick_count);
   dfree(h->m.brick_slot);
   dfree(h->m.counters);
@@ -501,11 +501,9 @@ int ibm_set_bodies(lbm_t *h, int nb, const double *centre, const double *omega,
   dfree(h->centre);
   dfree(h->omega);
   dfree(h->phase);
-  dfree(h->trig);
   h->nb = nb;
   h->desc_dirty = true;
   if (nb > 0) {
-    CK(h, dalloc(&h->trig, 4 * nb));
     CK(h, dalloc(&h->centre, 3 * nb));
     CK(h, dalloc(&h->omega, nb));
     CK(h, dalloc(&h->phase, nb));
@@ -556,7 +554,6 @@ static DomainDesc host_desc(const lbm_t *h) {
   d.centre = h->centre;
   d.omega = h->omega;
   d.phase = h->phase;
-  d.trig = h->trig;
   d.nb = h->nb;
   d.cblocks = h->nparts;
   d.pp = h->pp;
@@ -623,11 +620,11 @@ static int enqueue_prefix(StepCtx &c, bool *warm_out) {
   const bool warm = (c.warm_mode == LBM_WARM_PREVIOUS && c.have_du) || mlp;
   *warm_out = warm;
   {
-    StageTimer T(h, ST_KIN, c.dims.max_bodies > 0 ? 2 : 1);
+    StageTimer T(h, ST_KIN, 1);
     CK(h, launch_prepare_points(c.D, c.dims, c.st));
   }
   {
-    StageTimer T(h, ST_PAIRS, 4);
+    StageTimer T(h, ST_PAIRS, 3);
     CK(h, launch_build_pairs(c.D, c.dims, c.st));
   }
   {
@@ -717,8 +714,11 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     if (warm) CK(h, launch_brick_init(c.D, c.dims, 1, st));
   }
   int it = 0;
+  // the first chunk runs about as many iterations as the previous step took
+  // (the kernels of iterations past convergence return at once)
+  int chunk0 = std::max(kCheckChunk, h->tol_hint - kCheckChunk / 4);
   while (it < h->max_iter) {
-    const int chunk = std::min(kCheckChunk, h->max_iter - it);
+    const int chunk = std::min(it == 0 ? chunk0 : kCheckChunk, h->max_iter - it);
     for (int j = 0; j < chunk; j++, it++) {
       {
         StageTimer T(h, ST_UPDATE);
@@ -738,6 +738,7 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     if (h->state_host->done) break;
   }
   h->last_iters = h->state_host->iters;
+  h->tol_hint = h->last_iters;
   h->last_eps = h->state_host->last_eps;
   if (h->state_host->capped) {
     h->not_converged++;

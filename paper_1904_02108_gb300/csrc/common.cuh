@@ -212,7 +212,6 @@ struct DomainDesc {
   const float *area;  // [np]
   const float *utarget;  // [np][3]
   const double *centre, *omega, *phase;
-  double *trig;       // [nb][4]
   int nb;
   int cblocks;        // FP64 partial sums of the collide kernel, one per
                       // PARTIAL_CELLS cells

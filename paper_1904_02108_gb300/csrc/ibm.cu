@@ -6,7 +6,7 @@
 //                   brick its number of overlapping supports
 //   compact         bricks with a count -> slots of the sparse force storage,
 //                   in brick order, and each slot's first pair (one scan)
-//   pair_fill/sort/weights
+//   pair_fill/sort
 //                   one pair per (brick, point) with the point's support
 //                   overlapping the brick, grouped by brick, ascending point
 //                   index, with the brick-local weights of the point
@@ -22,6 +22,7 @@
 // partial sums combined in a fixed order, a point's shares in brick order), so
 // results are bitwise reproducible, unlike the atomicAdd scatter of Alg. 2.
 #include <algorithm>
+#include <climits>
 
 #include "kernels.h"
 #include "lattice.cuh"
@@ -114,18 +115,14 @@ __device__ __forceinline__ void for_support_bricks(const Geometry &g, int4 b, Fn
         fn(((c ? sz.hi : sz.lo) * g.nby + (a ? sy.hi : sy.lo)) * g.nbx + (e ? sx.hi : sx.lo));
 }
 
-// Per body, once per step: cos/sin of phi(t) = phase + omega t and the
-// differences cos phi(t) - cos phi(t-1), sin phi(t) - sin phi(t-1), the latter
-// without cancellation as -2 sin(phi - omega/2) sin(omega/2) and
-// 2 cos(phi - omega/2) sin(omega/2).
-__global__ void body_trig_kernel(const DomainDesc *__restrict__ D) {
-  pdl_wait();
-  pdl_launch_dependents();
-  const DomainDesc &d = D[blockIdx.y];
-  const Bodies bd{d.centre, d.omega, d.phase, d.nb, d.trig};
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= bd.nb) return;
-  const int64_t t = *d.t;
+// cos phi, sin phi and the differences cos phi - cos(phi - omega),
+// sin phi - sin(phi - omega) of a body with phi = phase + omega t, in FP64;
+// the differences as -2 sin(phi - omega/2) sin(omega/2) and
+// 2 cos(phi - omega/2) sin(omega/2), without cancellation.
+struct Trig {
+  double cs, sn, dc, ds;
+};
+__device__ __forceinline__ Trig body_trig(const Bodies &bd, int b, int64_t t) {
   const double om = bd.omega[b];
   const double phi = bd.phase[b] + om * (double)t;
   double sn, cs, sh, ch;
@@ -133,12 +130,13 @@ __global__ void body_trig_kernel(const DomainDesc *__restrict__ D) {
   sincos(0.5 * om, &sh, &ch);
   // phi - omega/2 by the angle-difference formulas
   const double sm = sn * ch - cs * sh, cm = cs * ch + sn * sh;
-  double *o = bd.trig + 4 * b;
-  o[0] = cs;
-  o[1] = sn;
-  o[2] = -2.0 * sm * sh;
-  o[3] = 2.0 * cm * sh;
+  return {cs, sn, -2.0 * sm * sh, 2.0 * cm * sh};
 }
+
+// Bodies whose rotation a block of prepare_points computes once in shared
+// memory (the points of a block are consecutive and belong to few bodies);
+// a block whose points span more takes them per point.
+constexpr int TRIG_CACHE = 16;
 
 __global__ void __launch_bounds__(512, 2)
     prepare_points_kernel(const DomainDesc *__restrict__ D) {
@@ -148,7 +146,7 @@ __global__ void __launch_bounds__(512, 2)
   const Geometry g = d.g;
   const int delta = d.delta;
   const PointsIn p{d.np, d.X, d.body, d.area, d.utarget};
-  const Bodies bd{d.centre, d.omega, d.phase, d.nb, d.trig};
+  const Bodies bd{d.centre, d.omega, d.phase, d.nb};
   const PointPrep pp = d.pp;
   const BrickMap m = d.m;
   const PairMap pm = d.pm;
@@ -158,17 +156,43 @@ __global__ void __launch_bounds__(512, 2)
     m.counters[0] = 0;
     m.counters[1] = 0;
   }
-  if (k >= p.np) return;
+  const bool in = k < p.np;
+  const int body = (bd.nb > 0 && in) ? (p.body ? p.body[k] : 0) : -1;
+  __shared__ Trig strig[TRIG_CACHE];
+  __shared__ int sb_lo, sb_hi;
+  int b0 = 0, nbk = 0;
+  int64_t tstep = 0;
+  if (bd.nb > 0) {
+    // the block's range of bodies, and their rotation once per block
+    const int lo = __reduce_min_sync(0xffffffffu, in ? body : INT_MAX);
+    const int hi = __reduce_max_sync(0xffffffffu, in ? body : -1);
+    if (threadIdx.x == 0) {
+      sb_lo = INT_MAX;
+      sb_hi = -1;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&sb_lo, lo);
+      atomicMax(&sb_hi, hi);
+    }
+    __syncthreads();
+    b0 = sb_lo;
+    nbk = sb_hi >= 0 ? sb_hi - sb_lo + 1 : 0;
+    tstep = *d.t;
+    if (nbk <= TRIG_CACHE && (int)threadIdx.x < nbk)
+      strig[threadIdx.x] = body_trig(bd, b0 + threadIdx.x, tstep);
+    __syncthreads();
+  }
+  if (!in) return;
   double x[3];
   float u[3];
   const double *X = p.X + 3 * k;
   if (bd.nb > 0) {
     // Alg. 1, first iteration: x(t) = M(t) [x_rest, 1], u_k = x(t) - x(t-1)
-    const int b = p.body ? p.body[k] : 0;
+    const int b = body;
     const double *c = bd.centre + 3 * b;
-    const double2 t0 = *(const double2 *)(bd.trig + 4 * b);
-    const double2 t1 = *(const double2 *)(bd.trig + 4 * b + 2);
-    const double cs = t0.x, sn = t0.y, dc = t1.x, ds = t1.y;
+    const Trig tr = nbk <= TRIG_CACHE ? strig[b - b0] : body_trig(bd, b, tstep);
+    const double cs = tr.cs, sn = tr.sn, dc = tr.dc, ds = tr.ds;
     const double rx = X[0] - c[0], ry = X[1] - c[1], rz = X[2] - c[2];
     x[0] = c[0] + (cs * rx - sn * ry);
     x[1] = c[1] + (sn * rx + cs * ry);
@@ -380,10 +404,57 @@ __global__ void __launch_bounds__(512) pair_fill_kernel(const DomainDesc *__rest
   });
 }
 
+// Pair p (point k, brick B, after the sort): the brick-local weights of its
+// point (the point's tap weights at the brick's cells 0..3 along each axis, 0
+// outside the support, periodic offsets resolved) and the pair's entry in the
+// point's list of bricks.
+__device__ __forceinline__ void pair_weights(const Geometry &g, const PointPrep &pp,
+                                             const PairMap &pm, int64_t p, int k, int B) {
+  const int bxb = B % g.nbx, rr = B / g.nbx;
+  const int byb = rr % g.nby, bzb = rr / g.nby;
+  const int X0 = bxb * 4, Y0 = byb * 4, Z0 = bzb * 4;
+  const int4 b = pp.base[k];
+  const float4 *wp = (const float4 *)(pp.wts + 12 * (int64_t)k);
+  const float4 w0 = wp[0], w1 = wp[1], w2 = wp[2];
+  const float wx[4] = {w0.x, w0.y, w0.z, w0.w};
+  const float wy[4] = {w1.x, w1.y, w1.z, w1.w};
+  const float wz[4] = {w2.x, w2.y, w2.z, w2.w};
+  float lx[4], ly[4], lz[4];
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    // tap index of the brick's cell c along each axis (periodic), or none
+    int dx = X0 + c - b.x + 1;
+    dx = dx < 0 ? dx + g.nx : (dx >= g.nx ? dx - g.nx : dx);
+    int dy = Y0 + c - b.y + 1;
+    dy = dy < 0 ? dy + g.ny : (dy >= g.ny ? dy - g.ny : dy);
+    int dz = Z0 + c - b.z + 1;
+    dz = dz < 0 ? dz + g.nz : (dz >= g.nz ? dz - g.nz : dz);
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      vx = dx == e ? wx[e] : vx;
+      vy = dy == e ? wy[e] : vy;
+      vz = dz == e ? wz[e] : vz;
+    }
+    lx[c] = vx;
+    ly[c] = vy;
+    lz[c] = vz;
+  }
+  pm.w[3 * p] = make_float4(lx[0], lx[1], lx[2], lx[3]);
+  pm.w[3 * p + 1] = make_float4(ly[0], ly[1], ly[2], ly[3]);
+  pm.w[3 * p + 2] = make_float4(lz[0], lz[1], lz[2], lz[3]);
+  const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
+                      sz = support_bricks(b.z, g.nz);
+  const int j = (sx.hi != sx.lo && bxb == sx.hi ? 1 : 0) |
+                (sy.hi != sy.lo && byb == sy.hi ? 2 : 0) |
+                (sz.hi != sz.lo && bzb == sz.hi ? 4 : 0);
+  pm.point_pairs[8 * (size_t)k + j] = (int)p;
+}
+
 // One warp per slot: sort the slot's points ascending (in registers up to 128
 // pairs, bitonic in shared memory up to SORT_CAP, else a rank sort through
 // this slot's not yet written weight storage; the points of a slot are
-// distinct) and record the slot's brick with each pair.
+// distinct), then record with each pair its brick and brick-local weights.
 constexpr int SORT_CAP = 512;
 
 __global__ void __launch_bounds__(128)
@@ -393,6 +464,8 @@ __global__ void __launch_bounds__(128)
   __shared__ int buf[4][SORT_CAP];
   const BrickMap m = D[blockIdx.y].m;
   const PairMap pm = D[blockIdx.y].pm;
+  const PointPrep pp = D[blockIdx.y].pp;
+  const Geometry g = D[blockIdx.y].g;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nslots = active_slots(m);
   for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
@@ -455,67 +528,13 @@ __global__ void __launch_bounds__(128)
     }
     __syncwarp();
     const int B = m.slot_brick[s];
-    for (int i = lane; i < cnt; i += 32) pm.brick[st + i] = B;
+    for (int i = lane; i < cnt; i += 32) {
+      pm.brick[st + i] = B;
+      pair_weights(g, pp, pm, (int64_t)st + i, a[i], B);
+    }
   }
 }
 
-// Per pair (after the sort): the brick-local weights of its point (the
-// point's tap weights at the brick's cells 0..3 along each axis, 0 outside
-// the support, periodic offsets resolved) and the pair's entry in the point's
-// list of bricks.
-__global__ void __launch_bounds__(512)
-    pair_weights_kernel(const DomainDesc *__restrict__ D) {
-  pdl_wait();
-  pdl_launch_dependents();
-  const DomainDesc &d = D[blockIdx.y];
-  if (d.np == 0) return;
-  const Geometry g = d.g;
-  const PointPrep pp = d.pp;
-  const BrickMap m = d.m;
-  const PairMap pm = d.pm;
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= pm.start[active_slots(m)]) return;
-  const int k = pm.k[p], B = pm.brick[p];
-  const int bxb = B % g.nbx, rr = B / g.nbx;
-  const int byb = rr % g.nby, bzb = rr / g.nby;
-  const int X0 = bxb * 4, Y0 = byb * 4, Z0 = bzb * 4;
-  const int4 b = pp.base[k];
-  const float4 *wp = (const float4 *)(pp.wts + 12 * (int64_t)k);
-  const float4 w0 = wp[0], w1 = wp[1], w2 = wp[2];
-  const float wx[4] = {w0.x, w0.y, w0.z, w0.w};
-  const float wy[4] = {w1.x, w1.y, w1.z, w1.w};
-  const float wz[4] = {w2.x, w2.y, w2.z, w2.w};
-  float lx[4], ly[4], lz[4];
-#pragma unroll
-  for (int c = 0; c < 4; c++) {
-    // tap index of the brick's cell c along each axis (periodic), or none
-    int dx = X0 + c - b.x + 1;
-    dx = dx < 0 ? dx + g.nx : (dx >= g.nx ? dx - g.nx : dx);
-    int dy = Y0 + c - b.y + 1;
-    dy = dy < 0 ? dy + g.ny : (dy >= g.ny ? dy - g.ny : dy);
-    int dz = Z0 + c - b.z + 1;
-    dz = dz < 0 ? dz + g.nz : (dz >= g.nz ? dz - g.nz : dz);
-    float vx = 0.f, vy = 0.f, vz = 0.f;
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      vx = dx == e ? wx[e] : vx;
-      vy = dy == e ? wy[e] : vy;
-      vz = dz == e ? wz[e] : vz;
-    }
-    lx[c] = vx;
-    ly[c] = vy;
-    lz[c] = vz;
-  }
-  pm.w[3 * p] = make_float4(lx[0], lx[1], lx[2], lx[3]);
-  pm.w[3 * p + 1] = make_float4(ly[0], ly[1], ly[2], ly[3]);
-  pm.w[3 * p + 2] = make_float4(lz[0], lz[1], lz[2], lz[3]);
-  const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
-                      sz = support_bricks(b.z, g.nz);
-  const int j = (sx.hi != sx.lo && bxb == sx.hi ? 1 : 0) |
-                (sy.hi != sy.lo && byb == sy.hi ? 2 : 0) |
-                (sz.hi != sz.lo && bzb == sz.hi ? 4 : 0);
-  pm.point_pairs[8 * (size_t)k + j] = (int)p;
-}
 
 // ---- the brick kernels: one 64-thread block per active brick ----------------
 
@@ -923,7 +942,7 @@ __global__ void __launch_bounds__(512)
   const BrickMap m = d.m;
   const float4 *__restrict__ du_prev = use_prev ? d.du : nullptr;
   const PointsIn p{d.np, d.X, d.body, d.area, d.utarget};
-  const Bodies bd{d.centre, d.omega, d.phase, d.nb, d.trig};
+  const Bodies bd{d.centre, d.omega, d.phase, d.nb};
   float *__restrict__ X = d.feat;
   const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
   const int4 a = pk[0], b = pk[1];
@@ -1072,11 +1091,6 @@ cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cu
   if (dims.max_points <= 0) return cudaSuccess;
   const int pb = dims.ls.point_block;
   if (pb != 128 && pb != 256 && pb != 512) return cudaErrorInvalidValue;
-  cudaError_t e = cudaSuccess;
-  if (dims.max_bodies > 0)
-    e = launch_pdl(body_trig_kernel, dim3(nblk(dims.max_bodies, 128), dims.nd), dim3(128), 0, st,
-                   D);
-  if (e != cudaSuccess) return e;
   return launch_pdl(prepare_points_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0,
                     st, D);
 }
@@ -1093,9 +1107,7 @@ cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaS
                      dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, dims.ls.sort_blocks),
                           dims.nd),
                      dim3(128), 0, st, D);
-    if (e == cudaSuccess)
-      e = launch_pdl(pair_weights_kernel, dim3(nblk(8 * (int64_t)dims.max_points, pb), dims.nd),
-                     dim3(pb), 0, st, D);
+
   }
   return e;
 }
@@ -1152,6 +1164,7 @@ cudaError_t launch_ibm_check(const DomainDesc *D, const BatchDims &dims, int it,
                              int max_iter, cudaStream_t st) {
   return launch_pdl(ibm_check_kernel, dim3(1, dims.nd), dim3(256), 0, st, D, it, tol, max_iter);
 }
+
 
 cudaError_t launch_point_residual0(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;

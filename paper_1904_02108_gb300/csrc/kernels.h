@@ -39,8 +39,6 @@ struct Bodies {
   const double *omega;   // [nb]
   const double *phase;   // [nb]
   int nb;
-  double *trig;          // [nb][4] scratch: cos phi, sin phi, and the
-                         // differences to phi - omega (set per step)
 };
 struct PointsIn {
   int64_t np;
@@ -50,10 +48,11 @@ struct PointsIn {
   const float *utarget;   // [np][3] or NULL (0)
 };
 // ---- step kernels over a batch of domains (D: device array of dims.nd) ----
-// Kinematics (Alg. 1, first iteration) + per-point weights + brick counts.
+// Kinematics (Alg. 1, first iteration; each block computes the rotation of
+// its points' bodies once) + per-point weights + brick counts.
 cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // counted bricks -> slots; (brick, point) pairs grouped by brick in a fixed
-// order, with brick-local weights (5 launches when points exist, else 1)
+// order, with brick-local weights (3 launches when points exist, else 1)
 cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // U0 on the active bricks (pull + Eq. 1) from lattice f[cur]
 cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDims &dims, int cur,

@@ -274,11 +274,11 @@ def test_timing_and_launch_counters(gpu_lib, torch_cuda):
     lat.step(3, 5)
     t = lat.timing()
     assert t["collide_stream"][1] == 3 and t["point_update"][1] == 15
-    assert t["brick_spread"][1] == 15 and t["brick_init"][1] == 6 and t["pairs"][1] == 12
+    assert t["brick_spread"][1] == 15 and t["brick_init"][1] == 6 and t["pairs"][1] == 9
     assert all(ms >= 0 for ms, _ in t.values()) and t["collide_stream"][0] > 0
-    # per step: trig + points, 4 pair kernels, moments + init, 5 x 2 iteration
+    # per step: kinematics, 3 pair kernels, moments + init, 5 x 2 iteration
     # kernels, collide-stream, stats
-    assert lat.stats()["kernel_launches"] == 3 * (2 + 4 + 2 + 10 + 1 + 1)
+    assert lat.stats()["kernel_launches"] == 3 * (1 + 3 + 2 + 10 + 1 + 1)
     lat.close()
 
 
