@@ -75,8 +75,12 @@ typedef struct {
 } lbm_opts;
 
 typedef struct {
-  double mass;           /* sum over cells and i of f_i (after the last step) */
-  double momentum[3];    /* sum of e_i f_i                                    */
+  double mass;           /* sum over cells and i of f_i after the last step,
+                            in FP64: per cell rho, from the step's moments
+                            (the BGK collision conserves it exactly)        */
+  double momentum[3];    /* sum of e_i f_i after the last step: per cell
+                            rho U + rho G (the collision adds exactly the
+                            force impulse rho G, Eqs. 2-3)                   */
   int64_t step;          /* number of completed steps                         */
   int last_ibm_iters;    /* fixed-point iterations of the last step           */
   double last_residual;  /* eps of the last iteration (tolerance mode), else

@@ -222,7 +222,7 @@ struct DomainDesc {
   float4 *du, *uint;
   double *xpos;
   double *partial, *sums;  // collide partials [cblocks][4], FP64 sums [4]
-  double *red_scratch;     // [128][4] block sums of the final reduction
+  double *red_scratch;     // [256][4] block sums of the final reduction
   unsigned *ticket;        // blocks of the final reduction done (reset by
                            // the last one)
   IbmState *state;

@@ -8,6 +8,9 @@
 // (post-collision values of step t-1), which realises Eq. 4, and writes the
 // post-collision value at X into the destination lattice, so every write is
 // coalesced and each population is read and written exactly once per step.
+// The FP64 mass and momentum need no sum over the 19 new values: the BGK
+// collision conserves mass and adds exactly the force impulse rho G, so a
+// cell's post-collision sums are rho and rho U + rho G from its moments.
 #include <algorithm>
 
 #include "kernels.h"
@@ -57,22 +60,31 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
     const float ux = jx * inv + tau * Gx;
     const float uy = jy * inv + tau * Gy;
     const float uz = jz * inv + tau * Gz;
-    const float uu = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float om = 1.f / tau;
+    // Eq. 3 minus t_i: t_i (c0 + rho (3 e.u + 4.5 (e.u)^2)) with c0 the part
+    // common to every direction; opposite directions share 4.5 rho (e.u)^2
+    const float c0 = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
+    const float r3 = 3.f * rho, r45 = 4.5f * rho;
     const size_t N = (size_t)g.ncell;
+    float dn[Q];
+    dn[0] = d[0] + om * (wt(0) * c0 - d[0]);
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-      // Eq. 3 (with rho) minus t_i, then Eq. 2
+    for (int i = 1; i < Q; i += 2) {
       const float eu = (float)ex(i) * ux + (float)ey(i) * uy + (float)ez(i) * uz;
-      const float eq = wt(i) * (drho + rho * (3.f * eu + 4.5f * eu * eu - uu));
-      const float dn = d[i] + om * (eq - d[i]);
-      Store<S>::st(dst + (size_t)i * N + n, dn);
-      if (STATS) {
-        sm += dn;
-        if (ex(i)) spx += ex(i) > 0 ? dn : -dn;
-        if (ey(i)) spy += ey(i) > 0 ? dn : -dn;
-        if (ez(i)) spz += ez(i) > 0 ? dn : -dn;
-      }
+      const float sym = c0 + r45 * eu * eu, anti = r3 * eu;
+      const float eqp = wt(i) * (sym + anti), eqm = wt(i) * (sym - anti);
+      dn[i] = d[i] + om * (eqp - d[i]);
+      dn[i + 1] = d[i + 1] + om * (eqm - d[i + 1]);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) Store<S>::st(dst + ((size_t)i * N + n), dn[i]);
+    if (STATS) {
+      // the collision conserves mass and adds rho G of momentum (Eqs. 2-3):
+      // the cell's post-collision sums, from its moments
+      sm = drho;
+      spx = jx + rho * Gx;
+      spy = jy + rho * Gy;
+      spz = jz + rho * Gz;
     }
   }
   if (STATS) {
@@ -121,11 +133,19 @@ __global__ void __launch_bounds__(256)
   collide_stream_cells<S, STATS>(D[blockIdx.y], cur);
 }
 
-// End of a step: the FP64 sum of the collide blocks' partials in a fixed
-// order (FINISH_BLOCKS blocks per domain each sum a strided subset with a
-// tree; the last of them to finish sums the block results the same way), and
-// t += 1.  With stats off only the step counter advances.
-constexpr int FINISH_BLOCKS = 128;
+// End of a step: the FP64 sum of the collide kernel's partials in a fixed
+// order (FINISH_BLOCKS blocks per domain: each thread adds the partials of a
+// fixed strided subset, a warp combines its lanes with a butterfly, the block
+// its warps in order; the last block to finish combines the block sums the
+// same way), and t += 1.  With stats off only the step counter advances.
+constexpr int FINISH_BLOCKS = 64;
+
+__device__ __forceinline__ void warp_sum4(double a[4]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < 4; c++) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+}
 
 __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__restrict__ D,
                                                           int stats) {
@@ -136,38 +156,50 @@ __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__re
     if (blockIdx.x == 0 && threadIdx.x == 0) *dd.t += 1;
     return;
   }
-  __shared__ double red[256][4];
+  __shared__ double red[8][4];
   __shared__ bool last;
-  const double *__restrict__ partial = dd.partial;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double4_32a *__restrict__ partial = (const double4_32a *)dd.partial;
   double a[4] = {0, 0, 0, 0};
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < dd.cblocks; p += gridDim.x * blockDim.x)
-    for (int c = 0; c < 4; c++) a[c] += partial[(size_t)p * 4 + c];
-  for (int c = 0; c < 4; c++) red[threadIdx.x][c] = a[c];
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int c = 0; c < 4; c++) red[threadIdx.x][c] += red[threadIdx.x + s][c];
-    __syncthreads();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < dd.cblocks; p += gridDim.x * blockDim.x) {
+    const double4_32a v = partial[p];
+    a[0] += v.x;
+    a[1] += v.y;
+    a[2] += v.z;
+    a[3] += v.w;
   }
+  warp_sum4(a);
+  if (lane == 0)
+    for (int c = 0; c < 4; c++) red[w][c] = a[c];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int k = 0; k < 8; k++) v += red[k][threadIdx.x];
+    dd.red_scratch[blockIdx.x * 4 + threadIdx.x] = v;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (int c = 0; c < 4; c++) dd.red_scratch[blockIdx.x * 4 + c] = red[0][c];
     __threadfence();
     last = atomicAdd(dd.ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the block sums, FINISH_BLOCKS of them, one per thread
   for (int c = 0; c < 4; c++)
-    red[threadIdx.x][c] =
-        threadIdx.x < gridDim.x ? ((volatile double *)dd.red_scratch)[threadIdx.x * 4 + c] : 0.0;
+    a[c] = (int)threadIdx.x < (int)gridDim.x
+               ? ((volatile double *)dd.red_scratch)[threadIdx.x * 4 + c]
+               : 0.0;
+  warp_sum4(a);
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int c = 0; c < 4; c++) red[threadIdx.x][c] += red[threadIdx.x + s][c];
-    __syncthreads();
+  if (lane == 0)
+    for (int c = 0; c < 4; c++) red[w][c] = a[c];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int k = 0; k < 8; k++) v += red[k][threadIdx.x];
+    dd.sums[threadIdx.x] = threadIdx.x == 0 ? (double)dd.g.ncell + v : v;
   }
-  if (threadIdx.x < 4)
-    dd.sums[threadIdx.x] = threadIdx.x == 0 ? (double)dd.g.ncell + red[0][0] : red[0][threadIdx.x];
   if (threadIdx.x == 0) {
     *dd.ticket = 0u;
     *dd.t += 1;
