@@ -128,6 +128,18 @@ int lbm_set_stream(lbm_t *h, void *stream);
 int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
                    const float *area, const int32_t *body);
 
+/* Moves the current points: new X[n][3] (and U_target[n][3] when not NULL)
+ * for the same n points, copied from host memory on the handle's stream
+ * (asynchronously for page-locked memory; the caller keeps the buffers valid
+ * until the stream has passed the copy).  No reallocation, no
+ * synchronisation, areas, bodies and the warm-start history are kept: the
+ * per-step input of a caller that moves its own points (the paper's
+ * immersedBoundary(object, U) with the object updated each step).  Positions
+ * are not checked here; a non-finite one gives an unspecified point, never an
+ * out-of-range access.  This entry point has no counterpart in the paper.
+ * Errors: LBM_EINVAL (n differs from the point count, X NULL), LBM_ECUDA. */
+int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_target);
+
 /* Rigid rotating bodies: M_b(t) rotates by phase[b] + omega[b] * t radians
  * about the z axis through centre[b][3] (Alg. 1 applies M(t) at the first
  * fixed-point iteration; u_k = x(t) - x(t-1)).  nb = 0 removes the bodies
@@ -204,7 +216,7 @@ void lbm_velocity_set(int *e, double *t);
 typedef struct {
   int collide_block; /* threads per block of the collide-stream kernel:
                         128 or 256                                         */
-  int brick_blocks;  /* blocks of the brick kernels (64 threads each,
+  int brick_blocks;  /* blocks of the brick kernels (one warp each,
                         grid-stride over the active bricks), >= 1          */
   int point_block;   /* threads per block of the per-point kernels:
                         128, 256 or 512                                    */
@@ -212,7 +224,7 @@ typedef struct {
   int sort_blocks;   /* blocks of the pair sort (a warp per brick), >= 1   */
 } lbm_launch_shape;
 
-/* The handle's launch shape (defaults: 256, 2432, 256, 4, 4864).  Set
+/* The handle's launch shape (defaults: 256, 3648, 256, 4, 4864).  Set
  * returns LBM_EINVAL for a value outside the ranges above. */
 int lbm_get_launch_shape(lbm_t *h, lbm_launch_shape *out);
 int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s);

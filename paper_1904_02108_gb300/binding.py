@@ -91,6 +91,7 @@ _SIGS = {
     "lbm_read_deviations": (_i, [_p, _p]),
     "lbm_read_residuals": (_i, [_p, _p, _i]),
     "lbm_set_graph": (_i, [_p, _i]),
+    "ibm_update_points": (_i, [_p, _i64, _p, _p]),
     "lbm_get_launch_shape": (_i, [_p, _p]),
     "lbm_set_launch_shape": (_i, [_p, _p]),
     "lbm_autotune": (_i, [_p, _i, _i, _p]),
@@ -231,6 +232,14 @@ class Lattice:
         bd = None if body is None else np.ascontiguousarray(body, np.int32).reshape(-1)
         self._c(load().ibm_set_points(self.h, n, _ptr(X), _ptr(ut), _ptr(ar), _ptr(bd)))
         self.np = n
+
+    def update_points(self, X, U_target=None):
+        """Moves the current points (same count) without synchronising; X
+        (and U_target) must stay alive until the stream has copied them."""
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        ut = None if U_target is None else np.ascontiguousarray(U_target, np.float32).reshape(-1, 3)
+        self._keep = (X, ut)
+        self._c(load().ibm_update_points(self.h, len(X), _ptr(X), _ptr(ut)))
 
     def set_bodies(self, centre, omega, phase):
         c = np.ascontiguousarray(centre, np.float64).reshape(-1, 3)

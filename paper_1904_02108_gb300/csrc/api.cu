@@ -486,6 +486,19 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
   return LBM_OK;
 }
 
+int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_target) {
+  if (!h) return LBM_EINVAL;
+  if (n != h->np) return fail(h, LBM_EINVAL, "%lld points, the handle has %lld", (long long)n,
+                              (long long)h->np);
+  if (n == 0) return LBM_OK;
+  if (!X) return fail(h, LBM_EINVAL, "X is NULL");
+  CK(h, cudaMemcpyAsync(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->st));
+  if (U_target)
+    CK(h, cudaMemcpyAsync(h->utarget, U_target, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
+                          h->st));
+  return LBM_OK;
+}
+
 int ibm_set_bodies(lbm_t *h, int nb, const double *centre, const double *omega,
                    const double *phase) {
   if (!h) return LBM_EINVAL;

@@ -536,33 +536,37 @@ __global__ void __launch_bounds__(128)
 }
 
 
-// ---- the brick kernels: one 64-thread block per active brick ----------------
+// ---- the brick kernels: one warp per active brick ---------------------------
 
+// A warp stages up to SP_CHUNK pairs of its brick at a time: their brick-local
+// weights and spread values.
 constexpr int SP_CHUNK = 128;
 
 struct BrickSmem {
   float4 swx[SP_CHUNK];
   float swy[SP_CHUNK][4], swz[SP_CHUNK][4];
   float4 sv[SP_CHUNK];
-  float sacc[4][3][64];
   float4 sF[3][16];  // U0 + G of the brick, rows of four x cells
-  float sred[2];
 };
 
-// G(X) = sum over the brick's pairs of v(k) wx wy wz, for the 64 cells of the
-// brick.  The block splits into four groups of 16 threads; a thread owns one
-// x-row of four cells, its group takes every fourth pair, and the four partial
-// sums are added in a fixed order.  Thread t returns the sum of cell t.
-__device__ __forceinline__ float3 brick_gather(BrickSmem &sm, const PairMap &pm, int p0, int cnt,
-                                               const float4 *__restrict__ vals,
-                                               bool scale_by_w = false) {
-  const int t = threadIdx.x;
+// G(X) = sum over the brick's pairs of v(k) wx wy wz (Alg. 2 as a gather),
+// for the 64 cells of the brick.  Lane l owns row l & 15 (an x-line of four
+// cells, row = z_local * 4 + y_local); the two half-warps take alternate pairs
+// (every lane of a half reads the same pair: shared-memory broadcasts) and
+// are added as h0 + h1 in both.  Returns the row's four cells per component;
+// on return the first chunk's pairs are staged (all of them when cnt <=
+// SP_CHUNK).
+__device__ __forceinline__ void brick_gather(BrickSmem &sm, const PairMap &pm, int p0, int cnt,
+                                             const float4 *__restrict__ vals, float4 out[3],
+                                             bool scale_by_w = false) {
+  const int t = threadIdx.x & 31;
   const int grp = t >> 4, tg = t & 15, yl = tg & 3, zl = tg >> 2;
   float acc[4][3];
 #pragma unroll
   for (int a = 0; a < 4; a++) acc[a][0] = acc[a][1] = acc[a][2] = 0.f;
   for (int c0 = 0; c0 < cnt; c0 += SP_CHUNK) {
-    for (int q = t; q < SP_CHUNK; q += 64) {
+    __syncwarp();
+    for (int q = t; q < SP_CHUNK; q += 32) {
       if (c0 + q < cnt) {
         const size_t p = (size_t)p0 + c0 + q;
         const float4 wy = pm.w[3 * p + 1], wz = pm.w[3 * p + 2];
@@ -584,9 +588,9 @@ __device__ __forceinline__ float3 brick_gather(BrickSmem &sm, const PairMap &pm,
         sm.sv[q] = v;
       }
     }
-    __syncthreads();
+    __syncwarp();
     const int mm = min(SP_CHUNK, cnt - c0);
-    for (int j = grp; j < mm; j += 4) {
+    for (int j = grp; j < mm; j += 2) {
       const float wyz = sm.swy[j][yl] * sm.swz[j][zl];
       const float4 wx = sm.swx[j];
       const float4 v = sm.sv[j];
@@ -596,29 +600,27 @@ __device__ __forceinline__ float3 brick_gather(BrickSmem &sm, const PairMap &pm,
       acc[2][0] += w2 * v.x; acc[2][1] += w2 * v.y; acc[2][2] += w2 * v.z;
       acc[3][0] += w3 * v.x; acc[3][1] += w3 * v.y; acc[3][2] += w3 * v.z;
     }
-    __syncthreads();
   }
-  const int row = (zl * 4 + yl) * 4;
+  __syncwarp();
 #pragma unroll
   for (int a = 0; a < 4; a++)
 #pragma unroll
-    for (int c = 0; c < 3; c++) sm.sacc[grp][c][row + a] = acc[a][c];
-  __syncthreads();
-  float3 r;
-  r.x = ((sm.sacc[0][0][t] + sm.sacc[1][0][t]) + sm.sacc[2][0][t]) + sm.sacc[3][0][t];
-  r.y = ((sm.sacc[0][1][t] + sm.sacc[1][1][t]) + sm.sacc[2][1][t]) + sm.sacc[3][1][t];
-  r.z = ((sm.sacc[0][2][t] + sm.sacc[1][2][t]) + sm.sacc[2][2][t]) + sm.sacc[3][2][t];
-  return r;
+    for (int c = 0; c < 3; c++) {
+      const float o = __shfl_xor_sync(0xffffffffu, acc[a][c], 16);
+      acc[a][c] = grp == 0 ? acc[a][c] + o : o + acc[a][c];
+    }
+  out[0] = make_float4(acc[0][0], acc[1][0], acc[2][0], acc[3][0]);
+  out[1] = make_float4(acc[0][1], acc[1][1], acc[2][1], acc[3][1]);
+  out[2] = make_float4(acc[0][2], acc[1][2], acc[2][2], acc[3][2]);
 }
 
 // Each pair's share of I[F] for F = sm.sF: sum over the brick's cells of
-// F(X) wx wy wz (one thread per pair; every thread reads the same F row at the
-// same time, a shared-memory broadcast).
-// staged: the pair weights of this brick are still in sm.swx/swy/swz (the
-// gather staged them and cnt <= SP_CHUNK).
+// F(X) wx wy wz (one lane per pair; every lane reads the same F row at the same
+// time, a shared-memory broadcast).  staged: the pair weights are still in
+// sm.swx/swy/swz (the gather staged them and cnt <= SP_CHUNK).
 __device__ __forceinline__ void brick_interp(BrickSmem &sm, const PairMap &pm, int p0, int cnt,
                                              bool staged) {
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+  for (int i = threadIdx.x & 31; i < cnt; i += 32) {
     // re-read F for every pair instead of holding all 192 values in registers
     asm volatile("" ::: "memory");
     const size_t p = (size_t)p0 + i;
@@ -654,11 +656,8 @@ __device__ __forceinline__ void brick_interp(BrickSmem &sm, const PairMap &pm, i
   }
 }
 
-__device__ __forceinline__ void store_F(BrickSmem &sm, float fx, float fy, float fz) {
-  const int t = threadIdx.x;
-  ((float *)sm.sF[0])[t] = fx;
-  ((float *)sm.sF[1])[t] = fy;
-  ((float *)sm.sF[2])[t] = fz;
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
 
 // U0 on every cell of every active brick: pull of Eq. 4 and Eq. 1 (the
@@ -695,8 +694,8 @@ __global__ void __launch_bounds__(256)
 
 // First pass of a step over each active brick after the moments: G_0 = 0 or
 // S[du_init] (warm start), and the pairs' shares of I[U0 + G_0] for the first
-// iteration.
-__global__ void __launch_bounds__(64, 16)
+// iteration.  One warp per brick, grid-stride over the active bricks.
+__global__ void __launch_bounds__(32, 32)
     brick_init_kernel(const DomainDesc *__restrict__ D, int use_du) {
   pdl_wait();
   pdl_launch_dependents();
@@ -708,28 +707,30 @@ __global__ void __launch_bounds__(64, 16)
   const float *__restrict__ U0s = d.U0s;
   float *__restrict__ Gs = d.Gs;
   const int nslots = active_slots(m);
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, r = t & 15;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
-    const float *u = U0s + (size_t)s * SLOT_FLOATS + t;
-    const float ux = u[0], uy = u[BRICK_CELLS], uz = u[2 * BRICK_CELLS];
     const int p0 = pm.start[s], cnt = pm.count[s];
-    float3 G = make_float3(0.f, 0.f, 0.f);
-    if (du_init) G = brick_gather(sm, pm, p0, cnt, du_init);
-    float *Gp = Gs + (size_t)s * SLOT_FLOATS + t;
-    Gp[0] = G.x;
-    Gp[BRICK_CELLS] = G.y;
-    Gp[2 * BRICK_CELLS] = G.z;
-    store_F(sm, ux + G.x, uy + G.y, uz + G.z);
-    __syncthreads();
+    float4 G[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                   make_float4(0.f, 0.f, 0.f, 0.f)};
+    if (du_init) brick_gather(sm, pm, p0, cnt, du_init, G);
+    const size_t o = (size_t)s * SLOT_FLOATS + 4 * r;
+    if (t < 16) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        *(float4 *)(Gs + o + c * BRICK_CELLS) = G[c];
+        sm.sF[c][r] = add4(*(const float4 *)(U0s + o + c * BRICK_CELLS), G[c]);
+      }
+    }
+    __syncwarp();
     brick_interp(sm, pm, p0, cnt, du_init != nullptr && cnt <= SP_CHUNK);
-    __syncthreads();
+    __syncwarp();
   }
 }
 
-// One iteration's spreading over each active brick: G = S[du] (Alg. 2 as a
-// gather), the squared change of G into res[slot] (if res), and, unless this
-// is the last iteration, the pairs' shares of I[U0 + G] for the next one.
-__global__ void __launch_bounds__(64, 16)
+// One iteration's spreading over each active brick: G = S[du], the squared
+// change of G into res[slot] (tolerance mode), and, unless this is the last
+// iteration, the pairs' shares of I[U0 + G] for the next one.
+__global__ void __launch_bounds__(32, 32)
     brick_spread_kernel(const DomainDesc *__restrict__ D, int do_interp, int tol_mode) {
   pdl_wait();
   pdl_launch_dependents();
@@ -743,35 +744,44 @@ __global__ void __launch_bounds__(64, 16)
   float *__restrict__ Gs = d.Gs;
   float *__restrict__ res = tol_mode ? d.res : nullptr;
   const int nslots = active_slots(m);
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, r = t & 15;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
     const int p0 = pm.start[s], cnt = pm.count[s];
-    const float3 G = brick_gather(sm, pm, p0, cnt, vals);
-    float *Gp = Gs + (size_t)s * SLOT_FLOATS + t;
+    float4 G[3];
+    brick_gather(sm, pm, p0, cnt, vals, G);
+    const size_t o = (size_t)s * SLOT_FLOATS + 4 * r;
     if (res) {
-      const float dx = G.x - Gp[0], dy = G.y - Gp[BRICK_CELLS], dz = G.z - Gp[2 * BRICK_CELLS];
-      float r = dx * dx + dy * dy + dz * dz;
+      float e = 0.f;
+      if (t < 16) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-      if ((t & 31) == 0) sm.sred[t >> 5] = r;
+        for (int c = 0; c < 3; c++) {
+          const float4 old = *(const float4 *)(Gs + o + c * BRICK_CELLS);
+          const float a = G[c].x - old.x, b = G[c].y - old.y, cc = G[c].z - old.z,
+                      dd = G[c].w - old.w;
+          e += ((a * a + b * b) + cc * cc) + dd * dd;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+      if (t == 0) res[s] = e;
     }
-    Gp[0] = G.x;
-    Gp[BRICK_CELLS] = G.y;
-    Gp[2 * BRICK_CELLS] = G.z;
-    if (do_interp) {
-      const float *u = U0s + (size_t)s * SLOT_FLOATS + t;
-      store_F(sm, u[0] + G.x, u[BRICK_CELLS] + G.y, u[2 * BRICK_CELLS] + G.z);
+    if (t < 16) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        *(float4 *)(Gs + o + c * BRICK_CELLS) = G[c];
+        if (do_interp)
+          sm.sF[c][r] = add4(*(const float4 *)(U0s + o + c * BRICK_CELLS), G[c]);
+      }
     }
-    __syncthreads();
-    if (res && t == 0) res[s] = sm.sred[0] + sm.sred[1];
+    __syncwarp();
     if (do_interp) brick_interp(sm, pm, p0, cnt, cnt <= SP_CHUNK);
-    __syncthreads();
+    __syncwarp();
   }
 }
 
 // ||S[v]||^2 per active brick into res[slot] (v = vals, scaled by .w when
-// scale_by_w): the denominator ||S[s u_k]|| of the residual.
-__global__ void __launch_bounds__(64, 16)
+// scale_by_w): the denominators of the residual.
+__global__ void __launch_bounds__(32, 32)
     brick_norm_kernel(const DomainDesc *__restrict__ D, int which) {
   pdl_wait();
   pdl_launch_dependents();
@@ -779,21 +789,24 @@ __global__ void __launch_bounds__(64, 16)
   const DomainDesc &d = D[blockIdx.y];
   const BrickMap m = d.m;
   const PairMap pm = d.pm;
-  // which 0: s(k) u_k (u_k with s(k) in .w); 1: the vectors left in uint
   const float4 *__restrict__ vals = which == 0 ? d.pp.ut : d.uint;
   const int scale_by_w = which == 0;
   float *__restrict__ res = d.res;
   const int nslots = active_slots(m);
   const int t = threadIdx.x;
   for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
-    const float3 G = brick_gather(sm, pm, pm.start[s], pm.count[s], vals, scale_by_w != 0);
-    float r = G.x * G.x + G.y * G.y + G.z * G.z;
+    float4 G[3];
+    brick_gather(sm, pm, pm.start[s], pm.count[s], vals, G, scale_by_w != 0);
+    float e = 0.f;
+    if (t < 16) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if ((t & 31) == 0) sm.sred[t >> 5] = r;
-    __syncthreads();
-    if (t == 0) res[s] = sm.sred[0] + sm.sred[1];
-    __syncthreads();
+      for (int c = 0; c < 3; c++)
+        e += ((G[c].x * G[c].x + G[c].y * G[c].y) + G[c].z * G[c].z) + G[c].w * G[c].w;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+    if (t == 0) res[s] = e;
+    __syncwarp();
   }
 }
 
@@ -1135,12 +1148,12 @@ static dim3 brick_grid(const BatchDims &dims) {
 
 cudaError_t launch_brick_init(const DomainDesc *D, const BatchDims &dims, int use_du,
                               cudaStream_t st) {
-  return launch_pdl(brick_init_kernel, brick_grid(dims), dim3(64), 0, st, D, use_du);
+  return launch_pdl(brick_init_kernel, brick_grid(dims), dim3(32), 0, st, D, use_du);
 }
 
 cudaError_t launch_brick_spread(const DomainDesc *D, const BatchDims &dims, int do_interp,
                                 int tol_mode, cudaStream_t st) {
-  return launch_pdl(brick_spread_kernel, brick_grid(dims), dim3(64), 0, st, D, do_interp, tol_mode);
+  return launch_pdl(brick_spread_kernel, brick_grid(dims), dim3(32), 0, st, D, do_interp, tol_mode);
 }
 
 cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int first, int warm,
@@ -1153,7 +1166,7 @@ cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int 
 
 cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,
                               cudaStream_t st) {
-  return launch_pdl(brick_norm_kernel, brick_grid(dims), dim3(64), 0, st, D, which);
+  return launch_pdl(brick_norm_kernel, brick_grid(dims), dim3(32), 0, st, D, which);
 }
 
 cudaError_t launch_ibm_den(const DomainDesc *D, const BatchDims &dims, int mode, cudaStream_t st) {

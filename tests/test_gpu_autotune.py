@@ -98,3 +98,34 @@ def test_batch_autotune_keeps_batch_equal_to_single_stepping(gpu_lib, torch_cuda
     batch.close()
     for lat in single + batched:
         lat.close()
+
+
+def test_update_points_moves_the_points_without_a_reset(gpu_lib, torch_cuda):
+    """ibm_update_points with the same positions changes nothing; with moved
+    positions it matches a lattice given those positions by ibm_set_points
+    (zero warm start, so the reset there makes no difference)."""
+    import numpy as np
+    torch = torch_cuda
+    rng = W.SplitMix64(71)
+    x0 = W.random_points(rng, 400, (32, 32, 32))
+    x1 = x0 + 0.3 * W.random_array(rng, x0.shape)
+    ut = 0.02 * W.random_array(rng, x0.shape)
+    mk = lambda: gpu_lib.Lattice((32, 32, 32), 0.8, stream=torch.cuda.current_stream())
+    a, b, c = mk(), mk(), mk()
+    for lat in (a, b, c):
+        lat.set_points(x0, ut)
+        lat.step(3, 5)
+    a.update_points(x0)  # unchanged positions
+    for lat in (a, b, c):
+        lat.step(2, 5)
+    assert np.array_equal(a.populations(), b.populations())
+    a.update_points(x1, ut)
+    c.set_points(x1, ut)
+    a.step(2, 5)
+    c.step(2, 5)
+    assert np.array_equal(a.populations(), c.populations())
+    assert np.array_equal(a.points()[2], c.points()[2])
+    with pytest.raises(gpu_lib.LbmError):
+        a.update_points(x1[:10])
+    for lat in (a, b, c):
+        lat.close()
