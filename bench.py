@@ -387,6 +387,7 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
         lat = binding.Lattice(w.shape, w.tau, storage=storage, warm=warm, ibm_tol=tol,
                               ibm_max_iter=max_iter, stream=st)
         lat.set_propellers(w.props)
+        lat.autotune(w.n_iter, 3)
         if warm == "mlp":
             lat.set_mlp_weights(P)
         lat.step(warmup, 0)
@@ -416,6 +417,7 @@ def bench_precision(steps=100, warmup=5):
     for storage in ("bf16", "f16"):
         lat = binding.Lattice(w.shape, w.tau, storage=storage, stream=st)
         lat.set_propellers(w.props)
+        shape = lat.autotune(w.n_iter, 3)
         lat.step(warmup, w.n_iter)
         lat.enable_timing(["collide_stream"])
         ms = _device_ms(lambda: lat.step(steps, w.n_iter), st)
@@ -424,7 +426,7 @@ def bench_precision(steps=100, warmup=5):
         alg = w.cells * 19 * 2 * 2 + s["active_bricks"] * 64 * 12
         ach = alg / (cms / 1e3 / cn) / 1e9
         out[storage] = {"value": w.cells * steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
-                        "ms_per_step": ms / steps,
+                        "ms_per_step": ms / steps, "launch_shape": shape,
                         "collide_roofline": {"achieved": ach, "peak": peak, "unit": "GB/s",
                                              "frac": ach / peak, "alg_bytes_per_launch": alg}}
         lat.close()
