@@ -387,9 +387,9 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
         lat = binding.Lattice(w.shape, w.tau, storage=storage, warm=warm, ibm_tol=tol,
                               ibm_max_iter=max_iter, stream=st)
         lat.set_propellers(w.props)
-        lat.autotune(w.n_iter, 3)
         if warm == "mlp":
             lat.set_mlp_weights(P)
+        lat.autotune(w.n_iter, 3)
         lat.step(warmup, 0)
         iters, capped = 0, 0
         t_ms = 0.0

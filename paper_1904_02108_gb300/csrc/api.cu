@@ -373,7 +373,7 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   h->nparts = collide_partials(h->g);
   if (e == cudaSuccess) e = dalloc(&h->partial, (size_t)h->nparts * 4);
   if (e == cudaSuccess) e = dalloc(&h->sums, 4);
-  if (e == cudaSuccess) e = dalloc(&h->red_scratch, 256 * 4);
+  if (e == cudaSuccess) e = dalloc(&h->red_scratch, 128 * 4);
   if (e == cudaSuccess) e = dalloc(&h->ticket, 1);
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dalloc(&h->desc, 1);

@@ -177,14 +177,18 @@ constexpr int MLP_NPARAM = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_H
 constexpr float MLP_VSCALE = 0.05f, MLP_LSCALE = 16.f;
 
 // State of the tolerance-driven fixed point, on the device.
+// Blocks of the multi-block residual sums (ibm_den / ibm_check).
+constexpr int RES_BLOCKS = 16;
+
 struct IbmState {
   static constexpr int HIST = 4096;
   int done;        // 1: converged or capped
   int iters;       // iterations taken this step
   int capped;      // 1: stopped at max_iter with eps > tol
-  int pad;
+  unsigned ticket; // blocks of the residual sum done (reset by the last)
   double den2;     // ||S[s u_k]||^2 (or the fallback)
   double last_eps;
+  double bsum[RES_BLOCKS];  // block sums of the residual sum
   double eps[HIST];  // eps of every iteration of this step
 };
 
@@ -222,7 +226,7 @@ struct DomainDesc {
   float4 *du, *uint;
   double *xpos;
   double *partial, *sums;  // collide partials [cblocks][4], FP64 sums [4]
-  double *red_scratch;     // [256][4] block sums of the final reduction
+  double *red_scratch;     // [128][4] block sums of the final reduction
   unsigned *ticket;        // blocks of the final reduction done (reset by
                            // the last one)
   IbmState *state;

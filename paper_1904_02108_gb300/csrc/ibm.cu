@@ -251,8 +251,9 @@ constexpr unsigned SCAN_SPIN_LIMIT = 1u << 22;
 // Bricks with a count -> slots in brick order, and each slot's first pair:
 // one pass over the bricks in tiles of COMPACT_TILE with a single-pass scan.
 // A tile takes its index from a ticket, so it only waits on tiles already
-// running; it publishes its totals, then adds up its predecessors' words
-// (stopping at the first inclusive prefix) and publishes its own prefix.
+// running; it publishes its totals, then its first warp adds up its
+// predecessors' words 32 at a time (stopping at the nearest inclusive prefix)
+// and publishes its own prefix.
 // Every wait is bounded: past SCAN_SPIN_LIMIT polls the tile sets error flag 4
 // and the step's slots are left empty.
 __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restrict__ D) {
@@ -310,20 +311,28 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
   }
   ia += ba - na;  // exclusive within the tile
   ic += bc - nc;
-  if (t == 0) {
+  if (w == 0) {
     unsigned long long *tw = m.tiles;
     long long pa = 0, pc = 0;
     if (tile == 0) {
-      atomicExch(tw + 0, tile_word(epoch, 2, (unsigned)ta, (unsigned)tc));
+      if (lane == 0) atomicExch(tw + 0, tile_word(epoch, 2, (unsigned)ta, (unsigned)tc));
     } else {
-      atomicExch(tw + tile, tile_word(epoch, 1, (unsigned)ta, (unsigned)tc));
+      if (lane == 0) atomicExch(tw + tile, tile_word(epoch, 1, (unsigned)ta, (unsigned)tc));
+      // look back 32 tiles at a time: lane l reads tile top - l (tiles before
+      // 0 read as an empty inclusive prefix), waits until all 32 are
+      // published, and the warp adds the words up to the nearest inclusive one
       bool ok = true;
-      for (int j = tile - 1; j >= 0 && ok; j--) {
+      for (int top = tile - 1; top >= 0; top -= 32) {
+        const int j = top - lane;
         unsigned long long v = 0;
+        unsigned stt = 2;
         unsigned spins = 0;
         for (;;) {
-          v = *(volatile unsigned long long *)(tw + j);
-          if ((unsigned)(v >> 58) == epoch && ((v >> 56) & 3u) != 0) break;
+          if (j >= 0) {
+            v = *(volatile unsigned long long *)(tw + j);
+            stt = (unsigned)(v >> 58) == epoch ? (unsigned)((v >> 56) & 3u) : 0u;
+          }
+          if (__all_sync(0xffffffffu, stt != 0)) break;
           if (++spins >= SCAN_SPIN_LIMIT) {
             ok = false;
             break;
@@ -331,20 +340,37 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
           __nanosleep(64);
         }
         if (!ok) break;
-        pa += (long long)((v >> 31) & 0x1ffffffull);
-        pc += (long long)(v & 0x7fffffffull);
-        if (((v >> 56) & 3u) == 2) break;
+        const unsigned incl = __ballot_sync(0xffffffffu, stt == 2);
+        const int stop = incl ? __ffs(incl) - 1 : 31;
+        long long sa = 0, sc = 0;
+        if (lane <= stop && j >= 0) {
+          sa = (long long)((v >> 31) & 0x1ffffffull);
+          sc = (long long)(v & 0x7fffffffull);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          sa += __shfl_xor_sync(0xffffffffu, sa, o);
+          sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        }
+        pa += sa;
+        pc += sc;
+        if (incl) break;
       }
       if (!ok) {
-        atomicOr(m.counters + 1, 4);
-        atomicOr(m.counters + 5, 4);  // kept until the host reads it
+        if (lane == 0) {
+          atomicOr(m.counters + 1, 4);
+          atomicOr(m.counters + 5, 4);  // kept until the host reads it
+        }
         pa = 0;
         pc = 0;
       }
-      atomicExch(tw + tile, tile_word(epoch, 2, (unsigned)(pa + ta), (unsigned)(pc + tc)));
+      if (lane == 0)
+        atomicExch(tw + tile, tile_word(epoch, 2, (unsigned)(pa + ta), (unsigned)(pc + tc)));
     }
-    pre_a = pa;
-    pre_c = pc;
+    if (lane == 0) {
+      pre_a = pa;
+      pre_c = pc;
+    }
   }
   __syncthreads();
   int slot = (int)pre_a + ia, first = (int)pre_c + ic;
@@ -404,21 +430,29 @@ __global__ void __launch_bounds__(512) pair_fill_kernel(const DomainDesc *__rest
   });
 }
 
-// Pair p (point k, brick B, after the sort): the brick-local weights of its
-// point (the point's tap weights at the brick's cells 0..3 along each axis, 0
-// outside the support, periodic offsets resolved) and the pair's entry in the
-// point's list of bricks.
-__device__ __forceinline__ void pair_weights(const Geometry &g, const PointPrep &pp,
-                                             const PairMap &pm, int64_t p, int k, int B) {
+// A point's base cell and tap weights, as prepare_points wrote them.
+struct PointTaps {
+  int4 base;
+  float4 w0, w1, w2;  // tap weights along x, y, z
+};
+__device__ __forceinline__ PointTaps load_taps(const PointPrep &pp, int k) {
+  const float4 *wp = (const float4 *)(pp.wts + 12 * (int64_t)k);
+  return {pp.base[k], wp[0], wp[1], wp[2]};
+}
+
+// Pair p (point k with taps pt, brick B, after the sort): the brick-local
+// weights of its point (the point's tap weights at the brick's cells 0..3
+// along each axis, 0 outside the support, periodic offsets resolved) and the
+// pair's entry in the point's list of bricks.
+__device__ __forceinline__ void pair_weights(const Geometry &g, const PairMap &pm, int64_t p,
+                                             int k, int B, const PointTaps &pt) {
   const int bxb = B % g.nbx, rr = B / g.nbx;
   const int byb = rr % g.nby, bzb = rr / g.nby;
   const int X0 = bxb * 4, Y0 = byb * 4, Z0 = bzb * 4;
-  const int4 b = pp.base[k];
-  const float4 *wp = (const float4 *)(pp.wts + 12 * (int64_t)k);
-  const float4 w0 = wp[0], w1 = wp[1], w2 = wp[2];
-  const float wx[4] = {w0.x, w0.y, w0.z, w0.w};
-  const float wy[4] = {w1.x, w1.y, w1.z, w1.w};
-  const float wz[4] = {w2.x, w2.y, w2.z, w2.w};
+  const int4 b = pt.base;
+  const float wx[4] = {pt.w0.x, pt.w0.y, pt.w0.z, pt.w0.w};
+  const float wy[4] = {pt.w1.x, pt.w1.y, pt.w1.z, pt.w1.w};
+  const float wz[4] = {pt.w2.x, pt.w2.y, pt.w2.z, pt.w2.w};
   float lx[4], ly[4], lz[4];
 #pragma unroll
   for (int c = 0; c < 4; c++) {
@@ -457,6 +491,31 @@ __device__ __forceinline__ void pair_weights(const Geometry &g, const PointPrep 
 // distinct), then record with each pair its brick and brick-local weights.
 constexpr int SORT_CAP = 512;
 
+// Rank sort of a[0..cnt) (distinct values, cnt <= 32 NR) in registers: lane
+// holds entries lane + 32 i, i < NR; the rank of a value is the number of
+// smaller ones.
+template <int NR>
+__device__ __forceinline__ void warp_rank_sort(int *a, int cnt, int lane) {
+  int v[NR], r[NR];
+#pragma unroll
+  for (int i = 0; i < NR; i++) {
+    v[i] = lane + 32 * i < cnt ? a[lane + 32 * i] : 0x7fffffff;
+    r[i] = 0;
+  }
+#pragma unroll
+  for (int i = 0; i < NR; i++)
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+      const int x = __shfl_sync(0xffffffffu, v[i], j);
+#pragma unroll
+      for (int q = 0; q < NR; q++) r[q] += x < v[q];
+    }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < NR; i++)
+    if (lane + 32 * i < cnt) a[r[i]] = v[i];
+}
+
 __global__ void __launch_bounds__(128)
     pair_sort_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
@@ -469,30 +528,16 @@ __global__ void __launch_bounds__(128)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nslots = active_slots(m);
   for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
-    const int cnt = pm.count[s], st = pm.start[s];
+    const int cnt = pm.count[s], st = pm.start[s], B = m.slot_brick[s];
     int *a = pm.k + st;
-    if (cnt <= 128) {
-      // rank sort in registers: lane holds entries lane + 32 i, i < nr; the
-      // rank of a value is the number of smaller ones (the points differ)
-      const int nr = (cnt + 31) >> 5;
-      int v[4], r[4] = {0, 0, 0, 0};
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-        v[i] = (i < nr && lane + 32 * i < cnt) ? a[lane + 32 * i] : 0x7fffffff;
-#pragma unroll
-      for (int i = 0; i < 4; i++) {
-        if (i < nr) {
-          for (int j = 0; j < 32; j++) {
-            const int x = __shfl_sync(0xffffffffu, v[i], j);
-#pragma unroll
-            for (int q = 0; q < 4; q++) r[q] += x < v[q];
-          }
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-        if (lane + 32 * i < cnt) a[r[i]] = v[i];
+    if (cnt <= 32) {
+      warp_rank_sort<1>(a, cnt, lane);
+    } else if (cnt <= 64) {
+      warp_rank_sort<2>(a, cnt, lane);
+    } else if (cnt <= 96) {
+      warp_rank_sort<3>(a, cnt, lane);
+    } else if (cnt <= 128) {
+      warp_rank_sort<4>(a, cnt, lane);
     } else if (cnt <= SORT_CAP) {
       int n2 = 2;
       while (n2 < cnt) n2 <<= 1;
@@ -527,10 +572,10 @@ __global__ void __launch_bounds__(128)
       }
     }
     __syncwarp();
-    const int B = m.slot_brick[s];
     for (int i = lane; i < cnt; i += 32) {
+      const int k = a[i];
       pm.brick[st + i] = B;
-      pair_weights(g, pp, pm, (int64_t)st + i, a[i], B);
+      pair_weights(g, pm, (int64_t)st + i, k, B, load_taps(pp, k));
     }
   }
 }
@@ -810,19 +855,39 @@ __global__ void __launch_bounds__(32, 32)
   }
 }
 
-// Deterministic FP64 sum of res[0 .. nslots) (one block of 256 threads).
-__device__ double block_sum_res(const BrickMap &m, const float *__restrict__ res) {
+// Deterministic FP64 sum of res[0 .. nslots) over RES_BLOCKS blocks of 256
+// threads: thread j of block b adds res[b*256 + j + k*RES_BLOCKS*256] in k
+// order, the block adds its threads' sums in a fixed pairwise tree, and the
+// last block to finish adds the block sums in block order.  Returns true on
+// that block's thread 0, with the sum in *total.  Every thread of every block
+// calls it.
+__device__ bool res_sum(const BrickMap &m, const float *__restrict__ res, IbmState *st,
+                        double *total) {
   __shared__ double red[256];
-  const int nslots = active_slots(m);
+  __shared__ bool last;
+  const int nslots = active_slots(m), t = threadIdx.x;
   double a = 0.0;
-  for (int s = threadIdx.x; s < nslots; s += 256) a += (double)res[s];
-  red[threadIdx.x] = a;
-  __syncthreads();
+  for (int s = blockIdx.x * 256 + t; s < nslots; s += RES_BLOCKS * 256) a += (double)res[s];
+  red[t] = a;
+#pragma unroll
   for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
+    if (t < o) red[t] += red[t + o];
   }
-  return red[0];
+  __syncthreads();
+  if (t == 0) {
+    st->bsum[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(&st->ticket, 1u) == (unsigned)RES_BLOCKS - 1;
+  }
+  __syncthreads();
+  if (!last || t != 0) return false;
+  __threadfence();
+  double v = 0.0;
+  for (int b = 0; b < RES_BLOCKS; b++) v += __ldcg(st->bsum + b);
+  st->ticket = 0u;
+  *total = v;
+  return true;
 }
 
 // mode 0: den2 = sum res (||S[s u_k]||^2); mode 1: fallback den2 (used when
@@ -833,20 +898,20 @@ __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restri
   pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
-  const double v = block_sum_res(d.m, d.res);
-  if (threadIdx.x == 0) {
-    if (mode == 0) {
-      st->den2 = v;
-      st->done = 0;
-      st->iters = 0;
-    } else if (st->den2 == 0.0) {
-      st->den2 = v > 0.0 ? v : 1.0;
-    }
+  double v;
+  if (!res_sum(d.m, d.res, st, &v)) return;
+  if (mode == 0) {
+    st->den2 = v;
+    st->done = 0;
+    st->iters = 0;
+  } else if (st->den2 == 0.0) {
+    st->den2 = v > 0.0 ? v : 1.0;
   }
 }
 
 // After iteration `it`: eps = ||G_{it+1} - G_it|| / den (Eulerian residual of
 // the fixed point); stop at the first eps <= tol or at max_iter iterations.
+// (done is read before any block counts itself, and set after all have.)
 __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__restrict__ D, int it,
                                                          double tol, int max_iter) {
   pdl_wait();
@@ -854,16 +919,15 @@ __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__rest
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
   if (st->done) return;
-  const double v = block_sum_res(d.m, d.res);
-  if (threadIdx.x == 0) {
-    const double eps = sqrt(v / st->den2);
-    if (it < IbmState::HIST) st->eps[it] = eps;
-    st->last_eps = eps;
-    if (eps <= tol || it + 1 >= max_iter) {
-      st->done = 1;
-      st->iters = it + 1;
-      st->capped = eps > tol;
-    }
+  double v;
+  if (!res_sum(d.m, d.res, st, &v)) return;
+  const double eps = sqrt(v / st->den2);
+  if (it < IbmState::HIST) st->eps[it] = eps;
+  st->last_eps = eps;
+  if (eps <= tol || it + 1 >= max_iter) {
+    st->done = 1;
+    st->iters = it + 1;
+    st->capped = eps > tol;
   }
 }
 
@@ -1170,12 +1234,13 @@ cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int wh
 }
 
 cudaError_t launch_ibm_den(const DomainDesc *D, const BatchDims &dims, int mode, cudaStream_t st) {
-  return launch_pdl(ibm_den_kernel, dim3(1, dims.nd), dim3(256), 0, st, D, mode);
+  return launch_pdl(ibm_den_kernel, dim3(RES_BLOCKS, dims.nd), dim3(256), 0, st, D, mode);
 }
 
 cudaError_t launch_ibm_check(const DomainDesc *D, const BatchDims &dims, int it, double tol,
                              int max_iter, cudaStream_t st) {
-  return launch_pdl(ibm_check_kernel, dim3(1, dims.nd), dim3(256), 0, st, D, it, tol, max_iter);
+  return launch_pdl(ibm_check_kernel, dim3(RES_BLOCKS, dims.nd), dim3(256), 0, st, D, it, tol,
+                    max_iter);
 }
 
 

@@ -134,17 +134,33 @@ __global__ void __launch_bounds__(256)
 }
 
 // End of a step: the FP64 sum of the collide kernel's partials in a fixed
-// order (FINISH_BLOCKS blocks per domain: each thread adds the partials of a
-// fixed strided subset, a warp combines its lanes with a butterfly, the block
-// its warps in order; the last block to finish combines the block sums the
-// same way), and t += 1.  With stats off only the step counter advances.
-constexpr int FINISH_BLOCKS = 64;
+// order, and t += 1.  A domain with P partials takes nb = min(FINISH_MAX,
+// ceil(P / 1024)) blocks of 256 threads, a function of its own size only (a
+// domain sums the same way alone or in a batch): thread j of block b adds the
+// partials b*256 + j + k*nb*256 in k order, the block adds its threads' sums
+// in a fixed tree, and the last block to finish adds the nb block sums with
+// the same tree.  FP64 arithmetic is slow on this part, so each partial is
+// added once and the trees use few warp instructions.  With stats off only the
+// step counter advances.
+constexpr int FINISH_MAX = 128;
 
-__device__ __forceinline__ void warp_sum4(double a[4]) {
+__host__ __device__ __forceinline__ int finish_blocks(int partials) {
+  const int nb = (partials + 1023) / 1024;
+  return nb < 1 ? 1 : (nb > FINISH_MAX ? FINISH_MAX : nb);
+}
+
+// red[c][0] = sum of red[c][0..256) for c < 4 (pairwise tree, fixed order);
+// every thread of the block calls it
+__device__ __forceinline__ void block_tree4(double (*red)[256]) {
+  const int t = threadIdx.x;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int o = 128; o > 0; o >>= 1) {
+    __syncthreads();
+    if (t < o)
 #pragma unroll
-    for (int c = 0; c < 4; c++) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+      for (int c = 0; c < 4; c++) red[c][t] += red[c][t + o];
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__restrict__ D,
@@ -156,51 +172,52 @@ __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__re
     if (blockIdx.x == 0 && threadIdx.x == 0) *dd.t += 1;
     return;
   }
-  __shared__ double red[8][4];
+  const int P = dd.cblocks, nb = finish_blocks(P);
+  if ((int)blockIdx.x >= nb) return;
+  __shared__ double red[4][256];
   __shared__ bool last;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int t = threadIdx.x;
   const double4_32a *__restrict__ partial = (const double4_32a *)dd.partial;
   double a[4] = {0, 0, 0, 0};
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < dd.cblocks; p += gridDim.x * blockDim.x) {
+  const int stride = nb * 256;
+  int p = blockIdx.x * 256 + t;
+  // four loads in flight per trip; the adds stay in k order
+  for (; p + 3 * stride < P; p += 4 * stride) {
+    double4_32a v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = partial[p + k * stride];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      a[0] += v[k].x;
+      a[1] += v[k].y;
+      a[2] += v[k].z;
+      a[3] += v[k].w;
+    }
+  }
+  for (; p < P; p += stride) {
     const double4_32a v = partial[p];
     a[0] += v.x;
     a[1] += v.y;
     a[2] += v.z;
     a[3] += v.w;
   }
-  warp_sum4(a);
-  if (lane == 0)
-    for (int c = 0; c < 4; c++) red[w][c] = a[c];
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double v = 0.0;
-    for (int k = 0; k < 8; k++) v += red[k][threadIdx.x];
-    dd.red_scratch[blockIdx.x * 4 + threadIdx.x] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+#pragma unroll
+  for (int c = 0; c < 4; c++) red[c][t] = a[c];
+  block_tree4(red);
+  if (t < 4) {
+    dd.red_scratch[blockIdx.x * 4 + t] = red[t][0];
     __threadfence();
-    last = atomicAdd(dd.ticket, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (t == 0) last = atomicAdd(dd.ticket, 1u) == (unsigned)nb - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // the block sums, FINISH_BLOCKS of them, one per thread
-  for (int c = 0; c < 4; c++)
-    a[c] = (int)threadIdx.x < (int)gridDim.x
-               ? ((volatile double *)dd.red_scratch)[threadIdx.x * 4 + c]
-               : 0.0;
-  warp_sum4(a);
-  __syncthreads();
-  if (lane == 0)
-    for (int c = 0; c < 4; c++) red[w][c] = a[c];
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double v = 0.0;
-    for (int k = 0; k < 8; k++) v += red[k][threadIdx.x];
-    dd.sums[threadIdx.x] = threadIdx.x == 0 ? (double)dd.g.ncell + v : v;
-  }
-  if (threadIdx.x == 0) {
+#pragma unroll
+  for (int c = 0; c < 4; c++) red[c][t] = t < nb ? __ldcg(dd.red_scratch + t * 4 + c) : 0.0;
+  block_tree4(red);
+  if (t < 4) dd.sums[t] = t == 0 ? (double)dd.g.ncell + red[0][0] : red[t][0];
+  if (t == 0) {
     *dd.ticket = 0u;
     *dd.t += 1;
   }
@@ -322,8 +339,10 @@ cudaError_t launch_collide_stream(int storage, const DomainDesc *D, const Domain
 
 cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats,
                                cudaStream_t st) {
-  return launch_pdl(finish_step_kernel, dim3(stats ? FINISH_BLOCKS : 1, dims.nd), dim3(256), 0, st,
-                    D, stats);
+  Geometry big{};
+  big.ncell = dims.max_cells;
+  const int nb = stats ? finish_blocks(collide_partials(big)) : 1;
+  return launch_pdl(finish_step_kernel, dim3(nb, dims.nd), dim3(256), 0, st, D, stats);
 }
 
 namespace {
