@@ -232,15 +232,31 @@ int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s);
 /* Picks the launch shape by timing trial steps on this handle's own lattice
  * and points: one parameter at a time (collide block, brick grid, point
  * block, moments bricks per block, sort grid), each candidate timed with CUDA
- * events over the stages it affects for steps_per_trial steps (>= 1) after
- * one untimed step, in two interleaved rounds (the faster kept), with
- * n_ibm_iter (> 0) fixed iterations; a candidate replaces the current value
- * only when more than 1 % faster.  The lattice is
+ * events around steps_per_trial whole steps (>= 1; the stages overlap, so
+ * the step is the objective) after one untimed step, in two interleaved
+ * rounds (the faster kept), with n_ibm_iter (> 0) fixed iterations; a
+ * candidate replaces the current value only when more than 1 % faster.  The
+ * lattice is
  * restored afterwards (populations, corrections, step counter, sums), so the
  * call does not advance the simulation; it allocates a copy of one
  * population lattice for that.  The chosen shape is set on the handle and
  * written to *chosen (may be NULL).  Stage timing is off on return. */
 int lbm_autotune(lbm_t *h, int n_ibm_iter, int steps_per_trial, lbm_launch_shape *chosen);
+
+/* on != 0: in a step with points, the cells outside that
+ * step's active bricks (those no point's support reaches, which need no IBM
+ * force, Sec. 2 step 3 with G = body force) collide on the handle's stream
+ * while the IBM stages (Sec. 3, Algs. 1-2) run on an internal stream of the
+ * greatest priority; the cells of the active bricks collide after the IBM
+ * loop on that stream, and the two meet before the step ends.  Every cell's
+ * arithmetic is the same either way; only the grouping of the FP64 partial
+ * sums of lbm_stats differs.  on == 0 (the default): one collide launch over
+ * every cell after the IBM loop, all on the handle's stream.  On a dense
+ * propeller array the overlapped step is slower (the latency-bound IBM
+ * kernels get SM slots only as collide blocks retire, and the collide's
+ * stream through L2 evicts their working set).  No counterpart in the paper
+ * (a scheduling choice).  Returns LBM_OK or LBM_EINVAL (NULL h). */
+int lbm_set_overlap(lbm_t *h, int on);
 
 /* ---- captured steps and batches of lattices ------------------------------ */
 

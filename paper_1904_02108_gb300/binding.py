@@ -91,6 +91,7 @@ _SIGS = {
     "lbm_read_deviations": (_i, [_p, _p]),
     "lbm_read_residuals": (_i, [_p, _p, _i]),
     "lbm_set_graph": (_i, [_p, _i]),
+    "lbm_set_overlap": (_i, [_p, _i]),
     "ibm_update_points": (_i, [_p, _i64, _p, _p]),
     "lbm_get_launch_shape": (_i, [_p, _p]),
     "lbm_set_launch_shape": (_i, [_p, _p]),
@@ -347,6 +348,11 @@ class Lattice:
     def set_graph(self, on=True):
         """Replay captured pairs of steps (fixed iteration counts)."""
         self._c(load().lbm_set_graph(self.h, int(on)))
+
+    def set_overlap(self, on=True):
+        """Collide the cells outside the active bricks while the IBM stages
+        run (the default), or every cell after the IBM loop."""
+        self._c(load().lbm_set_overlap(self.h, int(on)))
 
     def launch_shape(self):
         s = LaunchShape()

@@ -25,8 +25,8 @@ namespace {
 
 const char *kStageNames[] = {"kinematics",   "pairs",          "brick_init", "point_update",
                              "brick_spread", "collide_stream", "stats",      "residual",
-                             "mlp"};
-constexpr int kNumStages = 9;
+                             "mlp",          "collide_active"};
+constexpr int kNumStages = 10;
 enum Stage {
   ST_KIN,
   ST_PAIRS,
@@ -36,7 +36,8 @@ enum Stage {
   ST_COLLIDE,
   ST_STATS,
   ST_RESID,
-  ST_MLP
+  ST_MLP,
+  ST_COLLIDE_ACTIVE
 };
 // iterations launched between two host checks of the tolerance-mode stop flag
 constexpr int kCheckChunk = 16;
@@ -73,6 +74,15 @@ struct lbm {
   bool have_du = false;
   double gbody[3] = {0, 0, 0};
   int64_t t = 0;
+
+  // overlap: the collide of the cells outside the active bricks runs on st
+  // while the IBM stages and the active bricks' collide run on ibm_st
+  // (higher priority); off by default (slower on dense arrays, where the
+  // latency-bound IBM kernels lose their SM slots and L2 to the collide)
+  bool overlap = false;
+  cudaStream_t ibm_st = nullptr, ibm_cap = nullptr;  // ibm_cap: inside captures
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  double *slot_partial = nullptr;
 
   // statistics
   double *partial = nullptr, *sums = nullptr, *red_scratch = nullptr;
@@ -179,15 +189,19 @@ cudaEvent_t get_event(lbm_t *h) {
   return e;
 }
 
+// Times the launches of a stage on stream s with events (when the stage's
+// timing is on) and counts them.
 struct StageTimer {
   lbm_t *h;
   int stage;
   int n;
+  cudaStream_t s;
   cudaEvent_t a = nullptr;
-  StageTimer(lbm_t *h_, int stage_, int n_ = 1) : h(h_), stage(stage_), n(n_) {
+  StageTimer(lbm_t *h_, int stage_, cudaStream_t s_, int n_ = 1)
+      : h(h_), stage(stage_), n(n_), s(s_) {
     if (h->timing & (1 << stage)) {
       a = get_event(h);
-      if (a) cudaEventRecord(a, h->st);
+      if (a) cudaEventRecord(a, s);
     }
     h->nlaunch += n;
   }
@@ -195,7 +209,7 @@ struct StageTimer {
     if (a) {
       cudaEvent_t b = get_event(h);
       if (b) {
-        cudaEventRecord(b, h->st);
+        cudaEventRecord(b, s);
         h->pending.push_back({stage, a, b, n});
       }
     }
@@ -236,6 +250,7 @@ void free_points(lbm_t *h) {
   dfree(h->U0s);
   dfree(h->Gs);
   dfree(h->res);
+  dfree(h->slot_partial);
   h->cap_np = 0;
   h->m.max_slots = 0;
 }
@@ -307,6 +322,10 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->t_dev);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->ibm_st) cudaStreamDestroy(h->ibm_st);
+  if (h->ibm_cap) cudaStreamDestroy(h->ibm_cap);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   dfree(h->mlp_P);
@@ -459,6 +478,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->U0s, (size_t)ms * SLOT_FLOATS));
     CK(h, dalloc(&h->Gs, (size_t)ms * SLOT_FLOATS));
     CK(h, dalloc(&h->res, ms));
+    CK(h, dalloc(&h->slot_partial, (size_t)ms * 4));
     h->cap_np = n;
     h->m.max_slots = (int)ms;
   }
@@ -580,6 +600,7 @@ static DomainDesc host_desc(const lbm_t *h) {
   d.xpos = h->xpos;
   d.partial = h->partial;
   d.sums = h->sums;
+  d.slot_partial = h->slot_partial;
   d.red_scratch = h->red_scratch;
   d.ticket = h->ticket;
   d.state = h->state;
@@ -612,7 +633,11 @@ static BatchDims dims_of(const lbm_t *h) {
 }
 
 // What one step launches, for one lattice or a batch (uniform host-side
-// decisions; per-domain differences live in the descriptors).
+// decisions; per-domain differences live in the descriptors).  With split,
+// the cells outside the step's active bricks collide on st while the IBM
+// stages and then the active bricks' collide run on sti; the two meet
+// before the end of the step.  Without split, sti == st and one collide
+// launch does every cell after the IBM loop.
 struct StepCtx {
   lbm_t *acct;          // launch counting, timing, errors
   const DomainDesc *D;  // device descriptors
@@ -621,43 +646,63 @@ struct StepCtx {
   int storage, stats, cur;
   int warm_mode;
   bool have_du, features;
-  cudaStream_t st;
+  cudaStream_t st, sti;
+  bool split;
+  cudaEvent_t ev_fork, ev_join;
 };
 
-// Kinematics, pairs, moments, learned start / features, and the first
-// brick pass.  Returns the warm flag of the fixed point.
+// Kinematics and slots on st; with split, the fork to sti and the collide of
+// the cells outside the active bricks on st.
+static int enqueue_head(StepCtx &c) {
+  lbm_t *h = c.acct;
+  {
+    StageTimer T(h, ST_KIN, c.st, 1);
+    CK(h, launch_prepare_points(c.D, c.dims, c.st));
+  }
+  {
+    StageTimer T(h, ST_PAIRS, c.st, 1);
+    CK(h, launch_compact(c.D, c.dims, c.st));
+  }
+  if (c.split) {
+    CK(h, cudaEventRecord(c.ev_fork, c.st));
+    CK(h, cudaStreamWaitEvent(c.sti, c.ev_fork, 0));
+    StageTimer T(h, ST_COLLIDE, c.st);
+    CK(h, launch_collide_stream(c.storage, c.D, c.Dhost, c.dims, c.cur, c.stats, 1, c.st));
+  }
+  return LBM_OK;
+}
+
+// Pairs, moments, learned start / features, and the first brick pass, on
+// sti.  Returns the warm flag of the fixed point.
 static int enqueue_prefix(StepCtx &c, bool *warm_out) {
   lbm_t *h = c.acct;
   const bool mlp = c.warm_mode == LBM_WARM_MLP;
   const bool feat = mlp || c.features;
   const bool warm = (c.warm_mode == LBM_WARM_PREVIOUS && c.have_du) || mlp;
   *warm_out = warm;
+  const cudaStream_t s = c.sti;
   {
-    StageTimer T(h, ST_KIN, 1);
-    CK(h, launch_prepare_points(c.D, c.dims, c.st));
+    StageTimer T(h, ST_PAIRS, s, 2);
+    CK(h, launch_pair_lists(c.D, c.dims, s));
   }
   {
-    StageTimer T(h, ST_PAIRS, 3);
-    CK(h, launch_build_pairs(c.D, c.dims, c.st));
-  }
-  {
-    StageTimer T(h, ST_INIT, 1);
-    CK(h, launch_brick_moments(c.storage, c.D, c.dims, c.cur, c.st));
+    StageTimer T(h, ST_INIT, s, 1);
+    CK(h, launch_brick_moments(c.storage, c.D, c.dims, c.cur, s));
   }
   if (feat) {
     // features from the shares of I[U0 + S[du_prev]] (the previous step's
     // force applied); the learned start du = du_prev + V MLP(x)
-    StageTimer T(h, ST_MLP, mlp ? 3 : 2);
-    CK(h, launch_brick_init(c.D, c.dims, c.have_du, c.st));
-    CK(h, launch_mlp_features(c.D, c.dims, c.have_du, c.st));
-    if (mlp) CK(h, launch_mlp_warm(c.D, c.dims, c.have_du, c.st));
+    StageTimer T(h, ST_MLP, s, mlp ? 3 : 2);
+    CK(h, launch_brick_init(c.D, c.dims, c.have_du, s));
+    CK(h, launch_mlp_features(c.D, c.dims, c.have_du, s));
+    if (mlp) CK(h, launch_mlp_warm(c.D, c.dims, c.have_du, s));
   }
   // G_0 = S[du_init] and the shares of I[U0 + G_0], unless the feature pass
   // above already left exactly these
   const bool init_done = feat && !mlp && (warm == c.have_du);
   if (!init_done) {
-    StageTimer T(h, ST_INIT, 1);
-    CK(h, launch_brick_init(c.D, c.dims, warm, c.st));
+    StageTimer T(h, ST_INIT, s, 1);
+    CK(h, launch_brick_init(c.D, c.dims, warm, s));
   }
   return LBM_OK;
 }
@@ -666,26 +711,35 @@ static int enqueue_fixed_loop(StepCtx &c, int n_iter, bool warm) {
   lbm_t *h = c.acct;
   for (int it = 0; it < n_iter; it++) {
     {
-      StageTimer T(h, ST_UPDATE);
-      CK(h, launch_point_update(c.D, c.dims, it == 0, warm, 0, c.st));
+      StageTimer T(h, ST_UPDATE, c.sti);
+      CK(h, launch_point_update(c.D, c.dims, it == 0, warm, 0, c.sti));
     }
     {
-      StageTimer T(h, ST_SPREAD);
-      CK(h, launch_brick_spread(c.D, c.dims, it + 1 < n_iter, 0, c.st));
+      StageTimer T(h, ST_SPREAD, c.sti);
+      CK(h, launch_brick_spread(c.D, c.dims, it + 1 < n_iter, 0, c.sti));
     }
   }
   return LBM_OK;
 }
 
+// The collide of the cells with the IBM force (split: the active bricks on
+// sti, then the join), and the end of the step on st.
 static int enqueue_suffix(StepCtx &c) {
   lbm_t *h = c.acct;
-  {
-    StageTimer T(h, ST_COLLIDE);
-    CK(h, launch_collide_stream(c.storage, c.D, c.Dhost, c.dims, c.cur, c.stats, c.st));
+  if (c.split) {
+    {
+      StageTimer T(h, ST_COLLIDE_ACTIVE, c.sti);
+      CK(h, launch_collide_active(c.storage, c.D, c.dims, c.cur, c.stats, c.sti));
+    }
+    CK(h, cudaEventRecord(c.ev_join, c.sti));
+    CK(h, cudaStreamWaitEvent(c.st, c.ev_join, 0));
+  } else {
+    StageTimer T(h, ST_COLLIDE, c.st);
+    CK(h, launch_collide_stream(c.storage, c.D, c.Dhost, c.dims, c.cur, c.stats, 0, c.st));
   }
   {
-    StageTimer T(h, ST_STATS);
-    CK(h, launch_finish_step(c.D, c.dims, c.stats, c.st));
+    StageTimer T(h, ST_STATS, c.st);
+    CK(h, launch_finish_step(c.D, c.dims, c.stats, c.split, c.st));
   }
   return LBM_OK;
 }
@@ -693,8 +747,10 @@ static int enqueue_suffix(StepCtx &c) {
 // One full step with a fixed iteration count (n_iter > 0, or no points).
 static int enqueue_step(StepCtx &c, int n_iter) {
   if (c.dims.max_points > 0) {
+    int r = enqueue_head(c);
+    if (r) return r;
     bool warm = false;
-    int r = enqueue_prefix(c, &warm);
+    r = enqueue_prefix(c, &warm);
     if (r) return r;
     r = enqueue_fixed_loop(c, n_iter, warm);
     if (r) return r;
@@ -708,10 +764,10 @@ static int enqueue_step(StepCtx &c, int n_iter) {
 // when the cap was hit.
 static int tolerance_loop(StepCtx &c, bool warm) {
   lbm_t *h = c.acct;
-  cudaStream_t st = c.st;
+  cudaStream_t st = c.sti;
   {
     // denominator ||S[s u_k]||^2
-    StageTimer T(h, ST_RESID, 2);
+    StageTimer T(h, ST_RESID, st, 2);
     CK(h, launch_brick_norm(c.D, c.dims, 0, st));
     CK(h, launch_ibm_den(c.D, c.dims, 0, st));
   }
@@ -719,7 +775,7 @@ static int tolerance_loop(StepCtx &c, bool warm) {
   CK(h, cudaStreamSynchronize(st));
   if (h->state_host->den2 == 0.0) {
     // all surface velocities vanish: ||S[s (u_k - I[U0])]||^2 instead
-    StageTimer T(h, ST_RESID, warm ? 5 : 3);
+    StageTimer T(h, ST_RESID, st, warm ? 5 : 3);
     if (warm) CK(h, launch_brick_init(c.D, c.dims, 0, st));
     CK(h, launch_point_residual0(c.D, c.dims, st));
     CK(h, launch_brick_norm(c.D, c.dims, 1, st));
@@ -734,15 +790,15 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     const int chunk = std::min(it == 0 ? chunk0 : kCheckChunk, h->max_iter - it);
     for (int j = 0; j < chunk; j++, it++) {
       {
-        StageTimer T(h, ST_UPDATE);
+        StageTimer T(h, ST_UPDATE, st);
         CK(h, launch_point_update(c.D, c.dims, it == 0, warm, 1, st));
       }
       {
-        StageTimer T(h, ST_SPREAD);
+        StageTimer T(h, ST_SPREAD, st);
         CK(h, launch_brick_spread(c.D, c.dims, 1, 1, st));
       }
       {
-        StageTimer T(h, ST_RESID);
+        StageTimer T(h, ST_RESID, st);
         CK(h, launch_ibm_check(c.D, c.dims, it, h->tol, h->max_iter, st));
       }
     }
@@ -773,7 +829,29 @@ static StepCtx ctx_of(lbm_t *h, cudaStream_t st) {
   c.have_du = h->have_du;
   c.features = h->features_on;
   c.st = st;
+  c.sti = st;
+  c.split = false;
   return c;
+}
+
+// The IBM stream (greatest priority) and the fork/join events of a handle;
+// capture: the stream used inside graph captures.  Sets c.sti and c.split
+// when the step runs split.
+static int ensure_split(lbm_t *h, StepCtx &c, bool capture) {
+  if (!h->overlap || c.dims.max_points <= 0) return LBM_OK;
+  cudaStream_t *ps = capture ? &h->ibm_cap : &h->ibm_st;
+  if (!*ps) {
+    int lo = 0, hi = 0;
+    CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(h, cudaStreamCreateWithPriority(ps, cudaStreamNonBlocking, hi));
+  }
+  if (!h->ev_fork) CK(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  if (!h->ev_join) CK(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  c.sti = *ps;
+  c.split = true;
+  c.ev_fork = h->ev_fork;
+  c.ev_join = h->ev_join;
+  return LBM_OK;
 }
 
 // host-side bookkeeping after a step was enqueued
@@ -795,10 +873,14 @@ static void after_step(lbm_t *h, int n_iter) {
 
 static int step_once(lbm_t *h, int n_iter) {
   StepCtx c = ctx_of(h, h->st);
+  int r0 = ensure_split(h, c, false);
+  if (r0) return r0;
   int warn = LBM_OK;
   if (h->np > 0 && n_iter == 0) {
+    int r = enqueue_head(c);
+    if (r) return r;
     bool warm = false;
-    int r = enqueue_prefix(c, &warm);
+    r = enqueue_prefix(c, &warm);
     if (r) return r;
     warn = tolerance_loop(c, warm);
     if (warn < 0) return warn;
@@ -845,6 +927,10 @@ static int capture_two_steps(StepCtx c, int n_iter, cudaStream_t cs, cudaGraphEx
   const int64_t l0 = h->nlaunch;
   h->timing = 0;
   c.st = cs;
+  c.sti = cs;
+  c.split = false;
+  int r0 = ensure_split(h, c, true);
+  if (r0) return r0;
   CK(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   int r = enqueue_step(c, n_iter);
   if (r == LBM_OK) {
@@ -926,6 +1012,17 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
 int lbm_set_graph(lbm_t *h, int on) {
   if (!h) return LBM_EINVAL;
   h->graph_on = on != 0;
+  return LBM_OK;
+}
+
+int lbm_set_overlap(lbm_t *h, int on) {
+  if (!h) return LBM_EINVAL;
+  if (h->overlap != (on != 0)) {
+    if (h->st) cudaStreamSynchronize(h->st);
+    if (h->ibm_st) cudaStreamSynchronize(h->ibm_st);
+    h->overlap = on != 0;
+    h->version++;  // a new capture
+  }
   return LBM_OK;
 }
 
@@ -1065,7 +1162,11 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
       continue;
     }
     c.st = h0->st;
-    int r = enqueue_step(c, n_ibm_iter);
+    c.sti = h0->st;
+    c.split = false;
+    int r = ensure_split(h0, c, false);
+    if (r) return r;
+    r = enqueue_step(c, n_ibm_iter);
     if (r) return r;
     for (lbm_t *h : b->hs) after_step(h, n_ibm_iter);
     have_du = have_du || dims.max_points > 0;
@@ -1195,8 +1296,9 @@ std::vector<TuneParam> tune_params(bool points) {
 }
 
 // Coordinate search over tune_params: step(k) advances the lattices k steps
-// with the current shape, stage_ms(mask) reads the time of the stages in mask
-// since the last clear(mask).  Each candidate is timed in kRounds interleaved
+// with the current shape; clear(mask) starts timing (mask != 0) or stops it,
+// and stage_ms reads the device time of the steps timed since (whole steps:
+// the stages of a step overlap).  Each candidate is timed in kRounds interleaved
 // rounds and keeps its fastest; a candidate replaces the current value only
 // when it is more than kMargin faster (timing noise does not move the shape).
 constexpr int kRounds = 2;
@@ -1241,16 +1343,6 @@ int coordinate_search(LaunchShape &shape, bool points, int steps_per_trial, SetS
   return clear(0);
 }
 
-int read_stage_ms(lbm_t *h, int mask, double *out) {
-  double ms[kNumStages];
-  int r = lbm_read_timing(h, ms, nullptr);
-  if (r) return r;
-  double a = 0.0;
-  for (int i = 0; i < kNumStages; i++)
-    if (mask & (1 << i)) a += ms[i];
-  *out = a;
-  return LBM_OK;
-}
 
 }  // namespace
 
@@ -1281,17 +1373,39 @@ int lbm_autotune(lbm_t *h, int n_ibm_iter, int steps_per_trial, lbm_launch_shape
     return r;
   }
   const bool graph = h->graph_on;
-  h->graph_on = false;  // stage timing is not recorded in replayed steps
+  h->graph_on = false;
   LaunchShape shape = h->shape;
-  r = coordinate_search(
-      shape, h->np > 0, steps_per_trial,
-      [&](const LaunchShape &l) {
-        lbm_launch_shape c = to_c(l);
-        return lbm_set_launch_shape(h, &c);
-      },
-      [&](int k) { return lbm_step(h, k, n_ibm_iter); },
-      [&](int mask) { return lbm_enable_timing(h, mask); },
-      [&](int mask, double *ms) { return read_stage_ms(h, mask, ms); });
+  // whole steps, timed with events on the handle's stream
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float last_ms = 0.f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    r = fail(h, LBM_ECUDA, "event creation");
+  bool timing = false;
+  if (r == LBM_OK)
+    r = coordinate_search(
+        shape, h->np > 0, steps_per_trial,
+        [&](const LaunchShape &l) {
+          lbm_launch_shape c = to_c(l);
+          return lbm_set_launch_shape(h, &c);
+        },
+        [&](int k) {
+          if (timing) cudaEventRecord(e0, h->st);
+          const int rr = lbm_step(h, k, n_ibm_iter);
+          if (timing) cudaEventRecord(e1, h->st);
+          return rr;
+        },
+        [&](int mask) {
+          timing = mask != 0;
+          return LBM_OK;
+        },
+        [&](int, double *ms) {
+          CK(h, cudaEventSynchronize(e1));
+          CK(h, cudaEventElapsedTime(&last_ms, e0, e1));
+          *ms = last_ms;
+          return LBM_OK;
+        });
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   h->graph_on = graph;
   const int r2 = snapshot_restore(h, sn);
   snapshot_free(sn);
@@ -1813,7 +1927,8 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
     dims.max_slots = m.max_slots;
     if (e == cudaSuccess) e = cudaMemcpyAsync(D, &dd, sizeof dd, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_prepare_points(D, dims, st);
-    if (e == cudaSuccess) e = launch_build_pairs(D, dims, st);
+    if (e == cudaSuccess) e = launch_compact(D, dims, st);
+    if (e == cudaSuccess) e = launch_pair_lists(D, dims, st);
     if (e == cudaSuccess) e = launch_pack_vals(n, v, vals, st);
     if (e == cudaSuccess) e = launch_brick_spread(D, dims, 0, 0, st);
     if (e == cudaSuccess) e = launch_slots_to_dense(g, m, Gs, F, st);

@@ -72,12 +72,12 @@ struct Store<__half> {
 // step kernel calls pdl_wait() (which returns once the predecessor grid has
 // completed and its writes are visible) before it touches anything the
 // predecessor wrote, and pdl_wait() precedes every exit, so completion still
-// chains through the stream; pdl_launch_dependents() right after lets the
-// next kernel be scheduled early.  Both are no-ops for a plain launch.
+// chains through the stream.  No kernel triggers its dependents early
+// (griddepcontrol.launch_dependents): blocks of the next kernel would sit
+// resident at pdl_wait and take registers and shared memory from the running
+// one (measured slower); the implicit trigger at block exit is kept.  A no-op
+// for a plain launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Launches kern<<<grid, block, smem, st>>>(args...) with programmatic stream
 // serialization allowed.
@@ -89,11 +89,16 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  // the stream's priority goes with the launch (kept in captured graphs)
+  int prio = 0;
+  if (cudaStreamGetPriority(st, &prio) != cudaSuccess) prio = 0;
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = prio;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
@@ -141,6 +146,13 @@ struct BrickMap {
                               // compaction scan
   int max_slots;
 };
+
+// Active slots of this step (0 when the compaction did not complete).
+__device__ __forceinline__ int active_slots(const BrickMap &m) {
+  if (m.counters[1] & 4) return 0;
+  const int n = m.counters[0];
+  return n < m.max_slots ? n : m.max_slots;
+}
 
 // (brick, point) pairs: one per brick that a point's support overlaps (at most
 // eight per point).  Grouped by slot, ascending point index inside a slot (a
@@ -226,6 +238,8 @@ struct DomainDesc {
   float4 *du, *uint;
   double *xpos;
   double *partial, *sums;  // collide partials [cblocks][4], FP64 sums [4]
+  double *slot_partial;    // [max_slots][4] partials of the active bricks'
+                           // collide when it runs apart from the others
   double *red_scratch;     // [128][4] block sums of the final reduction
   unsigned *ticket;        // blocks of the final reduction done (reset by
                            // the last one)

@@ -141,7 +141,6 @@ constexpr int TRIG_CACHE = 16;
 __global__ void __launch_bounds__(512, 2)
     prepare_points_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
   const int delta = d.delta;
@@ -258,7 +257,6 @@ constexpr unsigned SCAN_SPIN_LIMIT = 1u << 22;
 // and the step's slots are left empty.
 __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
   const BrickMap m = d.m;
@@ -406,15 +404,9 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
   }
 }
 
-__device__ __forceinline__ int active_slots(const BrickMap &m) {
-  if (m.counters[1] & 4) return 0;  // the compaction did not complete
-  const int n = m.counters[0];
-  return n < m.max_slots ? n : m.max_slots;
-}
 
 __global__ void __launch_bounds__(512) pair_fill_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
   const int64_t np = d.np;
@@ -519,7 +511,6 @@ __device__ __forceinline__ void warp_rank_sort(int *a, int cnt, int lane) {
 __global__ void __launch_bounds__(128)
     pair_sort_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
-  pdl_launch_dependents();
   __shared__ int buf[4][SORT_CAP];
   const BrickMap m = D[blockIdx.y].m;
   const PairMap pm = D[blockIdx.y].pm;
@@ -712,7 +703,6 @@ template <typename S>
 __global__ void __launch_bounds__(256)
     brick_moments_kernel(const DomainDesc *__restrict__ D, int cur) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const S *__restrict__ f = (const S *)d.f[cur];
   const Geometry g = d.g;
@@ -743,7 +733,6 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(32, 32)
     brick_init_kernel(const DomainDesc *__restrict__ D, int use_du) {
   pdl_wait();
-  pdl_launch_dependents();
   __shared__ BrickSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   const BrickMap m = d.m;
@@ -778,7 +767,6 @@ __global__ void __launch_bounds__(32, 32)
 __global__ void __launch_bounds__(32, 32)
     brick_spread_kernel(const DomainDesc *__restrict__ D, int do_interp, int tol_mode) {
   pdl_wait();
-  pdl_launch_dependents();
   __shared__ BrickSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   if (tol_mode && d.state->done) return;
@@ -829,7 +817,6 @@ __global__ void __launch_bounds__(32, 32)
 __global__ void __launch_bounds__(32, 32)
     brick_norm_kernel(const DomainDesc *__restrict__ D, int which) {
   pdl_wait();
-  pdl_launch_dependents();
   __shared__ BrickSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   const BrickMap m = d.m;
@@ -895,7 +882,6 @@ __device__ bool res_sum(const BrickMap &m, const float *__restrict__ res, IbmSta
 __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restrict__ D,
                                                        int mode) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
   double v;
@@ -915,7 +901,6 @@ __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restri
 __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__restrict__ D, int it,
                                                          double tol, int max_iter) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
   if (st->done) return;
@@ -936,7 +921,6 @@ __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__rest
 __global__ void __launch_bounds__(512)
     point_update_kernel(const DomainDesc *__restrict__ D, int first, int warm, int tol_mode) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.np) return;
@@ -972,7 +956,6 @@ __global__ void __launch_bounds__(512)
 __global__ void __launch_bounds__(512)
     point_residual0_kernel(const DomainDesc *__restrict__ D) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.np) return;
@@ -1010,7 +993,6 @@ __global__ void __launch_bounds__(512)
 __global__ void __launch_bounds__(512)
     mlp_features_kernel(const DomainDesc *__restrict__ D, int use_prev) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.np) return;
@@ -1172,20 +1154,21 @@ cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cu
                     st, D);
 }
 
-cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
-  cudaError_t e = launch_pdl(compact_kernel, dim3(nblk(dims.max_bricks, COMPACT_TILE), dims.nd),
-                             dim3(256), 0, st, D);
-  if (e == cudaSuccess && dims.max_points > 0) {
-    const int pb = dims.ls.point_block;
-    e = launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0, st, D);
-    // one warp per slot
-    if (e == cudaSuccess)
-      e = launch_pdl(pair_sort_kernel,
-                     dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, dims.ls.sort_blocks),
-                          dims.nd),
-                     dim3(128), 0, st, D);
+cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+  return launch_pdl(compact_kernel, dim3(nblk(dims.max_bricks, COMPACT_TILE), dims.nd), dim3(256),
+                    0, st, D);
+}
 
-  }
+cudaError_t launch_pair_lists(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  const int pb = dims.ls.point_block;
+  cudaError_t e =
+      launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0, st, D);
+  // one warp per slot
+  if (e == cudaSuccess)
+    e = launch_pdl(pair_sort_kernel,
+                   dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, dims.ls.sort_blocks), dims.nd),
+                   dim3(128), 0, st, D);
   return e;
 }
 

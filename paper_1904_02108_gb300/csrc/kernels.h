@@ -9,15 +9,22 @@ namespace lbmibm {
 
 // ----------------------------------------------------------------- lbm.cu
 // Fused pull-stream + collision f[cur] -> f[1 - cur] of every domain, with
-// the IBM force of its active bricks and its body force; per-block FP64
-// partial sums when stats.
+// the IBM force of its active bricks and its body force; FP64 partial sums
+// per PARTIAL_CELLS cells when stats.  skip_active: the cells of the step's
+// active bricks are left out (launch_collide_active does them).
 // Dhost: host copy of D when dims.nd == 1 (passed as a kernel parameter), or
 // NULL.
 cudaError_t launch_collide_stream(int storage, const DomainDesc *D, const DomainDesc *Dhost,
-                                  const BatchDims &dims, int cur, int stats, cudaStream_t st);
+                                  const BatchDims &dims, int cur, int stats, int skip_active,
+                                  cudaStream_t st);
+// The same collision on the cells of the active bricks only (after the IBM
+// loop); FP64 partial sums per slot when stats.
+cudaError_t launch_collide_active(int storage, const DomainDesc *D, const BatchDims &dims,
+                                  int cur, int stats, cudaStream_t st);
 // End of a step: FP64 reduction of the collide partials into sums (if
-// stats) and t += 1 of every domain (one block per domain).
-cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats,
+// stats; split: with the active bricks' slot partials) and t += 1 of every
+// domain.
+cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats, int split,
                                cudaStream_t st);
 // FP64 partial sums per step of a lattice (one per PARTIAL_CELLS cells)
 int collide_partials(const Geometry &g);
@@ -51,9 +58,11 @@ struct PointsIn {
 // Kinematics (Alg. 1, first iteration; each block computes the rotation of
 // its points' bodies once) + per-point weights + brick counts.
 cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
-// counted bricks -> slots; (brick, point) pairs grouped by brick in a fixed
-// order, with brick-local weights (3 launches when points exist, else 1)
-cudaError_t launch_build_pairs(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
+// counted bricks -> slots (1 launch)
+cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
+// (brick, point) pairs grouped by slot in a fixed order, with brick-local
+// weights (2 launches when points exist, else none)
+cudaError_t launch_pair_lists(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // U0 on the active bricks (pull + Eq. 1) from lattice f[cur]
 cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDims &dims, int cur,
                                  cudaStream_t st);

@@ -20,10 +20,63 @@ namespace lbmibm {
 
 namespace {
 
+// One cell of the fused pull-stream + collision: pull of Eq. 4 into d, Eq. 1
+// moments, U^G = U + tau G (Sec. 2 step 3) and the BGK relaxation towards
+// Eq. 3, written to dst at n.  G is the cell's force (body force plus its
+// brick's IBM force).  st receives the cell's post-collision mass and
+// momentum sums (the collision conserves mass and adds rho G of momentum,
+// Eqs. 2-3, so they follow from the moments).
+template <typename S>
+__device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__restrict__ dst,
+                                             const Geometry &g, uint32_t n, int x, int y, int z,
+                                             float Gx, float Gy, float Gz, float tau,
+                                             float st[4]) {
+  float d[Q];
+  pull<S>(src, g, x, y, z, d);
+  float drho, jx, jy, jz;
+  moments(d, drho, jx, jy, jz);
+  const float rho = 1.f + drho;
+  const float inv = 1.f / rho;
+  const float ux = jx * inv + tau * Gx;
+  const float uy = jy * inv + tau * Gy;
+  const float uz = jz * inv + tau * Gz;
+  const float om = 1.f / tau;
+  // Eq. 3 minus t_i: t_i (c0 + rho (3 e.u + 4.5 (e.u)^2)) with c0 the part
+  // common to every direction; opposite directions share 4.5 rho (e.u)^2
+  const float c0 = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
+  const float r3 = 3.f * rho, r45 = 4.5f * rho;
+  const size_t N = (size_t)g.ncell;
+  float dn[Q];
+  dn[0] = d[0] + om * (wt(0) * c0 - d[0]);
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const float eu = (float)ex(i) * ux + (float)ey(i) * uy + (float)ez(i) * uz;
+    const float sym = c0 + r45 * eu * eu, anti = r3 * eu;
+    const float eqp = wt(i) * (sym + anti), eqm = wt(i) * (sym - anti);
+    dn[i] = d[i] + om * (eqp - d[i]);
+    dn[i + 1] = d[i + 1] + om * (eqm - d[i + 1]);
+  }
+#pragma unroll
+  for (int i = 0; i < Q; i++) Store<S>::st(dst + ((size_t)i * N + n), dn[i]);
+  st[0] = drho;
+  st[1] = jx + rho * Gx;
+  st[2] = jy + rho * Gy;
+  st[3] = jz + rho * Gz;
+}
+
+__device__ __forceinline__ void warp_sum4f(float a[4]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < 4; c++) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+}
+
 // One thread per cell.  dd is the domain of this block: a kernel parameter
 // for a single lattice (constant bank, no dependent loads before the first
-// population load), or D[blockIdx.y] of a batch.
-template <typename S, bool STATS>
+// population load), or D[blockIdx.y] of a batch.  SKIP: the cells of the
+// step's active bricks are left to collide_active_kernel (they need the IBM
+// force, the others do not); otherwise every cell, with its brick's force.
+template <typename S, bool STATS, bool SKIP>
 __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int cur) {
   const Geometry g = dd.g;
   // blocks past this domain's cells (batches of unequal domains) leave at once
@@ -31,80 +84,43 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
   const S *__restrict__ src = (const S *)dd.f[cur];
   S *__restrict__ dst = (S *)dd.f[cur ^ 1];
   const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
+  const int nact = SKIP && brick_slot ? active_slots(dd.m) : 0;
   const float *__restrict__ Gs = dd.Gs;
-  const float gbx = dd.gbody[0], gby = dd.gbody[1], gbz = dd.gbody[2], tau = dd.tau;
   double *__restrict__ partial = dd.partial;
-  float sm = 0.f, spx = 0.f, spy = 0.f, spz = 0.f;
+  float sv[4] = {0.f, 0.f, 0.f, 0.f};
   const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < (uint32_t)g.ncell) {
     int x, y, z;
     cell_coords(n, g, x, y, z);
-    float d[Q];
-    pull<S>(src, g, x, y, z, d);
-    float drho, jx, jy, jz;
-    moments(d, drho, jx, jy, jz);
-    const float rho = 1.f + drho;
-    const float inv = 1.f / rho;
-    // Sec. 2 step 3: U^G = U + tau G
-    float Gx = gbx, Gy = gby, Gz = gbz;
+    float Gx = dd.gbody[0], Gy = dd.gbody[1], Gz = dd.gbody[2];
+    bool mine = true;
     if (brick_slot) {
       const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
       const int s = __ldg(brick_slot + b);
-      if (s >= 0) {
+      if (SKIP) {
+        mine = !(s >= 0 && s < nact);
+      } else if (s >= 0) {
         const float *p = Gs + (size_t)s * SLOT_FLOATS + brick_local(x, y, z);
         Gx += __ldg(p);
         Gy += __ldg(p + BRICK_CELLS);
         Gz += __ldg(p + 2 * BRICK_CELLS);
       }
     }
-    const float ux = jx * inv + tau * Gx;
-    const float uy = jy * inv + tau * Gy;
-    const float uz = jz * inv + tau * Gz;
-    const float om = 1.f / tau;
-    // Eq. 3 minus t_i: t_i (c0 + rho (3 e.u + 4.5 (e.u)^2)) with c0 the part
-    // common to every direction; opposite directions share 4.5 rho (e.u)^2
-    const float c0 = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
-    const float r3 = 3.f * rho, r45 = 4.5f * rho;
-    const size_t N = (size_t)g.ncell;
-    float dn[Q];
-    dn[0] = d[0] + om * (wt(0) * c0 - d[0]);
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-      const float eu = (float)ex(i) * ux + (float)ey(i) * uy + (float)ez(i) * uz;
-      const float sym = c0 + r45 * eu * eu, anti = r3 * eu;
-      const float eqp = wt(i) * (sym + anti), eqm = wt(i) * (sym - anti);
-      dn[i] = d[i] + om * (eqp - d[i]);
-      dn[i + 1] = d[i + 1] + om * (eqm - d[i + 1]);
-    }
-#pragma unroll
-    for (int i = 0; i < Q; i++) Store<S>::st(dst + ((size_t)i * N + n), dn[i]);
-    if (STATS) {
-      // the collision conserves mass and adds rho G of momentum (Eqs. 2-3):
-      // the cell's post-collision sums, from its moments
-      sm = drho;
-      spx = jx + rho * Gx;
-      spy = jy + rho * Gy;
-      spz = jz + rho * Gz;
+    if (mine) {
+      float st[4];
+      collide_cell<S>(src, dst, g, n, x, y, z, Gx, Gy, Gz, dd.tau, st);
+      if (STATS)
+        for (int c = 0; c < 4; c++) sv[c] = st[c];
     }
   }
   if (STATS) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sm += __shfl_xor_sync(0xffffffffu, sm, o);
-      spx += __shfl_xor_sync(0xffffffffu, spx, o);
-      spy += __shfl_xor_sync(0xffffffffu, spy, o);
-      spz += __shfl_xor_sync(0xffffffffu, spz, o);
-    }
+    warp_sum4f(sv);
     // one partial per PARTIAL_CELLS cells (four warps), whatever the block
     // size: the sums do not depend on the launch shape
     __shared__ double red[8][4];
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-      red[w][0] = sm;
-      red[w][1] = spx;
-      red[w][2] = spy;
-      red[w][3] = spz;
-    }
+    if ((threadIdx.x & 31) == 0)
+      for (int c = 0; c < 4; c++) red[w][c] = sv[c];
     __syncthreads();
     const int groups = blockDim.x / PARTIAL_CELLS;
     if ((int)threadIdx.x < 4 * groups) {
@@ -117,20 +133,69 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
   }
 }
 
-template <typename S, bool STATS>
+template <typename S, bool STATS, bool SKIP>
 __global__ void __launch_bounds__(256)
     collide_stream_kernel(const __grid_constant__ DomainDesc dd, int cur) {
   pdl_wait();
-  pdl_launch_dependents();
-  collide_stream_cells<S, STATS>(dd, cur);
+  collide_stream_cells<S, STATS, SKIP>(dd, cur);
 }
 
-template <typename S, bool STATS>
+template <typename S, bool STATS, bool SKIP>
 __global__ void __launch_bounds__(256)
     collide_stream_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
   pdl_wait();
-  pdl_launch_dependents();
-  collide_stream_cells<S, STATS>(D[blockIdx.y], cur);
+  collide_stream_cells<S, STATS, SKIP>(D[blockIdx.y], cur);
+}
+
+// The cells of the active bricks, after the IBM loop: 64 threads per slot
+// (one per cell), four slots per block, grid-stride over the slots; the same
+// per-cell arithmetic as collide_stream_cells with G = body force + the
+// slot's G.  STATS: one FP64 partial per slot (its two warps' FP32 sums).
+template <typename S, bool STATS>
+__global__ void __launch_bounds__(256)
+    collide_active_kernel(const DomainDesc *__restrict__ D, int cur) {
+  pdl_wait();
+  const DomainDesc &dd = D[blockIdx.y];
+  if (dd.np <= 0) return;
+  const Geometry g = dd.g;
+  const S *__restrict__ src = (const S *)dd.f[cur];
+  S *__restrict__ dst = (S *)dd.f[cur ^ 1];
+  const float *__restrict__ Gs = dd.Gs;
+  const BrickMap m = dd.m;
+  const int nact = active_slots(m);
+  __shared__ float red[8][4];
+  const int t = threadIdx.x & 63, w = threadIdx.x >> 5;
+  // (every thread of a block takes the same number of trips)
+  for (int s0 = blockIdx.x * 4; s0 < nact; s0 += gridDim.x * 4) {
+    const int s = s0 + (threadIdx.x >> 6);
+    float sv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (s < nact) {
+      const int B = m.slot_brick[s];
+      const int bx = B % g.nbx, rr = B / g.nbx;
+      const int by = rr % g.nby, bz = rr / g.nby;
+      const int x = bx * 4 + (t & 3), y = by * 4 + ((t >> 2) & 3), z = bz * 4 + (t >> 4);
+      const uint32_t n = (uint32_t)(((size_t)z * g.ny + y) * g.nx + x);
+      const float *p = Gs + (size_t)s * SLOT_FLOATS + t;
+      float st[4];
+      collide_cell<S>(src, dst, g, n, x, y, z, dd.gbody[0] + p[0],
+                      dd.gbody[1] + p[BRICK_CELLS], dd.gbody[2] + p[2 * BRICK_CELLS], dd.tau,
+                      st);
+      if (STATS)
+        for (int c = 0; c < 4; c++) sv[c] = st[c];
+    }
+    if (STATS) {
+      warp_sum4f(sv);
+      if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 4; c++) red[w][c] = sv[c];
+      __syncthreads();
+      if ((threadIdx.x & 63) < 4) {
+        const int c = threadIdx.x & 3, q = threadIdx.x >> 6;
+        if (s < nact)
+          dd.slot_partial[(size_t)s * 4 + c] = (double)red[2 * q][c] + (double)red[2 * q + 1][c];
+      }
+      __syncthreads();
+    }
+  }
 }
 
 // End of a step: the FP64 sum of the collide kernel's partials in a fixed
@@ -139,7 +204,8 @@ __global__ void __launch_bounds__(256)
 // domain sums the same way alone or in a batch): thread j of block b adds the
 // partials b*256 + j + k*nb*256 in k order, the block adds its threads' sums
 // in a fixed tree, and the last block to finish adds the nb block sums with
-// the same tree.  FP64 arithmetic is slow on this part, so each partial is
+// the same tree (split: the active bricks' slot partials follow the cells'
+// partials in the index range).  FP64 arithmetic is slow on this part, so each partial is
 // added once and the trees use few warp instructions.  With stats off only the
 // step counter advances.
 constexpr int FINISH_MAX = 128;
@@ -164,16 +230,18 @@ __device__ __forceinline__ void block_tree4(double (*red)[256]) {
 }
 
 __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__restrict__ D,
-                                                          int stats) {
+                                                          int stats, int split) {
   pdl_wait();
-  pdl_launch_dependents();
   const DomainDesc &dd = D[blockIdx.y];
   if (!stats) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *dd.t += 1;
     return;
   }
-  const int P = dd.cblocks, nb = finish_blocks(P);
+  // the partials of the cells, then (split) those of the active bricks
+  const int P0 = dd.cblocks, nb = finish_blocks(P0);
   if ((int)blockIdx.x >= nb) return;
+  const int P = P0 + (split && dd.np > 0 ? active_slots(dd.m) : 0);
+  const double4_32a *__restrict__ sp = (const double4_32a *)dd.slot_partial;
   __shared__ double red[4][256];
   __shared__ bool last;
   const int t = threadIdx.x;
@@ -185,7 +253,10 @@ __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__re
   for (; p + 3 * stride < P; p += 4 * stride) {
     double4_32a v[4];
 #pragma unroll
-    for (int k = 0; k < 4; k++) v[k] = partial[p + k * stride];
+    for (int k = 0; k < 4; k++) {
+      const int q = p + k * stride;
+      v[k] = q < P0 ? partial[q] : sp[q - P0];
+    }
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       a[0] += v[k].x;
@@ -195,7 +266,7 @@ __global__ void __launch_bounds__(256) finish_step_kernel(const DomainDesc *__re
     }
   }
   for (; p < P; p += stride) {
-    const double4_32a v = partial[p];
+    const double4_32a v = p < P0 ? partial[p] : sp[p - P0];
     a[0] += v.x;
     a[1] += v.y;
     a[2] += v.z;
@@ -305,15 +376,27 @@ inline unsigned cell_blocks(const Geometry &g, int threads) {
 
 template <typename S>
 cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const BatchDims &dims,
-                          int cur, int stats, cudaStream_t st) {
+                          int cur, int stats, int skip_active, cudaStream_t st) {
   const int bs = dims.ls.collide_block;
   if (bs != 128 && bs != 256) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)((dims.max_cells + bs - 1) / bs), dims.nd), block(bs);
-  if (dims.nd == 1 && Dhost)
-    return stats ? launch_pdl(collide_stream_kernel<S, true>, grid, block, 0, st, *Dhost, cur)
-                 : launch_pdl(collide_stream_kernel<S, false>, grid, block, 0, st, *Dhost, cur);
-  return stats ? launch_pdl(collide_stream_batch_kernel<S, true>, grid, block, 0, st, D, cur)
-               : launch_pdl(collide_stream_batch_kernel<S, false>, grid, block, 0, st, D, cur);
+#define LBM_COLLIDE(ST, SK)                                                                 \
+  (dims.nd == 1 && Dhost                                                                    \
+       ? launch_pdl(collide_stream_kernel<S, ST, SK>, grid, block, 0, st, *Dhost, cur)      \
+       : launch_pdl(collide_stream_batch_kernel<S, ST, SK>, grid, block, 0, st, D, cur))
+  if (skip_active) return stats ? LBM_COLLIDE(true, true) : LBM_COLLIDE(false, true);
+  return stats ? LBM_COLLIDE(true, false) : LBM_COLLIDE(false, false);
+#undef LBM_COLLIDE
+}
+
+template <typename S>
+cudaError_t collide_active_typed(const DomainDesc *D, const BatchDims &dims, int cur, int stats,
+                                 cudaStream_t st) {
+  if (dims.max_slots <= 0) return cudaSuccess;
+  const unsigned nb = (unsigned)std::min((dims.max_slots + 3) / 4, 152 * 16);
+  const dim3 grid(nb, dims.nd);
+  return stats ? launch_pdl(collide_active_kernel<S, true>, grid, dim3(256), 0, st, D, cur)
+               : launch_pdl(collide_active_kernel<S, false>, grid, dim3(256), 0, st, D, cur);
 }
 
 }  // namespace
@@ -333,16 +416,22 @@ int collide_partials(const Geometry &g) { return (int)cell_blocks(g, PARTIAL_CEL
   }
 
 cudaError_t launch_collide_stream(int storage, const DomainDesc *D, const DomainDesc *Dhost,
-                                  const BatchDims &dims, int cur, int stats, cudaStream_t st) {
-  DISPATCH_STORAGE(storage, collide_typed, D, Dhost, dims, cur, stats, st);
+                                  const BatchDims &dims, int cur, int stats, int skip_active,
+                                  cudaStream_t st) {
+  DISPATCH_STORAGE(storage, collide_typed, D, Dhost, dims, cur, stats, skip_active, st);
 }
 
-cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats,
+cudaError_t launch_collide_active(int storage, const DomainDesc *D, const BatchDims &dims,
+                                  int cur, int stats, cudaStream_t st) {
+  DISPATCH_STORAGE(storage, collide_active_typed, D, dims, cur, stats, st);
+}
+
+cudaError_t launch_finish_step(const DomainDesc *D, const BatchDims &dims, int stats, int split,
                                cudaStream_t st) {
   Geometry big{};
   big.ncell = dims.max_cells;
   const int nb = stats ? finish_blocks(collide_partials(big)) : 1;
-  return launch_pdl(finish_step_kernel, dim3(nb, dims.nd), dim3(256), 0, st, D, stats);
+  return launch_pdl(finish_step_kernel, dim3(nb, dims.nd), dim3(256), 0, st, D, stats, split);
 }
 
 namespace {

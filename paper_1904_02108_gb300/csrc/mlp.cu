@@ -221,7 +221,6 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     mlp_warm_kernel(const DomainDesc *__restrict__ D, int use_prev) {
   pdl_wait();
-  pdl_launch_dependents();
   __shared__ MlpSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   if (d.np == 0 || !d.mlp_packed) return;

@@ -33,7 +33,7 @@ def test_velocity_set_matches_oracle_table(L, orc):
 def test_stage_names(L):
     assert binding.stage_names() == ["kinematics", "pairs", "brick_init", "point_update",
                                      "brick_spread", "collide_stream", "stats", "residual",
-                                     "mlp"]
+                                     "mlp", "collide_active"]
 
 
 @pytest.mark.parametrize("dims,tau", [((0, 8, 8), 0.8), ((8, 8, 6), 0.8), ((8, 8, 8), 0.5),

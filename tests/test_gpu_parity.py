@@ -275,6 +275,7 @@ def test_timing_and_launch_counters(gpu_lib, torch_cuda):
     t = lat.timing()
     assert t["collide_stream"][1] == 3 and t["point_update"][1] == 15
     assert t["brick_spread"][1] == 15 and t["brick_init"][1] == 6 and t["pairs"][1] == 9
+    assert t["collide_active"][1] == 0  # one collide over every cell (no overlap)
     assert all(ms >= 0 for ms, _ in t.values()) and t["collide_stream"][0] > 0
     # per step: kinematics, 3 pair kernels, moments + init, 5 x 2 iteration
     # kernels, collide-stream, stats
