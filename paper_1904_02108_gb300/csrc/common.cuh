@@ -42,15 +42,28 @@ constexpr int Q = 19;
 // rho U are sums of O(1e-3) numbers instead of O(0.1) ones.
 template <typename S>
 struct Store;
+// ld: read-only load.  ld_pf: the same with a 64-byte L2 prefetch size, for
+// scattered short rows (an L2 miss then fills the whole 64 B that HBM
+// delivers per access, so x-neighbouring rows read later hit L2).
 template <>
 struct Store<float> {
   static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ float ld_pf(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.L2::64B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+  }
   static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <>
 struct Store<__nv_bfloat16> {
   static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) {
     return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ float ld_pf(const __nv_bfloat16 *p) {
+    unsigned short v;
+    asm volatile("ld.global.nc.L2::64B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __bfloat162float(__ushort_as_bfloat16(v));
   }
   static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) {
     *p = __float2bfloat16_rn(v);
@@ -60,6 +73,11 @@ template <>
 struct Store<__half> {
   static __device__ __forceinline__ float ld(const __half *p) {
     return __half2float(__ldg(p));
+  }
+  static __device__ __forceinline__ float ld_pf(const __half *p) {
+    unsigned short v;
+    asm volatile("ld.global.nc.L2::64B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __half2float(__ushort_as_half(v));
   }
   static __device__ __forceinline__ void st(__half *p, float v) {
     *p = __float2half_rn(v);

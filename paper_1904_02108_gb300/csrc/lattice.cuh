@@ -15,8 +15,10 @@ __device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &
   y = (int)(r - (uint32_t)z * (uint32_t)g.ny);
 }
 
-// Pull of Eq. 4: d[i] = stored d_i at X - e_i (periodic).
-template <typename S>
+// Pull of Eq. 4: d[i] = stored d_i at X - e_i (periodic).  PF: loads with a
+// 64-byte L2 prefetch size (for the scattered 4-cell rows of the active
+// bricks; the dense collide reads whole lines anyway).
+template <typename S, bool PF = false>
 __device__ __forceinline__ void pull(const S *__restrict__ f, const Geometry &g, int x, int y,
                                      int z, float d[Q]) {
   const uint32_t nx = g.nx, ny = g.ny;
@@ -31,7 +33,7 @@ __device__ __forceinline__ void pull(const S *__restrict__ f, const Geometry &g,
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     const uint32_t src = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * nx + X[ex(i) + 1];
-    d[i] = Store<S>::ld(f + (size_t)i * N + src);
+    d[i] = PF ? Store<S>::ld_pf(f + (size_t)i * N + src) : Store<S>::ld(f + (size_t)i * N + src);
   }
 }
 
