@@ -477,35 +477,55 @@ __device__ __forceinline__ void pair_weights(const Geometry &g, const PairMap &p
   pm.point_pairs[8 * (size_t)k + j] = (int)p;
 }
 
-// One warp per slot: sort the slot's points ascending (in registers up to 128
-// pairs, bitonic in shared memory up to SORT_CAP, else a rank sort through
+// One warp per slot: sort the slot's points ascending (a bitonic network in
+// registers up to 128 pairs, in shared memory up to SORT_CAP, else a rank sort through
 // this slot's not yet written weight storage; the points of a slot are
 // distinct), then record with each pair its brick and brick-local weights.
 constexpr int SORT_CAP = 512;
 
-// Rank sort of a[0..cnt) (distinct values, cnt <= 32 NR) in registers: lane
-// holds entries lane + 32 i, i < NR; the rank of a value is the number of
-// smaller ones.
+// Sort of a[0..cnt) ascending (cnt <= 32 NR, NR a power of two) in
+// registers: lane holds entries lane + 32 i, i < NR, padded with INT_MAX, and
+// a bitonic network runs over the 32 NR entries: exchanges between lanes by
+// shuffles (distance j < 32), between a lane's registers otherwise.  Entry e
+// keeps the smaller of itself and its partner e ^ j when it is the lower of
+// the two in an ascending block (e & k == 0) or the upper one in a descending
+// block.
 template <int NR>
-__device__ __forceinline__ void warp_rank_sort(int *a, int cnt, int lane) {
-  int v[NR], r[NR];
+__device__ __forceinline__ void warp_bitonic_sort(int *a, int cnt, int lane) {
+  int v[NR];
 #pragma unroll
-  for (int i = 0; i < NR; i++) {
-    v[i] = lane + 32 * i < cnt ? a[lane + 32 * i] : 0x7fffffff;
-    r[i] = 0;
-  }
+  for (int i = 0; i < NR; i++) v[i] = lane + 32 * i < cnt ? a[lane + 32 * i] : 0x7fffffff;
 #pragma unroll
-  for (int i = 0; i < NR; i++)
+  for (int k = 2; k <= 32 * NR; k <<= 1) {
 #pragma unroll
-    for (int j = 0; j < 32; j++) {
-      const int x = __shfl_sync(0xffffffffu, v[i], j);
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        // k >= 64: the direction depends on the register only
+        const int jj = j >> 5;
 #pragma unroll
-      for (int q = 0; q < NR; q++) r[q] += x < v[q];
+        for (int i = 0; i < NR; i++) {
+          if ((i & jj) == 0) {
+            const bool up = ((32 * i) & k) == 0;
+            const int x = v[i], y = v[i | jj];
+            v[i] = up ? min(x, y) : max(x, y);
+            v[i | jj] = up ? max(x, y) : min(x, y);
+          }
+        }
+      } else {
+        const bool lo = (lane & j) == 0;
+#pragma unroll
+        for (int i = 0; i < NR; i++) {
+          const bool up = ((lane + 32 * i) & k) == 0;
+          const int y = __shfl_xor_sync(0xffffffffu, v[i], j);
+          v[i] = up == lo ? min(v[i], y) : max(v[i], y);
+        }
+      }
     }
+  }
   __syncwarp();
 #pragma unroll
   for (int i = 0; i < NR; i++)
-    if (lane + 32 * i < cnt) a[r[i]] = v[i];
+    if (lane + 32 * i < cnt) a[lane + 32 * i] = v[i];
 }
 
 __global__ void __launch_bounds__(128)
@@ -522,13 +542,11 @@ __global__ void __launch_bounds__(128)
     const int cnt = pm.count[s], st = pm.start[s], B = m.slot_brick[s];
     int *a = pm.k + st;
     if (cnt <= 32) {
-      warp_rank_sort<1>(a, cnt, lane);
+      warp_bitonic_sort<1>(a, cnt, lane);
     } else if (cnt <= 64) {
-      warp_rank_sort<2>(a, cnt, lane);
-    } else if (cnt <= 96) {
-      warp_rank_sort<3>(a, cnt, lane);
+      warp_bitonic_sort<2>(a, cnt, lane);
     } else if (cnt <= 128) {
-      warp_rank_sort<4>(a, cnt, lane);
+      warp_bitonic_sort<4>(a, cnt, lane);
     } else if (cnt <= SORT_CAP) {
       int n2 = 2;
       while (n2 < cnt) n2 <<= 1;
