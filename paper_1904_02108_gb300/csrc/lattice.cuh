@@ -7,12 +7,22 @@
 
 namespace lbmibm {
 
+// (x, y, z) of the cell with linear index n = (z ny + y) nx + x; shifts and
+// masks when nx and ny are powers of two (the same for every thread).
 __device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &x, int &y,
                                             int &z) {
-  uint32_t r = n / (uint32_t)g.nx;
-  x = (int)(n - r * (uint32_t)g.nx);
-  z = (int)(r / (uint32_t)g.ny);
-  y = (int)(r - (uint32_t)z * (uint32_t)g.ny);
+  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
+  if ((nx & (nx - 1)) == 0 && (ny & (ny - 1)) == 0) {
+    const uint32_t r = n >> (__ffs((int)nx) - 1);
+    x = (int)(n & (nx - 1));
+    y = (int)(r & (ny - 1));
+    z = (int)(r >> (__ffs((int)ny) - 1));
+    return;
+  }
+  const uint32_t r = n / nx;
+  x = (int)(n - r * nx);
+  z = (int)(r / ny);
+  y = (int)(r - (uint32_t)z * ny);
 }
 
 // Pull of Eq. 4: d[i] = stored d_i at X - e_i (periodic).  PF: loads with a

@@ -64,11 +64,23 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
   st[3] = jz + rho * Gz;
 }
 
-__device__ __forceinline__ void warp_sum4f(float a[4]) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int c = 0; c < 4; c++) a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+// Warp sums of four values in 6 shuffles: the first exchange splits the
+// components between the two half-warps (lanes with bit 4 keep 2, 3), the
+// second between the quarter-warps (bit 3), then three exchanges finish one
+// component per lane.  Lane l returns the sum of component
+// ((l >> 4) & 1) * 2 + ((l >> 3) & 1): lanes 0, 8, 16 and 24 hold 0..3.
+__device__ __forceinline__ float warp_sum4_split(const float a[4]) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const float s0 = h16 ? a[0] : a[2], s1 = h16 ? a[1] : a[3];
+  const float k0 = h16 ? a[2] : a[0], k1 = h16 ? a[3] : a[1];
+  const float b0 = k0 + __shfl_xor_sync(0xffffffffu, s0, 16);
+  const float b1 = k1 + __shfl_xor_sync(0xffffffffu, s1, 16);
+  float c = (h8 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, h8 ? b0 : b1, 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
 }
 
 // One thread per cell.  dd is the domain of this block: a kernel parameter
@@ -114,13 +126,12 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
     }
   }
   if (STATS) {
-    warp_sum4f(sv);
+    const float ws = warp_sum4_split(sv);
     // one partial per PARTIAL_CELLS cells (four warps), whatever the block
     // size: the sums do not depend on the launch shape
     __shared__ double red[8][4];
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-      for (int c = 0; c < 4; c++) red[w][c] = sv[c];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((lane & 7) == 0) red[w][lane >> 3] = ws;
     __syncthreads();
     const int groups = blockDim.x / PARTIAL_CELLS;
     if ((int)threadIdx.x < 4 * groups) {
@@ -184,9 +195,9 @@ __global__ void __launch_bounds__(256)
         for (int c = 0; c < 4; c++) sv[c] = st[c];
     }
     if (STATS) {
-      warp_sum4f(sv);
-      if ((threadIdx.x & 31) == 0)
-        for (int c = 0; c < 4; c++) red[w][c] = sv[c];
+      const float ws = warp_sum4_split(sv);
+      const int lane = threadIdx.x & 31;
+      if ((lane & 7) == 0) red[w][lane >> 3] = ws;
       __syncthreads();
       if ((threadIdx.x & 63) < 4) {
         const int c = threadIdx.x & 3, q = threadIdx.x >> 6;
