@@ -254,23 +254,42 @@ def run_ours(args):
     lat.set_graph(False)
 
     # ---- end to end through the C ABI with host buffers: per step the point
-    # positions are uploaded from pinned memory (ibm_update_points, on the
-    # library's stream), the step runs, and du + the FP64 sums are read back
+    # positions are uploaded from pinned memory (ibm_update_points), the step
+    # runs, and du and the FP64 sums are copied back into pinned memory
+    # (ibm_read_points_async, lbm_read_sums_async), all on the library's
+    # stream; the host waits for step s-1's results (an event) while step s
+    # runs, and checks them (double-buffered: every step's results reach
+    # the host)
     npnt = w.props.n_points
     pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).pin_memory().numpy()
     X = pin(w.props.xrest, np.float64)
-    du_host = torch.empty((npnt, 3), dtype=torch.float32).pin_memory().numpy()
+    du_host = [torch.empty((npnt, 3), dtype=torch.float32).pin_memory().numpy()
+               for _ in range(2)]
+    sums_host = [torch.zeros(4, dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
     L = binding.load()
     e2e_steps = max(3, args.steps // 2)
+    bad = 0
+
+    def consume(b):
+        evs[b].synchronize()
+        return int(not (np.isfinite(sums_host[b]).all() and np.isfinite(du_host[b][0]).all()))
+
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for k in range(e2e_steps):
+        b = k % 2
         binding._check(L.ibm_update_points(lat.h, npnt, binding._ptr(X), None), lat.h)
         lat.step(1, w.n_iter)
-        binding._check(L.ibm_read_points(lat.h, None, None, binding._ptr(du_host)), lat.h)
-        lat.stats()
+        lat.points_async(du=du_host[b])
+        lat.sums_async(sums_host[b])
+        evs[b].record(st)
+        if k > 0:
+            bad += consume(1 - b)
+    bad += consume((e2e_steps - 1) % 2)
     barrier()
     e2e_s = time.perf_counter() - t0
+    assert bad == 0, "non-finite results in the end-to-end loop"
     h2d = npnt * 24
     d2h = npnt * 12 + 32
 

@@ -187,6 +187,20 @@ int ibm_read_points_dev(lbm_t *h, double *x, float *u_interp, float *du);
 /* Statistics; the FP64 sums are those of the last step with stats on. */
 int lbm_read_stats(lbm_t *h, lbm_stats *s);
 
+/* Non-blocking read-back into host memory: the same values as
+ * ibm_read_points and as the sums of lbm_read_stats (sums[4] = mass,
+ * momentum x, y, z; left unchanged when the lattice has no sums yet), with
+ * the device-to-host copies enqueued on the handle's stream and no
+ * synchronisation.  The values are in the caller's buffers once the stream
+ * has passed the call (cudaStreamSynchronize, or an event recorded after it);
+ * the buffers must stay valid until then, and page-locked (pinned) host
+ * memory makes the copies asynchronous.  A later read-back of the same kind
+ * is ordered after this one on the stream.  No counterpart in the paper
+ * (pipelined host I/O).  Returns LBM_OK, LBM_EINVAL (NULL h or sums) or
+ * LBM_ECUDA. */
+int ibm_read_points_async(lbm_t *h, double *x, float *u_interp, float *du);
+int lbm_read_sums_async(lbm_t *h, double *sums);
+
 /* Full populations f[19][N] (FP32) of the current state, in the velocity
  * order of lbm_velocity_set, and their replacement.  Host buffers. */
 int lbm_read_populations(lbm_t *h, float *f);

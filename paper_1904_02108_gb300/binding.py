@@ -84,6 +84,8 @@ _SIGS = {
     "lbm_read_fields": (_i, [_p, _p, _p, _p]),
     "lbm_read_fields_dev": (_i, [_p, _p, _p, _p]),
     "ibm_read_points": (_i, [_p, _p, _p, _p]),
+    "ibm_read_points_async": (_i, [_p, _p, _p, _p]),
+    "lbm_read_sums_async": (_i, [_p, _p]),
     "ibm_read_points_dev": (_i, [_p, _p, _p, _p]),
     "lbm_read_stats": (_i, [_p, _p]),
     "lbm_read_populations": (_i, [_p, _p]),
@@ -286,6 +288,18 @@ class Lattice:
 
     def points_dev(self, x=None, u=None, du=None):
         self._c(load().ibm_read_points_dev(self.h, _ptr(x), _ptr(u), _ptr(du)))
+
+    def points_async(self, x=None, u=None, du=None):
+        """Enqueue the read-back of x [n][3] f64, u_interp and du [n][3] f32 into
+        the given host arrays (pinned for asynchrony) on the lattice's stream;
+        valid once the stream has passed this call."""
+        self._c(load().ibm_read_points_async(self.h, _ptr(x), _ptr(u), _ptr(du)))
+
+    def sums_async(self, sums):
+        """Enqueue the read-back of the FP64 sums (mass, momentum x, y, z) into
+        the host array sums[4]; valid once the stream has passed this call."""
+        assert sums.dtype == np.float64 and sums.size >= 4
+        self._c(load().lbm_read_sums_async(self.h, _ptr(sums)))
 
     def stats(self):
         s = LbmStats()

@@ -1530,7 +1530,7 @@ int ibm_read_points_dev(lbm_t *h, double *x, float *u_interp, float *du) {
   return LBM_OK;
 }
 
-int ibm_read_points(lbm_t *h, double *x, float *u_interp, float *du) {
+int ibm_read_points_async(lbm_t *h, double *x, float *u_interp, float *du) {
   if (!h) return LBM_EINVAL;
   const int64_t n = h->np;
   if (n == 0) return LBM_OK;
@@ -1544,7 +1544,20 @@ int ibm_read_points(lbm_t *h, double *x, float *u_interp, float *du) {
   if (u_interp)
     CK(h, cudaMemcpyAsync(u_interp, du_, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->st));
   if (du) CK(h, cudaMemcpyAsync(du, dd, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->st));
+  return LBM_OK;
+}
+
+int ibm_read_points(lbm_t *h, double *x, float *u_interp, float *du) {
+  const int r = ibm_read_points_async(h, x, u_interp, du);
+  if (r || h->np == 0) return r;
   CK(h, cudaStreamSynchronize(h->st));
+  return LBM_OK;
+}
+
+int lbm_read_sums_async(lbm_t *h, double *sums) {
+  if (!h || !sums) return LBM_EINVAL;
+  if (h->sums_valid)
+    CK(h, cudaMemcpyAsync(sums, h->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   return LBM_OK;
 }
 

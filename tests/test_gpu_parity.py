@@ -298,3 +298,38 @@ def test_bad_arguments_return_codes(gpu_lib, torch_cuda):
         lat.load_state(np.zeros(16, np.uint8))
     assert e.value.code == gpu_lib.LBM_ESTATE
     lat.close()
+
+
+def test_async_readback_matches_blocking(gpu_lib, torch_cuda):
+    torch = torch_cuda
+    w = W.single_propeller(2)
+    a = _lattice(gpu_lib, torch, w.shape, w.tau, warm="previous")
+    b = _lattice(gpu_lib, torch, w.shape, w.tau, warm="previous")
+    n = w.props.n_points
+    pin = lambda shape, dt: torch.zeros(shape, dtype=dt).pin_memory().numpy()
+    x, u, du = pin((n, 3), torch.float64), pin((n, 3), torch.float32), pin((n, 3), torch.float32)
+    sums = pin(4, torch.float64)
+    sums[:] = 7.0
+    a.sums_async(sums)  # no sums before the first step: left unchanged
+    torch.cuda.current_stream().synchronize()
+    assert np.all(sums == 7.0)
+    for lat in (a, b):
+        lat.set_propellers(w.props)
+        lat.step(3, 5)
+    a.points_async(x, u, du)
+    a.sums_async(sums)
+    a.step(1, 5)  # enqueued after the copies: they hold step 3's values
+    torch.cuda.current_stream().synchronize()
+    xb, ub, dub = b.points()
+    sb = b.stats()
+    assert np.array_equal(x, xb) and np.array_equal(u, ub) and np.array_equal(du, dub)
+    assert sums[0] == sb["mass"] and tuple(sums[1:]) == sb["momentum"]
+    a.points_async(du=du)
+    a.sums_async(sums)
+    torch.cuda.current_stream().synchronize()
+    _, _, du4 = a.points()
+    sa = a.stats()
+    assert np.array_equal(du, du4) and not np.array_equal(du4, dub)
+    assert sums[0] == sa["mass"] and tuple(sums[1:]) == sa["momentum"]
+    for lat in (a, b):
+        lat.close()
