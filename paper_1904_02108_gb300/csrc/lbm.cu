@@ -20,19 +20,14 @@ namespace lbmibm {
 
 namespace {
 
-// One cell of the fused pull-stream + collision: pull of Eq. 4 into d, Eq. 1
+// The collision of one cell from its pulled deviations d (Eq. 4): Eq. 1
 // moments, U^G = U + tau G (Sec. 2 step 3) and the BGK relaxation towards
-// Eq. 3, written to dst at n.  G is the cell's force (body force plus its
-// brick's IBM force).  st receives the cell's post-collision mass and
-// momentum sums (the collision conserves mass and adds rho G of momentum,
-// Eqs. 2-3, so they follow from the moments).
-template <typename S>
-__device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__restrict__ dst,
-                                             const Geometry &g, uint32_t n, int x, int y, int z,
-                                             float Gx, float Gy, float Gz, float tau,
-                                             float st[4]) {
-  float d[Q];
-  pull<S>(src, g, x, y, z, d);
+// Eq. 3, into dn.  G is the cell's force (body force plus its brick's IBM
+// force).  st receives the cell's post-collision mass and momentum sums (the
+// collision conserves mass and adds rho G of momentum, Eqs. 2-3, so they
+// follow from the moments).
+__device__ __forceinline__ void collide_math(const float d[Q], float Gx, float Gy, float Gz,
+                                             float tau, float dn[Q], float st[4]) {
   float drho, jx, jy, jz;
   moments(d, drho, jx, jy, jz);
   const float rho = 1.f + drho;
@@ -45,8 +40,6 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
   // common to every direction; opposite directions share 4.5 rho (e.u)^2
   const float c0 = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
   const float r3 = 3.f * rho, r45 = 4.5f * rho;
-  const size_t N = (size_t)g.ncell;
-  float dn[Q];
   dn[0] = d[0] + om * (wt(0) * c0 - d[0]);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -56,12 +49,25 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
     dn[i] = d[i] + om * (eqp - d[i]);
     dn[i + 1] = d[i + 1] + om * (eqm - d[i + 1]);
   }
-#pragma unroll
-  for (int i = 0; i < Q; i++) Store<S>::st(dst + ((size_t)i * N + n), dn[i]);
   st[0] = drho;
   st[1] = jx + rho * Gx;
   st[2] = jy + rho * Gy;
   st[3] = jz + rho * Gz;
+}
+
+// One cell of the fused pull-stream + collision: the pull of Eq. 4 from src,
+// collide_math, and the post-collision values written to dst at n.
+template <typename S>
+__device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__restrict__ dst,
+                                             const Geometry &g, uint32_t n, int x, int y, int z,
+                                             float Gx, float Gy, float Gz, float tau,
+                                             float st[4]) {
+  float d[Q], dn[Q];
+  pull<S>(src, g, x, y, z, d);
+  collide_math(d, Gx, Gy, Gz, tau, dn, st);
+  const size_t N = (size_t)g.ncell;
+#pragma unroll
+  for (int i = 0; i < Q; i++) Store<S>::st(dst + ((size_t)i * N + n), dn[i]);
 }
 
 // Warp sums of four values in 6 shuffles: the first exchange splits the
@@ -156,6 +162,132 @@ __global__ void __launch_bounds__(256)
     collide_stream_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
   pdl_wait();
   collide_stream_cells<S, STATS, SKIP>(D[blockIdx.y], cur);
+}
+
+// 16-bit storage: two x-neighbouring cells (x0 even, x0 + 1) per thread.
+// The pulls are 32-bit words of two deviations: directions without an x
+// component read one word (the two cells' values), the others the two words
+// holding x0 - 1 and x0 (e_x = +1) or x0 + 1 and x0 + 2 (e_x = -1); each
+// direction's two results go out as one word.  Rows, the brick's force and
+// the stats are shared by the two cells; each cell's arithmetic is
+// collide_math, so the results are those of collide_stream_cells.
+template <typename S>
+struct Word16;
+template <>
+struct Word16<__nv_bfloat16> {
+  static __device__ __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
+  static __device__ __forceinline__ float hi(uint32_t w) {
+    return __uint_as_float(w & 0xffff0000u);
+  }
+  static __device__ __forceinline__ uint32_t pack(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+  }
+};
+template <>
+struct Word16<__half> {
+  static __device__ __forceinline__ float lo(uint32_t w) {
+    return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+  }
+  static __device__ __forceinline__ float hi(uint32_t w) {
+    return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
+  }
+  static __device__ __forceinline__ uint32_t pack(float a, float b) {
+    const __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+  }
+};
+
+template <typename S, bool STATS>
+__device__ __forceinline__ void collide_pairs16(const DomainDesc &dd, int cur) {
+  const Geometry g = dd.g;
+  if ((int64_t)blockIdx.x * blockDim.x * 2 >= g.ncell) return;
+  const uint32_t *__restrict__ src = (const uint32_t *)dd.f[cur];
+  uint32_t *__restrict__ dst = (uint32_t *)dd.f[cur ^ 1];
+  const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
+  const float *__restrict__ Gs = dd.Gs;
+  float sv[4] = {0.f, 0.f, 0.f, 0.f};
+  const uint32_t n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (n < (uint32_t)g.ncell) {
+    int x, y, z;
+    cell_coords(n, g, x, y, z);
+    float Ga[3] = {dd.gbody[0], dd.gbody[1], dd.gbody[2]};
+    float Gb[3] = {Ga[0], Ga[1], Ga[2]};
+    if (brick_slot) {
+      const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
+      const int sl = __ldg(brick_slot + b);
+      if (sl >= 0) {
+        const float *p = Gs + (size_t)sl * SLOT_FLOATS + brick_local(x, y, z);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          Ga[c] += __ldg(p + c * BRICK_CELLS);
+          Gb[c] += __ldg(p + c * BRICK_CELLS + 1);
+        }
+      }
+    }
+    // word offsets of the rows y - e_y, z - e_z and of x0 - 2, x0, x0 + 2
+    const uint32_t nx = g.nx, ny = g.ny, hw = nx >> 1;
+    const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == (int)ny - 1 ? 0 : y + 1;
+    const uint32_t zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    const uint32_t Y[3] = {yp, (uint32_t)y, ym}, Z[3] = {zp, (uint32_t)z, zm};
+    const uint32_t w0 = (uint32_t)x >> 1;
+    const uint32_t wl = w0 == 0 ? hw - 1 : w0 - 1, wr = w0 == hw - 1 ? 0 : w0 + 1;
+    const size_t NW = (size_t)g.ncell >> 1;
+    float da[Q], db[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const uint32_t row = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * hw;
+      const uint32_t *fi = src + (size_t)i * NW + row;
+      if (ex(i) == 0) {
+        const uint32_t w = __ldg(fi + w0);
+        da[i] = Word16<S>::lo(w);
+        db[i] = Word16<S>::hi(w);
+      } else if (ex(i) > 0) {
+        da[i] = Word16<S>::hi(__ldg(fi + wl));
+        db[i] = Word16<S>::lo(__ldg(fi + w0));
+      } else {
+        da[i] = Word16<S>::hi(__ldg(fi + w0));
+        db[i] = Word16<S>::lo(__ldg(fi + wr));
+      }
+    }
+    float dna[Q], dnb[Q], sta[4], stb[4];
+    collide_math(da, Ga[0], Ga[1], Ga[2], dd.tau, dna, sta);
+    collide_math(db, Gb[0], Gb[1], Gb[2], dd.tau, dnb, stb);
+    const uint32_t wn = n >> 1;
+#pragma unroll
+    for (int i = 0; i < Q; i++) dst[(size_t)i * NW + wn] = Word16<S>::pack(dna[i], dnb[i]);
+    if (STATS)
+      for (int c = 0; c < 4; c++) sv[c] = sta[c] + stb[c];
+  }
+  if (STATS) {
+    const float ws = warp_sum4_split(sv);
+    // a warp covers 64 cells: one partial per PARTIAL_CELLS = two warps
+    __shared__ double red[8][4];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((lane & 7) == 0) red[w][lane >> 3] = ws;
+    __syncthreads();
+    const int groups = blockDim.x / (PARTIAL_CELLS / 2);
+    if ((int)threadIdx.x < 4 * groups) {
+      const int gi = threadIdx.x >> 2, c = threadIdx.x & 3;
+      const double a = red[2 * gi][c] + red[2 * gi + 1][c];
+      const int64_t pidx = (int64_t)blockIdx.x * groups + gi;
+      if (pidx < dd.cblocks) dd.partial[(size_t)pidx * 4 + c] = a;
+    }
+  }
+}
+
+template <typename S, bool STATS>
+__global__ void __launch_bounds__(256)
+    collide_pairs16_kernel(const __grid_constant__ DomainDesc dd, int cur) {
+  pdl_wait();
+  collide_pairs16<S, STATS>(dd, cur);
+}
+
+template <typename S, bool STATS>
+__global__ void __launch_bounds__(256)
+    collide_pairs16_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
+  pdl_wait();
+  collide_pairs16<S, STATS>(D[blockIdx.y], cur);
 }
 
 // The cells of the active bricks, after the IBM loop: 64 threads per slot
@@ -396,6 +528,21 @@ cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const Ba
        ? launch_pdl(collide_stream_kernel<S, ST, SK>, grid, block, 0, st, *Dhost, cur)      \
        : launch_pdl(collide_stream_batch_kernel<S, ST, SK>, grid, block, 0, st, D, cur))
   if (skip_active) return stats ? LBM_COLLIDE(true, true) : LBM_COLLIDE(false, true);
+#undef LBM_COLLIDE
+  if constexpr (sizeof(S) == 2) {
+    // two cells per thread (nx is a multiple of 4)
+    const dim3 grid2((unsigned)((dims.max_cells + 2 * bs - 1) / (2 * bs)), dims.nd);
+#define LBM_PAIRS(ST)                                                                     \
+  (dims.nd == 1 && Dhost                                                                  \
+       ? launch_pdl(collide_pairs16_kernel<S, ST>, grid2, block, 0, st, *Dhost, cur)      \
+       : launch_pdl(collide_pairs16_batch_kernel<S, ST>, grid2, block, 0, st, D, cur))
+    return stats ? LBM_PAIRS(true) : LBM_PAIRS(false);
+#undef LBM_PAIRS
+  }
+#define LBM_COLLIDE(ST, SK)                                                                 \
+  (dims.nd == 1 && Dhost                                                                    \
+       ? launch_pdl(collide_stream_kernel<S, ST, SK>, grid, block, 0, st, *Dhost, cur)      \
+       : launch_pdl(collide_stream_batch_kernel<S, ST, SK>, grid, block, 0, st, D, cur))
   return stats ? LBM_COLLIDE(true, false) : LBM_COLLIDE(false, false);
 #undef LBM_COLLIDE
 }
