@@ -238,7 +238,7 @@ typedef struct {
   int sort_blocks;   /* blocks of the pair sort (a warp per brick), >= 1   */
 } lbm_launch_shape;
 
-/* The handle's launch shape (defaults: 256, 3648, 256, 4, 4864).  Set
+/* The handle's launch shape (defaults: 256, 19456, 256, 4, 4864).  Set
  * returns LBM_EINVAL for a value outside the ranges above. */
 int lbm_get_launch_shape(lbm_t *h, lbm_launch_shape *out);
 int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s);
@@ -246,12 +246,12 @@ int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s);
 /* Picks the launch shape by timing trial steps on this handle's own lattice
  * and points: one parameter at a time (collide block, brick grid, point
  * block, moments bricks per block, sort grid), each candidate timed with CUDA
- * events around steps_per_trial whole steps (>= 1; the stages overlap, so
- * the step is the objective) after one untimed step, in two interleaved
- * rounds (the faster kept), with n_ibm_iter (> 0) fixed iterations; a
- * candidate replaces the current value only when more than 1 % faster.  The
- * lattice is
- * restored afterwards (populations, corrections, step counter, sums), so the
+ * events around steps_per_trial whole steps (>= 1; consecutive kernels
+ * overlap, so the step is the objective) after one untimed step, in two
+ * interleaved rounds (the faster kept), with n_ibm_iter (> 0) fixed
+ * iterations; a candidate replaces the current value only when more than 1 %
+ * faster.  The lattice is restored afterwards (populations, corrections,
+ * step counter, sums), so the
  * call does not advance the simulation; it allocates a copy of one
  * population lattice for that.  The chosen shape is set on the handle and
  * written to *chosen (may be NULL).  Stage timing is off on return. */

@@ -1283,7 +1283,7 @@ std::vector<TuneParam> tune_params(bool points) {
   ps.push_back({&LaunchShape::collide_block, {128, 256}, 1 << ST_COLLIDE});
   if (points) {
     ps.push_back({&LaunchShape::brick_blocks,
-                  {152 * 8, 152 * 16, 152 * 24, 152 * 32},
+                  {152 * 16, 152 * 32, 152 * 64, 152 * 128},
                   (1 << ST_SPREAD) | (1 << ST_INIT)});
     ps.push_back({&LaunchShape::point_block,
                   {128, 256, 512},

@@ -273,8 +273,11 @@ struct DomainDesc {
 struct LaunchShape {
   int collide_block = 256;       // threads per block of the collide-stream
                                  // kernel: 128 or 256
-  int brick_blocks = 152 * 24;   // grid of the brick kernels (grid-stride
-                                 // over the active bricks, a warp each)
+  int brick_blocks = 152 * 128;  // grid of the brick kernels (grid-stride
+                                 // over the active bricks, a warp each; a
+                                 // grid above the bricks' count gives one
+                                 // brick per block, which the hardware
+                                 // balances across the SMs)
   int point_block = 256;         // threads per block of the per-point
                                  // kernels: 128, 256 or 512
   int moments_spb = 4;           // bricks per block of the moments kernel
