@@ -39,7 +39,8 @@ enum Stage {
   ST_MLP,
   ST_COLLIDE_ACTIVE
 };
-// iterations launched between two host checks of the tolerance-mode stop flag
+// the fewest iterations launched between two host checks of the
+// tolerance-mode stop flag
 constexpr int kCheckChunk = 16;
 
 thread_local std::string g_create_error;
@@ -760,8 +761,8 @@ static int enqueue_step(StepCtx &c, int n_iter) {
 
 // The tolerance-driven fixed point of Sec. 3 for one lattice: iterations
 // until eps <= ibm_tol or ibm_max_iter, the stop decided on the device and
-// read by the host every kCheckChunk iterations.  Returns LBM_WNOTCONVERGED
-// when the cap was hit.
+// read by the host after each chunk of iterations (sized from the previous
+// step's count).  Returns LBM_WNOTCONVERGED when the cap was hit.
 static int tolerance_loop(StepCtx &c, bool warm) {
   lbm_t *h = c.acct;
   cudaStream_t st = c.sti;
@@ -783,11 +784,13 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     if (warm) CK(h, launch_brick_init(c.D, c.dims, 1, st));
   }
   int it = 0;
-  // the first chunk runs about as many iterations as the previous step took
-  // (the kernels of iterations past convergence return at once)
-  int chunk0 = std::max(kCheckChunk, h->tol_hint - kCheckChunk / 4);
+  // chunks of half the iterations the previous step still had to go at this
+  // point (at least kCheckChunk): few reads of the stop flag, and few
+  // launches past convergence (their kernels return at once, but are not free)
   while (it < h->max_iter) {
-    const int chunk = std::min(it == 0 ? chunk0 : kCheckChunk, h->max_iter - it);
+    const int left = h->tol_hint - it;
+    const int chunk = std::min(left > 0 ? std::max(kCheckChunk, left / 2) : kCheckChunk,
+                               h->max_iter - it);
     for (int j = 0; j < chunk; j++, it++) {
       {
         StageTimer T(h, ST_UPDATE, st);
