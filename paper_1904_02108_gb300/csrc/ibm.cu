@@ -102,19 +102,6 @@ __device__ __forceinline__ void for_support_bricks8(const Geometry &g, int4 b, F
   }
 }
 
-// Calls fn(brick) for each distinct brick of a point's support.
-template <typename Fn>
-__device__ __forceinline__ void for_support_bricks(const Geometry &g, int4 b, Fn fn) {
-  const SupportBricks sx = support_bricks(b.x, g.nx), sy = support_bricks(b.y, g.ny),
-                      sz = support_bricks(b.z, g.nz);
-  const int nzb = sz.hi != sz.lo ? 2 : 1, nyb = sy.hi != sy.lo ? 2 : 1,
-            nxb = sx.hi != sx.lo ? 2 : 1;
-  for (int c = 0; c < nzb; c++)
-    for (int a = 0; a < nyb; a++)
-      for (int e = 0; e < nxb; e++)
-        fn(((c ? sz.hi : sz.lo) * g.nby + (a ? sy.hi : sy.lo)) * g.nbx + (e ? sx.hi : sx.lo));
-}
-
 // cos phi, sin phi and the differences cos phi - cos(phi - omega),
 // sin phi - sin(phi - omega) of a body with phi = phase + omega t, in FP64;
 // the differences as -2 sin(phi - omega/2) sin(omega/2) and
