@@ -238,6 +238,7 @@ void free_points(lbm_t *h) {
   dfree(h->uint);
   dfree(h->xpos);
   dfree(h->m.slot_brick);
+  dfree(h->m.order);
   dfree(h->pm.count);
   dfree(h->pm.start);
   dfree(h->pm.cursor);
@@ -466,6 +467,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->uint, n));
     CK(h, dalloc(&h->xpos, 3 * n));
     CK(h, dalloc(&h->m.slot_brick, ms));
+    CK(h, dalloc(&h->m.order, ms));
     CK(h, dalloc(&h->pm.count, ms));
     CK(h, dalloc(&h->pm.start, ms + 1));
     CK(h, dalloc(&h->pm.cursor, ms));
@@ -1807,7 +1809,7 @@ int ibm_interpolate_dev(int nx, int ny, int nz, int delta, const float *U, int64
 namespace {
 
 struct SpreadLayout {
-  size_t desc, brick_count, brick_slot, slot_brick, counters, tiles, count, start, cursor, pk,
+  size_t desc, brick_count, brick_slot, slot_brick, order, counters, tiles, count, start, cursor, pk,
       pbrick, pw,
       ppart,
       point_pairs, base, wts, ut, vals, Gs, total;
@@ -1830,6 +1832,7 @@ SpreadLayout spread_layout(const Geometry &g, int64_t n) {
   L.brick_count = take(sizeof(int) * g.nbrick);
   L.brick_slot = take(sizeof(int) * g.nbrick);
   L.slot_brick = take(sizeof(int) * ms);
+  L.order = take(sizeof(int) * ms);
   L.counters = take(sizeof(int) * 8);
   L.tiles = take(sizeof(unsigned long long) * ((g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE));
   L.count = take(sizeof(int) * ms);
@@ -1895,6 +1898,7 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   m.brick_count = (int *)(base + L.brick_count);
   m.brick_slot = (int *)(base + L.brick_slot);
   m.slot_brick = (int *)(base + L.slot_brick);
+  m.order = (int *)(base + L.order);
   m.counters = (int *)(base + L.counters);
   m.tiles = (unsigned long long *)(base + L.tiles);
   m.max_slots = L.max_slots;

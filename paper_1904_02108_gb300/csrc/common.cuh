@@ -159,7 +159,12 @@ struct BrickMap {
   int *counters;     // [8]: 0 = active slots, 1 = error flags of the step
                      //      (1: slot overflow, 4: compaction scan timed
                      //      out), 3 = tile ticket, 4 = scan epoch, 5 = error
-                     //      flags kept until the host reads them
+                     //      flags kept until the host reads them, 6 / 7 =
+                     //      slots placed at the front / back of order
+  int *order;        // [max_slots] the active slots in the order the brick
+                     //             kernels take them: those with more than
+                     //             64 pairs first (their blocks start early,
+                     //             the short ones fill the end)
   unsigned long long *tiles;  // [compact tiles] look-back words of the
                               // compaction scan
   int max_slots;

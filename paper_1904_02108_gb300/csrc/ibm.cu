@@ -141,6 +141,8 @@ __global__ void __launch_bounds__(512, 2)
   if (k == 0) {
     m.counters[0] = 0;
     m.counters[1] = 0;
+    m.counters[6] = 0;
+    m.counters[7] = 0;
   }
   const bool in = k < p.np;
   const int body = (bd.nb > 0 && in) ? (p.body ? p.body[k] : 0) : -1;
@@ -528,6 +530,8 @@ __global__ void __launch_bounds__(128)
   for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
     const int cnt = pm.count[s], st = pm.start[s], B = m.slot_brick[s];
     int *a = pm.k + st;
+    if (lane == 0)
+      m.order[cnt > 64 ? atomicAdd(m.counters + 6, 1) : nslots - 1 - atomicAdd(m.counters + 7, 1)] = s;
     if (cnt <= 32) {
       warp_bitonic_sort<1>(a, cnt, lane);
     } else if (cnt <= 64) {
@@ -749,7 +753,8 @@ __global__ void __launch_bounds__(32, 32)
   float *__restrict__ Gs = d.Gs;
   const int nslots = active_slots(m);
   const int t = threadIdx.x, r = t & 15;
-  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
+    const int s = m.order[b];
     const int p0 = pm.start[s], cnt = pm.count[s];
     float4 G[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
                    make_float4(0.f, 0.f, 0.f, 0.f)};
@@ -785,7 +790,8 @@ __global__ void __launch_bounds__(32, 32)
   float *__restrict__ res = tol_mode ? d.res : nullptr;
   const int nslots = active_slots(m);
   const int t = threadIdx.x, r = t & 15;
-  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
+    const int s = m.order[b];
     const int p0 = pm.start[s], cnt = pm.count[s];
     float4 G[3];
     brick_gather(sm, pm, p0, cnt, vals, G);
@@ -833,7 +839,8 @@ __global__ void __launch_bounds__(32, 32)
   float *__restrict__ res = d.res;
   const int nslots = active_slots(m);
   const int t = threadIdx.x;
-  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
+    const int s = m.order[b];
     float4 G[3];
     brick_gather(sm, pm, pm.start[s], pm.count[s], vals, G, scale_by_w != 0);
     float e = 0.f;
