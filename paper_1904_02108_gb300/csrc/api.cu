@@ -384,8 +384,8 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   if (e == cudaSuccess) e = cudaMemset(h->m.brick_count, 0, sizeof(int) * h->g.nbrick);
   if (e == cudaSuccess) e = dalloc(&h->m.brick_slot, h->g.nbrick);
   if (e == cudaSuccess) e = cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick);
-  if (e == cudaSuccess) e = dalloc(&h->m.counters, 8);
-  if (e == cudaSuccess) e = cudaMemset(h->m.counters, 0, 8 * sizeof(int));
+  if (e == cudaSuccess) e = dalloc(&h->m.counters, BRICK_COUNTERS);
+  if (e == cudaSuccess) e = cudaMemset(h->m.counters, 0, BRICK_COUNTERS * sizeof(int));
   {
     const size_t nt = (h->g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE;
     if (e == cudaSuccess) e = dalloc(&h->m.tiles, nt);
@@ -467,7 +467,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->uint, n));
     CK(h, dalloc(&h->xpos, 3 * n));
     CK(h, dalloc(&h->m.slot_brick, ms));
-    CK(h, dalloc(&h->m.order, ms));
+    CK(h, dalloc(&h->m.order, (size_t)ORDER_BUCKETS * ms));
     CK(h, dalloc(&h->pm.count, ms));
     CK(h, dalloc(&h->pm.start, ms + 1));
     CK(h, dalloc(&h->pm.cursor, ms));
@@ -1832,8 +1832,8 @@ SpreadLayout spread_layout(const Geometry &g, int64_t n) {
   L.brick_count = take(sizeof(int) * g.nbrick);
   L.brick_slot = take(sizeof(int) * g.nbrick);
   L.slot_brick = take(sizeof(int) * ms);
-  L.order = take(sizeof(int) * ms);
-  L.counters = take(sizeof(int) * 8);
+  L.order = take(sizeof(int) * ORDER_BUCKETS * ms);
+  L.counters = take(sizeof(int) * BRICK_COUNTERS);
   L.tiles = take(sizeof(unsigned long long) * ((g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE));
   L.count = take(sizeof(int) * ms);
   L.start = take(sizeof(int) * (ms + 1));
@@ -1920,7 +1920,7 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
   float *Gs = (float *)(base + L.Gs);
   if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, sizeof(float) * 3 * g.ncell, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(m.brick_count, 0, sizeof(int) * g.nbrick, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m.counters, 0, sizeof(int) * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.counters, 0, sizeof(int) * BRICK_COUNTERS, st);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(m.tiles, 0,
                         sizeof(unsigned long long) *

@@ -148,6 +148,9 @@ __host__ __device__ __forceinline__ int wrapi(int a, int n) {
   return a < 0 ? a + n : (a >= n ? a - n : a);
 }
 
+constexpr int BRICK_COUNTERS = 16;
+constexpr int ORDER_BUCKETS = 4;
+
 // Sparse storage over the active bricks (those inside the support of some
 // point).  brick_slot[b] = slot or -1; slot_brick[s] = b.  Per slot the fields
 // U0 and G are [3][64] floats (component-major, brick-local cell order z,y,x).
@@ -156,15 +159,16 @@ struct BrickMap {
                      //           per step, cleared by the compaction)
   int *brick_slot;   // [nbrick]
   int *slot_brick;   // [max_slots]
-  int *counters;     // [8]: 0 = active slots, 1 = error flags of the step
-                     //      (1: slot overflow, 4: compaction scan timed
-                     //      out), 3 = tile ticket, 4 = scan epoch, 5 = error
-                     //      flags kept until the host reads them, 6 / 7 =
-                     //      slots placed at the front / back of order
-  int *order;        // [max_slots] the active slots in the order the brick
-                     //             kernels take them: those with more than
-                     //             64 pairs first (their blocks start early,
-                     //             the short ones fill the end)
+  int *counters;     // [BRICK_COUNTERS]: 0 = active slots, 1 = error
+                     //      flags of the step (1: slot overflow, 4:
+                     //      compaction scan timed out), 3 = tile ticket, 4 =
+                     //      scan epoch, 5 = error flags kept until the host
+                     //      reads them, 8 + q = slots in bucket q of order
+  int *order;        // [ORDER_BUCKETS][max_slots] the active slots in the
+                     //             order the brick kernels take them, by
+                     //             pair count, longest first (the long
+                     //             bricks start early, the short ones fill
+                     //             the end)
   unsigned long long *tiles;  // [compact tiles] look-back words of the
                               // compaction scan
   int max_slots;
@@ -278,11 +282,10 @@ struct DomainDesc {
 struct LaunchShape {
   int collide_block = 256;       // threads per block of the collide-stream
                                  // kernel: 128 or 256
-  int brick_blocks = 152 * 128;  // grid of the brick kernels (grid-stride
-                                 // over the active bricks, a warp each; a
-                                 // grid above the bricks' count gives one
-                                 // brick per block, which the hardware
-                                 // balances across the SMs)
+  int brick_blocks = 152 * 64;   // grid of the brick kernels (grid-stride
+                                 // over the active bricks in order, a warp
+                                 // each; about one brick per block, which
+                                 // the hardware balances across the SMs)
   int point_block = 256;         // threads per block of the per-point
                                  // kernels: 128, 256 or 512
   int moments_spb = 4;           // bricks per block of the moments kernel

@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(512, 2)
   if (k == 0) {
     m.counters[0] = 0;
     m.counters[1] = 0;
-    m.counters[6] = 0;
-    m.counters[7] = 0;
+#pragma unroll
+    for (int q = 0; q < ORDER_BUCKETS; q++) m.counters[8 + q] = 0;
   }
   const bool in = k < p.np;
   const int body = (bd.nb > 0 && in) ? (p.body ? p.body[k] : 0) : -1;
@@ -236,6 +236,13 @@ __device__ __forceinline__ unsigned long long tile_word(unsigned epoch, unsigned
 
 constexpr unsigned SCAN_SPIN_LIMIT = 1u << 22;
 
+// The brick kernels take the active bricks by pair count, the longest first:
+// bucket q of a brick with c pairs is 0 above 96, 1 above 64, 2 above 32, 3
+// otherwise.
+__device__ __forceinline__ int order_bucket(int c) {
+  return c > 96 ? 0 : (c > 64 ? 1 : (c > 32 ? 2 : 3));
+}
+
 // Bricks with a count -> slots in brick order, and each slot's first pair:
 // one pass over the bricks in tiles of COMPACT_TILE with a single-pass scan.
 // A tile takes its index from a ticket, so it only waits on tiles already
@@ -253,8 +260,10 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
   const int ntiles = (g.nbrick + COMPACT_TILE - 1) / COMPACT_TILE;
   if ((int)blockIdx.x >= ntiles) return;
   __shared__ int tile_s, wa[8], wc[8];
+  __shared__ unsigned long long wq[8];
   __shared__ unsigned epoch_s;
   __shared__ long long pre_a, pre_c;
+  __shared__ int pre_q[ORDER_BUCKETS];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   if (t == 0) {
     tile_s = atomicAdd(m.counters + 3, 1);
@@ -264,40 +273,51 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
   const int tile = tile_s;
   const unsigned epoch = epoch_s;
   const int b0 = tile * COMPACT_TILE + 4 * t;
+  // nq: active bricks per order bucket, 16 bits each (at most 1024 a tile)
   int c[4], na = 0, nc = 0;
+  unsigned long long nq = 0;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     c[i] = b0 + i < g.nbrick ? m.brick_count[b0 + i] : 0;
     na += c[i] > 0;
     nc += c[i];
+    if (c[i] > 0) nq += 1ull << (16 * order_bucket(c[i]));
   }
-  // block-exclusive scan of (na, nc)
+  // block-exclusive scan of (na, nc, nq)
   int ia = na, ic = nc;
+  unsigned long long iq = nq;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int ta = __shfl_up_sync(0xffffffffu, ia, o), tc = __shfl_up_sync(0xffffffffu, ic, o);
+    const unsigned long long tq = __shfl_up_sync(0xffffffffu, iq, o);
     if (lane >= o) {
       ia += ta;
       ic += tc;
+      iq += tq;
     }
   }
   if (lane == 31) {
     wa[w] = ia;
     wc[w] = ic;
+    wq[w] = iq;
   }
   __syncthreads();
   int ba = 0, bc = 0, ta = 0, tc = 0;
+  unsigned long long bq = 0, tq = 0;
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     if (k < w) {
       ba += wa[k];
       bc += wc[k];
+      bq += wq[k];
     }
     ta += wa[k];
     tc += wc[k];
+    tq += wq[k];
   }
   ia += ba - na;  // exclusive within the tile
   ic += bc - nc;
+  iq += bq - nq;
   if (w == 0) {
     unsigned long long *tw = m.tiles;
     long long pa = 0, pc = 0;
@@ -357,10 +377,19 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
     if (lane == 0) {
       pre_a = pa;
       pre_c = pc;
+      // the tile's places in each bucket of order
+#pragma unroll
+      for (int q = 0; q < ORDER_BUCKETS; q++) {
+        const int n = (int)((tq >> (16 * q)) & 0xffffu);
+        pre_q[q] = n > 0 ? atomicAdd(m.counters + 8 + q, n) : 0;
+      }
     }
   }
   __syncthreads();
   int slot = (int)pre_a + ia, first = (int)pre_c + ic;
+  int oq[ORDER_BUCKETS];
+#pragma unroll
+  for (int q = 0; q < ORDER_BUCKETS; q++) oq[q] = pre_q[q] + (int)((iq >> (16 * q)) & 0xffffu);
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     const int b = b0 + i;
@@ -373,12 +402,16 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
         pm.count[slot] = c[i];
         pm.start[slot] = first;
         pm.cursor[slot] = 0;
+        const int q = order_bucket(c[i]);
+        m.order[(size_t)q * m.max_slots + oq[q]] = slot;
       } else {
         m.brick_slot[b] = -1;
         atomicOr(m.counters + 1, 1);
       }
       slot++;
       first += c[i];
+#pragma unroll
+      for (int q = 0; q < ORDER_BUCKETS; q++) oq[q] += q == order_bucket(c[i]);
     } else {
       m.brick_slot[b] = -1;
     }
@@ -530,8 +563,6 @@ __global__ void __launch_bounds__(128)
   for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
     const int cnt = pm.count[s], st = pm.start[s], B = m.slot_brick[s];
     int *a = pm.k + st;
-    if (lane == 0)
-      m.order[cnt > 64 ? atomicAdd(m.counters + 6, 1) : nslots - 1 - atomicAdd(m.counters + 7, 1)] = s;
     if (cnt <= 32) {
       warp_bitonic_sort<1>(a, cnt, lane);
     } else if (cnt <= 64) {
@@ -738,6 +769,20 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The b-th active slot in the order the brick kernels take them: bucket by
+// bucket (m.counters[8 + q] slots in bucket q, at m.order[q * max_slots]);
+// index order after a slot overflow (an error step).
+__device__ __forceinline__ int slot_in_order(const BrickMap &m, int b) {
+  if (m.counters[1] & 1) return b;
+#pragma unroll
+  for (int q = 0; q < ORDER_BUCKETS - 1; q++) {
+    const int n = m.counters[8 + q];
+    if (b < n) return m.order[(size_t)q * m.max_slots + b];
+    b -= n;
+  }
+  return m.order[(size_t)(ORDER_BUCKETS - 1) * m.max_slots + b];
+}
+
 // First pass of a step over each active brick after the moments: G_0 = 0 or
 // S[du_init] (warm start), and the pairs' shares of I[U0 + G_0] for the first
 // iteration.  One warp per brick, grid-stride over the active bricks.
@@ -754,7 +799,7 @@ __global__ void __launch_bounds__(32, 32)
   const int nslots = active_slots(m);
   const int t = threadIdx.x, r = t & 15;
   for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
-    const int s = m.order[b];
+    const int s = slot_in_order(m, b);
     const int p0 = pm.start[s], cnt = pm.count[s];
     float4 G[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
                    make_float4(0.f, 0.f, 0.f, 0.f)};
@@ -791,7 +836,7 @@ __global__ void __launch_bounds__(32, 32)
   const int nslots = active_slots(m);
   const int t = threadIdx.x, r = t & 15;
   for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
-    const int s = m.order[b];
+    const int s = slot_in_order(m, b);
     const int p0 = pm.start[s], cnt = pm.count[s];
     float4 G[3];
     brick_gather(sm, pm, p0, cnt, vals, G);
@@ -840,7 +885,7 @@ __global__ void __launch_bounds__(32, 32)
   const int nslots = active_slots(m);
   const int t = threadIdx.x;
   for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
-    const int s = m.order[b];
+    const int s = slot_in_order(m, b);
     float4 G[3];
     brick_gather(sm, pm, pm.start[s], pm.count[s], vals, G, scale_by_w != 0);
     float e = 0.f;
