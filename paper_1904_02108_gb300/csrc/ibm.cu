@@ -499,6 +499,20 @@ __device__ __forceinline__ void pair_weights(const Geometry &g, const PairMap &p
   pm.point_pairs[8 * (size_t)k + j] = (int)p;
 }
 
+// The b-th active slot in the order the brick kernels take them: bucket by
+// bucket (m.counters[8 + q] slots in bucket q, at m.order[q * max_slots]);
+// index order after a slot overflow (an error step).
+__device__ __forceinline__ int slot_in_order(const BrickMap &m, int b) {
+  if (m.counters[1] & 1) return b;
+#pragma unroll
+  for (int q = 0; q < ORDER_BUCKETS - 1; q++) {
+    const int n = m.counters[8 + q];
+    if (b < n) return m.order[(size_t)q * m.max_slots + b];
+    b -= n;
+  }
+  return m.order[(size_t)(ORDER_BUCKETS - 1) * m.max_slots + b];
+}
+
 // One warp per slot: sort the slot's points ascending (a bitonic network in
 // registers up to 128 pairs, in shared memory up to SORT_CAP, else a rank sort through
 // this slot's not yet written weight storage; the points of a slot are
@@ -560,7 +574,8 @@ __global__ void __launch_bounds__(128)
   const Geometry g = D[blockIdx.y].g;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nslots = active_slots(m);
-  for (int s = blockIdx.x * 4 + w; s < nslots; s += gridDim.x * 4) {
+  for (int b = blockIdx.x * 4 + w; b < nslots; b += gridDim.x * 4) {
+    const int s = slot_in_order(m, b);  // the longest lists first
     const int cnt = pm.count[s], st = pm.start[s], B = m.slot_brick[s];
     int *a = pm.k + st;
     if (cnt <= 32) {
@@ -769,19 +784,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// The b-th active slot in the order the brick kernels take them: bucket by
-// bucket (m.counters[8 + q] slots in bucket q, at m.order[q * max_slots]);
-// index order after a slot overflow (an error step).
-__device__ __forceinline__ int slot_in_order(const BrickMap &m, int b) {
-  if (m.counters[1] & 1) return b;
-#pragma unroll
-  for (int q = 0; q < ORDER_BUCKETS - 1; q++) {
-    const int n = m.counters[8 + q];
-    if (b < n) return m.order[(size_t)q * m.max_slots + b];
-    b -= n;
-  }
-  return m.order[(size_t)(ORDER_BUCKETS - 1) * m.max_slots + b];
-}
 
 // First pass of a step over each active brick after the moments: G_0 = 0 or
 // S[du_init] (warm start), and the pairs' shares of I[U0 + G_0] for the first
