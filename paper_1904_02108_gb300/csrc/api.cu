@@ -663,8 +663,9 @@ static int enqueue_head(StepCtx &c) {
     CK(h, launch_prepare_points(c.D, c.dims, c.st));
   }
   {
-    StageTimer T(h, ST_PAIRS, c.st, 1);
+    StageTimer T(h, ST_PAIRS, c.st, c.dims.work_off ? 2 : 1);
     CK(h, launch_compact(c.D, c.dims, c.st));
+    CK(h, launch_batch_worklist(c.D, c.dims, c.st));
   }
   if (c.split) {
     CK(h, cudaEventRecord(c.ev_fork, c.st));
@@ -1046,6 +1047,7 @@ struct lbm_batch {
   int64_t g_launches = 0;
   LaunchShape shape;
   uint64_t shape_version = 0;  // changes with the shape (a new capture)
+  int *work_off = nullptr;     // [(ORDER_BUCKETS + 1) n + 2] the step's work list
   std::string err;
 };
 
@@ -1066,7 +1068,10 @@ int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out) {
   lbm_batch_t *b = new lbm_batch();
   b->hs.assign(handles, handles + n);
   b->shape = handles[0]->shape;
-  if (cudaMalloc(&b->D, sizeof(DomainDesc) * n) != cudaSuccess) {
+  if (cudaMalloc(&b->D, sizeof(DomainDesc) * n) != cudaSuccess ||
+      cudaMalloc(&b->work_off, sizeof(int) * ((size_t)(ORDER_BUCKETS + 1) * n + 2)) !=
+          cudaSuccess) {
+    if (b->D) cudaFree(b->D);
     delete b;
     return fail(nullptr, LBM_ENOMEM, "batch descriptors");
   }
@@ -1078,6 +1083,7 @@ void lbm_batch_destroy(lbm_batch_t *b) {
   if (!b) return;
   cudaDeviceSynchronize();
   if (b->D) cudaFree(b->D);
+  if (b->work_off) cudaFree(b->work_off);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -1115,6 +1121,7 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
   BatchDims dims{};
   dims.nd = (int)b->hs.size();
   dims.ls = b->shape;
+  if (dims.nd > 1) dims.work_off = b->work_off;
   bool have_du = false;
   for (lbm_t *h : b->hs) {
     ver = ver * 1000003u + h->version;

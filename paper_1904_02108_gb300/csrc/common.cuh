@@ -306,6 +306,11 @@ struct BatchDims {
   int max_bricks;
   int max_slots;
   LaunchShape ls;
+  // a batch's work list (device, [(ORDER_BUCKETS + 1) * nd + 2]: the
+  // bucket-major and the domain-major prefix of the active slots): the
+  // per-brick kernels then run one grid over the active slots of all
+  // domains; NULL for a single lattice
+  const int *work_off = nullptr;
 };
 
 }  // namespace lbmibm

@@ -403,7 +403,10 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
         pm.start[slot] = first;
         pm.cursor[slot] = 0;
         const int q = order_bucket(c[i]);
-        m.order[(size_t)q * m.max_slots + oq[q]] = slot;
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < ORDER_BUCKETS; k++) o = k == q ? oq[k] : o;
+        m.order[(size_t)q * m.max_slots + o] = slot;
       } else {
         m.brick_slot[b] = -1;
         atomicOr(m.counters + 1, 1);
@@ -513,6 +516,113 @@ __device__ __forceinline__ int slot_in_order(const BrickMap &m, int b) {
   return m.order[(size_t)(ORDER_BUCKETS - 1) * m.max_slots + b];
 }
 
+// The items of a per-brick kernel, item b from first by stride.  A batch with
+// a work list (WL) takes the active slots of all its domains as one list, so
+// an uneven batch keeps every block busy; otherwise the block's domain
+// D[blockIdx.y].  ORDERED: in the order of pair counts, longest first (in a
+// batch bucket-major: bucket q of domain d starts at off[q nd + d]); else in
+// slot order, domain by domain (domain d starts at off[ORDER_BUCKETS nd + 1 +
+// d]), which keeps neighbouring bricks together.  fn(domain, slot) for each
+// item.
+template <bool WL, bool ORDERED, typename Fn>
+__device__ __forceinline__ void for_each_slot(const DomainDesc *__restrict__ D,
+                                              const int *__restrict__ off, int nd, int first,
+                                              int stride, Fn fn) {
+  if constexpr (WL) {
+    const int nb = ORDERED ? ORDER_BUCKETS * nd : nd;
+    const int *o = ORDERED ? off : off + ORDER_BUCKETS * nd + 1;
+    const int total = o[nb];
+    for (int b = first; b < total; b += stride) {
+      int lo = 0, hi = nb;  // o[lo] <= b < o[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (o[mid] <= b) lo = mid;
+        else hi = mid;
+      }
+      const int q = ORDERED ? lo / nd : 0;
+      const DomainDesc &d = D[lo - q * nd];
+      const int local = b - o[lo];
+      if (ORDERED && !(d.m.counters[1] & 1))
+        fn(d, d.m.order[(size_t)q * d.m.max_slots + local]);
+      else
+        fn(d, local);
+    }
+  } else {
+    const DomainDesc &d = D[blockIdx.y];
+    const int n = active_slots(d.m);
+    for (int b = first; b < n; b += stride) fn(d, ORDERED ? slot_in_order(d.m, b) : b);
+  }
+}
+
+// The work list of a batch: off[q nd + d] = the items before bucket q of
+// domain d (bucket-major), off[ORDER_BUCKETS nd] = all active slots; then, at
+// off + ORDER_BUCKETS nd + 1, the same domain-major (nd + 1 entries).  A
+// domain without points or whose compaction failed contributes none; one
+// whose slots overflowed, all of them in the last bucket (index order).  One
+// block.
+__global__ void __launch_bounds__(1024)
+    batch_worklist_kernel(const DomainDesc *__restrict__ D, int nd, int *__restrict__ off) {
+  pdl_wait();
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) carry = 0;
+  const int nb = ORDER_BUCKETS * nd;
+  for (int i0 = 0; i0 < nb; i0 += 1024) {
+    const int i = i0 + t;
+    int c = 0;
+    if (i < nb) {
+      const int q = i / nd;
+      const DomainDesc &d = D[i - q * nd];
+      const int flags = d.np > 0 ? d.m.counters[1] : 4;
+      if (!(flags & 4))
+        c = (flags & 1) ? (q == ORDER_BUCKETS - 1 ? active_slots(d.m) : 0) : d.m.counters[8 + q];
+    }
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int before = carry;
+    for (int k = 0; k < w; k++) before += wsum[k];
+    if (i < nb) off[i] = before + x - c;
+    __syncthreads();
+    if (t == 1023) carry = before + x;
+    __syncthreads();
+  }
+  if (t == 0) off[nb] = carry;
+  // domain-major: the domains' active slots in order
+  int *od = off + nb + 1;
+  __syncthreads();
+  if (t == 0) carry = 0;
+  for (int i0 = 0; i0 < nd; i0 += 1024) {
+    const int i = i0 + t;
+    int c = 0;
+    if (i < nd) {
+      const DomainDesc &d = D[i];
+      c = (d.np > 0 && !(d.m.counters[1] & 4)) ? active_slots(d.m) : 0;
+    }
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int before = carry;
+    for (int k = 0; k < w; k++) before += wsum[k];
+    if (i < nd) od[i] = before + x - c;
+    __syncthreads();
+    if (t == 1023) carry = before + x;
+    __syncthreads();
+  }
+  if (t == 0) od[nd] = carry;
+}
+
 // One warp per slot: sort the slot's points ascending (a bitonic network in
 // registers up to 128 pairs, in shared memory up to SORT_CAP, else a rank sort through
 // this slot's not yet written weight storage; the points of a slot are
@@ -564,18 +674,18 @@ __device__ __forceinline__ void warp_bitonic_sort(int *a, int cnt, int lane) {
     if (lane + 32 * i < cnt) a[lane + 32 * i] = v[i];
 }
 
+template <bool WL>
 __global__ void __launch_bounds__(128)
-    pair_sort_kernel(const DomainDesc *__restrict__ D) {
+    pair_sort_kernel(const DomainDesc *__restrict__ D, const int *__restrict__ off, int nd) {
   pdl_wait();
   __shared__ int buf[4][SORT_CAP];
-  const BrickMap m = D[blockIdx.y].m;
-  const PairMap pm = D[blockIdx.y].pm;
-  const PointPrep pp = D[blockIdx.y].pp;
-  const Geometry g = D[blockIdx.y].g;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nslots = active_slots(m);
-  for (int b = blockIdx.x * 4 + w; b < nslots; b += gridDim.x * 4) {
-    const int s = slot_in_order(m, b);  // the longest lists first
+  // the longest lists first
+  for_each_slot<WL, true>(D, off, nd, blockIdx.x * 4 + w, gridDim.x * 4, [&](const DomainDesc &d, int s) {
+    const BrickMap &m = d.m;
+    const PairMap &pm = d.pm;
+    const PointPrep &pp = d.pp;
+    const Geometry &g = d.g;
     const int cnt = pm.count[s], st = pm.start[s], B = m.slot_brick[s];
     int *a = pm.k + st;
     if (cnt <= 32) {
@@ -623,9 +733,8 @@ __global__ void __launch_bounds__(128)
       pm.brick[st + i] = B;
       pair_weights(g, pm, (int64_t)st + i, k, B, load_taps(pp, k));
     }
-  }
+  });
 }
-
 
 // ---- the brick kernels: one warp per active brick ---------------------------
 
@@ -756,18 +865,18 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
 // U0 on every cell of every active brick: pull of Eq. 4 and Eq. 1 (the
 // paper's kernel strategy of Sec. 5 without duplicated cells).  One thread per
 // cell, 64 threads per brick, blockDim.x / 64 bricks per block.
-template <typename S>
+template <typename S, bool WL>
 __global__ void __launch_bounds__(256)
-    brick_moments_kernel(const DomainDesc *__restrict__ D, int cur) {
+    brick_moments_kernel(const DomainDesc *__restrict__ D, int cur, const int *__restrict__ off,
+                         int nd) {
   pdl_wait();
-  const DomainDesc &d = D[blockIdx.y];
-  const S *__restrict__ f = (const S *)d.f[cur];
-  const Geometry g = d.g;
-  const BrickMap m = d.m;
-  float *__restrict__ U0s = d.U0s;
-  const int nslots = active_slots(m);
   const int t = threadIdx.x & 63, spb = blockDim.x >> 6;
-  for (int s = blockIdx.x * spb + (threadIdx.x >> 6); s < nslots; s += gridDim.x * spb) {
+  for_each_slot<WL, false>(D, off, nd, blockIdx.x * spb + (threadIdx.x >> 6), gridDim.x * spb,
+                [&](const DomainDesc &dd, int s) {
+    const S *__restrict__ f = (const S *)dd.f[cur];
+    const Geometry &g = dd.g;
+    const BrickMap &m = dd.m;
+    float *__restrict__ U0s = dd.U0s;
     const int B = m.slot_brick[s];
     const int bx = B % g.nbx, rr = B / g.nbx;
     const int by = rr % g.nby, bz = rr / g.nby;
@@ -781,27 +890,25 @@ __global__ void __launch_bounds__(256)
     u[0] = jx * inv;
     u[BRICK_CELLS] = jy * inv;
     u[2 * BRICK_CELLS] = jz * inv;
-  }
+  });
 }
 
 
 // First pass of a step over each active brick after the moments: G_0 = 0 or
 // S[du_init] (warm start), and the pairs' shares of I[U0 + G_0] for the first
 // iteration.  One warp per brick, grid-stride over the active bricks.
+template <bool WL>
 __global__ void __launch_bounds__(32, 32)
-    brick_init_kernel(const DomainDesc *__restrict__ D, int use_du) {
+    brick_init_kernel(const DomainDesc *__restrict__ D, int use_du, const int *__restrict__ off,
+                      int nd) {
   pdl_wait();
   __shared__ BrickSmem sm;
-  const DomainDesc &d = D[blockIdx.y];
-  const BrickMap m = d.m;
-  const PairMap pm = d.pm;
-  const float4 *__restrict__ du_init = use_du ? d.du : nullptr;
-  const float *__restrict__ U0s = d.U0s;
-  float *__restrict__ Gs = d.Gs;
-  const int nslots = active_slots(m);
   const int t = threadIdx.x, r = t & 15;
-  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
-    const int s = slot_in_order(m, b);
+  for_each_slot<WL, true>(D, off, nd, blockIdx.x, gridDim.x, [&](const DomainDesc &d, int s) {
+    const PairMap &pm = d.pm;
+    const float4 *__restrict__ du_init = use_du ? d.du : nullptr;
+    const float *__restrict__ U0s = d.U0s;
+    float *__restrict__ Gs = d.Gs;
     const int p0 = pm.start[s], cnt = pm.count[s];
     float4 G[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
                    make_float4(0.f, 0.f, 0.f, 0.f)};
@@ -817,77 +924,124 @@ __global__ void __launch_bounds__(32, 32)
     __syncwarp();
     brick_interp(sm, pm, p0, cnt, du_init != nullptr && cnt <= SP_CHUNK);
     __syncwarp();
-  }
+  });
 }
 
-// One iteration's spreading over each active brick: G = S[du], the squared
-// change of G into res[slot] (tolerance mode), and, unless this is the last
-// iteration, the pairs' shares of I[U0 + G] for the next one.
-__global__ void __launch_bounds__(32, 32)
-    brick_spread_kernel(const DomainDesc *__restrict__ D, int do_interp, int tol_mode) {
-  pdl_wait();
-  __shared__ BrickSmem sm;
-  const DomainDesc &d = D[blockIdx.y];
-  if (tol_mode && d.state->done) return;
-  const BrickMap m = d.m;
-  const PairMap pm = d.pm;
-  const float4 *__restrict__ vals = d.du;
-  const float *__restrict__ U0s = d.U0s;
-  float *__restrict__ Gs = d.Gs;
-  float *__restrict__ res = tol_mode ? d.res : nullptr;
-  const int nslots = active_slots(m);
+// One iteration's spreading over one active brick (slot s): G = S[du], the
+// squared change of G into res[slot] (tolerance mode: res != nullptr), and,
+// unless this is the last iteration, the pairs' shares of I[U0 + G] for the
+// next one.
+__device__ __forceinline__ void spread_brick(BrickSmem &sm, const PairMap &pm,
+                                             const float4 *__restrict__ vals,
+                                             const float *__restrict__ U0s, float *__restrict__ Gs,
+                                             float *__restrict__ res, int s, int do_interp) {
   const int t = threadIdx.x, r = t & 15;
-  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
-    const int s = slot_in_order(m, b);
-    const int p0 = pm.start[s], cnt = pm.count[s];
-    float4 G[3];
-    brick_gather(sm, pm, p0, cnt, vals, G);
-    const size_t o = (size_t)s * SLOT_FLOATS + 4 * r;
-    if (res) {
-      float e = 0.f;
-      if (t < 16) {
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-          const float4 old = *(const float4 *)(Gs + o + c * BRICK_CELLS);
-          const float a = G[c].x - old.x, b = G[c].y - old.y, cc = G[c].z - old.z,
-                      dd = G[c].w - old.w;
-          e += ((a * a + b * b) + cc * cc) + dd * dd;
-        }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-      if (t == 0) res[s] = e;
-    }
+  const int p0 = pm.start[s], cnt = pm.count[s];
+  float4 G[3];
+  brick_gather(sm, pm, p0, cnt, vals, G);
+  const size_t o = (size_t)s * SLOT_FLOATS + 4 * r;
+  if (res) {
+    float e = 0.f;
     if (t < 16) {
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        *(float4 *)(Gs + o + c * BRICK_CELLS) = G[c];
-        if (do_interp)
-          sm.sF[c][r] = add4(*(const float4 *)(U0s + o + c * BRICK_CELLS), G[c]);
+        const float4 old = *(const float4 *)(Gs + o + c * BRICK_CELLS);
+        const float a = G[c].x - old.x, b = G[c].y - old.y, cc = G[c].z - old.z,
+                    dd = G[c].w - old.w;
+        e += ((a * a + b * b) + cc * cc) + dd * dd;
       }
     }
-    __syncwarp();
-    if (do_interp) brick_interp(sm, pm, p0, cnt, cnt <= SP_CHUNK);
-    __syncwarp();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+    if (t == 0) res[s] = e;
+  }
+  if (t < 16) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      *(float4 *)(Gs + o + c * BRICK_CELLS) = G[c];
+      if (do_interp)
+        sm.sF[c][r] = add4(*(const float4 *)(U0s + o + c * BRICK_CELLS), G[c]);
+    }
+  }
+  __syncwarp();
+  if (do_interp) brick_interp(sm, pm, p0, cnt, cnt <= SP_CHUNK);
+  __syncwarp();
+}
+
+// One iteration's spreading over each active brick (spread_brick; the single
+// lattice's loop keeps the per-domain fields in registers across bricks).
+template <bool WL>
+__global__ void __launch_bounds__(32, 32)
+    brick_spread_kernel(const DomainDesc *__restrict__ D, int do_interp, int tol_mode,
+                        const int *__restrict__ off, int nd) {
+  pdl_wait();
+  __shared__ BrickSmem sm;
+  if constexpr (WL) {
+    // (the tolerance mode runs single lattices only)
+    for_each_slot<true, true>(D, off, nd, blockIdx.x, gridDim.x, [&](const DomainDesc &d, int s) {
+      spread_brick(sm, d.pm, d.du, d.U0s, d.Gs, tol_mode ? d.res : nullptr, s, do_interp);
+    });
+  } else {
+    const DomainDesc &d = D[blockIdx.y];
+    if (tol_mode && d.state->done) return;
+    const BrickMap m = d.m;
+    const PairMap pm = d.pm;
+    const float4 *__restrict__ vals = d.du;
+    const float *__restrict__ U0s = d.U0s;
+    float *__restrict__ Gs = d.Gs;
+    float *__restrict__ res = tol_mode ? d.res : nullptr;
+    const int nslots = active_slots(m);
+    const int t = threadIdx.x, r = t & 15;
+    for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
+      const int s = slot_in_order(m, b);
+      const int p0 = pm.start[s], cnt = pm.count[s];
+      float4 G[3];
+      brick_gather(sm, pm, p0, cnt, vals, G);
+      const size_t o = (size_t)s * SLOT_FLOATS + 4 * r;
+      if (res) {
+        float e = 0.f;
+        if (t < 16) {
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const float4 old = *(const float4 *)(Gs + o + c * BRICK_CELLS);
+            const float a = G[c].x - old.x, bb = G[c].y - old.y, cc = G[c].z - old.z,
+                        dd = G[c].w - old.w;
+            e += ((a * a + bb * bb) + cc * cc) + dd * dd;
+          }
+        }
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) e += __shfl_xor_sync(0xffffffffu, e, sh);
+        if (t == 0) res[s] = e;
+      }
+      if (t < 16) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          *(float4 *)(Gs + o + c * BRICK_CELLS) = G[c];
+          if (do_interp)
+            sm.sF[c][r] = add4(*(const float4 *)(U0s + o + c * BRICK_CELLS), G[c]);
+        }
+      }
+      __syncwarp();
+      if (do_interp) brick_interp(sm, pm, p0, cnt, cnt <= SP_CHUNK);
+      __syncwarp();
+    }
   }
 }
 
 // ||S[v]||^2 per active brick into res[slot] (v = vals, scaled by .w when
 // scale_by_w): the denominators of the residual.
+template <bool WL>
 __global__ void __launch_bounds__(32, 32)
-    brick_norm_kernel(const DomainDesc *__restrict__ D, int which) {
+    brick_norm_kernel(const DomainDesc *__restrict__ D, int which, const int *__restrict__ off,
+                      int nd) {
   pdl_wait();
   __shared__ BrickSmem sm;
-  const DomainDesc &d = D[blockIdx.y];
-  const BrickMap m = d.m;
-  const PairMap pm = d.pm;
-  const float4 *__restrict__ vals = which == 0 ? d.pp.ut : d.uint;
-  const int scale_by_w = which == 0;
-  float *__restrict__ res = d.res;
-  const int nslots = active_slots(m);
   const int t = threadIdx.x;
-  for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
-    const int s = slot_in_order(m, b);
+  for_each_slot<WL, true>(D, off, nd, blockIdx.x, gridDim.x, [&](const DomainDesc &d, int s) {
+    const PairMap &pm = d.pm;
+    const float4 *__restrict__ vals = which == 0 ? d.pp.ut : d.uint;
+    const int scale_by_w = which == 0;
+    float *__restrict__ res = d.res;
     float4 G[3];
     brick_gather(sm, pm, pm.start[s], pm.count[s], vals, G, scale_by_w != 0);
     float e = 0.f;
@@ -900,7 +1054,7 @@ __global__ void __launch_bounds__(32, 32)
     for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
     if (t == 0) res[s] = e;
     __syncwarp();
-  }
+  });
 }
 
 // Deterministic FP64 sum of res[0 .. nslots) over RES_BLOCKS blocks of 256
@@ -1201,8 +1355,15 @@ cudaError_t brick_moments_typed(const DomainDesc *D, const BatchDims &dims, int 
                                 cudaStream_t st) {
   const int spb = dims.ls.moments_spb;
   if (spb != 1 && spb != 2 && spb != 4) return cudaErrorInvalidValue;
-  const dim3 grid(xblocks((dims.max_slots + spb - 1) / spb, dims.nd, 152 * 64 / spb), dims.nd);
-  return launch_pdl(brick_moments_kernel<S>, grid, dim3(64 * spb), 0, st, D, cur);
+  // a batch with a work list: one grid over all domains' slots
+  const dim3 grid = dims.work_off
+                        ? dim3(152 * 64 / spb)
+                        : dim3(xblocks((dims.max_slots + spb - 1) / spb, dims.nd, 152 * 64 / spb),
+                               dims.nd);
+  return dims.work_off ? launch_pdl(brick_moments_kernel<S, true>, grid, dim3(64 * spb), 0, st, D,
+                                    cur, dims.work_off, dims.nd)
+                       : launch_pdl(brick_moments_kernel<S, false>, grid, dim3(64 * spb), 0, st, D,
+                                    cur, dims.work_off, dims.nd);
 }
 
 }  // namespace
@@ -1220,6 +1381,12 @@ cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStrea
                     0, st, D);
 }
 
+cudaError_t launch_batch_worklist(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+  if (!dims.work_off) return cudaSuccess;
+  return launch_pdl(batch_worklist_kernel, dim3(1), dim3(1024), 0, st, D, dims.nd,
+                    const_cast<int *>(dims.work_off));
+}
+
 cudaError_t launch_pair_lists(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
   const int pb = dims.ls.point_block;
@@ -1227,9 +1394,13 @@ cudaError_t launch_pair_lists(const DomainDesc *D, const BatchDims &dims, cudaSt
       launch_pdl(pair_fill_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0, st, D);
   // one warp per slot
   if (e == cudaSuccess)
-    e = launch_pdl(pair_sort_kernel,
-                   dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, dims.ls.sort_blocks), dims.nd),
-                   dim3(128), 0, st, D);
+    e = dims.work_off
+            ? launch_pdl(pair_sort_kernel<true>, dim3(dims.ls.sort_blocks), dim3(128), 0, st, D,
+                         dims.work_off, dims.nd)
+            : launch_pdl(pair_sort_kernel<false>,
+                         dim3(xblocks((dims.max_slots + 3) / 4, dims.nd, dims.ls.sort_blocks),
+                              dims.nd),
+                         dim3(128), 0, st, D, dims.work_off, dims.nd);
   return e;
 }
 
@@ -1250,18 +1421,26 @@ cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDi
   DISPATCH_STORAGE(storage, brick_moments_typed, D, dims, cur, st);
 }
 
+// a batch with a work list: one grid over all domains' slots
 static dim3 brick_grid(const BatchDims &dims) {
+  if (dims.work_off) return dim3(dims.ls.brick_blocks);
   return dim3(xblocks(dims.max_slots, dims.nd, dims.ls.brick_blocks), dims.nd);
 }
 
 cudaError_t launch_brick_init(const DomainDesc *D, const BatchDims &dims, int use_du,
                               cudaStream_t st) {
-  return launch_pdl(brick_init_kernel, brick_grid(dims), dim3(32), 0, st, D, use_du);
+  return dims.work_off ? launch_pdl(brick_init_kernel<true>, brick_grid(dims), dim3(32), 0, st, D,
+                                    use_du, dims.work_off, dims.nd)
+                       : launch_pdl(brick_init_kernel<false>, brick_grid(dims), dim3(32), 0, st, D,
+                                    use_du, dims.work_off, dims.nd);
 }
 
 cudaError_t launch_brick_spread(const DomainDesc *D, const BatchDims &dims, int do_interp,
                                 int tol_mode, cudaStream_t st) {
-  return launch_pdl(brick_spread_kernel, brick_grid(dims), dim3(32), 0, st, D, do_interp, tol_mode);
+  return dims.work_off ? launch_pdl(brick_spread_kernel<true>, brick_grid(dims), dim3(32), 0, st, D,
+                                    do_interp, tol_mode, dims.work_off, dims.nd)
+                       : launch_pdl(brick_spread_kernel<false>, brick_grid(dims), dim3(32), 0, st, D,
+                                    do_interp, tol_mode, dims.work_off, dims.nd);
 }
 
 cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int first, int warm,
@@ -1274,7 +1453,10 @@ cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int 
 
 cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,
                               cudaStream_t st) {
-  return launch_pdl(brick_norm_kernel, brick_grid(dims), dim3(32), 0, st, D, which);
+  return dims.work_off ? launch_pdl(brick_norm_kernel<true>, brick_grid(dims), dim3(32), 0, st, D,
+                                    which, dims.work_off, dims.nd)
+                       : launch_pdl(brick_norm_kernel<false>, brick_grid(dims), dim3(32), 0, st, D,
+                                    which, dims.work_off, dims.nd);
 }
 
 cudaError_t launch_ibm_den(const DomainDesc *D, const BatchDims &dims, int mode, cudaStream_t st) {

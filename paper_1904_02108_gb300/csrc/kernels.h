@@ -60,6 +60,9 @@ struct PointsIn {
 cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // counted bricks -> slots (1 launch)
 cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
+// a batch's work list from the domains' slot counts (1 launch when
+// dims.work_off, else none)
+cudaError_t launch_batch_worklist(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // (brick, point) pairs grouped by slot in a fixed order, with brick-local
 // weights (2 launches when points exist, else none)
 cudaError_t launch_pair_lists(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
