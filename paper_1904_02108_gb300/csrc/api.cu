@@ -1137,6 +1137,8 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
   if (ver != b->built_for) {
     std::vector<DomainDesc> hd;
     for (lbm_t *h : b->hs) hd.push_back(host_desc(h));
+    // (earlier steps of the batch may still read the old descriptors)
+    CK(h0, h0->st ? cudaStreamSynchronize(h0->st) : cudaDeviceSynchronize());
     CK(h0, cudaMemcpy(b->D, hd.data(), sizeof(DomainDesc) * hd.size(), cudaMemcpyHostToDevice));
     b->built_for = ver;
   }
