@@ -377,13 +377,11 @@ __global__ void __launch_bounds__(256) compact_kernel(const DomainDesc *__restri
     if (lane == 0) {
       pre_a = pa;
       pre_c = pc;
-      // the tile's places in each bucket of order
-#pragma unroll
-      for (int q = 0; q < ORDER_BUCKETS; q++) {
-        const int n = (int)((tq >> (16 * q)) & 0xffffu);
-        pre_q[q] = n > 0 ? atomicAdd(m.counters + 8 + q, n) : 0;
-      }
     }
+  } else if (w == 1 && lane < ORDER_BUCKETS) {
+    // the tile's places in each bucket of order (beside warp 0's look-back)
+    const int n = (int)((tq >> (16 * lane)) & 0xffffu);
+    pre_q[lane] = n > 0 ? atomicAdd(m.counters + 8 + lane, n) : 0;
   }
   __syncthreads();
   int slot = (int)pre_a + ia, first = (int)pre_c + ic;
