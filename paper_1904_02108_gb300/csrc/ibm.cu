@@ -438,11 +438,36 @@ __global__ void __launch_bounds__(512) pair_fill_kernel(const DomainDesc *__rest
   const PairMap pm = d.pm;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= np || (m.counters[1] & 4)) return;
+  // the point's (up to) eight slots and their first pairs, then every slot's
+  // warp-aggregated increment issued before any result is used (one round
+  // trip for the eight, not eight)
+  int sl[8], first[8];
+  int j = 0;
   for_support_bricks8(g, pp.base[k], [&](int brick, bool valid) {
-    const int s = valid ? m.brick_slot[brick] : -1;
-    const int pos = aggregated_inc(pm.cursor, s, s >= 0);
-    if (s >= 0) pm.k[pm.start[s] + pos] = (int)k;
+    sl[j] = valid ? m.brick_slot[brick] : -1;
+    j++;
   });
+#pragma unroll
+  for (int i = 0; i < 8; i++) first[i] = sl[i] >= 0 ? pm.start[sl[i]] : 0;
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  unsigned grp[8];
+  int old[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    grp[i] = __match_any_sync(act, sl[i] >= 0 ? sl[i] : -1);
+    old[i] = 0;
+    if (sl[i] >= 0 && lane == __ffs(grp[i]) - 1)
+      old[i] = atomicAdd(pm.cursor + sl[i], __popc(grp[i]));
+  }
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    if (sl[i] >= 0) {
+      const int pos = __shfl_sync(grp[i], old[i], __ffs(grp[i]) - 1) +
+                      __popc(grp[i] & ((1u << lane) - 1u));
+      pm.k[first[i] + pos] = (int)k;
+    }
+  }
 }
 
 // A point's base cell and tap weights, as prepare_points wrote them.
