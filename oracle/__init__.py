@@ -65,9 +65,11 @@ def lib():
             L.orc_kinematics.argtypes = [l, p, p, p, p, p, l, p, p]
             L.orc_ibm.argtypes = [i, i, i, i, p, l, p, p, p, i, d, i, i, p, p, p, p, p]
             L.orc_ibm.restype = i
+            L.orc_ibm_cg.argtypes = [i, i, i, i, p, l, p, p, p, i, d, i, p, p, p, p, p, p]
+            L.orc_ibm_cg.restype = i
             L.orc_sums.argtypes = [i, i, i, p, p]
             L.orc_step.argtypes = [i, i, i, d, i, p, p, l, p, p, p, i, d, i, i,
-                                   p, p, p, p, p, p, p, p]
+                                   p, p, p, p, p, p, p, p, i]
             L.orc_step.restype = i
             L.orc_mlp_nparam.restype = i
             L.orc_mlp_forward.argtypes = [l, p, p, p]
@@ -193,6 +195,33 @@ def ibm(U0, x, ut, s, n_iter=5, tol=1e-4, max_iter=500, literal=False,
     return G, du, eps[:it], eps_pt[:it]
 
 
+def ibm_cg(U0, x, ut, s, n_iter=5, tol=1e-4, max_iter=500, du_init=None,
+           kernel="cosine"):
+    """Conjugate gradients on the lattice form B G = c of the fixed point of
+    Sec. 3 (not in the paper; orc_ibm_cg).  Returns (G, du, eps, eps_pt,
+    u_interp)."""
+    U0 = _f64(U0)
+    _, nz, ny, nx = U0.shape
+    x = _f64(x).reshape(-1, 3)
+    ut = _f64(ut).reshape(-1, 3)
+    s = _f64(s).reshape(-1)
+    n = len(x)
+    du = np.zeros((n, 3))
+    ui = np.zeros((n, 3))
+    G = np.zeros_like(U0)
+    cap = n_iter if n_iter > 0 else max_iter
+    eps = np.zeros(cap)
+    eps_pt = np.zeros(cap)
+    di = None if du_init is None else _f64(du_init).reshape(-1, 3)
+    it = lib().orc_ibm_cg(nx, ny, nz, KERNELS[kernel], _p(U0), n, _p(x), _p(ut), _p(s),
+                          int(n_iter), float(tol), int(max_iter), _p(di), _p(du), _p(G),
+                          _p(eps), _p(eps_pt), _p(ui))
+    return G, du, eps[:it], eps_pt[:it], ui
+
+
+SOLVERS = {"mdf": 0, "cg": 1}
+
+
 def sums(f):
     f = _f64(f)
     _, nz, ny, nx = f.shape
@@ -230,12 +259,14 @@ class Simulation:
     ``points`` (optional) is a dict with ``xrest`` [np,3], ``area`` [np],
     ``body`` [np] and per-body ``centre`` [nb,3], ``omega`` [nb], ``phase`` [nb]
     (rigid rotation about z, Alg. 1), or ``x`` [np,3] and ``ut`` [np,3] for
-    fixed points with a prescribed surface velocity.
+    fixed points with a prescribed surface velocity.  ``solver`` is "mdf"
+    (the multi-direct-forcing loop of Sec. 3) or "cg" (conjugate gradients
+    on the same fixed point, ``ibm_cg``).
     """
 
     def __init__(self, shape, tau, points=None, kernel="cosine", n_iter=5,
                  tol=1e-4, max_iter=500, literal=False, warm="zero",
-                 gbody=None):
+                 gbody=None, solver="mdf"):
         self.shape = tuple(shape)
         self.tau = float(tau)
         self.kernel = kernel
@@ -244,6 +275,7 @@ class Simulation:
         self.max_iter = int(max_iter)
         self.literal = bool(literal)
         self.warm = warm
+        self.solver = SOLVERS[solver]
         self.gbody = None if gbody is None else _f64(gbody, (3,))
         nz, ny, nx = self.shape
         self.f = init_equilibrium(self.shape)
@@ -292,7 +324,8 @@ class Simulation:
                             _p(self.ftmp), self.np, _p(_f64(x)), _p(_f64(ut)),
                             _p(self.area), self.n_iter, self.tol, self.max_iter,
                             int(self.literal), _p(du_init), _p(du), _p(self.gbody),
-                            _p(self.rho), _p(self.U0), _p(self.G), _p(eps), _p(eps_pt))
+                            _p(self.rho), _p(self.U0), _p(self.G), _p(eps), _p(eps_pt),
+                            self.solver)
             self.du = du
             self.iters.append(it)
             self.eps.append(eps[:it].copy())

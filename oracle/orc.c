@@ -252,6 +252,45 @@ static double norm_points(long np, const double *v) {
   return sqrt(s);
 }
 
+/* Denominators of the residuals: den = ||S[s u_t]|| (Eulerian) and
+ * den_pt = ||u_t|| (pointwise); where one vanishes, the same norm of the
+ * zero-start increment (s (u_t - I[U0]), resp. u_t - I[U0]), then 1. */
+static void residual_denominators(int nx, int ny, int nz, int kernel, const double *U0,
+                                  long np, const double *x, const double *ut,
+                                  const double *s, double *den_out, double *den_pt_out) {
+  long N = (long)nx * ny * nz;
+  double *tmp = malloc(sizeof(double) * 3 * N);
+  double *un = malloc(sizeof(double) * 3 * np);
+  double *v = malloc(sizeof(double) * 3 * np);
+  for (long k = 0; k < np; k++)
+    for (int c = 0; c < 3; c++) v[3 * k + c] = s[k] * ut[3 * k + c];
+  memset(tmp, 0, sizeof(double) * 3 * N);
+  orc_spread(nx, ny, nz, kernel, np, x, v, tmp);
+  double den = norm_field(N, tmp);
+  double den_pt = norm_points(np, ut);
+  if (den == 0.0 || den_pt == 0.0) {
+    orc_interpolate(nx, ny, nz, kernel, U0, np, x, un);
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++)
+        v[3 * k + c] = ut[3 * k + c] - un[3 * k + c];
+    if (den_pt == 0.0) den_pt = norm_points(np, v);
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++) v[3 * k + c] *= s[k];
+    if (den == 0.0) {
+      memset(tmp, 0, sizeof(double) * 3 * N);
+      orc_spread(nx, ny, nz, kernel, np, x, v, tmp);
+      den = norm_field(N, tmp);
+    }
+    if (den == 0.0) den = 1.0;
+    if (den_pt == 0.0) den_pt = 1.0;
+  }
+  *den_out = den;
+  *den_pt_out = den_pt;
+  free(tmp);
+  free(un);
+  free(v);
+}
+
 /* The multi-direct-forcing fixed point of Sec. 3.
  *
  *   U_0 = U0 + S[du_init]               (du_init = 0 in the paper)
@@ -287,29 +326,8 @@ int orc_ibm(int nx, int ny, int nz, int kernel, const double *U0, long np,
   for (long n = 0; n < 3 * np; n++) du[n] = du_init ? du_init[n] : 0.0;
   if (du_init) orc_spread(nx, ny, nz, kernel, np, x, du_init, Un);
 
-  /* residual denominators */
-  for (long k = 0; k < np; k++)
-    for (int c = 0; c < 3; c++) v[3 * k + c] = s[k] * ut[3 * k + c];
-  memset(tmp, 0, sizeof(double) * 3 * N);
-  orc_spread(nx, ny, nz, kernel, np, x, v, tmp);
-  double den = norm_field(N, tmp);
-  double den_pt = norm_points(np, ut);
-  if (den == 0.0 || den_pt == 0.0) {
-    orc_interpolate(nx, ny, nz, kernel, U0, np, x, un);
-    for (long k = 0; k < np; k++)
-      for (int c = 0; c < 3; c++)
-        v[3 * k + c] = ut[3 * k + c] - un[3 * k + c];
-    if (den_pt == 0.0) den_pt = norm_points(np, v);
-    for (long k = 0; k < np; k++)
-      for (int c = 0; c < 3; c++) v[3 * k + c] *= s[k];
-    if (den == 0.0) {
-      memset(tmp, 0, sizeof(double) * 3 * N);
-      orc_spread(nx, ny, nz, kernel, np, x, v, tmp);
-      den = norm_field(N, tmp);
-    }
-    if (den == 0.0) den = 1.0;
-    if (den_pt == 0.0) den_pt = 1.0;
-  }
+  double den, den_pt;
+  residual_denominators(nx, ny, nz, kernel, U0, np, x, ut, s, &den, &den_pt);
 
   int n = 0;
   for (;;) {
@@ -358,6 +376,117 @@ int orc_ibm(int nx, int ny, int nz, int kernel, const double *U0, long np,
   return n;
 }
 
+/* Conjugate gradients on the same fixed point (not in the paper; a Krylov
+ * replacement for the loop above).
+ *
+ * On the lattice, the loop above is Richardson's iteration with unit step,
+ * G_{n+1} = G_n + (c - B G_n), on the linear system
+ *
+ *   B G = c,   B = S diag(s) I,   c = S[s (u_t - I[U0])],
+ *
+ * whose residual c - B G_n = S[s g_n] is the one eps measures.  B is
+ * symmetric positive semi-definite (S is the adjoint of I) and c lies in its
+ * range, so conjugate gradients apply even where A = I S is singular (points
+ * closer than the kernel resolves: the point-space system A du = b is then
+ * inconsistent, and CG on it diverges).  Hestenes-Stiefel CG on B G = c:
+ *
+ *   R_0 = c - B G_0,  P_0 = R_0
+ *   for n = 0, 1, ...:
+ *     eps_n   = ||R_n|| / ||S[s u_t]||
+ *     alpha_n = (R_n . R_n) / (P_n . B P_n)
+ *     G_{n+1} = G_n + alpha_n P_n,   R_{n+1} = R_n - alpha_n B P_n
+ *     beta_n  = (R_{n+1} . R_{n+1}) / (R_n . R_n),   P_{n+1} = R_{n+1} + beta_n P_n
+ *
+ * Every iterate is a spread of point values, so the oracle carries those
+ * instead: G_n = S[du_n], R_n = S[s r_n] with r_n = u_t - I[U0 + G_n], and
+ * P_n = S[p_n]; then B P_n = S[s y_n] with y_n = I[P_n], P_n . B P_n =
+ * sum_k s(k) |y_n(k)|^2, and the updates read
+ *
+ *   du += alpha_n p_n,   r_{n+1} = r_n - alpha_n y_n,   p_{n+1} = s r_{n+1} + beta_n p_n,
+ *
+ * with R . R = ||S[s r]||^2 spread anew each iteration.  Where R_n . R_n or
+ * P_n . B P_n is not positive (an exact solution) alpha_n = 0, and beta_n = 0
+ * when R_n . R_n is 0.  Iteration counts, n_iter, tol, max_iter, the
+ * denominators and the pointwise residual ||r_n|| / ||u_t|| are as in
+ * orc_ibm; u_interp (NULL or [np][3]) receives u_t - r_n of the last
+ * iteration, the velocity interpolated from its iterate. */
+int orc_ibm_cg(int nx, int ny, int nz, int kernel, const double *U0, long np,
+               const double *x, const double *ut, const double *s, int n_iter,
+               double tol, int max_iter, const double *du_init, double *du, double *G,
+               double *eps, double *eps_pt, double *u_interp) {
+  long N = (long)nx * ny * nz;
+  long M = 3 * np;
+  double *F = malloc(sizeof(double) * 3 * N);
+  double *r = malloc(sizeof(double) * M);
+  double *v = malloc(sizeof(double) * M);
+  double *p = malloc(sizeof(double) * M);
+  double *y = malloc(sizeof(double) * M);
+  double den, den_pt;
+  residual_denominators(nx, ny, nz, kernel, U0, np, x, ut, s, &den, &den_pt);
+
+  for (long m = 0; m < M; m++) du[m] = du_init ? du_init[m] : 0.0;
+  memcpy(F, U0, sizeof(double) * 3 * N);
+  if (du_init) orc_spread(nx, ny, nz, kernel, np, x, du, F);
+  orc_interpolate(nx, ny, nz, kernel, F, np, x, y);
+  for (long k = 0; k < np; k++)
+    for (int c = 0; c < 3; c++) {
+      long m = 3 * k + c;
+      r[m] = ut[m] - y[m];
+      v[m] = s[k] * r[m];
+      p[m] = v[m];
+    }
+  memset(F, 0, sizeof(double) * 3 * N);
+  orc_spread(nx, ny, nz, kernel, np, x, v, F);
+  double rr = norm_field(N, F);
+  rr *= rr;
+
+  int n = 0;
+  for (;;) {
+    if (eps) eps[n] = sqrt(rr) / den;
+    if (eps_pt) eps_pt[n] = norm_points(np, r) / den_pt;
+    if (u_interp)
+      for (long m = 0; m < M; m++) u_interp[m] = ut[m] - r[m];
+
+    memset(F, 0, sizeof(double) * 3 * N);
+    orc_spread(nx, ny, nz, kernel, np, x, p, F);
+    orc_interpolate(nx, ny, nz, kernel, F, np, x, y);
+    double pbp = 0.0;
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++) pbp += s[k] * y[3 * k + c] * y[3 * k + c];
+    double alpha = (rr > 0.0 && pbp > 0.0) ? rr / pbp : 0.0;
+    for (long k = 0; k < np; k++)
+      for (int c = 0; c < 3; c++) {
+        long m = 3 * k + c;
+        du[m] += alpha * p[m];
+        r[m] -= alpha * y[m];
+        v[m] = s[k] * r[m];
+      }
+    memset(F, 0, sizeof(double) * 3 * N);
+    orc_spread(nx, ny, nz, kernel, np, x, v, F);
+    double rr_next = norm_field(N, F);
+    rr_next *= rr_next;
+    double beta = rr > 0.0 ? rr_next / rr : 0.0;
+    for (long m = 0; m < M; m++) p[m] = v[m] + beta * p[m];
+    double e = sqrt(rr) / den;
+    rr = rr_next;
+
+    n++;
+    if (n_iter > 0) {
+      if (n >= n_iter) break;
+    } else if (e <= tol || n >= max_iter) {
+      break;
+    }
+  }
+  memset(G, 0, sizeof(double) * 3 * N);
+  orc_spread(nx, ny, nz, kernel, np, x, du, G);
+  free(F);
+  free(r);
+  free(v);
+  free(p);
+  free(y);
+  return n;
+}
+
 /* Global sums of the populations: mass sum_X sum_i f_i and momentum
  * sum_X sum_i e_i f_i.  out[0] = mass, out[1..3] = momentum. */
 void orc_sums(int nx, int ny, int nz, const double *f, double *out) {
@@ -375,7 +504,8 @@ void orc_sums(int nx, int ny, int nz, const double *f, double *out) {
 
 /* One full time step in the order of the Sec. 2 summary:
  *   1. rho, U from Eq. 1 (U0 below);
- *   2. G = immersedBoundary(object, U) by orc_ibm (np > 0);
+ *   2. G = immersedBoundary(object, U) by orc_ibm (np > 0; solver 0) or
+ *      by orc_ibm_cg (solver 1);
  *      plus an optional uniform body force gbody (a test hook, not in the
  *      paper);
  *   3-5. U^G = U + tau G, equilibrium, BGK collision;
@@ -388,13 +518,16 @@ int orc_step(int nx, int ny, int nz, double tau, int kernel, double *f,
              const double *s, int n_iter, double tol, int max_iter,
              int literal, const double *du_init, double *du,
              const double *gbody, double *rho, double *U0, double *G,
-             double *eps, double *eps_pt) {
+             double *eps, double *eps_pt, int solver) {
   long N = (long)nx * ny * nz;
   double *r = rho ? rho : malloc(sizeof(double) * N);
   double *g = G ? G : malloc(sizeof(double) * 3 * N);
   orc_moments(nx, ny, nz, f, r, U0);
   int iters = 0;
-  if (np > 0)
+  if (np > 0 && solver == 1)
+    iters = orc_ibm_cg(nx, ny, nz, kernel, U0, np, x, ut, s, n_iter, tol,
+                       max_iter, du_init, du, g, eps, eps_pt, NULL);
+  else if (np > 0)
     iters = orc_ibm(nx, ny, nz, kernel, U0, np, x, ut, s, n_iter, tol,
                     max_iter, literal, du_init, du, g, eps, eps_pt);
   else

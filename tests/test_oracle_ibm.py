@@ -241,3 +241,148 @@ def test_warm_start_shifts_the_initial_field(orc):
     _, du5, _, _ = orc.ibm(U0, x, ut, s, n_iter=5)
     _, du32, _, _ = orc.ibm(U0, x, ut, s, n_iter=2, du_init=du3)
     assert np.abs(du32 - du5).max() < 1e-15
+
+
+# ---- conjugate gradients on the lattice form of the fixed point -------------
+
+def _dense_B(orc, shape, x, s, kernel="cosine"):
+    """B = S diag(s) I on one component of the lattice (cells x cells)."""
+    nz, ny, nx = shape
+    N = nx * ny * nz
+    B = np.zeros((N, N))
+    for j in range(N):
+        E = np.zeros((3,) + tuple(shape))
+        E[0].reshape(-1)[j] = 1.0
+        y = orc.interpolate(E, x, kernel) * s[:, None]
+        B[:, j] = orc.spread(shape, x, y, kernel)[0].reshape(-1)
+    return B
+
+
+def _energy(orc, E, x, s):
+    """E . B E = sum_k s(k) |I[E](k)|^2."""
+    y = orc.interpolate(E, x)
+    return float((s[:, None] * y * y).sum())
+
+
+def _sheet_case(seed, spacing=0.7, svals=(0.49,)):
+    shape = (6, 8, 6)
+    x = _sheet(shape, spacing)
+    n = len(x)
+    rng = W.SplitMix64(seed)
+    U0 = 0.01 * W.random_array(rng, (3,) + shape)
+    ut = 0.02 * W.random_array(rng, (n, 3))
+    s = np.array([svals[k % len(svals)] for k in range(n)], dtype=np.float64)
+    return shape, x, U0, ut, s
+
+
+def test_cg_iterates_are_textbook_cg_on_the_lattice_system(orc):
+    """The oracle's CG, run through point vectors, against scipy's CG on the
+    dense lattice system B G = c (B = S diag(s) I per component, the three
+    components one system), from a warm start, iterate by iterate."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    shape, x, U0, ut, s = _sheet_case(40, svals=(0.49, 0.3, 0.6))
+    n = len(x)
+    rng = W.SplitMix64(41)
+    du0 = 0.5 * W.random_array(rng, (n, 3))
+    B1 = _dense_B(orc, shape, x, s)
+    B = np.kron(np.eye(3), B1)
+    c = orc.spread(shape, x, s[:, None] * (ut - orc.interpolate(U0, x))).reshape(-1)
+    G0 = orc.spread(shape, x, du0).reshape(-1)
+    ref = []
+    sla.cg(B, c, x0=G0.copy(), rtol=0.0, atol=0.0, maxiter=8,
+           callback=lambda xk: ref.append(xk.copy()))
+    assert len(ref) == 8
+    for k in (1, 2, 3, 5, 8):
+        G, du, eps, _, _ = orc.ibm_cg(U0, x, ut, s, n_iter=k, du_init=du0)
+        scale = np.abs(ref[k - 1]).max()
+        assert np.abs(G.reshape(-1) - ref[k - 1]).max() < 1e-11 * scale
+        # eps_j is the norm of the lattice residual c - B G_j over ||S[s u_t]||
+        den = np.linalg.norm(orc.spread(shape, x, s[:, None] * ut))
+        Gj = G0 if k == 1 else ref[k - 2]
+        assert abs(eps[-1] - np.linalg.norm(c - B @ Gj) / den) < 1e-11 * eps[-1]
+
+
+def test_cg_exact_after_as_many_iterations_as_distinct_eigenvalues(orc):
+    """Points whose supports are disjoint: B restricted to them has the
+    eigenvalues s(k) (3/8)^3, so with two distinct areas CG is exact after two
+    iterations: du = (u_t - I[U0]) / (3/8)^3 (Sec. 3's single-point
+    self-interaction), and the residual vanishes."""
+    shape = (16, 16, 16)
+    x = np.array([(2.3 + 8 * i, 3.6 + 8 * j, 1.1 + 8 * k)
+                  for i in range(2) for j in range(2) for k in range(2)], dtype=np.float64)
+    n = len(x)
+    rng = W.SplitMix64(42)
+    U0 = 0.01 * W.random_array(rng, (3,) + shape)
+    ut = 0.02 * W.random_array(rng, (n, 3))
+    s = np.array([0.49 if k % 2 else 1.3 for k in range(n)])
+    b = ut - orc.interpolate(U0, x)
+    G, du, eps, _, _ = orc.ibm_cg(U0, x, ut, s, n_iter=3)
+    assert eps[0] > 0.1 and eps[1] > 1e-3 and eps[2] < 1e-14
+    assert np.abs(du - b / (3 / 8) ** 3).max() < 1e-13 * np.abs(du).max()
+    _, _, eps1, _, _ = orc.ibm_cg(U0, x, ut, np.full(n, 0.7), n_iter=2)
+    assert eps1[1] < 1e-14  # one distinct eigenvalue: exact after one iteration
+
+
+def test_cg_and_fixed_point_reach_the_same_force(orc):
+    """On the singular 0.7-spacing sheet both methods converge to the one
+    solution of B G = c in G_0 + range(B): CG in a few dozen iterations, the
+    loop of Sec. 3 in ~20k."""
+    shape, x, U0, ut, s = _sheet_case(28)
+    Gc, duc, epsc, _, _ = orc.ibm_cg(U0, x, ut, s, n_iter=0, tol=1e-12, max_iter=500)
+    Gm, dum, epsm, _ = orc.ibm(U0, x, ut, s, n_iter=0, tol=1e-12, max_iter=100000)
+    assert len(epsc) < 60 and len(epsm) > 10000
+    assert epsc[-1] <= 1e-12 and epsm[-1] <= 1e-12
+    assert np.abs(Gc - Gm).max() < 1e-9 * np.abs(Gm).max()
+    # converged: the corrected field meets the surface velocity in the sense
+    # the kernel resolves (the lattice residual), not pointwise
+    assert np.linalg.norm(orc.spread(shape, x, s[:, None] * (ut - orc.interpolate(U0 + Gc, x)))) \
+        < 1e-11 * np.linalg.norm(orc.spread(shape, x, s[:, None] * ut))
+
+
+def test_cg_energy_error_is_minimal_over_the_same_krylov_space(orc):
+    """Uniform s: the loop of Sec. 3 and CG build G_n in the same affine
+    Krylov space G_0 + K_n(B, R_0); CG's error in the energy norm of B is the
+    minimum over it, so it never exceeds the loop's and never increases."""
+    shape, x, U0, ut, s = _sheet_case(43)
+    Gs, _, _, _, _ = orc.ibm_cg(U0, x, ut, s, n_iter=0, tol=1e-13, max_iter=500)
+    prev = np.inf
+    for n in range(1, 13):
+        Gc = orc.ibm_cg(U0, x, ut, s, n_iter=n)[0]
+        Gm = orc.ibm(U0, x, ut, s, n_iter=n)[0]
+        ec, em = _energy(orc, Gc - Gs, x, s), _energy(orc, Gm - Gs, x, s)
+        assert ec <= em * (1 + 1e-10) + 1e-30
+        assert ec <= prev * (1 + 1e-10)
+        prev = ec
+    assert ec < 1e-2 * em  # 12 iterations: ~200x smaller
+
+
+def test_cg_residual_recursion_is_the_residual_of_the_iterate(orc):
+    """eps_n, carried by the recursion r_{n+1} = r_n - alpha y_n, equals the
+    definition ||S[s (u_t - I[U0 + S[du_n]])]|| / ||S[s u_t]|| recomputed from
+    the iterate du_n; u_interp = I[U0 + S[du_n]] of the last iterate."""
+    shape, x, U0, ut, s = _sheet_case(44, svals=(0.49, 0.35))
+    rng = W.SplitMix64(45)
+    du0 = 0.3 * W.random_array(rng, (len(x), 3))
+    _, _, eps, eps_pt, _ = orc.ibm_cg(U0, x, ut, s, n_iter=9, du_init=du0)
+    den = np.linalg.norm(orc.spread(shape, x, s[:, None] * ut))
+    for n in range(9):
+        du_n = du0 if n == 0 else orc.ibm_cg(U0, x, ut, s, n_iter=n, du_init=du0)[1]
+        ui = orc.interpolate(U0 + orc.spread(shape, x, du_n), x)
+        e = np.linalg.norm(orc.spread(shape, x, s[:, None] * (ut - ui))) / den
+        assert abs(eps[n] - e) < 1e-10 * e
+        assert abs(eps_pt[n] - np.linalg.norm(ut - ui) / np.linalg.norm(ut)) < 1e-10 * eps_pt[n]
+        if n:
+            ui_last = orc.ibm_cg(U0, x, ut, s, n_iter=n + 1, du_init=du0)[4]
+            assert np.abs(ui_last - ui).max() < 1e-12
+
+
+def test_cg_tolerance_mode_stops_at_first_iterate_below_tol(orc):
+    shape, x, U0, ut, s = _sheet_case(46)
+    _, _, eps_fixed, _, _ = orc.ibm_cg(U0, x, ut, s, n_iter=30)
+    tol = 0.05
+    assert eps_fixed[0] > tol > eps_fixed[-1]
+    _, _, eps, _, _ = orc.ibm_cg(U0, x, ut, s, n_iter=0, tol=tol, max_iter=30)
+    k = int(np.argmax(eps_fixed <= tol))
+    assert len(eps) == k + 1 and np.array_equal(eps, eps_fixed[:k + 1])
+    _, _, eps_cap, _, _ = orc.ibm_cg(U0, x, ut, s, n_iter=0, tol=1e-30, max_iter=7)
+    assert len(eps_cap) == 7
