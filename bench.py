@@ -400,22 +400,28 @@ def bench_batched(steps=100, warmup=4):
 def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
     """ms per step when every step iterates the fixed point to eps <= tol,
     on the 256^3 propeller array: zero start, previous-force start, the
-    learned start, and the previous-force start on 16-bit storage."""
+    learned start, and the previous-force start on 16-bit storage, with the
+    paper's loop ("mdf"); and the first three with conjugate gradients on the
+    same fixed point ("cg")."""
     import numpy as np
     import torch
     from paper_1904_02108_gb300 import binding, workload as W
     w = W.dense_array_256()
     st = torch.cuda.current_stream()
-    variants = [("zero_f32", "zero", "f32"), ("previous_f32", "previous", "f32")]
+    variants = [("zero_f32", "zero", "f32", "mdf"), ("previous_f32", "previous", "f32", "mdf")]
     P = None
     if os.path.exists(WEIGHTS):
         P = np.load(WEIGHTS)
-        variants.append(("learned_f32", "mlp", "f32"))
-    variants += [("previous_bf16", "previous", "bf16"), ("previous_f16", "previous", "f16")]
+        variants.append(("learned_f32", "mlp", "f32", "mdf"))
+    variants += [("previous_bf16", "previous", "bf16", "mdf"),
+                 ("previous_f16", "previous", "f16", "mdf"),
+                 ("cg_zero_f32", "zero", "f32", "cg"), ("cg_previous_f32", "previous", "f32", "cg")]
+    if P is not None:
+        variants.append(("cg_learned_f32", "mlp", "f32", "cg"))
     out = {"tol": tol, "max_iter": max_iter, "workload": w.name, "steps": steps}
-    for name, warm, storage in variants:
+    for name, warm, storage, solver in variants:
         lat = binding.Lattice(w.shape, w.tau, storage=storage, warm=warm, ibm_tol=tol,
-                              ibm_max_iter=max_iter, stream=st)
+                              ibm_max_iter=max_iter, stream=st, solver=solver)
         lat.set_propellers(w.props)
         if warm == "mlp":
             lat.set_mlp_weights(P)
@@ -429,7 +435,7 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
             iters += s["last_ibm_iters"]
             capped += int(s["last_residual"] > tol)
         out[name] = {"ms_per_step": t_ms / steps, "iters_per_step": iters / steps,
-                     "capped_steps": capped}
+                     "capped_steps": capped, "solver": solver}
         lat.close()
     return out
 

@@ -164,6 +164,24 @@ int lbm_set_body_force(lbm_t *h, double gx, double gy, double gz);
  * LBM_ENONFINITE (stats on and a NaN/Inf sum). */
 int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter);
 
+/* The iteration that solves the fixed point of Sec. 3 in lbm_step.
+ * LBM_SOLVER_MDF (default): the multi-direct-forcing loop of the paper,
+ * du += s g_n, G_{n+1} = G_n + S[s g_n].  LBM_SOLVER_CG: conjugate gradients
+ * on the same fixed point written on the lattice, B G = c with
+ * B = S diag(s) I and c = S[s (u_k - I[U0])] (the paper's loop is
+ * Richardson's iteration with unit step on this system, and eps is the norm
+ * of its residual); B is symmetric positive semi-definite and c in its range,
+ * so CG converges where the point-space system is singular.  Not in the
+ * paper (a Krylov replacement for the loop).  Both reach the same force; an
+ * iteration of either is one gather of the brick pass and one interpolation,
+ * with the same eps, stop rule, warm starts and outputs (du; u_interp of
+ * the last iteration's iterate).  Not part of the saved state.  Returns
+ * LBM_OK or LBM_EINVAL (NULL h, unknown solver). */
+#define LBM_SOLVER_MDF 0
+#define LBM_SOLVER_CG 1
+int ibm_set_solver(lbm_t *h, int solver);
+int ibm_get_solver(const lbm_t *h);   /* -1 for NULL h */
+
 /* Current step counter t (completed steps); lbm_set_time overrides it. */
 int64_t lbm_time(const lbm_t *h);
 int lbm_set_time(lbm_t *h, int64_t t);

@@ -94,6 +94,8 @@ _SIGS = {
     "lbm_read_residuals": (_i, [_p, _p, _i]),
     "lbm_set_graph": (_i, [_p, _i]),
     "lbm_set_overlap": (_i, [_p, _i]),
+    "ibm_set_solver": (_i, [_p, _i]),
+    "ibm_get_solver": (_i, [_p]),
     "ibm_update_points": (_i, [_p, _i64, _p, _p]),
     "lbm_get_launch_shape": (_i, [_p, _p]),
     "lbm_set_launch_shape": (_i, [_p, _p]),
@@ -192,7 +194,7 @@ class Lattice:
     """Owns one lbm_t handle."""
 
     def __init__(self, shape, tau, storage="f32", delta="cosine", warm="zero",
-                 ibm_tol=1e-4, ibm_max_iter=500, stats=True, stream=None):
+                 ibm_tol=1e-4, ibm_max_iter=500, stats=True, stream=None, solver="mdf"):
         L = load()
         nz, ny, nx = shape
         o = LbmOpts()
@@ -207,6 +209,8 @@ class Lattice:
         self.np = 0
         if stream is not None:
             self.set_stream(stream)
+        if solver != "mdf":
+            self.set_solver(solver)
 
     def close(self):
         if getattr(self, "h", None):
@@ -365,8 +369,18 @@ class Lattice:
 
     def set_overlap(self, on=True):
         """Collide the cells outside the active bricks while the IBM stages
-        run (the default), or every cell after the IBM loop."""
+        run, or (the default) every cell after the IBM loop."""
         self._c(load().lbm_set_overlap(self.h, int(on)))
+
+    SOLVERS = {"mdf": 0, "cg": 1}
+
+    def set_solver(self, solver):
+        """The fixed point's iteration: "mdf" (the paper's loop, default) or
+        "cg" (conjugate gradients on the same fixed point)."""
+        self._c(load().ibm_set_solver(self.h, self.SOLVERS[solver]))
+
+    def solver(self):
+        return {v: k for k, v in self.SOLVERS.items()}[load().ibm_get_solver(self.h)]
 
     def launch_shape(self):
         s = LaunchShape()

@@ -71,8 +71,11 @@ struct lbm {
   PairMap pm{};
   float *U0s = nullptr, *Gs = nullptr, *res = nullptr;
   float4 *du = nullptr, *uint = nullptr;
+  float4 *cg = nullptr;       // [5][np] conjugate-gradient point vectors
+  double *cg_part = nullptr;  // [ceil(np / 256)] block sums of delta
   double *xpos = nullptr;
   bool have_du = false;
+  int solver = LBM_SOLVER_MDF;  // the fixed point's iteration
   double gbody[3] = {0, 0, 0};
   int64_t t = 0;
 
@@ -236,6 +239,8 @@ void free_points(lbm_t *h) {
   dfree(h->pp.ut);
   dfree(h->du);
   dfree(h->uint);
+  dfree(h->cg);
+  dfree(h->cg_part);
   dfree(h->xpos);
   dfree(h->m.slot_brick);
   dfree(h->m.order);
@@ -465,6 +470,8 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->pp.ut, n));
     CK(h, dalloc(&h->du, n));
     CK(h, dalloc(&h->uint, n));
+    CK(h, dalloc(&h->cg, 5 * n));
+    CK(h, dalloc(&h->cg_part, (n + 255) / 256));
     CK(h, dalloc(&h->xpos, 3 * n));
     CK(h, dalloc(&h->m.slot_brick, ms));
     CK(h, dalloc(&h->m.order, (size_t)ORDER_BUCKETS * ms));
@@ -600,6 +607,8 @@ static DomainDesc host_desc(const lbm_t *h) {
   d.res = h->res;
   d.du = h->du;
   d.uint = h->uint;
+  d.cg = h->cg;
+  d.cg_part = h->cg_part;
   d.xpos = h->xpos;
   d.partial = h->partial;
   d.sums = h->sums;
@@ -648,6 +657,7 @@ struct StepCtx {
   BatchDims dims;
   int storage, stats, cur;
   int warm_mode;
+  int solver;  // LBM_SOLVER_*
   bool have_du, features;
   cudaStream_t st, sti;
   bool split;
@@ -711,8 +721,45 @@ static int enqueue_prefix(StepCtx &c, bool *warm_out) {
   return LBM_OK;
 }
 
+// Conjugate gradients on the lattice form of the fixed point, n_iter
+// iterations (or, tol_mode, until the device-side stop): r_0 from the shares
+// of brick_init, then per iteration the gather of S[v] with its pair shares,
+// the dot products and the updates; G = S[du] after the last.
+static int enqueue_cg_start(StepCtx &c, bool warm, cudaStream_t s) {
+  lbm_t *h = c.acct;
+  StageTimer T(h, ST_UPDATE, s);
+  CK(h, launch_cg_start(c.D, c.dims, warm, s));
+  return LBM_OK;
+}
+
+static int enqueue_cg_iteration(StepCtx &c, int it, int tol_mode, cudaStream_t s) {
+  lbm_t *h = c.acct;
+  {
+    StageTimer T(h, ST_SPREAD, s);
+    CK(h, launch_cg_brick(c.D, c.dims, tol_mode, s));
+  }
+  {
+    StageTimer T(h, ST_UPDATE, s, 2);
+    CK(h, launch_cg_dot(c.D, c.dims, it, h->tol, h->max_iter, tol_mode, s));
+    CK(h, launch_cg_update(c.D, c.dims, it, tol_mode, s));
+  }
+  return LBM_OK;
+}
+
+static int enqueue_final_spread(StepCtx &c, cudaStream_t s) {
+  lbm_t *h = c.acct;
+  StageTimer T(h, ST_SPREAD, s);
+  CK(h, launch_brick_spread(c.D, c.dims, 0, 0, s));
+  return LBM_OK;
+}
+
 static int enqueue_fixed_loop(StepCtx &c, int n_iter, bool warm) {
   lbm_t *h = c.acct;
+  if (c.solver == LBM_SOLVER_CG) {
+    int r = enqueue_cg_start(c, warm, c.sti);
+    for (int it = 0; r == LBM_OK && it < n_iter; it++) r = enqueue_cg_iteration(c, it, 0, c.sti);
+    return r ? r : enqueue_final_spread(c, c.sti);
+  }
   for (int it = 0; it < n_iter; it++) {
     {
       StageTimer T(h, ST_UPDATE, c.sti);
@@ -786,6 +833,11 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     CK(h, launch_ibm_den(c.D, c.dims, 1, st));
     if (warm) CK(h, launch_brick_init(c.D, c.dims, 1, st));
   }
+  const bool cg = c.solver == LBM_SOLVER_CG;
+  if (cg) {
+    int r = enqueue_cg_start(c, warm, st);
+    if (r) return r;
+  }
   int it = 0;
   // chunks of half the iterations the previous step still had to go at this
   // point (at least kCheckChunk): few reads of the stop flag, and few
@@ -795,6 +847,11 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     const int chunk = std::min(left > 0 ? std::max(kCheckChunk, left / 2) : kCheckChunk,
                                h->max_iter - it);
     for (int j = 0; j < chunk; j++, it++) {
+      if (cg) {
+        int r = enqueue_cg_iteration(c, it, 1, st);
+        if (r) return r;
+        continue;
+      }
       {
         StageTimer T(h, ST_UPDATE, st);
         CK(h, launch_point_update(c.D, c.dims, it == 0, warm, 1, st));
@@ -810,7 +867,29 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     }
     CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
+    if (!h->state_host->done) continue;
+    // CG: confirm the stop on the true residual (the recursion drifts from
+    // it by amplified FP32 rounding): replace r by u_k - I[U0 + S[du]] and run
+    // one more iteration, whose check then decides; if it fails, iterate on
+    it = h->state_host->iters;
+    if (!cg || h->state_host->capped || it >= h->max_iter) break;
+    {
+      StageTimer T(h, ST_SPREAD, st);
+      CK(h, launch_brick_spread(c.D, c.dims, 1, 0, st));
+    }
+    {
+      StageTimer T(h, ST_UPDATE, st);
+      CK(h, launch_cg_replace(c.D, c.dims, st));
+    }
+    int r = enqueue_cg_iteration(c, it++, 1, st);
+    if (r) return r;
+    CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
     if (h->state_host->done) break;
+  }
+  if (cg) {
+    int r = enqueue_final_spread(c, st);
+    if (r) return r;
   }
   h->last_iters = h->state_host->iters;
   h->tol_hint = h->last_iters;
@@ -832,6 +911,7 @@ static StepCtx ctx_of(lbm_t *h, cudaStream_t st) {
   c.stats = h->stats_on;
   c.cur = h->cur;
   c.warm_mode = h->warm;
+  c.solver = h->solver;
   c.have_du = h->have_du;
   c.features = h->features_on;
   c.st = st;
@@ -1032,6 +1112,20 @@ int lbm_set_overlap(lbm_t *h, int on) {
   return LBM_OK;
 }
 
+int ibm_set_solver(lbm_t *h, int solver) {
+  if (!h) return LBM_EINVAL;
+  if (solver != LBM_SOLVER_MDF && solver != LBM_SOLVER_CG)
+    return fail(h, LBM_EINVAL, "unknown solver %d", solver);
+  if (h->solver != solver) {
+    if (h->st) cudaStreamSynchronize(h->st);
+    h->solver = solver;
+    h->version++;  // a new capture
+  }
+  return LBM_OK;
+}
+
+int ibm_get_solver(const lbm_t *h) { return h ? h->solver : -1; }
+
 // ---- batches ----------------------------------------------------------------------
 
 struct lbm_batch {
@@ -1105,9 +1199,10 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
   // uniform host-side decisions
   for (lbm_t *h : b->hs) {
     if (h->stats_on != h0->stats_on || h->warm != h0->warm ||
-        h->features_on != h0->features_on || h->cur != h0->cur || h->st != h0->st)
-      return fail(h0, LBM_EINVAL, "batch handles differ in stats, warm start, features, stream "
-                                  "or lattice parity");
+        h->features_on != h0->features_on || h->cur != h0->cur || h->st != h0->st ||
+        h->solver != h0->solver)
+      return fail(h0, LBM_EINVAL, "batch handles differ in stats, warm start, features, stream, "
+                                  "solver or lattice parity");
     if ((h->np > 0 && h->have_du) != (h0->np > 0 && h0->have_du) && h->np > 0 && h0->np > 0)
       return fail(h0, LBM_EINVAL, "batch handles differ in warm-start history");
     if (h->nb > 0 && h->max_body >= h->nb)
@@ -1149,6 +1244,7 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
   c.storage = h0->storage;
   c.stats = h0->stats_on;
   c.warm_mode = h0->warm;
+  c.solver = h0->solver;
   c.have_du = have_du;
   c.features = h0->features_on;
   int s = 0;

@@ -1189,6 +1189,234 @@ __global__ void __launch_bounds__(512)
   uint[k] = make_float4(ux, uy, uz, 0.f);
 }
 
+// ---- conjugate gradients on the lattice form of the fixed point -----------
+//
+// The loop above is Richardson's iteration with unit step on B G = c, with
+// B = S diag(s) I (symmetric positive semi-definite: S is the adjoint of I)
+// and c = S[s (u_k - I[U0])]; its residual c - B G = S[s g] is the one eps
+// measures.  These kernels run conjugate gradients on the same system, in
+// the single-reduction form of Chronopoulos and Gear: with R_n the residual,
+// W_n = B R_n, rho_n = R_n . R_n and delta_n = W_n . R_n,
+//   beta_n  = rho_n / rho_{n-1},   alpha_n = rho_n / (delta_n - beta_n rho_n / alpha_{n-1})
+//   P_n = R_n + beta_n P_{n-1},   B P_n = W_n + beta_n B P_{n-1}
+//   G_{n+1} = G_n + alpha_n P_n,  R_{n+1} = R_n - alpha_n B P_n.
+// Every lattice vector is a spread of point vectors (R = S[v] with v = s r and
+// r the point residual, P = S[p], G = S[du]; B R = S[s a] with a = I[R], and
+// B P = S[s y] with y = I[P]), so only point vectors are carried:
+//   p = v + beta p,  y = a + beta y,  du += alpha p,  r -= alpha y,  v = s r,
+// and G = S[du] is spread once after the last iteration.  rho_n = |S[v_n]|^2
+// is summed per brick by the pass that gathers S[v_n] (and leaves the pair
+// shares of I[R_n]); delta_n = sum_k s(k) |a_n(k)|^2 per block of the point
+// pass that sums those shares, whose last block turns both into alpha_n and
+// beta_n.  Point arrays d.cg: [0] r, [1] v, [2] p, [3] y, [4] a (np each).
+
+constexpr int CG_BLOCK = 256;  // threads of the CG point kernels (fixed: the
+                               // block sums of delta do not depend on the
+                               // launch shape)
+
+__device__ __forceinline__ float4 shares_sum(const PairMap &pm, int64_t k) {
+  const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
+  const int4 a = pk[0], b = pk[1];
+  const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    if (idx[j] >= 0) {
+      const float4 v = pm.part[idx[j]];
+      ux += v.x;
+      uy += v.y;
+      uz += v.z;
+    }
+  }
+  return make_float4(ux, uy, uz, 0.f);
+}
+
+// r_0 = u_k - I[U0 + G_0] from the shares brick_init left, v_0 = s r_0,
+// p = y = 0 (beta_0 = 0), du = 0 without a warm start.
+__global__ void __launch_bounds__(CG_BLOCK) cg_start_kernel(const DomainDesc *__restrict__ D,
+                                                            int warm) {
+  pdl_wait();
+  const DomainDesc &d = D[blockIdx.y];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.np) return;
+  const int64_t np = d.np;
+  float4 *__restrict__ cg = d.cg;
+  const float4 u = shares_sum(d.pm, k);
+  const float4 ut = d.pp.ut[k];
+  const float4 r = make_float4(ut.x - u.x, ut.y - u.y, ut.z - u.z, 0.f);
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  cg[k] = r;
+  cg[np + k] = make_float4(ut.w * r.x, ut.w * r.y, ut.w * r.z, 0.f);
+  cg[2 * np + k] = z;
+  cg[3 * np + k] = z;
+  if (!warm) d.du[k] = z;
+}
+
+// Residual replacement (tolerance mode, after the recursion reported
+// convergence): r = u_k - I[U0 + S[du]] from the shares of the gather-and-
+// interpolate pass, v = s r; the search directions p, y are kept.  The
+// recursively updated r drifts from the true residual by FP32 rounding that
+// CG amplifies, so the stop is confirmed by one more iteration on the true
+// one.  Clears the stop flag for that iteration.
+__global__ void __launch_bounds__(CG_BLOCK) cg_replace_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  const DomainDesc &d = D[blockIdx.y];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) d.state->done = 0;
+  if (k >= d.np) return;
+  const float4 u = shares_sum(d.pm, k);
+  const float4 ut = d.pp.ut[k];
+  const float4 r = make_float4(ut.x - u.x, ut.y - u.y, ut.z - u.z, 0.f);
+  d.cg[k] = r;
+  d.cg[d.np + k] = make_float4(ut.w * r.x, ut.w * r.y, ut.w * r.z, 0.f);
+}
+
+// R_n = S[v_n] on each active brick, |R_n|^2 into res[slot], and the pair
+// shares of I[R_n].  One warp per brick.
+template <bool WL>
+__global__ void __launch_bounds__(32, 32)
+    cg_brick_kernel(const DomainDesc *__restrict__ D, int tol_mode, const int *__restrict__ off,
+                    int nd) {
+  pdl_wait();
+  __shared__ BrickSmem sm;
+  const int t = threadIdx.x, r = t & 15;
+  for_each_slot<WL, true>(D, off, nd, blockIdx.x, gridDim.x, [&](const DomainDesc &d, int s) {
+    if (tol_mode && d.state->done) return;
+    const PairMap &pm = d.pm;
+    const int p0 = pm.start[s], cnt = pm.count[s];
+    float4 R[3];
+    brick_gather(sm, pm, p0, cnt, d.cg + d.np, R);
+    float e = 0.f;
+    if (t < 16) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        e += ((R[c].x * R[c].x + R[c].y * R[c].y) + R[c].z * R[c].z) + R[c].w * R[c].w;
+        sm.sF[c][r] = R[c];
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (t == 0) d.res[s] = e;
+    __syncwarp();
+    brick_interp(sm, pm, p0, cnt, cnt <= SP_CHUNK);
+    __syncwarp();
+  });
+}
+
+// Sum over the block's threads of v (a fixed pairwise tree); every thread
+// calls it, thread 0 gets the result.
+__device__ __forceinline__ double block_sum256(double v, double *red) {
+  const int t = threadIdx.x;
+  __syncthreads();  // (red may still be read by a previous call)
+  red[t] = v;
+#pragma unroll
+  for (int o = CG_BLOCK / 2; o > 0; o >>= 1) {
+    __syncthreads();
+    if (t < o) red[t] += red[t + o];
+  }
+  __syncthreads();
+  return red[0];
+}
+
+// a_n = I[R_n] per point (kept for the update), delta_n = sum s |a_n|^2; the
+// last block of each domain adds the block sums of delta_n and the brick sums
+// of rho_n (in index order) and sets alpha_n, beta_n; in tolerance mode it
+// also records eps_n = sqrt(rho_n) / den and stops at the first eps_n <= tol
+// or at max_iter iterations (the update of that iteration still runs).
+__global__ void __launch_bounds__(CG_BLOCK)
+    cg_dot_kernel(const DomainDesc *__restrict__ D, int it, double tol, int max_iter,
+                  int tol_mode) {
+  pdl_wait();
+  __shared__ double red[CG_BLOCK];
+  __shared__ bool last;
+  const DomainDesc &d = D[blockIdx.y];
+  IbmState *st = d.state;
+  const int nbk = (d.np + CG_BLOCK - 1) / CG_BLOCK;
+  if ((int)blockIdx.x >= nbk) return;
+  if (tol_mode && st->done) return;
+  const int t = threadIdx.x;
+  const int64_t k = (int64_t)blockIdx.x * CG_BLOCK + t;
+  double e = 0.0;
+  if (k < d.np) {
+    const float4 a = shares_sum(d.pm, k);
+    d.cg[4 * (int64_t)d.np + k] = a;
+    e = (double)(d.pp.ut[k].w * ((a.x * a.x + a.y * a.y) + a.z * a.z));
+  }
+  const double bs = block_sum256(e, red);
+  if (t == 0) {
+    d.cg_part[blockIdx.x] = bs;
+    __threadfence();
+    last = atomicAdd(&st->cg_ticket, 1u) == (unsigned)nbk - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a1 = 0.0, a2 = 0.0;
+  for (int j = t; j < nbk; j += CG_BLOCK) a1 += __ldcg(d.cg_part + j);
+  const int nslots = active_slots(d.m);
+  for (int j = t; j < nslots; j += CG_BLOCK) a2 += (double)__ldcg(d.res + j);
+  const double delta = block_sum256(a1, red);
+  const double rho = block_sum256(a2, red);
+  if (t != 0) return;
+  double beta = (it > 0 && st->cg_rho > 0.0) ? rho / st->cg_rho : 0.0;
+  double den = delta;
+  if (beta > 0.0 && st->cg_alpha > 0.0) den = delta - beta * rho / st->cg_alpha;
+  if (!(den > 0.0)) {  // rounding lost the conjugacy: restart from R_n
+    beta = 0.0;
+    den = delta;
+  }
+  st->cg_alpha = (rho > 0.0 && den > 0.0) ? rho / den : 0.0;
+  st->cg_beta = beta;
+  st->cg_rho = rho;
+  st->cg_ticket = 0u;
+  if (tol_mode) {
+    const double eps = sqrt(rho / st->den2);
+    if (it < IbmState::HIST) st->eps[it] = eps;
+    st->last_eps = eps;
+    if (eps <= tol || it + 1 >= max_iter) {
+      st->done = 1;
+      st->iters = it + 1;
+      st->capped = eps > tol;
+    }
+  }
+}
+
+// The updates of iteration n (alpha_n, beta_n from cg_dot_kernel), and
+// u_interp = u_k - r_n, the velocity interpolated from the iterate.
+__global__ void __launch_bounds__(CG_BLOCK) cg_update_kernel(const DomainDesc *__restrict__ D,
+                                                             int it, int tol_mode) {
+  pdl_wait();
+  const DomainDesc &d = D[blockIdx.y];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.np) return;
+  const IbmState *st = d.state;
+  if (tol_mode && st->done && st->iters <= it) return;
+  const int64_t np = d.np;
+  float4 *__restrict__ cg = d.cg;
+  const float alpha = (float)st->cg_alpha, beta = (float)st->cg_beta;
+  float4 r = cg[k], p = cg[2 * np + k], y = cg[3 * np + k];
+  const float4 a = cg[4 * np + k], ut = d.pp.ut[k];
+  float4 dk = d.du[k];
+  d.uint[k] = make_float4(ut.x - r.x, ut.y - r.y, ut.z - r.z, 0.f);
+  p.x = fmaf(beta, p.x, ut.w * r.x);
+  p.y = fmaf(beta, p.y, ut.w * r.y);
+  p.z = fmaf(beta, p.z, ut.w * r.z);
+  y.x = fmaf(beta, y.x, a.x);
+  y.y = fmaf(beta, y.y, a.y);
+  y.z = fmaf(beta, y.z, a.z);
+  dk.x = fmaf(alpha, p.x, dk.x);
+  dk.y = fmaf(alpha, p.y, dk.y);
+  dk.z = fmaf(alpha, p.z, dk.z);
+  r.x = fmaf(-alpha, y.x, r.x);
+  r.y = fmaf(-alpha, y.y, r.y);
+  r.z = fmaf(-alpha, y.z, r.z);
+  cg[k] = r;
+  cg[np + k] = make_float4(ut.w * r.x, ut.w * r.y, ut.w * r.z, 0.f);
+  cg[2 * np + k] = p;
+  cg[3 * np + k] = y;
+  d.du[k] = dk;
+}
+
 // s(k) (u_k - u(k)) with u(k) the sum of the point's pair shares: the
 // first increment from a zero start, for the fallback residual denominator.
 __global__ void __launch_bounds__(512)
@@ -1472,6 +1700,41 @@ cudaError_t launch_point_update(const DomainDesc *D, const BatchDims &dims, int 
   const int pb = dims.ls.point_block;
   return launch_pdl(point_update_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0, st,
                     D, first, warm, tol_mode);
+}
+
+cudaError_t launch_cg_start(const DomainDesc *D, const BatchDims &dims, int warm,
+                            cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  return launch_pdl(cg_start_kernel, dim3(nblk(dims.max_points, CG_BLOCK), dims.nd),
+                    dim3(CG_BLOCK), 0, st, D, warm);
+}
+
+cudaError_t launch_cg_replace(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  return launch_pdl(cg_replace_kernel, dim3(nblk(dims.max_points, CG_BLOCK), dims.nd),
+                    dim3(CG_BLOCK), 0, st, D);
+}
+
+cudaError_t launch_cg_brick(const DomainDesc *D, const BatchDims &dims, int tol_mode,
+                            cudaStream_t st) {
+  return dims.work_off ? launch_pdl(cg_brick_kernel<true>, brick_grid(dims), dim3(32), 0, st, D,
+                                    tol_mode, dims.work_off, dims.nd)
+                       : launch_pdl(cg_brick_kernel<false>, brick_grid(dims), dim3(32), 0, st, D,
+                                    tol_mode, dims.work_off, dims.nd);
+}
+
+cudaError_t launch_cg_dot(const DomainDesc *D, const BatchDims &dims, int it, double tol,
+                          int max_iter, int tol_mode, cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  return launch_pdl(cg_dot_kernel, dim3(nblk(dims.max_points, CG_BLOCK), dims.nd),
+                    dim3(CG_BLOCK), 0, st, D, it, tol, max_iter, tol_mode);
+}
+
+cudaError_t launch_cg_update(const DomainDesc *D, const BatchDims &dims, int it, int tol_mode,
+                             cudaStream_t st) {
+  if (dims.max_points <= 0) return cudaSuccess;
+  return launch_pdl(cg_update_kernel, dim3(nblk(dims.max_points, CG_BLOCK), dims.nd),
+                    dim3(CG_BLOCK), 0, st, D, it, tol_mode);
 }
 
 cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,

@@ -1,0 +1,195 @@
+"""Conjugate gradients on the lattice form B G = c of the fixed point (B =
+S diag(s) I, c = S[s (u_k - I[U0])]; not in the paper) on the GPU against the
+FP64 oracle's CG: fields after fixed iteration counts, iteration counts and
+residual histories in tolerance mode, and a force at least as close to the
+solution as the paper's loop's, in far fewer iterations."""
+import numpy as np
+import pytest
+
+from paper_1904_02108_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _lattice(gpu_lib, torch, w, **kw):
+    lat = gpu_lib.Lattice(w.shape, w.tau, stream=torch.cuda.current_stream(), solver="cg", **kw)
+    lat.set_propellers(w.props)
+    return lat
+
+
+@pytest.mark.parametrize("warm", ["zero", "previous"])
+def test_cg_fixed_iterations_match_oracle(gpu_lib, torch_cuda, orc, warm):
+    """32^3, one propeller, 5 CG iterations per step, 20 steps."""
+    w = W.single_propeller()
+    lat = _lattice(gpu_lib, torch_cuda, w, warm=warm)
+    assert lat.solver() == "cg"
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=5, warm=warm, solver="cg")
+    for chunk in (1, 9, 10):
+        lat.step(chunk, 5)
+        sim.step(chunk)
+        _, U, G = lat.fields()
+        _, U_o = sim.fields()
+        assert rel_l2(U, U_o) < 1e-5, (sim.t, rel_l2(U, U_o))
+        assert rel_l2(G, sim.G) < 1e-4, (sim.t, rel_l2(G, sim.G))
+        _, _, du = lat.points()
+        assert rel_l2(du, sim.du) < 1e-4
+    assert lat.stats()["last_ibm_iters"] == 5
+    lat.close()
+
+
+def test_cg_dense_array_downscale_from_perturbed_state(gpu_lib, torch_cuda, orc):
+    """64^3 array of 216 small propellers (overlapping supports), perturbed
+    start, 8 steps of 5 CG iterations: several tiles, ragged brick lists."""
+    w = W.dense_array_64()
+    rng = W.SplitMix64(47)
+    rho = 1.0 + 0.01 * W.random_array(rng, w.shape)
+    U = 0.01 * W.random_array(rng, (3,) + w.shape)
+    f0 = orc.init_equilibrium(w.shape, rho, U)
+    lat = _lattice(gpu_lib, torch_cuda, w, warm="previous")
+    lat.set_populations(f0)
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=5, warm="previous",
+                         solver="cg")
+    sim.f = f0.copy()
+    lat.step(8, 5)
+    sim.step(8)
+    _, U, G = lat.fields()
+    _, U_o = sim.fields()
+    assert rel_l2(U, U_o) < 1e-5
+    assert rel_l2(G, sim.G) < 1e-4
+    lat.close()
+
+
+def _true_eps(orc, w, lat, U0, t):
+    """eps of the GPU's final iterate recomputed in FP64 by the oracle from
+    its definition, ||S[s (u_k - I[U0 + S[du]])]|| / ||S[s u_k]||, with the
+    GPU's own U0 (read before the step) and du."""
+    p = w.props.as_dict()
+    x, ut = orc.kinematics(p["xrest"], p["body"], p["centre"], p["omega"], p["phase"], t)
+    s = np.asarray(p["area"], np.float64)[:, None]
+    du = lat.points()[2].astype(np.float64)
+    r = ut - orc.interpolate(U0 + orc.spread(w.shape, x, du), x)
+    return (np.linalg.norm(orc.spread(w.shape, x, s * r))
+            / np.linalg.norm(orc.spread(w.shape, x, s * ut)))
+
+
+@pytest.mark.parametrize("warm,tol,steps", [("zero", 1e-3, 3), ("previous", 1e-4, 4)])
+def test_cg_tolerance_mode_against_oracle(gpu_lib, torch_cuda, orc, warm, tol, steps):
+    """Every step stops once an iterate's residual is <= tol, the recursively
+    updated one confirmed by an iteration on the true one, and the true
+    residual of the result, recomputed by the oracle, is within tol as well.  The first step starts from rest, where
+    the residual history equals the oracle's CG until FP32 rounding, which
+    CG's conjugacy amplifies near the tolerance, takes over; CG in FP32 may
+    then take some more iterations than in FP64."""
+    w = W.single_propeller()
+    lat = _lattice(gpu_lib, torch_cuda, w, warm=warm, ibm_tol=tol, ibm_max_iter=500)
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=0, tol=tol, max_iter=500,
+                         warm=warm, solver="cg")
+    for step in range(steps):
+        U0 = lat.fields()[1].astype(np.float64)
+        assert lat.step(1, 0) == gpu_lib.LBM_OK
+        sim.step(1)
+        eps = lat.residuals()
+        # the stop is confirmed by one more iteration on the true residual
+        first = int(np.argmax(eps <= tol))
+        assert eps[-1] <= tol and first >= 1 and eps[first - 1] > tol
+        assert first + 2 <= len(eps)
+        assert lat.stats()["last_ibm_iters"] == len(eps)
+        assert len(eps) <= 2 * len(sim.eps[-1]) + 5
+        assert _true_eps(orc, w, lat, U0, step) <= 1.5 * tol
+        if step == 0:
+            eo = sim.eps[-1]
+            m = int(np.argmax(eo < 30 * tol))
+            np.testing.assert_allclose(eps[:m], eo[:m], rtol=1e-3)
+    lat.close()
+
+
+def test_cg_is_closer_to_the_solution_in_fewer_iterations(gpu_lib, torch_cuda, orc):
+    """One step from rest, both solvers to eps <= 1e-3: CG stops in under a
+    tenth of the iterations, and its force is at least as close to the
+    solution G* of B G = c (the oracle's CG to 1e-9) in the energy norm of B,
+    ||E||_B^2 = sum_k s(k) |I[E](k)|^2, which CG minimises."""
+    w = W.single_propeller(2)
+    p = w.props.as_dict()
+    x, ut = orc.kinematics(p["xrest"], p["body"], p["centre"], p["omega"], p["phase"], 0)
+    s = np.asarray(p["area"], np.float64)
+    Gs = orc.ibm_cg(np.zeros((3,) + w.shape), x, ut, s, n_iter=0, tol=1e-9, max_iter=20000)[0]
+    err, its = {}, {}
+    for solver in ("mdf", "cg"):
+        lat = gpu_lib.Lattice(w.shape, w.tau, stream=torch_cuda.cuda.current_stream(),
+                              ibm_tol=1e-3, ibm_max_iter=2000, solver=solver)
+        lat.set_propellers(w.props)
+        assert lat.step(1, 0) == gpu_lib.LBM_OK
+        its[solver] = lat.stats()["last_ibm_iters"]
+        E = lat.fields()[2].astype(np.float64) - Gs
+        y = orc.interpolate(E, x)
+        err[solver] = float(np.sqrt((s[:, None] * y * y).sum()))
+        lat.close()
+    assert 10 * its["cg"] < its["mdf"], its
+    assert err["cg"] <= err["mdf"], err
+
+
+def test_cg_graph_batch_and_launch_count(gpu_lib, torch_cuda):
+    """Captured CG steps and a batch of CG lattices give bitwise the eager
+    per-lattice results; a fixed-count step launches start + 3 per iteration
+    + the final spread for the loop."""
+    torch = torch_cuda
+    a = _lattice(gpu_lib, torch, W.single_propeller(3), warm="previous")
+    b = _lattice(gpu_lib, torch, W.single_propeller(3), warm="previous")
+    b.set_graph(True)
+    a.step(9, 5)
+    b.step(9, 5)
+    assert np.array_equal(a.populations(), b.populations())
+    assert np.array_equal(a.points()[2], b.points()[2])
+    assert a.stats()["kernel_launches"] == b.stats()["kernel_launches"] \
+        == 9 * (1 + 3 + 2 + (1 + 3 * 5 + 1) + 1 + 1)
+    w2 = W.Workload("two", (44, 40, 48), 0.7,
+                    W.propellers([(12.0, 20.0, 14.0), (34.0, 20.0, 30.0)], 8.0, 2.0, 0.04,
+                                 [0.3, 1.9]), 5)
+    singles = [_lattice(gpu_lib, torch, w, warm="previous") for w in (W.single_propeller(3), w2)]
+    members = [_lattice(gpu_lib, torch, w, warm="previous") for w in (W.single_propeller(3), w2)]
+    for lat in singles:
+        lat.step(6, 5)
+    batch = gpu_lib.Batch(members)
+    batch.step(6, 5)
+    for s, m in zip(singles, members):
+        assert np.array_equal(s.populations(), m.populations())
+        assert np.array_equal(s.points()[2], m.points()[2])
+    c = _lattice(gpu_lib, torch, W.single_propeller(3))
+    d = _lattice(gpu_lib, torch, W.single_propeller(3))
+    mixed = gpu_lib.Batch([c, d])
+    mixed.step(1, 5)
+    d.set_solver("mdf")
+    with pytest.raises(gpu_lib.LbmError):
+        mixed.step(1, 5)  # solvers differ
+    for x in (batch, mixed):
+        x.close()
+    for lat in [a, b, c, d] + singles + members:
+        lat.close()
+
+
+@pytest.mark.parametrize("n_iter", [5, 0])
+def test_cg_exact_solution_stays_at_rest(gpu_lib, torch_cuda, n_iter):
+    """Static points with zero surface velocity in a fluid at rest: the
+    residual is zero from the start, alpha = 0 (no division by zero), and the
+    lattice stays bitwise at rest."""
+    xs = np.array([(3.3 + 1.7 * i, 8.2, 4.1 + 0.9 * k) for i in range(5) for k in range(6)])
+    lat = gpu_lib.Lattice((16, 16, 16), 0.8, stream=torch_cuda.cuda.current_stream(),
+                          solver="cg", ibm_tol=1e-6)
+    lat.set_points(xs, None, np.full(len(xs), 0.5))
+    assert lat.step(4, n_iter) == gpu_lib.LBM_OK
+    assert not np.any(lat.deviations())
+    _, u, du = lat.points()
+    assert not np.any(du) and not np.any(u)
+    lat.close()
