@@ -42,6 +42,7 @@ enum Stage {
 // the fewest iterations launched between two host checks of the
 // tolerance-mode stop flag
 constexpr int kCheckChunk = 16;
+constexpr int kCgChunk = 4;
 
 thread_local std::string g_create_error;
 
@@ -72,7 +73,7 @@ struct lbm {
   float *U0s = nullptr, *Gs = nullptr, *res = nullptr;
   float4 *du = nullptr, *uint = nullptr;
   float4 *cg = nullptr;       // [5][np] conjugate-gradient point vectors
-  double *cg_part = nullptr;  // [ceil(np / 256)] block sums of delta
+  double *cg_part = nullptr;  // [ceil(np / 256)][2] block sums of delta, rho
   double *xpos = nullptr;
   bool have_du = false;
   int solver = LBM_SOLVER_MDF;  // the fixed point's iteration
@@ -471,7 +472,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->du, n));
     CK(h, dalloc(&h->uint, n));
     CK(h, dalloc(&h->cg, 5 * n));
-    CK(h, dalloc(&h->cg_part, (n + 255) / 256));
+    CK(h, dalloc(&h->cg_part, 2 * ((n + 255) / 256)));
     CK(h, dalloc(&h->xpos, 3 * n));
     CK(h, dalloc(&h->m.slot_brick, ms));
     CK(h, dalloc(&h->m.order, (size_t)ORDER_BUCKETS * ms));
@@ -740,8 +741,8 @@ static int enqueue_cg_iteration(StepCtx &c, int it, int tol_mode, cudaStream_t s
   }
   {
     StageTimer T(h, ST_UPDATE, s, 2);
-    CK(h, launch_cg_dot(c.D, c.dims, it, h->tol, h->max_iter, tol_mode, s));
-    CK(h, launch_cg_update(c.D, c.dims, it, tol_mode, s));
+    CK(h, launch_cg_dot(c.D, c.dims, tol_mode, s));
+    CK(h, launch_cg_update(c.D, c.dims, it, h->tol, h->max_iter, tol_mode, s));
   }
   return LBM_OK;
 }
@@ -842,10 +843,13 @@ static int tolerance_loop(StepCtx &c, bool warm) {
   // chunks of half the iterations the previous step still had to go at this
   // point (at least kCheckChunk): few reads of the stop flag, and few
   // launches past convergence (their kernels return at once, but are not free)
+  // (CG, which converges in a few dozen iterations: chunks of the previous
+  // step's remaining count, then of kCgChunk)
   while (it < h->max_iter) {
     const int left = h->tol_hint - it;
-    const int chunk = std::min(left > 0 ? std::max(kCheckChunk, left / 2) : kCheckChunk,
-                               h->max_iter - it);
+    const int want = cg ? (left > 0 ? left : kCgChunk)
+                        : (left > 0 ? std::max(kCheckChunk, left / 2) : kCheckChunk);
+    const int chunk = std::min(want, h->max_iter - it);
     for (int j = 0; j < chunk; j++, it++) {
       if (cg) {
         int r = enqueue_cg_iteration(c, it, 1, st);

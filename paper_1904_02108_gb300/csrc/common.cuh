@@ -227,10 +227,10 @@ struct IbmState {
   unsigned ticket; // blocks of the residual sum done (reset by the last)
   double den2;     // ||S[s u_k]||^2 (or the fallback)
   double last_eps;
-  // conjugate gradients: rho_{n-1}, alpha_{n-1} of the last iteration and
-  // alpha_n, beta_n of the current one; blocks of the delta sum done
-  double cg_rho, cg_alpha, cg_beta;
-  unsigned cg_ticket;
+  // conjugate gradients: rho_n and alpha_n of the iterations of either
+  // parity (iteration n reads those of n - 1 and stores its own)
+  double cg_rho[2], cg_alpha[2];
+  int cg_stop;     // the iteration at which CG stopped this step, or INT_MAX
   int cg_pad;
   double bsum[RES_BLOCKS];  // block sums of the residual sum
   double eps[HIST];  // eps of every iteration of this step
@@ -269,7 +269,7 @@ struct DomainDesc {
   float *U0s, *Gs, *res;
   float4 *du, *uint;
   float4 *cg;              // [5][np] point vectors of conjugate gradients
-  double *cg_part;         // [ceil(np / 256)] block sums of its dot product
+  double *cg_part;         // [ceil(np / 256)][2] block sums of its dot products
   double *xpos;
   double *partial, *sums;  // collide partials [cblocks][4], FP64 sums [4]
   double *slot_partial;    // [max_slots][4] partials of the active bricks'

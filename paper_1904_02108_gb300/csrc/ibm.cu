@@ -1207,8 +1207,9 @@ __global__ void __launch_bounds__(512)
 // and G = S[du] is spread once after the last iteration.  rho_n = |S[v_n]|^2
 // is summed per brick by the pass that gathers S[v_n] (and leaves the pair
 // shares of I[R_n]); delta_n = sum_k s(k) |a_n(k)|^2 per block of the point
-// pass that sums those shares, whose last block turns both into alpha_n and
-// beta_n.  Point arrays d.cg: [0] r, [1] v, [2] p, [3] y, [4] a (np each).
+// pass that sums those shares (which also adds up slices of the brick sums),
+// and every block of the update pass adds the block sums itself.  Point
+// arrays d.cg: [0] r, [1] v, [2] p, [3] y, [4] a (np each).
 
 constexpr int CG_BLOCK = 256;  // threads of the CG point kernels (fixed: the
                                // block sums of delta do not depend on the
@@ -1238,6 +1239,7 @@ __global__ void __launch_bounds__(CG_BLOCK) cg_start_kernel(const DomainDesc *__
   pdl_wait();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) d.state->cg_stop = INT_MAX;
   if (k >= d.np) return;
   const int64_t np = d.np;
   float4 *__restrict__ cg = d.cg;
@@ -1262,7 +1264,10 @@ __global__ void __launch_bounds__(CG_BLOCK) cg_replace_kernel(const DomainDesc *
   pdl_wait();
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == 0) d.state->done = 0;
+  if (k == 0) {
+    d.state->done = 0;
+    d.state->cg_stop = INT_MAX;
+  }
   if (k >= d.np) return;
   const float4 u = shares_sum(d.pm, k);
   const float4 ut = d.pp.ut[k];
@@ -1318,82 +1323,102 @@ __device__ __forceinline__ double block_sum256(double v, double *red) {
   return red[0];
 }
 
-// a_n = I[R_n] per point (kept for the update), delta_n = sum s |a_n|^2; the
-// last block of each domain adds the block sums of delta_n and the brick sums
-// of rho_n (in index order) and sets alpha_n, beta_n; in tolerance mode it
-// also records eps_n = sqrt(rho_n) / den and stops at the first eps_n <= tol
-// or at max_iter iterations (the update of that iteration still runs).
-__global__ void __launch_bounds__(CG_BLOCK)
-    cg_dot_kernel(const DomainDesc *__restrict__ D, int it, double tol, int max_iter,
-                  int tol_mode) {
+// a_n = I[R_n] per point (kept for the update); block b's sums of
+// delta_n = sum_k s(k) |a_n(k)|^2 over its points and of rho_n over the
+// bricks [b m, (b + 1) m) of res (m = ceil(nslots / blocks)), each in a fixed
+// tree, into cg_part[b].
+__global__ void __launch_bounds__(CG_BLOCK) cg_dot_kernel(const DomainDesc *__restrict__ D,
+                                                          int tol_mode) {
   pdl_wait();
   __shared__ double red[CG_BLOCK];
-  __shared__ bool last;
   const DomainDesc &d = D[blockIdx.y];
-  IbmState *st = d.state;
   const int nbk = (d.np + CG_BLOCK - 1) / CG_BLOCK;
   if ((int)blockIdx.x >= nbk) return;
-  if (tol_mode && st->done) return;
-  const int t = threadIdx.x;
-  const int64_t k = (int64_t)blockIdx.x * CG_BLOCK + t;
+  if (tol_mode && d.state->done) return;
+  const int t = threadIdx.x, b = blockIdx.x;
+  const int64_t k = (int64_t)b * CG_BLOCK + t;
   double e = 0.0;
   if (k < d.np) {
     const float4 a = shares_sum(d.pm, k);
     d.cg[4 * (int64_t)d.np + k] = a;
     e = (double)(d.pp.ut[k].w * ((a.x * a.x + a.y * a.y) + a.z * a.z));
   }
-  const double bs = block_sum256(e, red);
-  if (t == 0) {
-    d.cg_part[blockIdx.x] = bs;
-    __threadfence();
-    last = atomicAdd(&st->cg_ticket, 1u) == (unsigned)nbk - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double a1 = 0.0, a2 = 0.0;
-  for (int j = t; j < nbk; j += CG_BLOCK) a1 += __ldcg(d.cg_part + j);
   const int nslots = active_slots(d.m);
-  for (int j = t; j < nslots; j += CG_BLOCK) a2 += (double)__ldcg(d.res + j);
-  const double delta = block_sum256(a1, red);
-  const double rho = block_sum256(a2, red);
-  if (t != 0) return;
-  double beta = (it > 0 && st->cg_rho > 0.0) ? rho / st->cg_rho : 0.0;
-  double den = delta;
-  if (beta > 0.0 && st->cg_alpha > 0.0) den = delta - beta * rho / st->cg_alpha;
-  if (!(den > 0.0)) {  // rounding lost the conjugacy: restart from R_n
-    beta = 0.0;
-    den = delta;
-  }
-  st->cg_alpha = (rho > 0.0 && den > 0.0) ? rho / den : 0.0;
-  st->cg_beta = beta;
-  st->cg_rho = rho;
-  st->cg_ticket = 0u;
-  if (tol_mode) {
-    const double eps = sqrt(rho / st->den2);
-    if (it < IbmState::HIST) st->eps[it] = eps;
-    st->last_eps = eps;
-    if (eps <= tol || it + 1 >= max_iter) {
-      st->done = 1;
-      st->iters = it + 1;
-      st->capped = eps > tol;
-    }
+  const int m = (nslots + nbk - 1) / nbk;
+  double f = 0.0;
+  for (int j = b * m + t; j < min(nslots, (b + 1) * m); j += CG_BLOCK) f += (double)d.res[j];
+  const double bd = block_sum256(e, red);
+  const double br = block_sum256(f, red);
+  if (t == 0) {
+    d.cg_part[2 * b] = bd;
+    d.cg_part[2 * b + 1] = br;
   }
 }
 
-// The updates of iteration n (alpha_n, beta_n from cg_dot_kernel), and
-// u_interp = u_k - r_n, the velocity interpolated from the iterate.
-__global__ void __launch_bounds__(CG_BLOCK) cg_update_kernel(const DomainDesc *__restrict__ D,
-                                                             int it, int tol_mode) {
+// The updates of iteration n, and u_interp = u_k - r_n (the velocity
+// interpolated from the iterate).  Every block adds the block sums of
+// cg_dot_kernel in block order (the same bits in every block) and forms
+// alpha_n and beta_n from them and from rho_{n-1}, alpha_{n-1} (kept by
+// iteration parity, so that no block reads a value this launch replaces);
+// block 0 stores rho_n, alpha_n, and in tolerance mode records
+// eps_n = sqrt(rho_n) / den and stops at the first eps_n <= tol or at
+// max_iter iterations (this iteration's update still runs everywhere).
+__global__ void __launch_bounds__(CG_BLOCK)
+    cg_update_kernel(const DomainDesc *__restrict__ D, int it, double tol, int max_iter,
+                     int tol_mode) {
   pdl_wait();
+  __shared__ double red[CG_BLOCK];
+  __shared__ float coef[2];
   const DomainDesc &d = D[blockIdx.y];
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  IbmState *st = d.state;
+  const int nbk = (d.np + CG_BLOCK - 1) / CG_BLOCK;
+  if ((int)blockIdx.x >= nbk) return;
+  // (cg_stop, one word, is the index of the iteration that converged; block
+  // 0 of this launch may set it to it, which reads the same here as before)
+  if (tol_mode && st->cg_stop < it) return;
+  const int t = threadIdx.x;
+  double a1 = 0.0, a2 = 0.0;
+  for (int j = t; j < nbk; j += CG_BLOCK) {
+    a1 += d.cg_part[2 * j];
+    a2 += d.cg_part[2 * j + 1];
+  }
+  const double delta = block_sum256(a1, red);
+  const double rho = block_sum256(a2, red);
+  if (t == 0) {
+    const int cur = it & 1, prev = cur ^ 1;
+    const double rho_prev = st->cg_rho[prev], alpha_prev = st->cg_alpha[prev];
+    double beta = (it > 0 && rho_prev > 0.0) ? rho / rho_prev : 0.0;
+    double den = delta;
+    if (beta > 0.0 && alpha_prev > 0.0) den = delta - beta * rho / alpha_prev;
+    if (!(den > 0.0)) {  // rounding lost the conjugacy: restart from R_n
+      beta = 0.0;
+      den = delta;
+    }
+    const double alpha = (rho > 0.0 && den > 0.0) ? rho / den : 0.0;
+    coef[0] = (float)alpha;
+    coef[1] = (float)beta;
+    if (blockIdx.x == 0) {
+      st->cg_rho[cur] = rho;
+      st->cg_alpha[cur] = alpha;
+      if (tol_mode) {
+        const double eps = sqrt(rho / st->den2);
+        if (it < IbmState::HIST) st->eps[it] = eps;
+        st->last_eps = eps;
+        if (eps <= tol || it + 1 >= max_iter) {
+          st->cg_stop = it;
+          st->iters = it + 1;
+          st->capped = eps > tol;
+          st->done = 1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t k = (int64_t)blockIdx.x * CG_BLOCK + t;
   if (k >= d.np) return;
-  const IbmState *st = d.state;
-  if (tol_mode && st->done && st->iters <= it) return;
   const int64_t np = d.np;
   float4 *__restrict__ cg = d.cg;
-  const float alpha = (float)st->cg_alpha, beta = (float)st->cg_beta;
+  const float alpha = coef[0], beta = coef[1];
   float4 r = cg[k], p = cg[2 * np + k], y = cg[3 * np + k];
   const float4 a = cg[4 * np + k], ut = d.pp.ut[k];
   float4 dk = d.du[k];
@@ -1723,18 +1748,18 @@ cudaError_t launch_cg_brick(const DomainDesc *D, const BatchDims &dims, int tol_
                                     tol_mode, dims.work_off, dims.nd);
 }
 
-cudaError_t launch_cg_dot(const DomainDesc *D, const BatchDims &dims, int it, double tol,
-                          int max_iter, int tol_mode, cudaStream_t st) {
+cudaError_t launch_cg_dot(const DomainDesc *D, const BatchDims &dims, int tol_mode,
+                          cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
   return launch_pdl(cg_dot_kernel, dim3(nblk(dims.max_points, CG_BLOCK), dims.nd),
-                    dim3(CG_BLOCK), 0, st, D, it, tol, max_iter, tol_mode);
+                    dim3(CG_BLOCK), 0, st, D, tol_mode);
 }
 
-cudaError_t launch_cg_update(const DomainDesc *D, const BatchDims &dims, int it, int tol_mode,
-                             cudaStream_t st) {
+cudaError_t launch_cg_update(const DomainDesc *D, const BatchDims &dims, int it, double tol,
+                             int max_iter, int tol_mode, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
   return launch_pdl(cg_update_kernel, dim3(nblk(dims.max_points, CG_BLOCK), dims.nd),
-                    dim3(CG_BLOCK), 0, st, D, it, tol_mode);
+                    dim3(CG_BLOCK), 0, st, D, it, tol, max_iter, tol_mode);
 }
 
 cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,

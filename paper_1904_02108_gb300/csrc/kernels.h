@@ -94,10 +94,10 @@ cudaError_t launch_cg_start(const DomainDesc *D, const BatchDims &dims, int warm
 cudaError_t launch_cg_brick(const DomainDesc *D, const BatchDims &dims, int tol_mode,
                             cudaStream_t st);
 cudaError_t launch_cg_replace(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
-cudaError_t launch_cg_dot(const DomainDesc *D, const BatchDims &dims, int it, double tol,
-                          int max_iter, int tol_mode, cudaStream_t st);
-cudaError_t launch_cg_update(const DomainDesc *D, const BatchDims &dims, int it, int tol_mode,
-                             cudaStream_t st);
+cudaError_t launch_cg_dot(const DomainDesc *D, const BatchDims &dims, int tol_mode,
+                          cudaStream_t st);
+cudaError_t launch_cg_update(const DomainDesc *D, const BatchDims &dims, int it, double tol,
+                             int max_iter, int tol_mode, cudaStream_t st);
 // uint = s (u_k - u) from the pair shares (fallback denominator)
 cudaError_t launch_point_residual0(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // features of the learned warm start from the pair shares (see ibm.cu)
