@@ -339,6 +339,8 @@ def run_ours(args):
         line["batched"] = bench_batched()
         line["precision"] = bench_precision()
         line["tolerance"] = bench_tolerance()
+        line["paper_sweep"] = bench_paper_sweep()
+        line["delta_kernels"] = bench_delta_kernels()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         wcpu = W.dense_array_256()
         dt, cores = cpu_oracle_run(wcpu, 2)
@@ -437,6 +439,61 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
         out[name] = {"ms_per_step": t_ms / steps, "iters_per_step": iters / steps,
                      "capped_steps": capped, "solver": solver}
         lat.close()
+    return out
+
+
+def bench_paper_sweep(steps=200, warmup=5):
+    """The shape of the paper's own benchmark (Sec. 6): MLUPS of the coupled
+    step (5 iterations) on a 160 x 160 x 320 lattice with 1 to 6 and 18
+    rotating propellers of 3872 points each (the paper's Blender propeller,
+    not available, has 3930), FP32.  The paper's P100 figures quoted in its
+    text are given beside them for context."""
+    import torch
+    from paper_1904_02108_gb300 import binding, workload as W
+    st = torch.cuda.current_stream()
+    out = {"workload": "paper_sweep_160x160x320", "cells": 160 * 160 * 320, "n_iter": 5,
+           "steps": steps, "points_per_propeller": W.paper_sweep(1).props.n_points,
+           "paper_p100_mlups": {"1": 893.0, "6": 650.0, "18": 344.2}, "mlups": {}}
+    for n in (1, 2, 3, 4, 5, 6, 18):
+        w = W.paper_sweep(n)
+        lat = binding.Lattice(w.shape, w.tau, stream=st)
+        lat.set_propellers(w.props)
+        lat.autotune(w.n_iter, 3)
+        lat.step(warmup, w.n_iter)
+        ms = _device_ms(lambda: lat.step(steps, w.n_iter), st)
+        out["mlups"][str(n)] = w.cells * steps / (ms / 1e3) / 1e6
+        lat.close()
+    return out
+
+
+def bench_delta_kernels(steps=100, warmup=5, tol_steps=6, tol=1e-4):
+    """The paper's two weighting functions on the 256^3 array: the cosine
+    kernel (the default) and Peskin's four-point kernel (Sec. 3).  Per kernel:
+    MLUPS at 5 iterations, and the iterations and ms per step to the residual
+    eps <= tol (conjugate gradients from the previous step's force)."""
+    import torch
+    from paper_1904_02108_gb300 import binding, workload as W
+    w = W.dense_array_256()
+    st = torch.cuda.current_stream()
+    out = {"workload": w.name, "steps": steps, "tol": tol, "tol_steps": tol_steps}
+    for delta in ("cosine", "peskin"):
+        lat = binding.Lattice(w.shape, w.tau, delta=delta, stream=st)
+        lat.set_propellers(w.props)
+        lat.autotune(w.n_iter, 3)
+        lat.step(warmup, w.n_iter)
+        ms = _device_ms(lambda: lat.step(steps, w.n_iter), st)
+        lat.close()
+        lat = binding.Lattice(w.shape, w.tau, delta=delta, warm="previous", ibm_tol=tol,
+                              ibm_max_iter=1000, stream=st, solver="cg")
+        lat.set_propellers(w.props)
+        lat.step(3, 0)
+        t_ms, iters = 0.0, 0
+        for _ in range(tol_steps):
+            t_ms += _device_ms(lambda: lat.step(1, 0), st)
+            iters += lat.stats()["last_ibm_iters"]
+        lat.close()
+        out[delta] = {"mlups": w.cells * steps / (ms / 1e3) / 1e6,
+                      "tol_ms_per_step": t_ms / tol_steps, "tol_iters_per_step": iters / tol_steps}
     return out
 
 

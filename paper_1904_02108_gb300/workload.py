@@ -172,6 +172,33 @@ def dense_array_64() -> Workload:
     return Workload("propeller_array_64", (64, 64, 64), 0.6, p, 5, 100)
 
 
+# slots of the paper-shaped sweep: z layers from the middle outward, four
+# (x, y) positions per layer
+_SWEEP_LAYERS = (160.0, 96.0, 224.0, 32.0, 288.0)
+_SWEEP_XY = ((40.0, 40.0), (120.0, 120.0), (120.0, 40.0), (40.0, 120.0))
+
+
+def paper_sweep(n_props: int, seed: int = 1240) -> Workload:
+    """The shape of the paper's benchmark (Sec. 6): a 160 x 160 x 320 lattice
+    with 1 to 6 or 18 rotating propellers of ~3.9k points each (the paper's
+    Blender propeller has 3930; 18 of them 70,740).  Here blades 30 x 15 at the
+    0.7 spacing: 3872 points per propeller (69,696 for 18), tip radius 31;
+    propeller i in slot i (z layers 64 apart from the middle outward, four
+    (x, y) positions 80 apart per layer, no overlapping supports); tip speed
+    U[0.02, 0.06], phase U[0, 2pi); tau 0.6, 5 iterations."""
+    if not 1 <= n_props <= len(_SWEEP_LAYERS) * len(_SWEEP_XY):
+        raise ValueError("1 to 20 propellers")
+    rng = SplitMix64(seed)
+    centres, vt, ph = [], [], []
+    for i in range(n_props):
+        x, y = _SWEEP_XY[i % 4]
+        centres.append((x, y, _SWEEP_LAYERS[i // 4]))
+        vt.append(rng.uniform(0.02, 0.06))
+        ph.append(rng.uniform(0.0, 2.0 * math.pi))
+    p = propellers(centres, 30.0, 15.0, np.asarray(vt), np.asarray(ph))
+    return Workload("paper_sweep_%d" % n_props, (320, 160, 160), 0.6, p, 5, 1000)
+
+
 def batched_domains(n_domains: int = 48, seed: int = 1238, max_tries: int = 1000):
     """Independent periodic cubes of side U{48,64,80,96}, each with 1-8
     propellers of the 32^3 box's geometry at seeded positions; tip speeds

@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_1904_02108_gb300 import workload as W
 
@@ -56,3 +57,26 @@ def test_batched_domains_do_not_overlap():
                 dxy = math.hypot(*(c[i, :2] - c[j, :2]))
                 assert dxy >= 2 * 13 + 4 or abs(c[i, 2] - c[j, 2]) >= 3 + 4
         assert d.props.xrest.min() >= 2 and d.props.xrest.max() <= n - 2
+
+
+def test_paper_sweep_shape_counts_and_separation():
+    """The paper-shaped sweep: 160 x 160 x 320, 3872 points per propeller
+    (4 blades of 44 x 22), 18 propellers 69,696 points; no two propellers'
+    swept discs plus kernel supports meet, and every point stays inside the box."""
+    for n in (1, 2, 3, 4, 5, 6, 18):
+        w = W.paper_sweep(n)
+        p = w.props
+        assert w.shape == (320, 160, 160) and w.cells == 8_192_000
+        assert p.n_bodies == n and p.n_points == n * 4 * 44 * 22
+        c = p.centre
+        for i in range(n):
+            for j in range(i):
+                dxy = math.hypot(*(c[i, :2] - c[j, :2]))
+                assert dxy >= 2 * 31 + 4 or abs(c[i, 2] - c[j, 2]) >= 15 + 4
+        lo, hi = p.xrest.min(axis=0), p.xrest.max(axis=0)
+        assert np.all(lo >= 2) and np.all(hi <= np.array([160, 160, 320]) - 2)
+        vt = p.omega * 31.0
+        assert vt.min() >= 0.02 and vt.max() <= 0.06
+    assert W.paper_sweep(18).props.n_points == 69696
+    with pytest.raises(ValueError):
+        W.paper_sweep(21)
