@@ -1308,19 +1308,21 @@ __global__ void __launch_bounds__(32, 32)
   });
 }
 
-// Sum over the block's threads of v (a fixed pairwise tree); every thread
-// calls it, thread 0 gets the result.
+// Sum over the block's threads of v in a fixed order: a shuffle tree within
+// each warp, then, in every warp alike, a shuffle tree over the warps' sums.
+// Every thread calls it and gets lane 0's result.  red: CG_BLOCK / 32 doubles
+// of shared memory.
 __device__ __forceinline__ double block_sum256(double v, double *red) {
-  const int t = threadIdx.x;
-  __syncthreads();  // (red may still be read by a previous call)
-  red[t] = v;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 #pragma unroll
-  for (int o = CG_BLOCK / 2; o > 0; o >>= 1) {
-    __syncthreads();
-    if (t < o) red[t] += red[t + o];
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();  // (red may still be read by a previous call)
+  if (lane == 0) red[wid] = v;
   __syncthreads();
-  return red[0];
+  double w = lane < CG_BLOCK / 32 ? red[lane] : 0.0;
+#pragma unroll
+  for (int o = CG_BLOCK / 64; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  return __shfl_sync(0xffffffffu, w, 0);  // (lane 0's order: the same in every warp and block)
 }
 
 // a_n = I[R_n] per point (kept for the update); block b's sums of
@@ -1330,7 +1332,7 @@ __device__ __forceinline__ double block_sum256(double v, double *red) {
 __global__ void __launch_bounds__(CG_BLOCK) cg_dot_kernel(const DomainDesc *__restrict__ D,
                                                           int tol_mode) {
   pdl_wait();
-  __shared__ double red[CG_BLOCK];
+  __shared__ double red[CG_BLOCK / 32];
   const DomainDesc &d = D[blockIdx.y];
   const int nbk = (d.np + CG_BLOCK - 1) / CG_BLOCK;
   if ((int)blockIdx.x >= nbk) return;
@@ -1367,7 +1369,7 @@ __global__ void __launch_bounds__(CG_BLOCK)
     cg_update_kernel(const DomainDesc *__restrict__ D, int it, double tol, int max_iter,
                      int tol_mode) {
   pdl_wait();
-  __shared__ double red[CG_BLOCK];
+  __shared__ double red[CG_BLOCK / 32];
   __shared__ float coef[2];
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
