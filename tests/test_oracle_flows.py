@@ -137,3 +137,25 @@ def test_kinematics_rotates_rigidly(orc):
     d = p.xrest - p.centre[0]
     ref = p.centre[0] + np.stack([c * d[:, 0] - s * d[:, 1], s * d[:, 0] + c * d[:, 1], d[:, 2]], 1)
     assert np.abs(x0 - ref).max() < 1e-12
+
+
+def test_poiseuille_with_conjugate_gradients(orc):
+    """The same channel with the fixed point solved by conjugate gradients
+    (5 iterations per step): the bulk is the same parabola (curvature -g/nu,
+    vertex on the mid-plane), and the steady flow equals the paper loop's to
+    within what their different 5-iterate forces leave (the planes' slip)."""
+    ny, n, tau, g = 32, 4, 1.0, 1e-6
+    P = _planes(n, n, 6, ((8.0, 0.0), (24.0, 0.0)))
+    sims = [orc.Simulation((n, ny, n), tau, P, gbody=(g, 0.0, 0.0), solver=s)
+            for s in ("cg", "mdf")]
+    for sim in sims:
+        sim.step(4000)
+    prof, prof_m = (sim.fields()[1][0].mean(axis=(0, 2)) for sim in sims)
+    nu = (tau - 0.5) / 3
+    y = np.arange(ny)
+    sel = (y >= 11) & (y <= 21)
+    c = np.polyfit(y[sel], prof[sel], 2)
+    assert abs(c[0] / (-g / (2 * nu)) - 1) < 1e-6
+    assert abs(-c[1] / (2 * c[0]) - 16.0) < 1e-6
+    assert np.abs(prof[sel] - np.polyval(c, y[sel])).max() < 1e-3 * prof.max()
+    assert np.abs(prof - prof_m).max() < 2e-2 * prof_m.max()
