@@ -174,9 +174,11 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter);
  * so CG converges where the point-space system is singular.  Not in the
  * paper (a Krylov replacement for the loop).  Both reach the same force; an
  * iteration of either is one gather of the brick pass and one interpolation,
- * with the same eps, stop rule, warm starts and outputs (du; u_interp of
- * the last iteration's iterate).  Not part of the saved state.  Returns
- * LBM_OK or LBM_EINVAL (NULL h, unknown solver). */
+ * with the same eps, warm starts and outputs (du; u_interp of the last
+ * iteration's iterate).  In tolerance mode CG confirms each stop on the
+ * true residual u_k - I[U0 + S[du]] (its FP32 recursion drifts from it) and
+ * returns the iterate whose true residual met ibm_tol.  Not part of the
+ * saved state.  Returns LBM_OK or LBM_EINVAL (NULL h, unknown solver). */
 #define LBM_SOLVER_MDF 0
 #define LBM_SOLVER_CG 1
 int ibm_set_solver(lbm_t *h, int solver);

@@ -733,7 +733,10 @@ static int enqueue_cg_start(StepCtx &c, bool warm, cudaStream_t s) {
   return LBM_OK;
 }
 
-static int enqueue_cg_iteration(StepCtx &c, int it, int tol_mode, cudaStream_t s) {
+// confirm: r is the true residual, and an iterate that meets tol is kept
+// without this iteration's update
+static int enqueue_cg_iteration(StepCtx &c, int it, int tol_mode, cudaStream_t s,
+                                bool confirm = false) {
   lbm_t *h = c.acct;
   {
     StageTimer T(h, ST_SPREAD, s);
@@ -742,7 +745,7 @@ static int enqueue_cg_iteration(StepCtx &c, int it, int tol_mode, cudaStream_t s
   {
     StageTimer T(h, ST_UPDATE, s, 2);
     CK(h, launch_cg_dot(c.D, c.dims, tol_mode, s));
-    CK(h, launch_cg_update(c.D, c.dims, it, h->tol, h->max_iter, tol_mode, s));
+    CK(h, launch_cg_update(c.D, c.dims, it, h->tol, h->max_iter, tol_mode, confirm, s));
   }
   return LBM_OK;
 }
@@ -874,7 +877,8 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     if (!h->state_host->done) continue;
     // CG: confirm the stop on the true residual (the recursion drifts from
     // it by amplified FP32 rounding): replace r by u_k - I[U0 + S[du]] and run
-    // one more iteration, whose check then decides; if it fails, iterate on
+    // one more iteration, whose check then decides (and, if it passes, keeps
+    // the checked iterate); if it fails, iterate on
     it = h->state_host->iters;
     if (!cg || h->state_host->capped || it >= h->max_iter) break;
     {
@@ -885,7 +889,7 @@ static int tolerance_loop(StepCtx &c, bool warm) {
       StageTimer T(h, ST_UPDATE, st);
       CK(h, launch_cg_replace(c.D, c.dims, st));
     }
-    int r = enqueue_cg_iteration(c, it++, 1, st);
+    int r = enqueue_cg_iteration(c, it++, 1, st, true);
     if (r) return r;
     CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));

@@ -1310,16 +1310,18 @@ __global__ void __launch_bounds__(32, 32)
 
 // Sum over the block's threads of v in a fixed order: a shuffle tree within
 // each warp, then, in every warp alike, a shuffle tree over the warps' sums.
-// Every thread calls it and gets lane 0's result.  red: CG_BLOCK / 32 doubles
-// of shared memory.
-__device__ __forceinline__ double block_sum256(double v, double *red) {
+// Every thread calls it and gets lane 0's result.  FP32: FP64 arithmetic is
+// slow on this part (~1/64 of the FP32 rate) and sat on the critical path of
+// these short kernels; a 256-term FP32 tree is within ~8 ulp, ample for the
+// CG coefficients.  red: CG_BLOCK / 32 floats of shared memory.
+__device__ __forceinline__ float block_sum256(float v, float *red) {
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();  // (red may still be read by a previous call)
   if (lane == 0) red[wid] = v;
   __syncthreads();
-  double w = lane < CG_BLOCK / 32 ? red[lane] : 0.0;
+  float w = lane < CG_BLOCK / 32 ? red[lane] : 0.f;
 #pragma unroll
   for (int o = CG_BLOCK / 64; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
   return __shfl_sync(0xffffffffu, w, 0);  // (lane 0's order: the same in every warp and block)
@@ -1332,25 +1334,25 @@ __device__ __forceinline__ double block_sum256(double v, double *red) {
 __global__ void __launch_bounds__(CG_BLOCK) cg_dot_kernel(const DomainDesc *__restrict__ D,
                                                           int tol_mode) {
   pdl_wait();
-  __shared__ double red[CG_BLOCK / 32];
+  __shared__ float red[CG_BLOCK / 32];
   const DomainDesc &d = D[blockIdx.y];
   const int nbk = (d.np + CG_BLOCK - 1) / CG_BLOCK;
   if ((int)blockIdx.x >= nbk) return;
   if (tol_mode && d.state->done) return;
   const int t = threadIdx.x, b = blockIdx.x;
   const int64_t k = (int64_t)b * CG_BLOCK + t;
-  double e = 0.0;
+  float e = 0.f;
   if (k < d.np) {
     const float4 a = shares_sum(d.pm, k);
     d.cg[4 * (int64_t)d.np + k] = a;
-    e = (double)(d.pp.ut[k].w * ((a.x * a.x + a.y * a.y) + a.z * a.z));
+    e = d.pp.ut[k].w * ((a.x * a.x + a.y * a.y) + a.z * a.z);
   }
   const int nslots = active_slots(d.m);
   const int m = (nslots + nbk - 1) / nbk;
-  double f = 0.0;
-  for (int j = b * m + t; j < min(nslots, (b + 1) * m); j += CG_BLOCK) f += (double)d.res[j];
-  const double bd = block_sum256(e, red);
-  const double br = block_sum256(f, red);
+  float f = 0.f;
+  for (int j = b * m + t; j < min(nslots, (b + 1) * m); j += CG_BLOCK) f += d.res[j];
+  const float bd = block_sum256(e, red);
+  const float br = block_sum256(f, red);
   if (t == 0) {
     d.cg_part[2 * b] = bd;
     d.cg_part[2 * b + 1] = br;
@@ -1361,16 +1363,18 @@ __global__ void __launch_bounds__(CG_BLOCK) cg_dot_kernel(const DomainDesc *__re
 // interpolated from the iterate).  Every block adds the block sums of
 // cg_dot_kernel in block order (the same bits in every block) and forms
 // alpha_n and beta_n from them and from rho_{n-1}, alpha_{n-1} (kept by
-// iteration parity, so that no block reads a value this launch replaces);
+// iteration parity, so that no block reads a value this launch replaces; in
+// FP32, like the sums);
 // block 0 stores rho_n, alpha_n, and in tolerance mode records
 // eps_n = sqrt(rho_n) / den and stops at the first eps_n <= tol or at
 // max_iter iterations (this iteration's update still runs everywhere).
 __global__ void __launch_bounds__(CG_BLOCK)
     cg_update_kernel(const DomainDesc *__restrict__ D, int it, double tol, int max_iter,
-                     int tol_mode) {
+                     int tol_mode, int confirm) {
   pdl_wait();
-  __shared__ double red[CG_BLOCK / 32];
+  __shared__ float red[CG_BLOCK / 32];
   __shared__ float coef[2];
+  __shared__ bool keep;
   const DomainDesc &d = D[blockIdx.y];
   IbmState *st = d.state;
   const int nbk = (d.np + CG_BLOCK - 1) / CG_BLOCK;
@@ -1379,31 +1383,34 @@ __global__ void __launch_bounds__(CG_BLOCK)
   // 0 of this launch may set it to it, which reads the same here as before)
   if (tol_mode && st->cg_stop < it) return;
   const int t = threadIdx.x;
-  double a1 = 0.0, a2 = 0.0;
+  float a1 = 0.f, a2 = 0.f;
   for (int j = t; j < nbk; j += CG_BLOCK) {
-    a1 += d.cg_part[2 * j];
-    a2 += d.cg_part[2 * j + 1];
+    a1 += (float)d.cg_part[2 * j];  // (FP32 values held in the FP64 array)
+    a2 += (float)d.cg_part[2 * j + 1];
   }
-  const double delta = block_sum256(a1, red);
-  const double rho = block_sum256(a2, red);
+  const float delta = block_sum256(a1, red);
+  const float rho = block_sum256(a2, red);
   if (t == 0) {
     const int cur = it & 1, prev = cur ^ 1;
-    const double rho_prev = st->cg_rho[prev], alpha_prev = st->cg_alpha[prev];
-    double beta = (it > 0 && rho_prev > 0.0) ? rho / rho_prev : 0.0;
-    double den = delta;
-    if (beta > 0.0 && alpha_prev > 0.0) den = delta - beta * rho / alpha_prev;
-    if (!(den > 0.0)) {  // rounding lost the conjugacy: restart from R_n
-      beta = 0.0;
+    const float rho_prev = (float)st->cg_rho[prev], alpha_prev = (float)st->cg_alpha[prev];
+    float beta = (it > 0 && rho_prev > 0.f) ? rho / rho_prev : 0.f;
+    float den = delta;
+    if (beta > 0.f && alpha_prev > 0.f) den = delta - beta * rho / alpha_prev;
+    if (!(den > 0.f)) {  // rounding lost the conjugacy: restart from R_n
+      beta = 0.f;
       den = delta;
     }
-    const double alpha = (rho > 0.0 && den > 0.0) ? rho / den : 0.0;
-    coef[0] = (float)alpha;
-    coef[1] = (float)beta;
+    const float alpha = (rho > 0.f && den > 0.f) ? rho / den : 0.f;
+    coef[0] = alpha;
+    coef[1] = beta;
+    // a confirming iteration (r the true residual) that meets tol keeps its
+    // iterate: the one whose residual was checked
+    keep = confirm && tol_mode && (double)rho <= tol * tol * st->den2;
     if (blockIdx.x == 0) {
       st->cg_rho[cur] = rho;
       st->cg_alpha[cur] = alpha;
       if (tol_mode) {
-        const double eps = sqrt(rho / st->den2);
+        const double eps = sqrt((double)rho / st->den2);
         if (it < IbmState::HIST) st->eps[it] = eps;
         st->last_eps = eps;
         if (eps <= tol || it + 1 >= max_iter) {
@@ -1420,6 +1427,11 @@ __global__ void __launch_bounds__(CG_BLOCK)
   if (k >= d.np) return;
   const int64_t np = d.np;
   float4 *__restrict__ cg = d.cg;
+  if (keep) {
+    const float4 r = cg[k], ut = d.pp.ut[k];
+    d.uint[k] = make_float4(ut.x - r.x, ut.y - r.y, ut.z - r.z, 0.f);
+    return;
+  }
   const float alpha = coef[0], beta = coef[1];
   float4 r = cg[k], p = cg[2 * np + k], y = cg[3 * np + k];
   const float4 a = cg[4 * np + k], ut = d.pp.ut[k];
@@ -1758,10 +1770,10 @@ cudaError_t launch_cg_dot(const DomainDesc *D, const BatchDims &dims, int tol_mo
 }
 
 cudaError_t launch_cg_update(const DomainDesc *D, const BatchDims &dims, int it, double tol,
-                             int max_iter, int tol_mode, cudaStream_t st) {
+                             int max_iter, int tol_mode, int confirm, cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
   return launch_pdl(cg_update_kernel, dim3(nblk(dims.max_points, CG_BLOCK), dims.nd),
-                    dim3(CG_BLOCK), 0, st, D, it, tol, max_iter, tol_mode);
+                    dim3(CG_BLOCK), 0, st, D, it, tol, max_iter, tol_mode, confirm);
 }
 
 cudaError_t launch_brick_norm(const DomainDesc *D, const BatchDims &dims, int which,

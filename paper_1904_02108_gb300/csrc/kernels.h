@@ -97,7 +97,7 @@ cudaError_t launch_cg_replace(const DomainDesc *D, const BatchDims &dims, cudaSt
 cudaError_t launch_cg_dot(const DomainDesc *D, const BatchDims &dims, int tol_mode,
                           cudaStream_t st);
 cudaError_t launch_cg_update(const DomainDesc *D, const BatchDims &dims, int it, double tol,
-                             int max_iter, int tol_mode, cudaStream_t st);
+                             int max_iter, int tol_mode, int confirm, cudaStream_t st);
 // uint = s (u_k - u) from the pair shares (fallback denominator)
 cudaError_t launch_point_residual0(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // features of the learned warm start from the pair shares (see ibm.cu)
