@@ -1080,28 +1080,27 @@ __global__ void __launch_bounds__(32, 32)
   });
 }
 
-// Deterministic FP64 sum of res[0 .. nslots) over RES_BLOCKS blocks of 256
+// Deterministic sum of res[0 .. nslots) over RES_BLOCKS blocks of 256
 // threads: thread j of block b adds res[b*256 + j + k*RES_BLOCKS*256] in k
-// order, the block adds its threads' sums in a fixed pairwise tree, and the
-// last block to finish adds the block sums in block order.  Returns true on
-// that block's thread 0, with the sum in *total.  Every thread of every block
-// calls it.
+// order, the block adds its threads' sums in a fixed shuffle tree (FP32: FP64
+// arithmetic runs at ~1/64 of the FP32 rate here and sat on the critical path
+// of this per-iteration check), and the last block to finish adds the block
+// sums in block order in FP64.  Returns true on that block's thread 0, with
+// the sum in *total.  Every thread of every block calls it.
 __device__ bool res_sum(const BrickMap &m, const float *__restrict__ res, IbmState *st,
                         double *total) {
-  __shared__ double red[256];
+  __shared__ float red[8];
   __shared__ bool last;
-  const int nslots = active_slots(m), t = threadIdx.x;
-  double a = 0.0;
-  for (int s = blockIdx.x * 256 + t; s < nslots; s += RES_BLOCKS * 256) a += (double)res[s];
-  red[t] = a;
+  const int nslots = active_slots(m), t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  float a = 0.f;
+  for (int s = blockIdx.x * 256 + t; s < nslots; s += RES_BLOCKS * 256) a += res[s];
 #pragma unroll
-  for (int o = 128; o > 0; o >>= 1) {
-    __syncthreads();
-    if (t < o) red[t] += red[t + o];
-  }
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if (lane == 0) red[wid] = a;
   __syncthreads();
   if (t == 0) {
-    st->bsum[blockIdx.x] = red[0];
+    const float b = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+    st->bsum[blockIdx.x] = (double)b;
     __threadfence();
     last = atomicAdd(&st->ticket, 1u) == (unsigned)RES_BLOCKS - 1;
   }
