@@ -193,3 +193,27 @@ def test_cg_exact_solution_stays_at_rest(gpu_lib, torch_cuda, n_iter):
     _, u, du = lat.points()
     assert not np.any(du) and not np.any(u)
     lat.close()
+
+
+@pytest.mark.parametrize("storage,delta,tol_u,tol_g", [("f32", "peskin", 1e-5, 1e-4),
+                                                       ("bf16", "cosine", 5e-3, 5e-2),
+                                                       ("f16", "cosine", 1e-3, 1e-2)])
+def test_cg_with_peskin_kernel_and_16bit_storage(gpu_lib, torch_cuda, orc, storage, delta,
+                                                 tol_u, tol_g):
+    """CG with Peskin's kernel (FP32) and with 16-bit deviation storage: 10
+    steps of 5 iterations against the FP64 oracle's CG (the 16-bit forms
+    within their storage rounding, as the paper's loop is in the precision
+    tests)."""
+    w = W.single_propeller(4)
+    lat = gpu_lib.Lattice(w.shape, w.tau, storage=storage, delta=delta, warm="previous",
+                          stream=torch_cuda.cuda.current_stream(), solver="cg")
+    lat.set_propellers(w.props)
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=5, warm="previous",
+                         kernel=delta, solver="cg")
+    lat.step(10, 5)
+    sim.step(10)
+    _, U, G = lat.fields()
+    _, U_o = sim.fields()
+    assert rel_l2(U, U_o) < tol_u, rel_l2(U, U_o)
+    assert rel_l2(G, sim.G) < tol_g, rel_l2(G, sim.G)
+    lat.close()
