@@ -838,6 +838,7 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     if (warm) CK(h, launch_brick_init(c.D, c.dims, 1, st));
   }
   const bool cg = c.solver == LBM_SOLVER_CG;
+  bool g_current = false;  // (CG) G = S[du] already holds for the result
   if (cg) {
     int r = enqueue_cg_start(c, warm, st);
     if (r) return r;
@@ -893,9 +894,11 @@ static int tolerance_loop(StepCtx &c, bool warm) {
     if (r) return r;
     CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
+    // a confirmed stop keeps the iterate whose G = S[du] the pass above left
+    g_current = h->state_host->done && !h->state_host->capped;
     if (h->state_host->done) break;
   }
-  if (cg) {
+  if (cg && !g_current) {
     int r = enqueue_final_spread(c, st);
     if (r) return r;
   }

@@ -1403,8 +1403,9 @@ __global__ void __launch_bounds__(CG_BLOCK)
     coef[0] = alpha;
     coef[1] = beta;
     // a confirming iteration (r the true residual) that meets tol keeps its
-    // iterate: the one whose residual was checked
-    keep = confirm && tol_mode && (double)rho <= tol * tol * st->den2;
+    // iterate: the one whose residual was checked (the same test as the stop
+    // below, so that a stop without the cap means a kept iterate)
+    keep = confirm && tol_mode && sqrt((double)rho / st->den2) <= tol;
     if (blockIdx.x == 0) {
       st->cg_rho[cur] = rho;
       st->cg_alpha[cur] = alpha;

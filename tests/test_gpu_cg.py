@@ -108,6 +108,11 @@ def test_cg_tolerance_mode_against_oracle(gpu_lib, torch_cuda, orc, warm, tol, s
         assert lat.stats()["last_ibm_iters"] == len(eps)
         assert len(eps) <= 2 * len(sim.eps[-1]) + 5
         assert _true_eps(orc, w, lat, U0, step) <= 1.5 * tol
+        # the force applied is the spread of the returned correction
+        p = w.props.as_dict()
+        x, _ = orc.kinematics(p["xrest"], p["body"], p["centre"], p["omega"], p["phase"], step)
+        G_du = orc.spread(w.shape, x, lat.points()[2].astype(np.float64))
+        assert rel_l2(lat.fields()[2], G_du) < 1e-5
         if step == 0:
             eo = sim.eps[-1]
             m = int(np.argmax(eo < 30 * tol))
