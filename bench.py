@@ -341,6 +341,7 @@ def run_ours(args):
         line["tolerance"] = bench_tolerance()
         line["paper_sweep"] = bench_paper_sweep()
         line["delta_kernels"] = bench_delta_kernels()
+        line["point_order"] = bench_point_order()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         wcpu = W.dense_array_256()
         dt, cores = cpu_oracle_run(wcpu, 2)
@@ -494,6 +495,44 @@ def bench_delta_kernels(steps=100, warmup=5, tol_steps=6, tol=1e-4):
         lat.close()
         out[delta] = {"mlups": w.cells * steps / (ms / 1e3) / 1e6,
                       "tol_ms_per_step": t_ms / tol_steps, "tol_iters_per_step": iters / tol_steps}
+    return out
+
+
+def bench_point_order(steps=200, warmup=5):
+    """Ablation of the points' order (the paper notes that per-point accesses
+    to the neighbourhood are uncoalesced): the 256^3 array at 5 iterations
+    with its points in the generated order (blade by blade, radius-major), in
+    a seeded random permutation, and in Morton order of the 4^3 brick holding
+    each rest position.  Results are the same up to the FP32 order of sums."""
+    import numpy as np
+    import torch
+    from paper_1904_02108_gb300 import binding, workload as W
+    w = W.dense_array_256()
+    p = w.props
+    st = torch.cuda.current_stream()
+    b = np.floor(p.xrest / 4.0).astype(np.int64)
+
+    def morton(v):
+        out = np.zeros(len(v), np.int64)
+        for bit in range(7):
+            for c in range(3):
+                out |= ((v[:, c] >> bit) & 1) << (3 * bit + c)
+        return out
+
+    orders = {"generated": np.arange(p.n_points),
+              "random": np.random.default_rng(1241).permutation(p.n_points),
+              "brick_morton": np.argsort(morton(b), kind="stable")}
+    out = {"workload": w.name, "steps": steps, "mlups": {}}
+    for name, perm in orders.items():
+        q = W.Propellers(p.xrest[perm], p.area[perm], p.body[perm], p.centre, p.omega, p.phase,
+                         p.blade_length, p.blade_width)
+        lat = binding.Lattice(w.shape, w.tau, stream=st)
+        lat.set_propellers(q)
+        lat.autotune(w.n_iter, 3)
+        lat.step(warmup, w.n_iter)
+        ms = _device_ms(lambda: lat.step(steps, w.n_iter), st)
+        out["mlups"][name] = w.cells * steps / (ms / 1e3) / 1e6
+        lat.close()
     return out
 
 
