@@ -77,6 +77,10 @@ struct lbm {
   double *xpos = nullptr;
   bool have_du = false;
   int solver = LBM_SOLVER_MDF;  // the fixed point's iteration
+  // the surface velocities are known not to vanish (rotating bodies, or
+  // non-zero targets given to ibm_set_points): tolerance mode then needs no
+  // host check of the residual denominator before iterating
+  bool bodies_moving = false, targets_nonzero = false;
   double gbody[3] = {0, 0, 0};
   int64_t t = 0;
 
@@ -507,6 +511,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, cudaMemcpy(h->body, b.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     std::vector<float> u(3 * n, 0.0f);
     if (U_target) memcpy(u.data(), U_target, sizeof(float) * 3 * n);
+    h->targets_nonzero = std::any_of(u.begin(), u.end(), [](float v) { return v != 0.0f; });
     CK(h, cudaMemcpy(h->utarget, u.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice));
     CK(h, cudaMemset(h->du, 0, sizeof(float4) * n));
     CK(h, cudaMemset(h->uint, 0, sizeof(float4) * n));
@@ -524,9 +529,11 @@ int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_targe
   if (n == 0) return LBM_OK;
   if (!X) return fail(h, LBM_EINVAL, "X is NULL");
   CK(h, cudaMemcpyAsync(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->st));
-  if (U_target)
+  if (U_target) {
     CK(h, cudaMemcpyAsync(h->utarget, U_target, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
                           h->st));
+    h->targets_nonzero = false;  // (not scanned here: checked on the device again)
+  }
   return LBM_OK;
 }
 
@@ -546,6 +553,7 @@ int ibm_set_bodies(lbm_t *h, int nb, const double *centre, const double *omega,
   dfree(h->omega);
   dfree(h->phase);
   h->nb = nb;
+  h->bodies_moving = nb > 0 && std::any_of(omega, omega + nb, [](double w) { return w != 0.0; });
   h->desc_dirty = true;
   if (nb > 0) {
     CK(h, dalloc(&h->centre, 3 * nb));
@@ -820,15 +828,20 @@ static int enqueue_step(StepCtx &c, int n_iter) {
 static int tolerance_loop(StepCtx &c, bool warm) {
   lbm_t *h = c.acct;
   cudaStream_t st = c.sti;
+  // where the surface velocities are known not to vanish, the denominator
+  // needs no check by the host (and no round trip before the iterations)
+  const bool moving = h->nb > 0 ? h->bodies_moving : h->targets_nonzero;
   {
     // denominator ||S[s u_k]||^2
     StageTimer T(h, ST_RESID, st, 2);
     CK(h, launch_brick_norm(c.D, c.dims, 0, st));
-    CK(h, launch_ibm_den(c.D, c.dims, 0, st));
+    CK(h, launch_ibm_den(c.D, c.dims, moving ? 2 : 0, st));
   }
-  CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
-  CK(h, cudaStreamSynchronize(st));
-  if (h->state_host->den2 == 0.0) {
+  if (!moving) {
+    CK(h, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+  }
+  if (!moving && h->state_host->den2 == 0.0) {
     // all surface velocities vanish: ||S[s (u_k - I[U0])]||^2 instead
     StageTimer T(h, ST_RESID, st, warm ? 5 : 3);
     if (warm) CK(h, launch_brick_init(c.D, c.dims, 0, st));

@@ -1115,7 +1115,8 @@ __device__ bool res_sum(const BrickMap &m, const float *__restrict__ res, IbmSta
 }
 
 // mode 0: den2 = sum res (||S[s u_k]||^2); mode 1: fallback den2 (used when
-// the first is 0): sum res, or 1 if that is 0 as well.
+// the first is 0): sum res, or 1 if that is 0 as well; mode 2: as mode 0 where
+// the surface velocities are known not to vanish (1 should the sum still be 0).
 __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restrict__ D,
                                                        int mode) {
   pdl_wait();
@@ -1123,8 +1124,8 @@ __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restri
   IbmState *st = d.state;
   double v;
   if (!res_sum(d.m, d.res, st, &v)) return;
-  if (mode == 0) {
-    st->den2 = v;
+  if (mode == 0 || mode == 2) {
+    st->den2 = mode == 2 && !(v > 0.0) ? 1.0 : v;
     st->done = 0;
     st->iters = 0;
   } else if (st->den2 == 0.0) {
