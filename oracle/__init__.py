@@ -75,6 +75,8 @@ def lib():
             L.orc_mlp_forward.argtypes = [l, p, p, p]
             L.orc_mlp_loss_grad.argtypes = [l, p, p, p, p]
             L.orc_mlp_loss_grad.restype = d
+            L.orc_mlp_features.argtypes = [i, i, i, i, p, l, p, p, p, p, i, p, p, d, d, p]
+            L.orc_learned_init.argtypes = [l, p, p, p, d, p]
             _lib = L
     return _lib
 
@@ -253,6 +255,48 @@ def mlp_loss_grad(P, x, t):
     return loss, g
 
 
+# Feature scaling of the learned warm start (the values the library's C ABI
+# documents for its feature layout): velocities in units of VSCALE, lengths in
+# units of LSCALE.
+VSCALE = 0.05
+LSCALE = 16.0
+
+
+def mlp_features(U0, x, ut, du_prev=None, body=None, centre=None, omega=None,
+                 kernel="cosine", vscale=VSCALE, lscale=LSCALE):
+    """The 16 per-point inputs of the learned warm start (orc_mlp_features):
+    I[U0 + S[du_prev]], u_k, du_prev, the density of supports on the bricks
+    the point's support touches, r and z about the body's axis, |omega| r and
+    the slip u_k - I[U0 + S[du_prev]]; velocities / vscale, lengths / lscale.
+    Returns [np, 16]."""
+    U0 = _f64(U0)
+    _, nz, ny, nx = U0.shape
+    x = _f64(x).reshape(-1, 3)
+    ut = _f64(ut).reshape(-1, 3)
+    n = len(x)
+    dp = None if du_prev is None else _f64(du_prev).reshape(-1, 3)
+    nb = 0 if centre is None else len(_f64(centre).reshape(-1, 3))
+    b = None if body is None else np.ascontiguousarray(body, dtype=np.int32)
+    c = None if centre is None else _f64(centre).reshape(-1, 3)
+    om = None if omega is None else _f64(omega).reshape(-1)
+    feat = np.zeros((n, 16))
+    lib().orc_mlp_features(nx, ny, nz, KERNELS[kernel], _p(U0), n, _p(x), _p(ut), _p(dp),
+                           _p(b), nb, _p(c), _p(om), float(vscale), float(lscale),
+                           _p(feat))
+    return feat
+
+
+def learned_init(P, feat, du_prev=None, vscale=VSCALE):
+    """du_init = du_prev + vscale * MLP(feat) (orc_learned_init)."""
+    P = _f64(P).reshape(-1)
+    feat = _f64(feat).reshape(-1, 16)
+    n = len(feat)
+    dp = None if du_prev is None else _f64(du_prev).reshape(-1, 3)
+    out = np.zeros((n, 3))
+    lib().orc_learned_init(n, _p(P), _p(feat), _p(dp), float(vscale), _p(out))
+    return out
+
+
 class Simulation:
     """The coupled step of Sec. 2 driven over time on the CPU, in FP64.
 
@@ -261,12 +305,16 @@ class Simulation:
     (rigid rotation about z, Alg. 1), or ``x`` [np,3] and ``ut`` [np,3] for
     fixed points with a prescribed surface velocity.  ``solver`` is "mdf"
     (the multi-direct-forcing loop of Sec. 3) or "cg" (conjugate gradients
-    on the same fixed point, ``ibm_cg``).
+    on the same fixed point, ``ibm_cg``).  ``warm`` is the initial guess of
+    each step's fixed point: "zero" (the paper), "previous" (the previous
+    step's final du) or "mlp" (the learned start du_prev + V MLP(features)
+    with the FP64 parameter vector ``mlp``; the features of the last step
+    are kept in ``features`` and its initial guess in ``du_init``).
     """
 
     def __init__(self, shape, tau, points=None, kernel="cosine", n_iter=5,
                  tol=1e-4, max_iter=500, literal=False, warm="zero",
-                 gbody=None, solver="mdf"):
+                 gbody=None, solver="mdf", mlp=None):
         self.shape = tuple(shape)
         self.tau = float(tau)
         self.kernel = kernel
@@ -275,6 +323,11 @@ class Simulation:
         self.max_iter = int(max_iter)
         self.literal = bool(literal)
         self.warm = warm
+        if warm == "mlp" and mlp is None:
+            raise ValueError("warm='mlp' needs the MLP parameters")
+        self.mlp = None if mlp is None else _f64(mlp).reshape(-1)
+        self.features = None
+        self.du_init = None
         self.solver = SOLVERS[solver]
         self.gbody = None if gbody is None else _f64(gbody, (3,))
         nz, ny, nx = self.shape
@@ -319,6 +372,17 @@ class Simulation:
             du_init = None
             if self.warm == "previous" and self.t > 0:
                 du_init = self.du.copy()
+            elif self.warm == "mlp" and self.np:
+                du_prev = self.du.copy() if self.t > 0 else None
+                _, U0 = moments(self.f)
+                P = self.points
+                rigid = "xrest" in P
+                self.features = mlp_features(
+                    U0, x, ut, du_prev, body=P["body"] if rigid else None,
+                    centre=P["centre"] if rigid else None,
+                    omega=P["omega"] if rigid else None, kernel=self.kernel)
+                du_init = learned_init(self.mlp, self.features, du_prev)
+                self.du_init = du_init.copy()
             du = np.zeros((self.np, 3))
             it = L.orc_step(nx, ny, nz, self.tau, KERNELS[self.kernel], _p(self.f),
                             _p(self.ftmp), self.np, _p(_f64(x)), _p(_f64(ut)),

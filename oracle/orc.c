@@ -647,3 +647,113 @@ double orc_mlp_loss_grad(long n, const double *P, const double *x, const double 
   }
   return loss;
 }
+
+/* ---- inputs and initial guess of the learned warm start (not in the paper)
+ *
+ * Features of point k for the per-point MLP above, in this order:
+ *   0-2   u_i(k) = I[U0 + S[du_prev]](k): the velocity interpolated on the
+ *         lattice with the previous step's correction already spread on it
+ *         (the first estimate U_0 of the Sec. 3 loop when it starts from
+ *         du_prev), divided by vscale;
+ *   3-5   u_k / vscale, the surface velocity of the point (Alg. 1);
+ *   6-8   du_prev(k) / vscale (zero when du_prev is NULL);
+ *   9     local point density: over the 4x4x4 bricks that the point's support
+ *         touches, the mean number of supports touching each brick, per cell
+ *         of a brick (divided by 64);
+ *   10-11 distance from the body's rotation axis (the z line through its
+ *         centre) and axial offset z - z_c, divided by lscale (0 without
+ *         bodies);
+ *   12    |omega_b| r / vscale, the speed of rigid rotation at that radius;
+ *   13-15 (u_k - u_i(k)) / vscale, the slip the fixed point has to remove.
+ *
+ * Reading: the support of a point is the block of four cells per axis,
+ * floor(x) - 1 .. floor(x) + 2 (wrapped), at which the kernel's taps sit (the
+ * 5-wide window of Alg. 2 contains them; its fifth tap has weight 0).  A
+ * brick is touched when one of those cells lies in it.
+ * body: [np] body of each point (NULL: 0); centre [nb][3], omega [nb]; nb = 0
+ * means no bodies.  feat: [np][16]. */
+static long brick_of_cell(long X, long Y, long Z, int nx, int ny, int nz) {
+  long bx = wrap(X, nx) / 4, by = wrap(Y, ny) / 4, bz = wrap(Z, nz) / 4;
+  return (bz * (ny / 4) + by) * (nx / 4) + bx;
+}
+
+/* The distinct bricks touched by the support of a point at xk (at most 8). */
+static int touched_bricks(int nx, int ny, int nz, const double *xk, long out[8]) {
+  long f0 = (long)floor(xk[0]), f1 = (long)floor(xk[1]), f2 = (long)floor(xk[2]);
+  int m = 0;
+  for (long c = -1; c <= 2; c++)
+    for (long b = -1; b <= 2; b++)
+      for (long a = -1; a <= 2; a++) {
+        long br = brick_of_cell(f0 + a, f1 + b, f2 + c, nx, ny, nz);
+        int seen = 0;
+        for (int j = 0; j < m; j++) seen |= out[j] == br;
+        if (!seen) out[m++] = br;
+      }
+  return m;
+}
+
+void orc_mlp_features(int nx, int ny, int nz, int kernel, const double *U0, long np,
+                      const double *x, const double *ut, const double *du_prev,
+                      const int *body, int nb, const double *centre, const double *omega,
+                      double vscale, double lscale, double *feat) {
+  long N = (long)nx * ny * nz;
+  long nbrick = (long)(nx / 4) * (ny / 4) * (nz / 4);
+  double *Uf = malloc(sizeof(double) * 3 * N);
+  double *ui = malloc(sizeof(double) * 3 * np);
+  long *touch = malloc(sizeof(long) * 8 * np);
+  int *ntouch = malloc(sizeof(int) * np);
+  long *count = calloc(nbrick, sizeof(long));
+
+  /* u_i = I[U0 + S[du_prev]] */
+  memcpy(Uf, U0, sizeof(double) * 3 * N);
+  if (du_prev) orc_spread(nx, ny, nz, kernel, np, x, du_prev, Uf);
+  orc_interpolate(nx, ny, nz, kernel, Uf, np, x, ui);
+
+  /* supports touching each brick */
+  for (long k = 0; k < np; k++) {
+    ntouch[k] = touched_bricks(nx, ny, nz, x + 3 * k, touch + 8 * k);
+    for (int j = 0; j < ntouch[k]; j++) count[touch[8 * k + j]]++;
+  }
+
+  for (long k = 0; k < np; k++) {
+    double *o = feat + 16 * k;
+    double dens = 0.0;
+    for (int j = 0; j < ntouch[k]; j++) dens += (double)count[touch[8 * k + j]];
+    dens /= 64.0 * ntouch[k];
+    double r = 0.0, dz = 0.0, speed = 0.0;
+    if (nb > 0) {
+      int b = body ? body[k] : 0;
+      double ex = x[3 * k] - centre[3 * b], ey = x[3 * k + 1] - centre[3 * b + 1];
+      r = sqrt(ex * ex + ey * ey);
+      dz = x[3 * k + 2] - centre[3 * b + 2];
+      speed = fabs(omega[b]) * r;
+    }
+    for (int c = 0; c < 3; c++) {
+      o[c] = ui[3 * k + c] / vscale;
+      o[3 + c] = ut[3 * k + c] / vscale;
+      o[6 + c] = du_prev ? du_prev[3 * k + c] / vscale : 0.0;
+      o[13 + c] = (ut[3 * k + c] - ui[3 * k + c]) / vscale;
+    }
+    o[9] = dens;
+    o[10] = r / lscale;
+    o[11] = dz / lscale;
+    o[12] = speed / vscale;
+  }
+  free(Uf);
+  free(ui);
+  free(touch);
+  free(ntouch);
+  free(count);
+}
+
+/* The learned initial guess of the fixed point: du_init = du_prev + V MLP(x)
+ * with x the features above (V = vscale); du_prev NULL counts as zero. */
+void orc_learned_init(long np, const double *P, const double *feat, const double *du_prev,
+                      double vscale, double *du_init) {
+  double *y = malloc(sizeof(double) * MLP_OUT * np);
+  orc_mlp_forward(np, P, feat, y);
+  for (long k = 0; k < np; k++)
+    for (int c = 0; c < 3; c++)
+      du_init[3 * k + c] = (du_prev ? du_prev[3 * k + c] : 0.0) + vscale * y[3 * k + c];
+  free(y);
+}
