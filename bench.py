@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LBM-IBM MLUPS"
 UNIT = "MLUPS"
+WINDOWS = 5  # timed windows of --steps steps; the reported value is their median
 
 
 def _peaks():
@@ -39,28 +40,31 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """nvidia-smi sampler (every 5 ms) around the timed region; only samples
+    that arrive between mark_start() and mark_end() count."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, interval_ms=5):
         self.dev = device_index
+        self.interval = interval_ms
         self.p = None
+        self.lines = []
+        self.t_start = self.t_end = None
 
     def __enter__(self):
         """Starts the sampler and waits for its first sample, so that the
         tool's start-up (which can hold the driver for seconds on a fresh
         machine) falls before the timed region rather than inside it."""
         import threading
-        self.lines = []
         first = threading.Event()
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "20"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except Exception:
             self.p = None
             return self
@@ -68,30 +72,40 @@ class Clocks:
         def reader():
             for l in self.p.stdout:
                 if l.strip():
-                    self.lines.append(l)
+                    self.lines.append((time.perf_counter(), l))
                     first.set()
             first.set()
 
         self.t = threading.Thread(target=reader, daemon=True)
         self.t.start()
         first.wait(timeout=30)
-        self.skip = len(self.lines)  # samples taken before the timed region
         return self
+
+    def mark_start(self):
+        self.t_start = time.perf_counter()
+
+    def mark_end(self):
+        self.t_end = time.perf_counter()
 
     def __exit__(self, *a):
         if self.p is not None:
+            # let the samples taken during the region reach the reader
+            time.sleep(3 * self.interval / 1e3)
             self.p.terminate()
             try:
                 self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
             self.t.join(timeout=5)
-            self.lines = self.lines[self.skip:]
 
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        t0 = self.t_start if self.t_start is not None else -1e30
+        t1 = self.t_end if self.t_end is not None else 1e30
+        for ts, l in self.lines:
+            if not (t0 <= ts <= t1):
+                continue
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -104,9 +118,11 @@ class Clocks:
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"],
+                    "interval_ms": self.interval}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": self.interval,
+                "region_s": (t1 - t0) if self.t_end is not None else None}
 
 
 def _captured_traffic(name):
@@ -222,20 +238,28 @@ def run_ours(args):
     barrier()
 
     # ---- timed region (device time, CUDA events on the library's stream);
-    # the collide-stream kernel is bracketed by events inside the library
+    # the collide-stream kernel is bracketed by events inside the library.
+    # WINDOWS windows of exactly K steps each, every one bracketed by a
+    # barrier and a synchronisation; the line reports the median window.
     lat.enable_timing(["collide_stream"])
     launches0 = lat.stats()["kernel_launches"]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs_t = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(WINDOWS)]
     barrier()
     with Clocks(local) as clk:
-        e0.record(st)
-        lat.step(args.steps, w.n_iter)
-        e1.record(st)
-        barrier()
-    ms = e0.elapsed_time(e1)
+        clk.mark_start()
+        for e0, e1 in evs_t:
+            barrier()
+            e0.record(st)
+            lat.step(args.steps, w.n_iter)
+            e1.record(st)
+            barrier()
+        clk.mark_end()
+    window_ms = [e0.elapsed_time(e1) for e0, e1 in evs_t]
+    ms = statistics.median(window_ms)
     stage = lat.timing()
     s = lat.stats()
-    launches = s["kernel_launches"] - launches0
+    launches = (s["kernel_launches"] - launches0) // WINDOWS
     ms, value = combine_ranks(ms, w.cells, args.steps, ws, device="cuda")
     lat.enable_timing(False)
 
@@ -316,6 +340,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w, "f32"),
+        "windows": {"n": WINDOWS, "steps_each": args.steps,
+                    "ms_per_step": [round(t / args.steps, 5) for t in window_ms],
+                    "value": "median window"},
         "point_updates_per_s": ws * npnt * w.n_iter * args.steps / (ms / 1e3),
         "gpu_launches": launches,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -439,6 +466,15 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
             capped += int(s["last_residual"] > tol)
         out[name] = {"ms_per_step": t_ms / steps, "iters_per_step": iters / steps,
                      "capped_steps": capped, "solver": solver}
+        if warm == "mlp":
+            # device time of the learned start's kernels (features, MLP,
+            # initial guess) per step, in a separate pass with that stage timed
+            lat.enable_timing(["mlp"])
+            lat.step(2, 0)
+            mlp_ms, mlp_n = lat.timing()["mlp"]
+            lat.enable_timing(False)
+            out[name]["mlp_stage_ms_per_step"] = mlp_ms / 2
+            out[name]["mlp_stage_launches_per_step"] = mlp_n / 2
         lat.close()
     return out
 

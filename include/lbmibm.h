@@ -160,8 +160,10 @@ int lbm_set_body_force(lbm_t *h, double gx, double gy, double gz);
  * fixed-point iterations (the paper uses 5).  n_ibm_iter == 0: iterate until
  * the residual eps = ||S[s g_n]|| / ||S[s u_k]|| <= ibm_tol or ibm_max_iter
  * iterations; returns LBM_WNOTCONVERGED if any step hit the cap.
- * Errors: LBM_EINVAL (n_steps < 0, n_ibm_iter < 0), LBM_ECUDA,
- * LBM_ENONFINITE (stats on and a NaN/Inf sum). */
+ * Errors: LBM_EINVAL (n_steps < 0, n_ibm_iter < 0), LBM_ECUDA.  The call
+ * does not wait for the GPU: a step whose FP64 mass or momentum sum is not
+ * finite (stats on) is reported as LBM_ENONFINITE by the next
+ * lbm_read_stats. */
 int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter);
 
 /* The iteration that solves the fixed point of Sec. 3 in lbm_step.
@@ -204,7 +206,9 @@ int lbm_read_fields_dev(lbm_t *h, float *rho, float *U, float *G);
 int ibm_read_points(lbm_t *h, double *x, float *u_interp, float *du);
 int ibm_read_points_dev(lbm_t *h, double *x, float *u_interp, float *du);
 
-/* Statistics; the FP64 sums are those of the last step with stats on. */
+/* Statistics; the FP64 sums are those of the last step with stats on.
+ * Returns LBM_ENONFINITE (with the statistics filled in) when one of those
+ * sums is NaN or infinite. */
 int lbm_read_stats(lbm_t *h, lbm_stats *s);
 
 /* Non-blocking read-back into host memory: the same values as
@@ -222,7 +226,9 @@ int ibm_read_points_async(lbm_t *h, double *x, float *u_interp, float *du);
 int lbm_read_sums_async(lbm_t *h, double *sums);
 
 /* Full populations f[19][N] (FP32) of the current state, in the velocity
- * order of lbm_velocity_set, and their replacement.  Host buffers. */
+ * order of lbm_velocity_set, and their replacement.  Host buffers.
+ * lbm_write_populations returns LBM_ENONFINITE, and leaves the state as it
+ * was, when a value is NaN or infinite. */
 int lbm_read_populations(lbm_t *h, float *f);
 int lbm_write_populations(lbm_t *h, const float *f);
 
@@ -426,9 +432,14 @@ int ibm_read_mlp_sample_dev(lbm_t *h, float *X, float *T);
  * LBM_EINVAL (for example 64^3 with 12,000 points needs about 4.3 MiB).
  *
  * The first call on a device (the current device when it is made) looks up
- * the array's device address; make that first call before any stream capture
- * begins.  All calls on a device share the one array and it keeps the
- * previous call's contents (the call clears what must start at zero), so
+ * the array's device address and keeps it for the rest of the process; make
+ * that first call before any stream capture begins.  After cudaDeviceReset
+ * on a device (or any other teardown of its primary context) the kept
+ * address is stale: do not call this entry point on that device again.  The
+ * descriptor of the problem goes to the device as a kernel parameter, not
+ * as a copy from host memory.  All calls on a device share the one array
+ * and it keeps the previous call's contents (the call clears what must start
+ * at zero), so
  * calls that overlap on the GPU, on different streams or from different host
  * threads, race: serialise them. */
 int ibm_spread_dev_noalloc(int nx, int ny, int nz, int delta, int64_t n,

@@ -2074,7 +2074,7 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
     dims.max_points = (int)n;
     dims.max_bricks = g.nbrick;
     dims.max_slots = m.max_slots;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(D, &dd, sizeof dd, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_store_desc(dd, D, st);
     if (e == cudaSuccess) e = launch_prepare_points(D, dims, st);
     if (e == cudaSuccess) e = launch_compact(D, dims, st);
     if (e == cudaSuccess) e = launch_pair_lists(D, dims, st);
@@ -2098,7 +2098,9 @@ int ibm_spread_dev(int nx, int ny, int nz, int delta, int64_t n, const double *x
 //
 // Scratch for ibm_spread_dev_noalloc: a static device array, so the call never
 // allocates.  Host code only knows the symbol; its device address comes from
-// cudaGetSymbolAddress, looked up once per device with that device current.
+// cudaGetSymbolAddress, looked up once per device with that device current
+// and kept for the life of the process (a device reset would invalidate it;
+// the header states that limit).
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LBM_NOALLOC_SCRATCH_BYTES];
 

@@ -1607,6 +1607,12 @@ __global__ void pack_vals_kernel(int64_t n, const float *__restrict__ v, float4 
   o[k] = make_float4(v[3 * k], v[3 * k + 1], v[3 * k + 2], 1.f);
 }
 
+// Writes a descriptor passed by value into device memory: the descriptor is
+// then part of the launch, not a copy from (pageable) host memory.
+__global__ void store_desc_kernel(DomainDesc dd, DomainDesc *__restrict__ D) {
+  if (threadIdx.x == 0) *D = dd;
+}
+
 __global__ void pack_points_kernel(int64_t n, const float4 *__restrict__ a, float *__restrict__ o) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -1828,6 +1834,11 @@ cudaError_t launch_interp_dense(const Geometry &g, int delta, const float *U, in
 cudaError_t launch_pack_vals(int64_t n, const float *v, float4 *vals, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   pack_vals_kernel<<<nblk(n, 256), 256, 0, st>>>(n, v, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_desc(const DomainDesc &dd, DomainDesc *D, cudaStream_t st) {
+  store_desc_kernel<<<1, 32, 0, st>>>(dd, D);
   return cudaGetLastError();
 }
 

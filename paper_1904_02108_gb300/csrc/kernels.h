@@ -129,6 +129,8 @@ cudaError_t launch_mlp_adam(float *P, float *m, float *v, const float *grad, int
 cudaError_t launch_interp_dense(const Geometry &g, int delta, const float *U, int64_t n,
                                 const double *x, float *u, cudaStream_t st);
 cudaError_t launch_pack_vals(int64_t n, const float *v, float4 *vals, cudaStream_t st);
+// *D = dd, with dd passed as a kernel parameter
+cudaError_t launch_store_desc(const DomainDesc &dd, DomainDesc *D, cudaStream_t st);
 cudaError_t launch_slots_to_dense(const Geometry &g, const BrickMap &m, const float *Gs,
                                   float *F, cudaStream_t st);
 cudaError_t launch_pack_points(int64_t n, const float4 *a, float *out, cudaStream_t st);

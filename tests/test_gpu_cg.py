@@ -219,6 +219,8 @@ def test_cg_with_peskin_kernel_and_16bit_storage(gpu_lib, torch_cuda, orc, stora
     sim.step(10)
     _, U, G = lat.fields()
     _, U_o = sim.fields()
+    print("CG %s %s: rel L2 U %.3e (bound %.1e), G %.3e (bound %.1e)"
+          % (storage, delta, rel_l2(U, U_o), tol_u, rel_l2(G, sim.G), tol_g))
     assert rel_l2(U, U_o) < tol_u, rel_l2(U, U_o)
     assert rel_l2(G, sim.G) < tol_g, rel_l2(G, sim.G)
     lat.close()

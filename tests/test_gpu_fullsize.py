@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size and launch configuration: the 256^3
-array of 64 propellers (89,600 points, 5 iterations per step), two steps from
-rest, against the FP64 oracle on the whole lattice."""
+array of 64 propellers (89,600 points, 5 iterations per step) against the
+FP64 oracle on the whole lattice: two steps from rest, ten steps from the
+previous step's force, and the paper's loop iterated to a residual target."""
 import numpy as np
 import pytest
 
@@ -61,4 +62,56 @@ def test_dense_array_256_conjugate_gradients_to_tolerance(gpu_lib, orc):
         eps = (np.linalg.norm(orc.spread(w.shape, x, s * r))
                / np.linalg.norm(orc.spread(w.shape, x, s * ut)))
         assert eps <= 1.5e-4, (step, eps)
+    lat.close()
+
+
+def test_dense_array_256_previous_force_ten_steps(gpu_lib, orc):
+    """Ten fixed-count steps from the previous step's force, the pair lists
+    (up to 128 pairs per brick, ~10k active bricks) rebuilt every step as the
+    propellers turn: fields, forces and corrections at the FP32 bar."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.dense_array_256()
+    lat = gpu_lib.Lattice(w.shape, w.tau, warm="previous", stream=torch.cuda.current_stream())
+    lat.set_propellers(w.props)
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=w.n_iter, warm="previous")
+    for chunk in (3, 7):
+        lat.step(chunk, w.n_iter)
+        sim.step(chunk)
+        _, U, G = lat.fields()
+        _, _, du = lat.points()
+        _, U_o = sim.fields()
+        assert rel_l2(U, U_o) < 1e-5, (sim.t, rel_l2(U, U_o))
+        assert rel_l2(G, sim.G) < 1e-5
+        assert rel_l2(du, sim.du) < 1e-5
+    assert lat.stats()["step"] == 10
+    lat.close()
+
+
+def test_dense_array_256_paper_loop_to_tolerance(gpu_lib, orc):
+    """The paper's loop iterated until eps <= 1e-3 (tolerance mode, previous
+    step's force) at full size: per step the same iteration count as the
+    oracle and the same residual history, then the fields."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.dense_array_256()
+    tol = 1e-3
+    lat = gpu_lib.Lattice(w.shape, w.tau, warm="previous", ibm_tol=tol, ibm_max_iter=2000,
+                          stream=torch.cuda.current_stream())
+    lat.set_propellers(w.props)
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=0, tol=tol, max_iter=2000,
+                         warm="previous")
+    for _ in range(2):
+        assert lat.step(1, 0) == gpu_lib.LBM_OK
+        sim.step(1)
+        eps, eo = lat.residuals(), sim.eps[-1]
+        assert len(eps) == len(eo) == sim.iters[-1]
+        assert eps[-1] <= tol < eps[-2]
+        np.testing.assert_allclose(eps, eo, rtol=2e-3, atol=1e-7)
+    _, U, G = lat.fields()
+    _, U_o = sim.fields()
+    assert rel_l2(U, U_o) < 1e-5
+    assert rel_l2(G, sim.G) < 1e-4
     lat.close()

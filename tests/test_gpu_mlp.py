@@ -104,8 +104,9 @@ def test_training_fits_a_teacher_network(gpu_lib, torch_cuda, orc):
 def test_learned_start_needs_fewer_iterations(gpu_lib, torch_cuda):
     """Trained on trajectories of single propellers with fresh seeds, the
     network's starting guess reaches the residual target in fewer fixed-point
-    iterations than the zero start on a held-out propeller, and the converged
-    step still meets the target."""
+    iterations than both the zero start and the previous-force start (which
+    the learned start corrects: du_prev + V MLP(x)) on a held-out propeller,
+    and the converged step still meets the target."""
     torch = torch_cuda
     tol = 1e-3
     train_w = [W.single_propeller(5000 + i) for i in range(4)]
@@ -129,3 +130,4 @@ def test_learned_start_needs_fewer_iterations(gpu_lib, torch_cuda):
         lat.close()
     print("iterations to eps <= %g over 20 steps: %s" % (tol, iters))
     assert iters["mlp"] < iters["zero"]
+    assert iters["mlp"] < iters["previous"]

@@ -333,3 +333,30 @@ def test_async_readback_matches_blocking(gpu_lib, torch_cuda):
     assert sums[0] == sa["mass"] and tuple(sums[1:]) == sa["momentum"]
     for lat in (a, b):
         lat.close()
+
+
+def test_non_finite_populations_are_refused_and_overflow_is_reported(gpu_lib, torch_cuda, orc):
+    """Failure paths on the host: a NaN population given to
+    lbm_write_populations is refused (LBM_ENONFINITE) and the state is left
+    as it was; finite populations whose density overflows FP32 (two rest
+    populations of 3e38 in one 128-cell partial sum) make the step's FP64 mass
+    sum infinite, which lbm_read_stats reports as LBM_ENONFINITE."""
+    shape = (8, 8, 8)
+    lat = _lattice(gpu_lib, torch_cuda, shape, 0.8)
+    f = orc.init_equilibrium(shape)
+    bad = f.copy()
+    bad[5, 3, 2, 1] = np.nan
+    with pytest.raises(gpu_lib.LbmError) as e:
+        lat.set_populations(bad)
+    assert e.value.code == gpu_lib.LBM_ENONFINITE
+    assert np.abs(lat.populations() - f).max() < 1e-7
+    assert lat.step(1, 5) == gpu_lib.LBM_OK
+    assert np.isfinite(lat.stats()["mass"])
+    big = f.copy()
+    big[0, 0, 0, 0] = big[0, 0, 0, 1] = 3e38  # rest population: not streamed
+    lat.set_populations(big)
+    assert lat.step(1, 5) == gpu_lib.LBM_OK  # does not wait for the GPU
+    with pytest.raises(gpu_lib.LbmError) as e:
+        lat.stats()
+    assert e.value.code == gpu_lib.LBM_ENONFINITE
+    lat.close()

@@ -2,10 +2,16 @@
 FP32 arithmetic) against the FP64 oracle on the 64^3 downscale of the 384^3
 propeller array (216 propellers), and FP32 for reference.
 
-The bound per format follows from its unit roundoff u (FP16: 2^-11, BF16:
-2^-8): each stored deviation carries a relative error u per step; over the
-run the velocity error grows like the accumulated rounding, and the test holds
-each format to a fixed multiple of u measured on this workload.
+The bound per format is its unit roundoff u (FP16: 2^-11, BF16: 2^-8) on
+the relative L2 error of U after STEPS steps.  Each step rounds every stored
+deviation once (relative error <= u), which moves U at a cell by at most
+about u of its size; the errors do not pile up over the steps (the IBM force
+re-imposes the surface velocity every step and the relaxation damps the
+rest), and the measured error is about 0.3 u for both formats at 50 steps
+(1.5e-4 FP16, 1.2e-3 BF16), so the bound u leaves a margin of ~3.  A lost
+deviation form (storing f instead of f - t: the rounding then scales with
+t_i, ~20 times the deviations) or a biased rounding that accumulates over
+the steps breaks it.
 """
 import numpy as np
 import pytest
@@ -16,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 STEPS = 50
 # relative L2 bound on U after STEPS steps
-BOUND = {"f32": 1e-5, "f16": 40 * 2.0 ** -11, "bf16": 40 * 2.0 ** -8}
+BOUND = {"f32": 1e-5, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
 
 
 def rel_l2(a, b):
