@@ -480,26 +480,42 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
 
 
 def bench_paper_sweep(steps=200, warmup=5):
-    """The shape of the paper's own benchmark (Sec. 6): MLUPS of the coupled
-    step (5 iterations) on a 160 x 160 x 320 lattice with 1 to 6 and 18
-    rotating propellers of 3872 points each (the paper's Blender propeller,
-    not available, has 3930), FP32.  The paper's P100 figures quoted in its
-    text are given beside them for context."""
+    """The shape of the paper's own benchmark (Sec. 6, Figs. 5-6): MLUPS of
+    the coupled step (5 iterations) on a 160 x 160 x 320 lattice with 1 to 6
+    and 18 rotating propellers of 3872 points each (the paper's Blender
+    propeller, not available, has 3930), FP32, for each way of pre-computing
+    U0 before the fixed point: the active bricks (this library's default),
+    the paper's box strategy and its kernel strategy (Sec. 5).  Beside the
+    MLUPS, the device time per step of the stage that holds the U0
+    pre-computation (with the first brick pass of the fixed point).  The
+    paper's P100 figures quoted in its text are given for context."""
     import torch
     from paper_1904_02108_gb300 import binding, workload as W
     st = torch.cuda.current_stream()
+    strategies = ("bricks", "box", "kernel")
     out = {"workload": "paper_sweep_160x160x320", "cells": 160 * 160 * 320, "n_iter": 5,
            "steps": steps, "points_per_propeller": W.paper_sweep(1).props.n_points,
-           "paper_p100_mlups": {"1": 893.0, "6": 650.0, "18": 344.2}, "mlups": {}}
+           "paper_p100_mlups": {"1": 893.0, "6": 650.0, "18": 344.2},
+           "mlups": {s: {} for s in strategies}, "u0_stage_ms": {s: {} for s in strategies}}
     for n in (1, 2, 3, 4, 5, 6, 18):
         w = W.paper_sweep(n)
-        lat = binding.Lattice(w.shape, w.tau, stream=st)
-        lat.set_propellers(w.props)
-        lat.autotune(w.n_iter, 3)
-        lat.step(warmup, w.n_iter)
-        ms = _device_ms(lambda: lat.step(steps, w.n_iter), st)
-        out["mlups"][str(n)] = w.cells * steps / (ms / 1e3) / 1e6
-        lat.close()
+        shape = None
+        for strat in strategies:
+            lat = binding.Lattice(w.shape, w.tau, stream=st)
+            lat.set_u0_strategy(strat)
+            lat.set_propellers(w.props)
+            if shape is None:
+                shape = lat.autotune(w.n_iter, 3)
+            else:
+                lat.set_launch_shape(**shape)
+            lat.step(warmup, w.n_iter)
+            ms = _device_ms(lambda: lat.step(steps, w.n_iter), st)
+            out["mlups"][strat][str(n)] = w.cells * steps / (ms / 1e3) / 1e6
+            lat.enable_timing(["brick_init"])
+            lat.step(20, w.n_iter)
+            out["u0_stage_ms"][strat][str(n)] = lat.timing()["brick_init"][0] / 20
+            lat.enable_timing(False)
+            lat.close()
     return out
 
 

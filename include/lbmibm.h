@@ -186,6 +186,28 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter);
 int ibm_set_solver(lbm_t *h, int solver);
 int ibm_get_solver(const lbm_t *h);   /* -1 for NULL h */
 
+/* How U (Eq. 1) is pre-computed before the fixed point on the cells the
+ * interpolation reads (Sec. 5: U is needed only near the surfaces).
+ * LBM_U0_BRICKS (default): every cell of the 4x4x4 bricks that some point's
+ * support touches, each cell once.  LBM_U0_BOX: the paper's box strategy,
+ * every cell of each body's bounding box (the box of its points' rest
+ * positions moved by M(t), widened by the support and rounded out to whole
+ * bricks; for points without bodies, the box of their positions) into a
+ * full-lattice U, as in the paper, from which the active bricks take their
+ * cells; allocates 12 B per cell on first use and recomputes the boxes from
+ * the host positions of ibm_set_points / ibm_update_points.  LBM_U0_KERNEL:
+ * the paper's kernel strategy, the cells of every point's support (its 4 x 4
+ * x 4 taps: the fifth tap of the paper's 5 x 5 x 5 block has weight 0), a
+ * cell computed once per support that covers it.  All three give bitwise the
+ * same steps; they differ in work and memory traffic.  Single lattices only
+ * (lbm_batch_step refuses other strategies).  Not part of the saved state.
+ * Returns LBM_OK, LBM_EINVAL (NULL h, unknown strategy) or LBM_ENOMEM. */
+#define LBM_U0_BRICKS 0
+#define LBM_U0_BOX 1
+#define LBM_U0_KERNEL 2
+int lbm_set_u0_strategy(lbm_t *h, int strategy);
+int lbm_get_u0_strategy(const lbm_t *h);   /* -1 for NULL h */
+
 /* Current step counter t (completed steps); lbm_set_time overrides it. */
 int64_t lbm_time(const lbm_t *h);
 int lbm_set_time(lbm_t *h, int64_t t);

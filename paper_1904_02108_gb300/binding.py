@@ -96,6 +96,8 @@ _SIGS = {
     "lbm_set_overlap": (_i, [_p, _i]),
     "ibm_set_solver": (_i, [_p, _i]),
     "ibm_get_solver": (_i, [_p]),
+    "lbm_set_u0_strategy": (_i, [_p, _i]),
+    "lbm_get_u0_strategy": (_i, [_p]),
     "ibm_update_points": (_i, [_p, _i64, _p, _p]),
     "lbm_get_launch_shape": (_i, [_p, _p]),
     "lbm_set_launch_shape": (_i, [_p, _p]),
@@ -382,6 +384,16 @@ class Lattice:
     def solver(self):
         return {v: k for k, v in self.SOLVERS.items()}[load().ibm_get_solver(self.h)]
 
+    U0_STRATEGIES = {"bricks": 0, "box": 1, "kernel": 2}
+
+    def set_u0_strategy(self, strategy):
+        """How U0 is pre-computed before the fixed point: "bricks" (the active
+        bricks, default), "box" or "kernel" (the paper's two strategies)."""
+        self._c(load().lbm_set_u0_strategy(self.h, self.U0_STRATEGIES[strategy]))
+
+    def u0_strategy(self):
+        return {v: k for k, v in self.U0_STRATEGIES.items()}[load().lbm_get_u0_strategy(self.h)]
+
     def launch_shape(self):
         s = LaunchShape()
         self._c(load().lbm_get_launch_shape(self.h, _c.byref(s)))
@@ -502,6 +514,16 @@ class Batch:
 
     def set_graph(self, on=True):
         _check(load().lbm_batch_set_graph(self.b, int(on)))
+
+    U0_STRATEGIES = {"bricks": 0, "box": 1, "kernel": 2}
+
+    def set_u0_strategy(self, strategy):
+        """How U0 is pre-computed before the fixed point: "bricks" (the active
+        bricks, default), "box" or "kernel" (the paper's two strategies)."""
+        self._c(load().lbm_set_u0_strategy(self.h, self.U0_STRATEGIES[strategy]))
+
+    def u0_strategy(self):
+        return {v: k for k, v in self.U0_STRATEGIES.items()}[load().lbm_get_u0_strategy(self.h)]
 
     def launch_shape(self):
         s = LaunchShape()

@@ -77,6 +77,15 @@ struct lbm {
   double *xpos = nullptr;
   bool have_du = false;
   int solver = LBM_SOLVER_MDF;  // the fixed point's iteration
+  // U0 pre-computation (LBM_U0_*); the box strategy's rest-pose boxes per
+  // body (host copy, uploaded to rest_box when box_dirty) and full-lattice U
+  int u0_mode = LBM_U0_BRICKS;
+  std::vector<double> box_host;
+  std::vector<int> body_host;  // body of each point as given (empty: all 0)
+  double *rest_box = nullptr;
+  int nbox = 0, cap_box = 0;
+  bool box_dirty = false;
+  float *Ufull = nullptr;
   // the surface velocities are known not to vanish (rotating bodies, or
   // non-zero targets given to ibm_set_points): tolerance mode then needs no
   // host check of the residual denominator before iterating
@@ -260,6 +269,8 @@ void free_points(lbm_t *h) {
   h->pm.max_pairs = 0;
   dfree(h->feat);
   dfree(h->U0s);
+  dfree(h->rest_box);
+  h->cap_box = 0;
   dfree(h->Gs);
   dfree(h->res);
   dfree(h->slot_partial);
@@ -276,6 +287,31 @@ bool all_finite(const float *a, size_t n) {
   for (size_t i = 0; i < n; i++)
     if (!isfinite(a[i])) return false;
   return true;
+}
+
+// The bounding box of each body's points (their rest positions when bodies
+// rotate them, else their fixed positions): [nbox][6] = min x, y, z, max x,
+// y, z, for the box strategy of the U0 pre-computation.
+void rest_boxes(const double *X, const int *body, int64_t n, std::vector<double> &out) {
+  int nbox = 0;
+  for (int64_t k = 0; k < n; k++) nbox = std::max(nbox, (body ? body[k] : 0) + 1);
+  out.assign(6 * (size_t)nbox, 0.0);
+  for (int b = 0; b < nbox; b++)
+    for (int a = 0; a < 3; a++) {
+      out[6 * b + a] = HUGE_VAL;
+      out[6 * b + 3 + a] = -HUGE_VAL;
+    }
+  for (int64_t k = 0; k < n; k++) {
+    const int b = body ? body[k] : 0;
+    for (int a = 0; a < 3; a++) {
+      out[6 * b + a] = std::min(out[6 * b + a], X[3 * k + a]);
+      out[6 * b + 3 + a] = std::max(out[6 * b + 3 + a], X[3 * k + a]);
+    }
+  }
+  // a body index without points: an empty box at the origin
+  for (int b = 0; b < nbox; b++)
+    if (out[6 * b] > out[6 * b + 3])
+      for (int a = 0; a < 6; a++) out[6 * b + a] = 0.0;
 }
 
 }  // namespace
@@ -332,6 +368,7 @@ void lbm_destroy(lbm_t *h) {
   if (h->state_host) cudaFreeHost(h->state_host);
   dfree(h->desc);
   dfree(h->t_dev);
+  dfree(h->Ufull);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ibm_st) cudaStreamDestroy(h->ibm_st);
@@ -491,6 +528,9 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->pm.point_pairs, 8 * n));
     h->pm.max_pairs = 8 * n;
     CK(h, dalloc(&h->U0s, (size_t)ms * SLOT_FLOATS));
+    // finite from the start: the kernel strategy of the U0 pre-computation
+    // leaves the cells of an active brick outside every support as they were
+    CK(h, cudaMemset(h->U0s, 0, sizeof(float) * ms * SLOT_FLOATS));
     CK(h, dalloc(&h->Gs, (size_t)ms * SLOT_FLOATS));
     CK(h, dalloc(&h->res, ms));
     CK(h, dalloc(&h->slot_partial, (size_t)ms * 4));
@@ -501,6 +541,10 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
   h->max_body = maxb;
   h->have_du = false;
   h->desc_dirty = true;
+  if (body) h->body_host.assign(body, body + n);
+  else h->body_host.clear();
+  rest_boxes(X, body, n, h->box_host);
+  h->box_dirty = true;
   if (n > 0) {
     CK(h, cudaMemcpy(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
     std::vector<float> a(n, 1.0f);
@@ -529,6 +573,11 @@ int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_targe
   if (n == 0) return LBM_OK;
   if (!X) return fail(h, LBM_EINVAL, "X is NULL");
   CK(h, cudaMemcpyAsync(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->st));
+  if (h->u0_mode == LBM_U0_BOX) {
+    // the boxes of the moved points (bodies keep their indices)
+    rest_boxes(X, h->body_host.empty() ? nullptr : h->body_host.data(), n, h->box_host);
+    h->box_dirty = true;
+  }
   if (U_target) {
     CK(h, cudaMemcpyAsync(h->utarget, U_target, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
                           h->st));
@@ -627,6 +676,10 @@ static DomainDesc host_desc(const lbm_t *h) {
   d.state = h->state;
   d.feat = h->feat;
   d.mlp_packed = h->mlp_packed;
+  d.u0_mode = h->u0_mode;
+  d.nbox = h->nbox;
+  d.rest_box = h->rest_box;
+  d.Ufull = h->Ufull;
   return d;
 }
 
@@ -667,6 +720,7 @@ struct StepCtx {
   int storage, stats, cur;
   int warm_mode;
   int solver;  // LBM_SOLVER_*
+  int u0_mode, nbox;  // U0 pre-computation (single lattice; a batch: bricks)
   bool have_du, features;
   cudaStream_t st, sti;
   bool split;
@@ -708,7 +762,16 @@ static int enqueue_prefix(StepCtx &c, bool *warm_out) {
     StageTimer T(h, ST_PAIRS, s, 2);
     CK(h, launch_pair_lists(c.D, c.dims, s));
   }
-  {
+  if (c.u0_mode == LBM_U0_BOX) {
+    // the paper's box strategy (Sec. 5): U on each body's moved bounding
+    // box, then the active bricks' cells from it
+    StageTimer T(h, ST_INIT, s, 2);
+    CK(h, launch_box_moments(c.storage, c.D, c.nbox, c.cur, s));
+  } else if (c.u0_mode == LBM_U0_KERNEL) {
+    // the paper's kernel strategy (Sec. 5): U on every point's support
+    StageTimer T(h, ST_INIT, s, 1);
+    CK(h, launch_point_moments(c.storage, c.D, c.dims.max_points, c.cur, s));
+  } else {
     StageTimer T(h, ST_INIT, s, 1);
     CK(h, launch_brick_moments(c.storage, c.D, c.dims, c.cur, s));
   }
@@ -936,6 +999,8 @@ static StepCtx ctx_of(lbm_t *h, cudaStream_t st) {
   c.cur = h->cur;
   c.warm_mode = h->warm;
   c.solver = h->solver;
+  c.u0_mode = h->u0_mode;
+  c.nbox = h->nbox;
   c.have_du = h->have_du;
   c.features = h->features_on;
   c.st = st;
@@ -1083,6 +1148,22 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
     return fail(h, LBM_EINVAL, "points refer to body %d, only %d bodies", h->max_body, h->nb);
   if (h->warm == LBM_WARM_MLP && !h->mlp_packed && h->np > 0)
     return fail(h, LBM_EINVAL, "learned warm start without weights (mlp_set_weights)");
+  if (h->u0_mode == LBM_U0_BOX && h->box_dirty) {
+    const int nbox = (int)(h->box_host.size() / 6);
+    if (nbox > h->cap_box) {
+      CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
+      dfree(h->rest_box);
+      CK(h, dalloc(&h->rest_box, 6 * (size_t)nbox));
+      h->cap_box = nbox;
+      h->desc_dirty = true;
+    }
+    if (nbox != h->nbox) h->desc_dirty = true;
+    h->nbox = nbox;
+    if (nbox > 0)
+      CK(h, cudaMemcpyAsync(h->rest_box, h->box_host.data(), sizeof(double) * 6 * nbox,
+                            cudaMemcpyHostToDevice, h->st));
+    h->box_dirty = false;
+  }
   int r = sync_desc(h);
   if (r) return r;
   int warn = LBM_OK;
@@ -1149,6 +1230,27 @@ int ibm_set_solver(lbm_t *h, int solver) {
 }
 
 int ibm_get_solver(const lbm_t *h) { return h ? h->solver : -1; }
+
+int lbm_set_u0_strategy(lbm_t *h, int strategy) {
+  if (!h) return LBM_EINVAL;
+  if (strategy != LBM_U0_BRICKS && strategy != LBM_U0_BOX && strategy != LBM_U0_KERNEL)
+    return fail(h, LBM_EINVAL, "unknown U0 strategy %d", strategy);
+  if (h->u0_mode == strategy) return LBM_OK;
+  CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
+  if (strategy == LBM_U0_BOX && !h->Ufull) {
+    cudaError_t e = dalloc(&h->Ufull, 3 * (size_t)h->g.ncell);
+    if (e != cudaSuccess) {
+      h->Ufull = nullptr;
+      return fail(h, LBM_ENOMEM, "full-lattice U of the box strategy: %s", cudaGetErrorString(e));
+    }
+    h->box_dirty = true;
+  }
+  h->u0_mode = strategy;
+  h->desc_dirty = true;  // (a new capture)
+  return LBM_OK;
+}
+
+int lbm_get_u0_strategy(const lbm_t *h) { return h ? h->u0_mode : -1; }
 
 // ---- batches ----------------------------------------------------------------------
 
@@ -1227,6 +1329,9 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
         h->solver != h0->solver)
       return fail(h0, LBM_EINVAL, "batch handles differ in stats, warm start, features, stream, "
                                   "solver or lattice parity");
+    if (h->u0_mode != LBM_U0_BRICKS)
+      return fail(h0, LBM_EINVAL, "batches pre-compute U0 on the active bricks only "
+                                  "(lbm_set_u0_strategy)");
     if ((h->np > 0 && h->have_du) != (h0->np > 0 && h0->have_du) && h->np > 0 && h0->np > 0)
       return fail(h0, LBM_EINVAL, "batch handles differ in warm-start history");
     if (h->nb > 0 && h->max_body >= h->nb)

@@ -280,6 +280,11 @@ struct DomainDesc {
   IbmState *state;
   float *feat;
   const void *mlp_packed;
+  int u0_mode;             // LBM_U0_* of the U0 pre-computation
+  int nbox;                // bodies with a rest-pose bounding box (box mode)
+  const double *rest_box;  // [nbox][6] min x, y, z, max x, y, z of the rest
+                           // positions of each body's points
+  float *Ufull;            // [3][ncell] full-lattice U0 of the box strategy
 };
 
 // Launch shapes of the step kernels, picked by the autotuner (lbm_autotune).

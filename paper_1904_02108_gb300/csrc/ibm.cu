@@ -904,16 +904,140 @@ __global__ void __launch_bounds__(256)
     const int bx = B % g.nbx, rr = B / g.nbx;
     const int by = rr % g.nby, bz = rr / g.nby;
     const int x = bx * 4 + (t & 3), y = by * 4 + ((t >> 2) & 3), z = bz * 4 + (t >> 4);
-    float d[Q];
-    pull<S, true>(f, g, x, y, z, d);
-    float drho, jx, jy, jz;
-    moments(d, drho, jx, jy, jz);
-    const float inv = 1.f / (1.f + drho);
     float *u = U0s + (size_t)s * SLOT_FLOATS + t;
-    u[0] = jx * inv;
-    u[BRICK_CELLS] = jy * inv;
-    u[2 * BRICK_CELLS] = jz * inv;
+    cell_velocity<S, true>(f, g, x, y, z, u[0], u[BRICK_CELLS], u[2 * BRICK_CELLS]);
   });
+}
+
+// The two U0 pre-computations that the paper compares in Sec. 5, as
+// alternatives to the brick set above.
+//
+// Box strategy: U0 on every cell of each body's bounding box, the box of its
+// points' rest positions moved by the body's rigid transform M(t) (Alg. 1)
+// and widened by the support (taps floor(x) - 1 .. floor(x) + 2), rounded out
+// to whole bricks so that it holds every active brick of the body; written to
+// a full-lattice field like the paper's U, from which the active bricks take
+// their cells.  Cells where boxes overlap are computed once per box.  One
+// block row (blockIdx.y) per body, grid-stride over the box's cells, x
+// fastest.
+struct CellBox {
+  int lo[3], ext[3];
+};
+
+__device__ CellBox body_cell_box(const DomainDesc &d, int b) {
+  const double *rb = d.rest_box + 6 * b;
+  double mn[3] = {rb[0], rb[1], rb[2]}, mx[3] = {rb[3], rb[4], rb[5]};
+  if (d.nb > 0) {
+    // the rest box's corners under M(t): a rotation about z through the
+    // body's centre (Alg. 1); z is unchanged
+    const double *c = d.centre + 3 * b;
+    const double phi = d.phase[b] + d.omega[b] * (double)(*d.t);
+    double sn, cs;
+    sincos(phi, &sn, &cs);
+    double lo0 = 1e300, lo1 = 1e300, hi0 = -1e300, hi1 = -1e300;
+    for (int q = 0; q < 4; q++) {
+      const double rx = ((q & 1) ? rb[3] : rb[0]) - c[0], ry = ((q & 2) ? rb[4] : rb[1]) - c[1];
+      const double X = c[0] + (cs * rx - sn * ry), Y = c[1] + (sn * rx + cs * ry);
+      lo0 = fmin(lo0, X);
+      hi0 = fmax(hi0, X);
+      lo1 = fmin(lo1, Y);
+      hi1 = fmax(hi1, Y);
+    }
+    mn[0] = lo0;
+    mx[0] = hi0;
+    mn[1] = lo1;
+    mx[1] = hi1;
+  }
+  // cells floor(min) - 1 .. floor(max) + 2, rounded out to whole bricks (the
+  // bounds widened by 1e-6 first: a point's own rotation may round a last
+  // bit past the moved corners); the first cell wrapped into the lattice (a
+  // multiple of 4, as n is), the extent at most the lattice
+  const int n[3] = {d.g.nx, d.g.ny, d.g.nz};
+  CellBox cb;
+  for (int a = 0; a < 3; a++) {
+    const double lo = 4.0 * floor((floor(mn[a] - 1e-6) - 1.0) / 4.0);
+    const double hi = 4.0 * floor((floor(mx[a] + 1e-6) + 2.0) / 4.0) + 3.0;
+    const double w = lo - (double)n[a] * floor(lo / (double)n[a]);
+    cb.lo[a] = min((int)w, n[a] - 4);
+    cb.ext[a] = (int)fmin(hi - lo + 1.0, (double)n[a]);
+  }
+  return cb;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) box_moments_kernel(const DomainDesc *__restrict__ D,
+                                                          int cur) {
+  pdl_wait();
+  const DomainDesc &d = D[0];
+  const int b = blockIdx.y;
+  if (b >= d.nbox) return;
+  __shared__ CellBox sb;
+  if (threadIdx.x == 0) sb = body_cell_box(d, b);
+  __syncthreads();
+  const CellBox cb = sb;
+  const Geometry &g = d.g;
+  const S *__restrict__ f = (const S *)d.f[cur];
+  float *__restrict__ U = d.Ufull;
+  const size_t N = (size_t)g.ncell;
+  const int64_t cells = (int64_t)cb.ext[0] * cb.ext[1] * cb.ext[2];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % cb.ext[0]);
+    const int64_t r = i / cb.ext[0];
+    const int iy = (int)(r % cb.ext[1]), iz = (int)(r / cb.ext[1]);
+    const int x = wrapi(cb.lo[0] + ix, g.nx), y = wrapi(cb.lo[1] + iy, g.ny),
+              z = wrapi(cb.lo[2] + iz, g.nz);
+    const size_t n = ((size_t)z * g.ny + y) * g.nx + x;
+    cell_velocity<S>(f, g, x, y, z, U[n], U[N + n], U[2 * N + n]);
+  }
+}
+
+// The active bricks' U0 from the full-lattice field of the box strategy: 64
+// threads per slot.
+__global__ void __launch_bounds__(256) box_gather_kernel(const DomainDesc *__restrict__ D) {
+  pdl_wait();
+  const int t = threadIdx.x & 63, spb = blockDim.x >> 6;
+  for_each_slot<false, false>(D, nullptr, 1, blockIdx.x * spb + (threadIdx.x >> 6),
+                              gridDim.x * spb, [&](const DomainDesc &d, int s) {
+    const Geometry &g = d.g;
+    const int B = d.m.slot_brick[s];
+    const int bx = B % g.nbx, rr = B / g.nbx;
+    const int by = rr % g.nby, bz = rr / g.nby;
+    const int x = bx * 4 + (t & 3), y = by * 4 + ((t >> 2) & 3), z = bz * 4 + (t >> 4);
+    const size_t N = (size_t)g.ncell, n = ((size_t)z * g.ny + y) * g.nx + x;
+    float *u = d.U0s + (size_t)s * SLOT_FLOATS + t;
+    u[0] = d.Ufull[n];
+    u[BRICK_CELLS] = d.Ufull[N + n];
+    u[2 * BRICK_CELLS] = d.Ufull[2 * N + n];
+  });
+}
+
+// Kernel strategy: U0 on the 4 x 4 x 4 support of every point (the taps at
+// which its weights can be non-zero; the paper's 5 x 5 x 5 block adds a fifth
+// tap per axis of weight 0), 64 threads per point, written into the slots of
+// the active bricks; a cell covered by several supports is computed and
+// written once per support (the same value each time).  The other cells of
+// an active brick keep finite values of earlier steps: every pair weighs them
+// by exactly 0.
+template <typename S>
+__global__ void __launch_bounds__(256) point_moments_kernel(const DomainDesc *__restrict__ D,
+                                                            int cur) {
+  pdl_wait();
+  const DomainDesc &d = D[0];
+  const Geometry &g = d.g;
+  const S *__restrict__ f = (const S *)d.f[cur];
+  const int nact = active_slots(d.m);
+  const int t = threadIdx.x & 63, ppb = blockDim.x >> 6;
+  for (int64_t k = (int64_t)blockIdx.x * ppb + (threadIdx.x >> 6); k < d.np;
+       k += (int64_t)gridDim.x * ppb) {
+    const int4 b = d.pp.base[k];
+    const int x = wrapi(b.x - 1 + (t & 3), g.nx), y = wrapi(b.y - 1 + ((t >> 2) & 3), g.ny),
+              z = wrapi(b.z - 1 + (t >> 4), g.nz);
+    const int s = d.m.brick_slot[((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2)];
+    if (s < 0 || s >= nact) continue;
+    float *u = d.U0s + (size_t)s * SLOT_FLOATS + brick_local(x, y, z);
+    cell_velocity<S>(f, g, x, y, z, u[0], u[BRICK_CELLS], u[2 * BRICK_CELLS]);
+  }
 }
 
 
@@ -1716,6 +1840,33 @@ cudaError_t launch_pair_lists(const DomainDesc *D, const BatchDims &dims, cudaSt
 cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDims &dims, int cur,
                                  cudaStream_t st) {
   DISPATCH_STORAGE(storage, brick_moments_typed, D, dims, cur, st);
+}
+
+template <typename S>
+cudaError_t box_moments_typed(const DomainDesc *D, int nbox, int cur, cudaStream_t st) {
+  cudaError_t e = launch_pdl(box_moments_kernel<S>, dim3(std::max(1, 152 * 8 / std::max(1, nbox)),
+                                                         nbox),
+                             dim3(256), 0, st, D, cur);
+  if (e == cudaSuccess)
+    e = launch_pdl(box_gather_kernel, dim3(152 * 16), dim3(256), 0, st, D);
+  return e;
+}
+
+template <typename S>
+cudaError_t point_moments_typed(const DomainDesc *D, int64_t np, int cur, cudaStream_t st) {
+  return launch_pdl(point_moments_kernel<S>, dim3(nblk(np, 4)), dim3(256), 0, st, D, cur);
+}
+
+cudaError_t launch_box_moments(int storage, const DomainDesc *D, int nbox, int cur,
+                               cudaStream_t st) {
+  if (nbox <= 0) return cudaSuccess;
+  DISPATCH_STORAGE(storage, box_moments_typed, D, nbox, cur, st);
+}
+
+cudaError_t launch_point_moments(int storage, const DomainDesc *D, int64_t np, int cur,
+                                 cudaStream_t st) {
+  if (np <= 0) return cudaSuccess;
+  DISPATCH_STORAGE(storage, point_moments_typed, D, np, cur, st);
 }
 
 // a batch with a work list: one grid over all domains' slots

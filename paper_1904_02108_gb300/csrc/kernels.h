@@ -69,6 +69,14 @@ cudaError_t launch_pair_lists(const DomainDesc *D, const BatchDims &dims, cudaSt
 // U0 on the active bricks (pull + Eq. 1) from lattice f[cur]
 cudaError_t launch_brick_moments(int storage, const DomainDesc *D, const BatchDims &dims, int cur,
                                  cudaStream_t st);
+// The paper's two other U0 pre-computations (Sec. 5), single lattice:
+// box strategy (every cell of each body's moved bounding box into the
+// full-lattice D->Ufull, then the active bricks' cells from it; 2 launches)
+// and kernel strategy (the support of every point, 1 launch).
+cudaError_t launch_box_moments(int storage, const DomainDesc *D, int nbox, int cur,
+                               cudaStream_t st);
+cudaError_t launch_point_moments(int storage, const DomainDesc *D, int64_t np, int cur,
+                                 cudaStream_t st);
 // G_0 = 0 or S[du] (use_du), pair shares of I[U0 + G_0]
 cudaError_t launch_brick_init(const DomainDesc *D, const BatchDims &dims, int use_du,
                               cudaStream_t st);

@@ -61,5 +61,20 @@ __device__ __forceinline__ void moments(const float d[Q], float &drho, float &jx
   }
 }
 
+// U0 of Eq. 1 at cell (x, y, z) from the populations after the pull of Eq. 4:
+// the one arithmetic every U0 pre-computation uses (so that they agree
+// bitwise).
+template <typename S, bool PF = false>
+__device__ __forceinline__ void cell_velocity(const S *__restrict__ f, const Geometry &g, int x,
+                                              int y, int z, float &ux, float &uy, float &uz) {
+  float d[Q];
+  pull<S, PF>(f, g, x, y, z, d);
+  float drho, jx, jy, jz;
+  moments(d, drho, jx, jy, jz);
+  const float inv = 1.f / (1.f + drho);
+  ux = jx * inv;
+  uy = jy * inv;
+  uz = jz * inv;
+}
 
 }  // namespace lbmibm
