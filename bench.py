@@ -431,8 +431,8 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
     """ms per step when every step iterates the fixed point to eps <= tol,
     on the 256^3 propeller array: zero start, previous-force start, the
     learned start, and the previous-force start on 16-bit storage, with the
-    paper's loop ("mdf"); and the first three with conjugate gradients on the
-    same fixed point ("cg")."""
+    paper's loop ("mdf") and with conjugate gradients on the same fixed point
+    ("cg")."""
     import numpy as np
     import torch
     from paper_1904_02108_gb300 import binding, workload as W
@@ -445,7 +445,9 @@ def bench_tolerance(steps=8, warmup=3, tol=1e-4, max_iter=1000):
         variants.append(("learned_f32", "mlp", "f32", "mdf"))
     variants += [("previous_bf16", "previous", "bf16", "mdf"),
                  ("previous_f16", "previous", "f16", "mdf"),
-                 ("cg_zero_f32", "zero", "f32", "cg"), ("cg_previous_f32", "previous", "f32", "cg")]
+                 ("cg_zero_f32", "zero", "f32", "cg"), ("cg_previous_f32", "previous", "f32", "cg"),
+                 ("cg_previous_bf16", "previous", "bf16", "cg"),
+                 ("cg_previous_f16", "previous", "f16", "cg")]
     if P is not None:
         variants.append(("cg_learned_f32", "mlp", "f32", "cg"))
     out = {"tol": tol, "max_iter": max_iter, "workload": w.name, "steps": steps}

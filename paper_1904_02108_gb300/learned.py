@@ -34,9 +34,10 @@ def init_params(seed: int = 7):
 
 
 def generate(workloads, steps, tol=1e-4, max_iter=2000, samples_per_step=4096, seed=0,
-             storage="f32", skip=2):
+             storage="f32", skip=2, solver="mdf"):
     """Runs each workload for `steps` steps (tolerance mode, previous-force
-    start) and returns device tensors X [N,16], T [N,3]."""
+    start, with the paper's loop ("mdf") or conjugate gradients ("cg") on the
+    fixed point) and returns device tensors X [N,16], T [N,3]."""
     import torch
     st = torch.cuda.current_stream()
     g = torch.Generator(device="cuda")
@@ -44,7 +45,7 @@ def generate(workloads, steps, tol=1e-4, max_iter=2000, samples_per_step=4096, s
     xs, ts = [], []
     for w in workloads:
         lat = binding.Lattice(w.shape, w.tau, storage=storage, warm="previous", ibm_tol=tol,
-                              ibm_max_iter=max_iter, stream=st)
+                              ibm_max_iter=max_iter, stream=st, solver=solver)
         lat.set_propellers(w.props)
         lat.set_features(True)
         n = w.props.n_points
