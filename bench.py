@@ -424,6 +424,41 @@ def bench_batched(steps=100, warmup=4):
     batch.close()
     for lat in lats:
         lat.close()
+    out["tolerance"] = bench_batched_tolerance(doms, shape)
+    return out
+
+
+def bench_batched_tolerance(doms, shape, steps=5, warmup=3, tol=1e-4, max_iter=2000):
+    """The same 48 domains with every domain iterating the paper's loop to
+    its own eps <= tol from the previous step's force (one batch launch per
+    stage and iteration, the host reading all domains' stop flags between
+    chunks): ms per step and the iterations the domains took."""
+    import numpy as np
+    import torch
+    from paper_1904_02108_gb300 import binding
+    st = torch.cuda.current_stream()
+    lats = []
+    for w in doms:
+        lat = binding.Lattice(w.shape, w.tau, warm="previous", ibm_tol=tol, ibm_max_iter=max_iter,
+                              stream=st)
+        lat.set_propellers(w.props)
+        lats.append(lat)
+    batch = binding.Batch(lats)
+    batch.set_launch_shape(**shape)
+    batch.step(warmup, 0)
+    t_ms, its, capped = 0.0, [], 0
+    for _ in range(steps):
+        t_ms += _device_ms(lambda: batch.step(1, 0), st)
+        it = [lat.stats()["last_ibm_iters"] for lat in lats]
+        its.append(it)
+        capped += sum(int(lat.stats()["last_residual"] > tol) for lat in lats)
+    its = np.array(its)
+    out = {"tol": tol, "solver": "mdf", "start": "previous", "steps": steps,
+           "ms_per_step": t_ms / steps, "iters_mean": float(its.mean()),
+           "iters_max_per_step": float(its.max(axis=1).mean()), "capped_domain_steps": capped}
+    batch.close()
+    for lat in lats:
+        lat.close()
     return out
 
 

@@ -334,8 +334,14 @@ int lbm_set_graph(lbm_t *h, int on);
  * The handles stay owned by the caller and must not be destroyed before the
  * batch; they must share the storage format, the stats option, the warm-start
  * mode and history, the stream, and be at the same lattice parity (created
- * together or stepped together).  lbm_batch_step needs n_ibm_iter > 0;
- * results are read through the individual handles. */
+ * together or stepped together).  Results are read through the individual
+ * handles.  n_ibm_iter > 0: that many fixed-point iterations in every
+ * domain.  n_ibm_iter == 0 (the paper's loop only, every handle with the
+ * same ibm_tol and ibm_max_iter): every domain iterates until its own
+ * residual meets ibm_tol or the cap, exactly the iterations it would take
+ * alone (lbm_read_residuals and lbm_read_stats per handle); returns
+ * LBM_WNOTCONVERGED if a domain hit the cap.  Captured graphs are used for
+ * fixed counts only. */
 typedef struct lbm_batch lbm_batch_t;
 int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out);
 int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter);

@@ -1317,13 +1317,105 @@ int lbm_batch_set_graph(lbm_batch_t *b, int on) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+// The tolerance-driven fixed point for a batch (the paper's loop): every
+// domain iterates until its own eps <= ibm_tol or ibm_max_iter (the kernels
+// of a converged domain return at once, so each domain's iterations are
+// those it would take alone), the host reading all domains' stop flags after
+// each chunk.  Returns LBM_WNOTCONVERGED when a domain hit the cap.
+static int batch_tolerance_loop(lbm_batch_t *b, StepCtx &c, bool warm) {
+  lbm_t *h0 = c.acct;
+  cudaStream_t st = c.sti;
+  bool moving = true;
+  int hint = 0;
+  for (lbm_t *h : b->hs) {
+    if (h->np > 0 && !(h->nb > 0 ? h->bodies_moving : h->targets_nonzero)) moving = false;
+    hint = std::max(hint, h->tol_hint);
+  }
+  auto read_states = [&]() -> int {
+    for (lbm_t *h : b->hs)
+      if (h->np > 0)
+        CK(h0, cudaMemcpyAsync(h->state_host, h->state, 64, cudaMemcpyDeviceToHost, st));
+    CK(h0, cudaStreamSynchronize(st));
+    return LBM_OK;
+  };
+  {
+    // denominators ||S[s u_k]||^2 of every domain
+    StageTimer T(h0, ST_RESID, st, 2);
+    CK(h0, launch_brick_norm(c.D, c.dims, 0, st));
+    CK(h0, launch_ibm_den(c.D, c.dims, moving ? 2 : 0, st));
+  }
+  if (!moving) {
+    int r = read_states();
+    if (r) return r;
+    bool zero = false;
+    for (lbm_t *h : b->hs) zero = zero || (h->np > 0 && h->state_host->den2 == 0.0);
+    if (zero) {
+      // the fallback denominators ||S[s (u_k - I[U0])]||^2; domains whose
+      // first denominator is non-zero keep it (ibm_den mode 1)
+      StageTimer T(h0, ST_RESID, st, warm ? 5 : 3);
+      if (warm) CK(h0, launch_brick_init(c.D, c.dims, 0, st));
+      CK(h0, launch_point_residual0(c.D, c.dims, st));
+      CK(h0, launch_brick_norm(c.D, c.dims, 1, st));
+      CK(h0, launch_ibm_den(c.D, c.dims, 1, st));
+      if (warm) CK(h0, launch_brick_init(c.D, c.dims, 1, st));
+    }
+  }
+  int it = 0;
+  const int max_iter = h0->max_iter;
+  while (it < max_iter) {
+    const int left = hint - it;
+    const int chunk = std::min(left > 0 ? std::max(kCheckChunk, left / 2) : kCheckChunk,
+                               max_iter - it);
+    for (int j = 0; j < chunk; j++, it++) {
+      {
+        StageTimer T(h0, ST_UPDATE, st);
+        CK(h0, launch_point_update(c.D, c.dims, it == 0, warm, 1, st));
+      }
+      {
+        StageTimer T(h0, ST_SPREAD, st);
+        CK(h0, launch_brick_spread(c.D, c.dims, 1, 1, st));
+      }
+      {
+        StageTimer T(h0, ST_RESID, st);
+        CK(h0, launch_ibm_check(c.D, c.dims, it, h0->tol, max_iter, st));
+      }
+    }
+    int r = read_states();
+    if (r) return r;
+    bool all = true;
+    for (lbm_t *h : b->hs) all = all && (h->np == 0 || h->state_host->done);
+    if (all) break;
+  }
+  int warn = LBM_OK;
+  for (lbm_t *h : b->hs) {
+    if (h->np == 0) continue;
+    h->last_iters = h->state_host->iters;
+    h->tol_hint = h->last_iters;
+    h->last_eps = h->state_host->last_eps;
+    if (h->state_host->capped) {
+      h->not_converged++;
+      warn = LBM_WNOTCONVERGED;
+    }
+  }
+  return warn;
+}
+
+extern "C" {
+
 int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
   if (!b) return LBM_EINVAL;
   lbm_t *h0 = b->hs[0];
-  if (n_steps < 0 || n_ibm_iter <= 0)
-    return fail(h0, LBM_EINVAL, "batch steps need n_steps >= 0 and n_ibm_iter > 0");
+  if (n_steps < 0 || n_ibm_iter < 0)
+    return fail(h0, LBM_EINVAL, "batch steps need n_steps >= 0 and n_ibm_iter >= 0");
+  if (n_ibm_iter == 0 && h0->solver != LBM_SOLVER_MDF)
+    return fail(h0, LBM_EINVAL, "a batch iterates to the residual target with the paper's loop "
+                                "only (ibm_set_solver)");
   // uniform host-side decisions
   for (lbm_t *h : b->hs) {
+    if (n_ibm_iter == 0 && (h->tol != h0->tol || h->max_iter != h0->max_iter))
+      return fail(h0, LBM_EINVAL, "batch handles differ in ibm_tol or ibm_max_iter");
     if (h->stats_on != h0->stats_on || h->warm != h0->warm ||
         h->features_on != h0->features_on || h->cur != h0->cur || h->st != h0->st ||
         h->solver != h0->solver)
@@ -1377,10 +1469,11 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
   c.have_du = have_du;
   c.features = h0->features_on;
   int s = 0;
+  int warn = LBM_OK;
   while (s < n_steps) {
     c.cur = h0->cur;
     const bool steady = have_du || dims.max_points == 0;
-    if (b->graph_on && steady && n_steps - s >= 2) {
+    if (b->graph_on && steady && n_steps - s >= 2 && n_ibm_iter > 0) {
       if (!b->gexec || b->g_iters != n_ibm_iter || b->g_cur != c.cur || b->g_version != ver) {
         int r = ensure_capture_stream(h0, &b->cap_stream, &b->ev_in, &b->ev_out);
         if (r) return r;
@@ -1405,14 +1498,26 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
     c.split = false;
     int r = ensure_split(h0, c, false);
     if (r) return r;
-    r = enqueue_step(c, n_ibm_iter);
+    if (n_ibm_iter == 0 && dims.max_points > 0) {
+      r = enqueue_head(c);
+      if (r) return r;
+      bool warm = false;
+      r = enqueue_prefix(c, &warm);
+      if (r) return r;
+      const int w = batch_tolerance_loop(b, c, warm);
+      if (w < 0) return w;
+      if (w == LBM_WNOTCONVERGED) warn = w;
+      r = enqueue_suffix(c);
+    } else {
+      r = enqueue_step(c, n_ibm_iter);
+    }
     if (r) return r;
     for (lbm_t *h : b->hs) after_step(h, n_ibm_iter);
     have_du = have_du || dims.max_points > 0;
     c.have_du = have_du;
     s++;
   }
-  return LBM_OK;
+  return warn;
 }
 
 }  // extern "C"

@@ -1124,8 +1124,9 @@ __global__ void __launch_bounds__(32, 32)
   pdl_wait();
   __shared__ BrickSmem sm;
   if constexpr (WL) {
-    // (the tolerance mode runs single lattices only)
+    // (tolerance mode: the bricks of a domain that has converged are skipped)
     for_each_slot<true, true>(D, off, nd, blockIdx.x, gridDim.x, [&](const DomainDesc &d, int s) {
+      if (tol_mode && d.state->done) return;
       spread_brick(sm, d.pm, d.du, d.U0s, d.Gs, tol_mode ? d.res : nullptr, s, do_interp);
     });
   } else {
@@ -1245,6 +1246,7 @@ __global__ void __launch_bounds__(256) ibm_den_kernel(const DomainDesc *__restri
                                                        int mode) {
   pdl_wait();
   const DomainDesc &d = D[blockIdx.y];
+  if (d.np == 0) return;  // (a domain of a batch without points)
   IbmState *st = d.state;
   double v;
   if (!res_sum(d.m, d.res, st, &v)) return;
@@ -1264,6 +1266,7 @@ __global__ void __launch_bounds__(256) ibm_check_kernel(const DomainDesc *__rest
                                                          double tol, int max_iter) {
   pdl_wait();
   const DomainDesc &d = D[blockIdx.y];
+  if (d.np == 0) return;  // (a domain of a batch without points)
   IbmState *st = d.state;
   if (st->done) return;
   double v;

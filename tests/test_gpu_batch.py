@@ -87,8 +87,60 @@ def test_batch_rejects_mismatched_handles(gpu_lib, torch_cuda):
     batch = gpu_lib.Batch([a, c])
     with pytest.raises(gpu_lib.LbmError):
         batch.step(1, 5)  # warm-start modes differ
-    with pytest.raises(gpu_lib.LbmError):
-        batch.step(1, 0)  # tolerance mode needs a single lattice
     batch.close()
-    for lat in (a, b, c):
+    # tolerance mode: the paper's loop only, one residual target for all
+    d = _make(gpu_lib, torch, specs[0], warm="previous", solver="cg")
+    e = _make(gpu_lib, torch, specs[1], warm="previous", solver="cg")
+    batch = gpu_lib.Batch([d, e])
+    with pytest.raises(gpu_lib.LbmError):
+        batch.step(1, 0)
+    batch.close()
+    f = _make(gpu_lib, torch, specs[0], warm="previous", ibm_tol=1e-3)
+    g = _make(gpu_lib, torch, specs[1], warm="previous", ibm_tol=2e-3)
+    batch = gpu_lib.Batch([f, g])
+    with pytest.raises(gpu_lib.LbmError):
+        batch.step(1, 0)
+    batch.close()
+    for lat in (a, b, c, d, e, f, g):
+        lat.close()
+
+
+@pytest.mark.parametrize("warm,tol", [("previous", 2e-3), ("zero", 0.05)])
+def test_batch_tolerance_mode_is_bitwise_per_lattice_stepping(gpu_lib, torch_cuda, warm, tol):
+    """Every domain of a batch iterates the paper's loop to its own residual
+    target (the domains need different counts): the same iteration counts,
+    residual histories and bitwise the same states as each lattice stepped
+    alone in tolerance mode; an empty domain and the cap warning included."""
+    torch = torch_cuda
+    specs = _domains()
+    kw = dict(warm=warm, ibm_tol=tol, ibm_max_iter=3000)
+    single = [_make(gpu_lib, torch, s, **kw) for s in specs]
+    batched = [_make(gpu_lib, torch, s, **kw) for s in specs]
+    batch = gpu_lib.Batch(batched)
+    counts = []
+    for _ in range(3):
+        for lat in single:
+            assert lat.step(1, 0) == gpu_lib.LBM_OK
+        assert batch.step(1, 0) == gpu_lib.LBM_OK
+        for s, b in zip(single, batched):
+            assert s.stats()["last_ibm_iters"] == b.stats()["last_ibm_iters"]
+            if s.np:
+                assert np.array_equal(s.residuals(), b.residuals())
+        counts.append([b.stats()["last_ibm_iters"] for b in batched if b.np])
+    for s, b in zip(single, batched):
+        assert np.array_equal(s.populations(), b.populations())
+        assert s.stats()["mass"] == b.stats()["mass"]
+        if s.np:
+            assert np.array_equal(s.points()[2], b.points()[2])
+    assert any(len(set(c)) > 1 for c in counts), counts  # the domains differ
+    # a fixed-count batch step afterwards, and the cap
+    assert batch.step(1, 5) == gpu_lib.LBM_OK
+    batch.close()
+    capped = [_make(gpu_lib, torch, s, warm=warm, ibm_tol=1e-12, ibm_max_iter=9)
+              for s in specs]
+    batch = gpu_lib.Batch(capped)
+    assert batch.step(1, 0) == gpu_lib.LBM_WNOTCONVERGED
+    assert [c.stats()["last_ibm_iters"] for c in capped if c.np] == [9, 9]
+    batch.close()
+    for lat in single + batched + capped:
         lat.close()
