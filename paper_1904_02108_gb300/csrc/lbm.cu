@@ -290,6 +290,206 @@ __global__ void __launch_bounds__(256)
   collide_pairs16<S, STATS>(D[blockIdx.y], cur);
 }
 
+// 16-bit storage, single lattice: the pulls staged in shared memory by the
+// bulk-copy engine.  A tile is R consecutive rows (y) of one z plane, whole
+// rows in x; for each population the R source rows (the tile's rows shifted by
+// -e_y, -e_z, wrapped) arrive as at most two contiguous bulk copies
+// (cp.async.bulk, global -> shared, completing on the stage's mbarrier).  A
+// persistent grid walks the tiles with NS stages in flight per block, so the
+// loads need no registers and overlap the arithmetic of earlier tiles.  Each
+// thread takes two x-neighbouring cells exactly as collide_pairs16 does (the
+// same words, the same collide_math, the same warps of 64 cells and the same
+// FP64 partial per 128 cells), so the results are bitwise those of
+// collide_pairs16.  Needs nx % 8 == 0 (16-byte rows), ny % R == 0 and R nx a
+// multiple of 128 (a tile holds whole partials); the launcher checks.  Every
+// wait is bounded: a stage that does not arrive within ROWS_SPIN_LIMIT polls
+// sets bit 8 of the error flags, the block drains its other copies (bounded
+// again) and returns.
+constexpr unsigned ROWS_SPIN_LIMIT = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// true once the phase of parity `phase` has completed; false after
+// ROWS_SPIN_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase) {
+  for (unsigned i = 0; i < ROWS_SPIN_LIMIT; i++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct RowsTiling {
+  int R;            // rows per tile
+  int NS;           // stages
+  int tiles;        // nz * ny / R
+  int stage_bytes;  // 19 R nx 2
+};
+
+// Issues the copies of tile t into stage buffer `buf` (one thread).
+__device__ __forceinline__ void rows_issue(const uint16_t *__restrict__ f, const Geometry &g,
+                                           int R, int t, unsigned char *buf, uint64_t *bar,
+                                           unsigned stage_bytes) {
+  const int ny = g.ny, nx = g.nx;
+  const int z = t / (ny / R), y0 = (t - z * (ny / R)) * R;
+  const size_t N = (size_t)g.ncell;
+  const unsigned rowb = (unsigned)nx * 2u;
+  mbar_expect_tx(bar, stage_bytes);
+#pragma unroll 1
+  for (int i = 0; i < Q; i++) {
+    const int zs = wrapi(z - ez(i), g.nz);
+    const int ya = wrapi(y0 - ey(i), ny);
+    const int first = min(R, ny - ya);  // rows before the y seam
+    unsigned char *d = buf + (size_t)i * R * rowb;
+    const uint16_t *src = f + (size_t)i * N + ((size_t)zs * ny + ya) * nx;
+    bulk_g2s(d, src, (unsigned)first * rowb, bar);
+    if (first < R)
+      bulk_g2s(d + (size_t)first * rowb, f + (size_t)i * N + (size_t)zs * ny * nx,
+               (unsigned)(R - first) * rowb, bar);
+  }
+}
+
+template <typename S, bool STATS>
+__global__ void __launch_bounds__(384, 2)
+    collide_rows16_kernel(const __grid_constant__ DomainDesc dd, int cur, RowsTiling tl) {
+  pdl_wait();
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smraw);
+  unsigned char *stages = smraw + 128;
+  __shared__ double red[16][4];
+  const Geometry g = dd.g;
+  const int nx = g.nx, R = tl.R, NS = tl.NS;
+  const uint16_t *__restrict__ f = (const uint16_t *)dd.f[cur];
+  uint32_t *__restrict__ dst = (uint32_t *)dd.f[cur ^ 1];
+  const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
+  const float *__restrict__ Gs = dd.Gs;
+  const unsigned rowb = (unsigned)nx * 2u;
+  const size_t NW = (size_t)g.ncell >> 1;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NS; q++) mbar_init(bars + q, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int q = 0; q < NS; q++) {
+      const int t = blockIdx.x + q * gridDim.x;
+      if (t < tl.tiles)
+        rows_issue(f, g, R, t, stages + (size_t)q * tl.stage_bytes, bars + q,
+                   (unsigned)tl.stage_bytes);
+    }
+  const int hw = nx >> 1;
+  const int r = threadIdx.x / hw, j = threadIdx.x - r * hw;  // row, word of this thread
+  const int x = 2 * j;
+  const uint32_t wl = j == 0 ? hw - 1 : j - 1, wr = j == hw - 1 ? 0 : j + 1;
+  int k = 0;
+  for (int t = blockIdx.x; t < tl.tiles; t += gridDim.x, k++) {
+    const int q = k % NS;
+    const bool ok = mbar_wait(bars + q, (unsigned)(k / NS) & 1u);
+    if (!__syncthreads_and(ok)) {
+      // a stage that never arrived: flag it, let the other copies land, leave
+      if (threadIdx.x == 0) {
+        atomicOr(dd.m.counters + 5, 8);
+        for (int p = 1; p < NS; p++) {
+          const int kk = k + p;
+          if (blockIdx.x + kk * gridDim.x < tl.tiles) mbar_wait(bars + kk % NS, (kk / NS) & 1u);
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    const int z = t / (g.ny / R), y = (t - z * (g.ny / R)) * R + r;
+    const unsigned char *buf = stages + (size_t)q * tl.stage_bytes;
+    float Ga[3] = {dd.gbody[0], dd.gbody[1], dd.gbody[2]};
+    float Gb[3] = {Ga[0], Ga[1], Ga[2]};
+    if (brick_slot) {
+      const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
+      const int sl = __ldg(brick_slot + b);
+      if (sl >= 0) {
+        const float *p = Gs + (size_t)sl * SLOT_FLOATS + brick_local(x, y, z);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          Ga[c] += __ldg(p + c * BRICK_CELLS);
+          Gb[c] += __ldg(p + c * BRICK_CELLS + 1);
+        }
+      }
+    }
+    float da[Q], db[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const uint32_t *row = (const uint32_t *)(buf + ((size_t)i * R + r) * rowb);
+      if (ex(i) == 0) {
+        const uint32_t w = row[j];
+        da[i] = Word16<S>::lo(w);
+        db[i] = Word16<S>::hi(w);
+      } else if (ex(i) > 0) {
+        da[i] = Word16<S>::hi(row[wl]);
+        db[i] = Word16<S>::lo(row[j]);
+      } else {
+        da[i] = Word16<S>::hi(row[j]);
+        db[i] = Word16<S>::lo(row[wr]);
+      }
+    }
+    // every thread has read stage q: it may be refilled
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int tn = t + NS * gridDim.x;
+      if (tn < tl.tiles) rows_issue(f, g, R, tn, (unsigned char *)buf, bars + q, (unsigned)tl.stage_bytes);
+    }
+    float dna[Q], dnb[Q], sta[4], stb[4];
+    collide_math(da, Ga[0], Ga[1], Ga[2], dd.tau, dna, sta);
+    collide_math(db, Gb[0], Gb[1], Gb[2], dd.tau, dnb, stb);
+    const size_t cell0 = ((size_t)z * g.ny + (y - r)) * nx;  // first cell of the tile
+    const uint32_t wn = (uint32_t)((cell0 >> 1) + threadIdx.x);
+#pragma unroll
+    for (int i = 0; i < Q; i++) dst[(size_t)i * NW + wn] = Word16<S>::pack(dna[i], dnb[i]);
+    if (STATS) {
+      float sv[4];
+      for (int c = 0; c < 4; c++) sv[c] = sta[c] + stb[c];
+      const float ws = warp_sum4_split(sv);
+      // a warp covers 64 cells: one partial per PARTIAL_CELLS = two warps
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      if ((lane & 7) == 0) red[w][lane >> 3] = ws;
+      __syncthreads();
+      const int groups = blockDim.x / (PARTIAL_CELLS / 2);
+      if ((int)threadIdx.x < 4 * groups) {
+        const int gi = threadIdx.x >> 2, c = threadIdx.x & 3;
+        const double a = red[2 * gi][c] + red[2 * gi + 1][c];
+        const int64_t pidx = (int64_t)(cell0 / PARTIAL_CELLS) + gi;
+        if (pidx < dd.cblocks) dd.partial[(size_t)pidx * 4 + c] = a;
+      }
+      __syncthreads();  // (red is reused by the next tile)
+    }
+  }
+}
+
 // The cells of the active bricks, after the IBM loop: 64 threads per slot
 // (one per cell), four slots per block, grid-stride over the slots; the same
 // per-cell arithmetic as collide_stream_cells with G = body force + the
@@ -517,6 +717,51 @@ inline unsigned cell_blocks(const Geometry &g, int threads) {
   return (unsigned)((g.ncell + threads - 1) / threads);
 }
 
+// Tiling of the staged 16-bit collide: R the largest divisor of ny with
+// R nx / 2 <= 384 threads (two blocks of at most 85 registers per thread on
+// an SM) and R nx a multiple of 128 cells; three stages when they fit in
+// ~112 KB (two blocks per SM), else two within 200 KB.  False when no tiling
+// applies (the two-cell kernel runs instead).
+bool rows_tiling(const Geometry &g, RowsTiling &tl) {
+  if (g.nx % 8 || g.nx / 2 > 384) return false;
+  int R = 0;
+  for (int r = 1; r <= g.ny && r * g.nx / 2 <= 384; r++)
+    if (g.ny % r == 0 && (r * g.nx) % 128 == 0) R = r;
+  if (!R || (R * g.nx / 2) % 32) return false;
+  const int stage = Q * R * g.nx * 2;
+  int NS = 3;
+  if (NS * stage + 128 > 112 * 1024) NS = 2;
+  if (NS * stage + 128 > 200 * 1024) return false;
+  tl.R = R;
+  tl.NS = NS;
+  tl.tiles = g.nz * (g.ny / R);
+  tl.stage_bytes = stage;
+  return true;
+}
+
+template <typename S, bool STATS>
+cudaError_t launch_rows16(const DomainDesc &dd, int cur, const RowsTiling &tl, cudaStream_t st) {
+  const size_t smem = 128 + (size_t)tl.NS * tl.stage_bytes;
+  const int threads = tl.R * dd.g.nx / 2;
+  static size_t set_for = 0;  // (the attribute is per kernel instantiation)
+  if (smem > set_for) {
+    cudaError_t e = cudaFuncSetAttribute(collide_rows16_kernel<S, STATS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    set_for = smem;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, collide_rows16_kernel<S, STATS>, threads, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(tl.tiles, std::max(1, per_sm) * sms));
+  return launch_pdl(collide_rows16_kernel<S, STATS>, dim3(grid), dim3(threads), smem, st, dd, cur,
+                    tl);
+}
+
 template <typename S>
 cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const BatchDims &dims,
                           int cur, int stats, int skip_active, cudaStream_t st) {
@@ -530,6 +775,11 @@ cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const Ba
   if (skip_active) return stats ? LBM_COLLIDE(true, true) : LBM_COLLIDE(false, true);
 #undef LBM_COLLIDE
   if constexpr (sizeof(S) == 2) {
+    // a single lattice whose rows tile: pulls staged by bulk copies
+    RowsTiling tl{};
+    if (dims.nd == 1 && Dhost && rows_tiling(Dhost->g, tl))
+      return stats ? launch_rows16<S, true>(*Dhost, cur, tl, st)
+                   : launch_rows16<S, false>(*Dhost, cur, tl, st);
     // two cells per thread (nx is a multiple of 4)
     const dim3 grid2((unsigned)((dims.max_cells + 2 * bs - 1) / (2 * bs)), dims.nd);
 #define LBM_PAIRS(ST)                                                                     \

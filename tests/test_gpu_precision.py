@@ -77,3 +77,46 @@ def test_roundtrip_rounds_deviations_to_nearest(gpu_lib, orc, storage, u):
     tiny = (6e-8 if storage == "f16" else 0.0) + 2.0 ** -24 * 0.34
     assert np.all(np.abs(d - dev) <= u * np.abs(dev) + tiny)
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("case", ["single_propeller_32", "propeller_array_64", "box_48x64x80"])
+def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, case):
+    """A single lattice with 16-bit storage collides with the staged kernel
+    (rows of the pulls brought into shared memory by bulk copies), a batch
+    with the two-cell kernel; both use the same per-cell arithmetic and the
+    same partial sums, so populations and FP64 sums must agree bitwise.  The
+    shapes cover tiles of 16, 8 and 16 rows, the y and z seams and a lattice
+    whose rows are not a power of two."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if case == "single_propeller_32":
+        w = W.single_propeller(21)
+        shape, props = w.shape, w.props
+    elif case == "propeller_array_64":
+        w = W.dense_array_64()
+        shape, props = w.shape, w.props
+    else:
+        shape = (80, 64, 48)
+        props = W.propellers([(20.0, 30.0, 40.0), (30.0, 12.0, 70.0)], 10.0, 3.0, 0.05,
+                             [0.4, 2.2])
+    st = torch.cuda.current_stream()
+    a = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
+    b = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
+    rng = W.SplitMix64(22)
+    f0 = orc.init_equilibrium(shape, 1 + 0.01 * W.random_array(rng, shape),
+                              0.02 * W.random_array(rng, (3,) + shape))
+    for lat in (a, b):
+        lat.set_propellers(props)
+        lat.set_populations(f0)
+    batch = gpu_lib.Batch([b])
+    for _ in range(3):
+        a.step(1, 5)
+        batch.step(1, 5)
+    assert np.array_equal(a.deviations(), b.deviations())
+    sa, sb = a.stats(), b.stats()
+    assert sa["mass"] == sb["mass"] and sa["momentum"] == sb["momentum"]
+    batch.close()
+    a.close()
+    b.close()
