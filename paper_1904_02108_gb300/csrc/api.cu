@@ -644,6 +644,7 @@ static DomainDesc host_desc(const lbm_t *h) {
   d.delta = h->delta;
   d.np = (int)h->np;
   d.tau = (float)h->tau;
+  d.om = 1.0f / d.tau;
   for (int c = 0; c < 3; c++) d.gbody[c] = (float)h->gbody[c];
   d.f[0] = h->f[0];
   d.f[1] = h->f[1];

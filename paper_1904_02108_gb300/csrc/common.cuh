@@ -252,6 +252,7 @@ struct DomainDesc {
   int delta;          // weighting function
   int np;             // Lagrangian points
   float tau;
+  float om;           // 1 / tau (FP32, rounded to nearest)
   float gbody[3];
   void *f[2];         // the two population lattices
   int64_t *t;         // device step counter

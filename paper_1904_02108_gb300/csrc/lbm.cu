@@ -20,39 +20,119 @@ namespace lbmibm {
 
 namespace {
 
-// The collision of one cell from its pulled deviations d (Eq. 4): Eq. 1
-// moments, U^G = U + tau G (Sec. 2 step 3) and the BGK relaxation towards
-// Eq. 3, into dn.  G is the cell's force (body force plus its brick's IBM
-// force).  st receives the cell's post-collision mass and momentum sums (the
-// collision conserves mass and adds rho G of momentum, Eqs. 2-3, so they
-// follow from the moments).
-__device__ __forceinline__ void collide_math(const float d[Q], float Gx, float Gy, float Gz,
-                                             float tau, float dn[Q], float st[4]) {
-  float drho, jx, jy, jz;
-  moments(d, drho, jx, jy, jz);
-  const float rho = 1.f + drho;
-  const float inv = 1.f / rho;
-  const float ux = jx * inv + tau * Gx;
-  const float uy = jy * inv + tau * Gy;
-  const float uz = jz * inv + tau * Gz;
-  const float om = 1.f / tau;
+// Arithmetic of the collision on one cell (float) or on two cells at once
+// (float2, the packed FP32 instructions of this architecture): every operation
+// is written out with explicit rounding (no contraction or reordering by the
+// compiler), and each packed operation computes exactly the scalar one in
+// each lane, so one-cell and two-cell kernels give bitwise the same values.
+template <typename V>
+__device__ __forceinline__ V vsplat(float a);
+template <>
+__device__ __forceinline__ float vsplat<float>(float a) {
+  return a;
+}
+template <>
+__device__ __forceinline__ float2 vsplat<float2>(float a) {
+  return make_float2(a, a);
+}
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vrcp(float a) { return __fdiv_rn(1.f, a); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));  // (x - y is x + (-y) exactly)
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vrcp(float2 a) {
+  return make_float2(__fdiv_rn(1.f, a.x), __fdiv_rn(1.f, a.y));
+}
+
+// The collision of one cell (V = float) or of two cells (V = float2) from its
+// pulled deviations d (Eq. 4): Eq. 1 moments, U^G = U + tau G (Sec. 2 step 3)
+// and the BGK relaxation towards Eq. 3 (om = 1 / tau), into dn.  G is the
+// cell's force (body force plus its brick's IBM force).  st receives the
+// cell's post-collision mass and momentum sums (the collision conserves mass
+// and adds rho G of momentum, Eqs. 2-3, so they follow from the moments).
+template <typename V>
+__device__ __forceinline__ void collide_core(const V d[Q], V Gx, V Gy, V Gz, float tau,
+                                             float om, V dn[Q], V st[4]) {
+  // Eq. 1 in deviation form, the sums in index order
+  V drho = d[0], jx = vsplat<V>(0.f), jy = vsplat<V>(0.f), jz = vsplat<V>(0.f);
+#pragma unroll
+  for (int i = 1; i < Q; i++) {
+    drho = vadd(drho, d[i]);
+    if (ex(i)) jx = ex(i) > 0 ? vadd(jx, d[i]) : vsub(jx, d[i]);
+    if (ey(i)) jy = ey(i) > 0 ? vadd(jy, d[i]) : vsub(jy, d[i]);
+    if (ez(i)) jz = ez(i) > 0 ? vadd(jz, d[i]) : vsub(jz, d[i]);
+  }
+  const V rho = vadd(vsplat<V>(1.f), drho);
+  const V inv = vrcp(rho);
+  const V vt = vsplat<V>(tau);
+  const V ux = vfma(vt, Gx, vmul(jx, inv));
+  const V uy = vfma(vt, Gy, vmul(jy, inv));
+  const V uz = vfma(vt, Gz, vmul(jz, inv));
+  st[0] = drho;
+  st[1] = vfma(rho, Gx, jx);
+  st[2] = vfma(rho, Gy, jy);
+  st[3] = vfma(rho, Gz, jz);
+  const V vom = vsplat<V>(om);
   // Eq. 3 minus t_i: t_i (c0 + rho (3 e.u + 4.5 (e.u)^2)) with c0 the part
   // common to every direction; opposite directions share 4.5 rho (e.u)^2
-  const float c0 = drho - 1.5f * rho * (ux * ux + uy * uy + uz * uz);
-  const float r3 = 3.f * rho, r45 = 4.5f * rho;
-  dn[0] = d[0] + om * (wt(0) * c0 - d[0]);
+  const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
+  const V c0 = vfma(vmul(vsplat<V>(-1.5f), rho), usq, drho);
+  const V r3 = vmul(vsplat<V>(3.f), rho), r45 = vmul(vsplat<V>(4.5f), rho);
+  dn[0] = vfma(vom, vsub(vmul(vsplat<V>(wt(0)), c0), d[0]), d[0]);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
-    const float eu = (float)ex(i) * ux + (float)ey(i) * uy + (float)ez(i) * uz;
-    const float sym = c0 + r45 * eu * eu, anti = r3 * eu;
-    const float eqp = wt(i) * (sym + anti), eqm = wt(i) * (sym - anti);
-    dn[i] = d[i] + om * (eqp - d[i]);
-    dn[i + 1] = d[i + 1] + om * (eqm - d[i + 1]);
+    // e_i . u with the components of e_i in {-1, 0, 1}
+    V eu = vsplat<V>(0.f);
+    bool first = true;
+    const V uc[3] = {ux, uy, uz};
+    const int ec[3] = {ex(i), ey(i), ez(i)};
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      if (!ec[c]) continue;
+      if (first) eu = ec[c] > 0 ? uc[c] : vsub(vsplat<V>(0.f), uc[c]);
+      else eu = ec[c] > 0 ? vadd(eu, uc[c]) : vsub(eu, uc[c]);
+      first = false;
+    }
+    const V sym = vfma(r45, vmul(eu, eu), c0), anti = vmul(r3, eu);
+    const V w = vsplat<V>(wt(i));
+    const V eqp = vmul(w, vadd(sym, anti)), eqm = vmul(w, vsub(sym, anti));
+    dn[i] = vfma(vom, vsub(eqp, d[i]), d[i]);
+    dn[i + 1] = vfma(vom, vsub(eqm, d[i + 1]), d[i + 1]);
   }
-  st[0] = drho;
-  st[1] = jx + rho * Gx;
-  st[2] = jy + rho * Gy;
-  st[3] = jz + rho * Gz;
+}
+
+__device__ __forceinline__ void collide_math(const float d[Q], float Gx, float Gy, float Gz,
+                                             float tau, float om, float dn[Q], float st[4]) {
+  collide_core<float>(d, Gx, Gy, Gz, tau, om, dn, st);
+}
+
+// Two cells a, b at once with the packed instructions; bitwise two calls of
+// collide_math.
+__device__ __forceinline__ void collide_math2(const float da[Q], const float db[Q],
+                                              const float Ga[3], const float Gb[3], float tau,
+                                              float om, float dna[Q], float dnb[Q], float sta[4],
+                                              float stb[4]) {
+  float2 d[Q], dn[Q], st[4];
+#pragma unroll
+  for (int i = 0; i < Q; i++) d[i] = make_float2(da[i], db[i]);
+  collide_core<float2>(d, make_float2(Ga[0], Gb[0]), make_float2(Ga[1], Gb[1]),
+                       make_float2(Ga[2], Gb[2]), tau, om, dn, st);
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    dna[i] = dn[i].x;
+    dnb[i] = dn[i].y;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    sta[c] = st[c].x;
+    stb[c] = st[c].y;
+  }
 }
 
 // One cell of the fused pull-stream + collision: the pull of Eq. 4 from src,
@@ -61,10 +141,10 @@ template <typename S>
 __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__restrict__ dst,
                                              const Geometry &g, uint32_t n, int x, int y, int z,
                                              float Gx, float Gy, float Gz, float tau,
-                                             float st[4]) {
+                                             float om, float st[4]) {
   float d[Q], dn[Q];
   pull<S>(src, g, x, y, z, d);
-  collide_math(d, Gx, Gy, Gz, tau, dn, st);
+  collide_math(d, Gx, Gy, Gz, tau, om, dn, st);
   const size_t N = (size_t)g.ncell;
 #pragma unroll
   for (int i = 0; i < Q; i++) Store<S>::st(dst + ((size_t)i * N + n), dn[i]);
@@ -126,7 +206,7 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
     }
     if (mine) {
       float st[4];
-      collide_cell<S>(src, dst, g, n, x, y, z, Gx, Gy, Gz, dd.tau, st);
+      collide_cell<S>(src, dst, g, n, x, y, z, Gx, Gy, Gz, dd.tau, dd.om, st);
       if (STATS)
         for (int c = 0; c < 4; c++) sv[c] = st[c];
     }
@@ -251,8 +331,7 @@ __device__ __forceinline__ void collide_pairs16(const DomainDesc &dd, int cur) {
       }
     }
     float dna[Q], dnb[Q], sta[4], stb[4];
-    collide_math(da, Ga[0], Ga[1], Ga[2], dd.tau, dna, sta);
-    collide_math(db, Gb[0], Gb[1], Gb[2], dd.tau, dnb, stb);
+    collide_math2(da, db, Ga, Gb, dd.tau, dd.om, dna, dnb, sta, stb);
     const uint32_t wn = n >> 1;
 #pragma unroll
     for (int i = 0; i < Q; i++) dst[(size_t)i * NW + wn] = Word16<S>::pack(dna[i], dnb[i]);
@@ -354,27 +433,30 @@ struct RowsTiling {
   int stage_bytes;  // 19 R nx 2
 };
 
-// Issues the copies of tile t into stage buffer `buf` (one thread).
+// Issues the copies of tile t into stage buffer `buf`: called by the 32
+// lanes of warp 0, lane i < 19 copies population i (lane 0 first posts the
+// stage's byte count).
 __device__ __forceinline__ void rows_issue(const uint16_t *__restrict__ f, const Geometry &g,
                                            int R, int t, unsigned char *buf, uint64_t *bar,
                                            unsigned stage_bytes) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) mbar_expect_tx(bar, stage_bytes);
+  __syncwarp();
+  if (lane >= Q) return;
+  const int i = lane;
   const int ny = g.ny, nx = g.nx;
   const int z = t / (ny / R), y0 = (t - z * (ny / R)) * R;
   const size_t N = (size_t)g.ncell;
   const unsigned rowb = (unsigned)nx * 2u;
-  mbar_expect_tx(bar, stage_bytes);
-#pragma unroll 1
-  for (int i = 0; i < Q; i++) {
-    const int zs = wrapi(z - ez(i), g.nz);
-    const int ya = wrapi(y0 - ey(i), ny);
-    const int first = min(R, ny - ya);  // rows before the y seam
-    unsigned char *d = buf + (size_t)i * R * rowb;
-    const uint16_t *src = f + (size_t)i * N + ((size_t)zs * ny + ya) * nx;
-    bulk_g2s(d, src, (unsigned)first * rowb, bar);
-    if (first < R)
-      bulk_g2s(d + (size_t)first * rowb, f + (size_t)i * N + (size_t)zs * ny * nx,
-               (unsigned)(R - first) * rowb, bar);
-  }
+  const int zs = wrapi(z - ez(i), g.nz);
+  const int ya = wrapi(y0 - ey(i), ny);
+  const int first = min(R, ny - ya);  // rows before the y seam
+  unsigned char *d = buf + (size_t)i * R * rowb;
+  const uint16_t *src = f + (size_t)i * N + ((size_t)zs * ny + ya) * nx;
+  bulk_g2s(d, src, (unsigned)first * rowb, bar);
+  if (first < R)
+    bulk_g2s(d + (size_t)first * rowb, f + (size_t)i * N + (size_t)zs * ny * nx,
+             (unsigned)(R - first) * rowb, bar);
 }
 
 template <typename S, bool STATS>
@@ -398,7 +480,7 @@ __global__ void __launch_bounds__(384, 2)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0)
+  if (threadIdx.x < 32)
     for (int q = 0; q < NS; q++) {
       const int t = blockIdx.x + q * gridDim.x;
       if (t < tl.tiles)
@@ -459,13 +541,13 @@ __global__ void __launch_bounds__(384, 2)
     }
     // every thread has read stage q: it may be refilled
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       const int tn = t + NS * gridDim.x;
-      if (tn < tl.tiles) rows_issue(f, g, R, tn, (unsigned char *)buf, bars + q, (unsigned)tl.stage_bytes);
+      if (tn < tl.tiles)
+        rows_issue(f, g, R, tn, (unsigned char *)buf, bars + q, (unsigned)tl.stage_bytes);
     }
     float dna[Q], dnb[Q], sta[4], stb[4];
-    collide_math(da, Ga[0], Ga[1], Ga[2], dd.tau, dna, sta);
-    collide_math(db, Gb[0], Gb[1], Gb[2], dd.tau, dnb, stb);
+    collide_math2(da, db, Ga, Gb, dd.tau, dd.om, dna, dnb, sta, stb);
     const size_t cell0 = ((size_t)z * g.ny + (y - r)) * nx;  // first cell of the tile
     const uint32_t wn = (uint32_t)((cell0 >> 1) + threadIdx.x);
 #pragma unroll
@@ -521,7 +603,7 @@ __global__ void __launch_bounds__(256)
       const float *p = Gs + (size_t)s * SLOT_FLOATS + t;
       float st[4];
       collide_cell<S>(src, dst, g, n, x, y, z, dd.gbody[0] + p[0],
-                      dd.gbody[1] + p[BRICK_CELLS], dd.gbody[2] + p[2 * BRICK_CELLS], dd.tau,
+                      dd.gbody[1] + p[BRICK_CELLS], dd.gbody[2] + p[2 * BRICK_CELLS], dd.tau, dd.om,
                       st);
       if (STATS)
         for (int c = 0; c < 4; c++) sv[c] = st[c];
