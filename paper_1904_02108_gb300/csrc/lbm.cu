@@ -40,12 +40,44 @@ __device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ float vrcp(float a) { return __fdiv_rn(1.f, a); }
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));  // (x - y is x + (-y) exactly)
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+// The packed operations in PTX with an explicit rounding mode: the code
+// generator neither fuses nor reorders them (the packed intrinsics were
+// fused, a multiply and a following add becoming one fma, which rounds
+// once where the scalar form rounds twice).
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "add.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
 }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "sub.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "mul.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, c, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "mov.b64 c, {%6, %7};\n\tfma.rn.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
 __device__ __forceinline__ float2 vrcp(float2 a) {
   return make_float2(__fdiv_rn(1.f, a.x), __fdiv_rn(1.f, a.y));
 }
@@ -80,11 +112,15 @@ __device__ __forceinline__ void collide_core(const V d[Q], V Gx, V Gy, V Gz, flo
   st[3] = vfma(rho, Gz, jz);
   const V vom = vsplat<V>(om);
   // Eq. 3 minus t_i: t_i (c0 + rho (3 e.u + 4.5 (e.u)^2)) with c0 the part
-  // common to every direction; opposite directions share 4.5 rho (e.u)^2
+  // common to every direction; opposite directions share 4.5 rho (e.u)^2.
+  // Every product that meets an addition is one fma (no separate multiply
+  // and add that the code generator could contract in one form and not the
+  // other): the relaxation is d + om (t_i E - d) with t_i E - d one fma.
   const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
   const V c0 = vfma(vmul(vsplat<V>(-1.5f), rho), usq, drho);
   const V r3 = vmul(vsplat<V>(3.f), rho), r45 = vmul(vsplat<V>(4.5f), rho);
-  dn[0] = vfma(vom, vsub(vmul(vsplat<V>(wt(0)), c0), d[0]), d[0]);
+  const V nr3 = vneg(r3);
+  dn[0] = vfma(vom, vfma(vsplat<V>(wt(0)), c0, vneg(d[0])), d[0]);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     // e_i . u with the components of e_i in {-1, 0, 1}
@@ -99,11 +135,11 @@ __device__ __forceinline__ void collide_core(const V d[Q], V Gx, V Gy, V Gz, flo
       else eu = ec[c] > 0 ? vadd(eu, uc[c]) : vsub(eu, uc[c]);
       first = false;
     }
-    const V sym = vfma(r45, vmul(eu, eu), c0), anti = vmul(r3, eu);
+    const V sym = vfma(r45, vmul(eu, eu), c0);
+    const V ep = vfma(r3, eu, sym), em = vfma(nr3, eu, sym);  // E/t_i for e_i and -e_i
     const V w = vsplat<V>(wt(i));
-    const V eqp = vmul(w, vadd(sym, anti)), eqm = vmul(w, vsub(sym, anti));
-    dn[i] = vfma(vom, vsub(eqp, d[i]), d[i]);
-    dn[i + 1] = vfma(vom, vsub(eqm, d[i + 1]), d[i + 1]);
+    dn[i] = vfma(vom, vfma(w, ep, vneg(d[i])), d[i]);
+    dn[i + 1] = vfma(vom, vfma(w, em, vneg(d[i + 1])), d[i + 1]);
   }
 }
 
