@@ -284,16 +284,21 @@ typedef struct {
                         128, 256 or 512                                    */
   int moments_spb;   /* bricks per block of the moments kernel: 1, 2 or 4   */
   int sort_blocks;   /* blocks of the pair sort (a warp per brick), >= 1   */
+  int collide_staged; /* 16-bit storage, single lattice: 1 brings the pulled
+                         rows into shared memory with bulk asynchronous
+                         copies (rows of 8k cells, 16-byte aligned; other
+                         sizes fall back), 0 pulls them with loads         */
 } lbm_launch_shape;
 
-/* The handle's launch shape (defaults: 256, 9728, 256, 4, 4864).  Set
+/* The handle's launch shape (defaults: 256, 9728, 256, 4, 4864, 0).  Set
  * returns LBM_EINVAL for a value outside the ranges above. */
 int lbm_get_launch_shape(lbm_t *h, lbm_launch_shape *out);
 int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s);
 
 /* Picks the launch shape by timing trial steps on this handle's own lattice
  * and points: one parameter at a time (collide block, brick grid, point
- * block, moments bricks per block, sort grid), each candidate timed with CUDA
+ * block, moments bricks per block, sort grid, and with 16-bit storage the
+ * staged collide), each candidate timed with CUDA
  * events around steps_per_trial whole steps (>= 1; consecutive kernels
  * overlap, so the step is the objective) after one untimed step, in two
  * interleaved rounds (the faster kept), with n_ibm_iter (> 0) fixed

@@ -54,7 +54,7 @@ class LbmStats(_c.Structure):
 
 class LaunchShape(_c.Structure):
     _fields_ = [("collide_block", _i), ("brick_blocks", _i), ("point_block", _i),
-                ("moments_spb", _i), ("sort_blocks", _i)]
+                ("moments_spb", _i), ("sort_blocks", _i), ("collide_staged", _i)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1534,11 +1534,13 @@ bool shape_ok(const lbm_launch_shape &s) {
          (s.point_block == 128 || s.point_block == 256 || s.point_block == 512) &&
          s.brick_blocks >= 1 && s.brick_blocks <= (1 << 20) && s.sort_blocks >= 1 &&
          s.sort_blocks <= (1 << 20) &&
-         (s.moments_spb == 1 || s.moments_spb == 2 || s.moments_spb == 4);
+         (s.moments_spb == 1 || s.moments_spb == 2 || s.moments_spb == 4) &&
+         (s.collide_staged == 0 || s.collide_staged == 1);
 }
 
 lbm_launch_shape to_c(const LaunchShape &l) {
-  return {l.collide_block, l.brick_blocks, l.point_block, l.moments_spb, l.sort_blocks};
+  return {l.collide_block, l.brick_blocks, l.point_block, l.moments_spb, l.sort_blocks,
+          l.collide_staged};
 }
 
 LaunchShape from_c(const lbm_launch_shape &c) {
@@ -1548,6 +1550,7 @@ LaunchShape from_c(const lbm_launch_shape &c) {
   l.point_block = c.point_block;
   l.moments_spb = c.moments_spb;
   l.sort_blocks = c.sort_blocks;
+  l.collide_staged = c.collide_staged;
   return l;
 }
 
@@ -1623,9 +1626,10 @@ struct TuneParam {
   int stage_mask;
 };
 
-std::vector<TuneParam> tune_params(bool points) {
+std::vector<TuneParam> tune_params(bool points, bool staged) {
   std::vector<TuneParam> ps;
   ps.push_back({&LaunchShape::collide_block, {128, 256}, 1 << ST_COLLIDE});
+  if (staged) ps.push_back({&LaunchShape::collide_staged, {0, 1}, 1 << ST_COLLIDE});
   if (points) {
     ps.push_back({&LaunchShape::brick_blocks,
                   {152 * 16, 152 * 32, 152 * 64, 152 * 128},
@@ -1650,9 +1654,9 @@ constexpr int kRounds = 2;
 constexpr double kMargin = 0.01;
 
 template <typename SetShape, typename Step, typename Clear, typename StageMs>
-int coordinate_search(LaunchShape &shape, bool points, int steps_per_trial, SetShape set_shape,
-                      Step step, Clear clear, StageMs stage_ms) {
-  for (const TuneParam &p : tune_params(points)) {
+int coordinate_search(LaunchShape &shape, bool points, bool staged, int steps_per_trial,
+                      SetShape set_shape, Step step, Clear clear, StageMs stage_ms) {
+  for (const TuneParam &p : tune_params(points, staged)) {
     const int incumbent = shape.*p.field;
     std::vector<double> best_ms(p.values.size(), 1e300);
     for (int round = 0; round < kRounds; round++) {
@@ -1728,7 +1732,7 @@ int lbm_autotune(lbm_t *h, int n_ibm_iter, int steps_per_trial, lbm_launch_shape
   bool timing = false;
   if (r == LBM_OK)
     r = coordinate_search(
-        shape, h->np > 0, steps_per_trial,
+        shape, h->np > 0, h->storage != LBM_STORE_F32, steps_per_trial,
         [&](const LaunchShape &l) {
           lbm_launch_shape c = to_c(l);
           return lbm_set_launch_shape(h, &c);
@@ -1796,7 +1800,7 @@ int lbm_batch_autotune(lbm_batch_t *b, int n_ibm_iter, int steps_per_trial,
   bool timing = false;
   if (r == LBM_OK)
     r = coordinate_search(
-        shape, points, steps_per_trial,
+        shape, points, false, steps_per_trial,
         [&](const LaunchShape &l) {
           lbm_launch_shape c = to_c(l);
           return lbm_batch_set_launch_shape(b, &c);

@@ -305,6 +305,9 @@ struct LaunchShape {
                                  // (64 threads each): 1, 2 or 4
   int sort_blocks = 152 * 32;    // grid of the sort kernel (a warp per slot,
                                  // four per block)
+  int collide_staged = 0;        // 16-bit storage, single lattice: the pulls
+                                 // staged in shared memory by bulk copies (1)
+                                 // or loaded by the threads (0)
 };
 
 // Cells per FP64 partial sum of the collide kernel.

@@ -409,18 +409,20 @@ __global__ void __launch_bounds__(256)
 // bulk-copy engine.  A tile is R consecutive rows (y) of one z plane, whole
 // rows in x; for each population the R source rows (the tile's rows shifted by
 // -e_y, -e_z, wrapped) arrive as at most two contiguous bulk copies
-// (cp.async.bulk, global -> shared, completing on the stage's mbarrier).  A
-// persistent grid walks the tiles with NS stages in flight per block, so the
-// loads need no registers and overlap the arithmetic of earlier tiles.  Each
-// thread takes two x-neighbouring cells exactly as collide_pairs16 does (the
-// same words, the same collide_math, the same warps of 64 cells and the same
-// FP64 partial per 128 cells), so the results are bitwise those of
-// collide_pairs16.  Needs nx % 8 == 0 (16-byte rows), ny % R == 0 and R nx a
-// multiple of 128 (a tile holds whole partials); the launcher checks.  Every
-// wait is bounded: a stage that does not arrive within ROWS_SPIN_LIMIT polls
-// sets bit 8 of the error flags, the block drains its other copies (bounded
-// again) and returns.
+// (cp.async.bulk, global -> shared, completing on the stage's "full"
+// mbarrier).  A persistent grid walks the tiles; in each block one producer
+// warp keeps NS stages in flight (it refills a stage once every consumer warp
+// has arrived on its "empty" mbarrier) and R nx / 2 consumer threads take two
+// x-neighbouring cells each, exactly as collide_pairs16 does (the same words,
+// the same collide_math2, the same warps of 64 cells and the same FP64 partial
+// per 128 cells, formed by the two warps of a pair at a named barrier of
+// their own), so the results are bitwise those of collide_pairs16.  No
+// block-wide barrier in the steady state.  Needs nx % 8 == 0 (16-byte rows),
+// ny % R == 0 and R nx a multiple of 128; the launcher checks.  Every wait is
+// bounded: past ROWS_SPIN_LIMIT polls the waiting warp sets bit 8 of the error
+// flags and leaves (the producer stops issuing, so the others time out too).
 constexpr unsigned ROWS_SPIN_LIMIT = 1u << 24;
+constexpr int ROWS_MAX_CONSUMERS = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -435,6 +437,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // true once the phase of parity `phase` has completed; false after
@@ -462,6 +468,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
       : "memory");
 }
 
+// barrier 1 + pair among the 64 threads of warps 2 pair and 2 pair + 1 (the
+// ids are constants, so the block reserves only the barriers it uses)
+__device__ __forceinline__ void pair_sync(int pair) {
+  switch (pair) {
+    case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+  }
+}
+
 struct RowsTiling {
   int R;            // rows per tile
   int NS;           // stages
@@ -470,8 +487,8 @@ struct RowsTiling {
 };
 
 // Issues the copies of tile t into stage buffer `buf`: called by the 32
-// lanes of warp 0, lane i < 19 copies population i (lane 0 first posts the
-// stage's byte count).
+// lanes of the producer warp, lane i < 19 copies population i (lane 0 first
+// posts the stage's byte count).
 __device__ __forceinline__ void rows_issue(const uint16_t *__restrict__ f, const Geometry &g,
                                            int R, int t, unsigned char *buf, uint64_t *bar,
                                            unsigned stage_bytes) {
@@ -496,69 +513,69 @@ __device__ __forceinline__ void rows_issue(const uint16_t *__restrict__ f, const
 }
 
 template <typename S, bool STATS>
-__global__ void __launch_bounds__(384, 2)
+__global__ void __launch_bounds__(ROWS_MAX_CONSUMERS + 32, 2)
     collide_rows16_kernel(const __grid_constant__ DomainDesc dd, int cur, RowsTiling tl) {
   pdl_wait();
   extern __shared__ __align__(128) unsigned char smraw[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smraw);
-  unsigned char *stages = smraw + 128;
-  __shared__ double red[16][4];
+  const int NS = tl.NS, R = tl.R;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smraw);
+  uint64_t *empty = full + NS;
+  unsigned char *stages = smraw + 256;
+  __shared__ float red[2][ROWS_MAX_CONSUMERS / 32][4];
+  __shared__ int pair_abort[2][ROWS_MAX_CONSUMERS / 64];  // by tile parity
   const Geometry g = dd.g;
-  const int nx = g.nx, R = tl.R, NS = tl.NS;
+  const int nx = g.nx, hw = nx >> 1;
+  const int ncons = R * hw, cw = ncons >> 5;  // consumer threads and warps
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint16_t *__restrict__ f = (const uint16_t *)dd.f[cur];
+  if (threadIdx.x < ROWS_MAX_CONSUMERS / 32) (&pair_abort[0][0])[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NS; q++) {
+      mbar_init(full + q, 1);
+      mbar_init(empty + q, cw);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == cw) {
+    // producer: stage q of the k-th tile is refilled once the consumers have
+    // released its previous use (the empty phase of use k / NS - 1)
+    int k = 0;
+    for (int t = blockIdx.x; t < tl.tiles; t += gridDim.x, k++) {
+      const int q = k % NS;
+      if (k >= NS && !mbar_wait(empty + q, (unsigned)(k / NS - 1) & 1u)) {
+        if (lane == 0) atomicOr(dd.m.counters + 5, 8);
+        return;
+      }
+      rows_issue(f, g, R, t, stages + (size_t)q * tl.stage_bytes, full + q,
+                 (unsigned)tl.stage_bytes);
+    }
+    return;
+  }
   uint32_t *__restrict__ dst = (uint32_t *)dd.f[cur ^ 1];
   const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
   const float *__restrict__ Gs = dd.Gs;
   const unsigned rowb = (unsigned)nx * 2u;
   const size_t NW = (size_t)g.ncell >> 1;
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < NS; q++) mbar_init(bars + q, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x < 32)
-    for (int q = 0; q < NS; q++) {
-      const int t = blockIdx.x + q * gridDim.x;
-      if (t < tl.tiles)
-        rows_issue(f, g, R, t, stages + (size_t)q * tl.stage_bytes, bars + q,
-                   (unsigned)tl.stage_bytes);
-    }
-  const int hw = nx >> 1;
   const int r = threadIdx.x / hw, j = threadIdx.x - r * hw;  // row, word of this thread
   const int x = 2 * j;
   const uint32_t wl = j == 0 ? hw - 1 : j - 1, wr = j == hw - 1 ? 0 : j + 1;
+  const int pair = warp >> 1;
   int k = 0;
   for (int t = blockIdx.x; t < tl.tiles; t += gridDim.x, k++) {
     const int q = k % NS;
-    const bool ok = mbar_wait(bars + q, (unsigned)(k / NS) & 1u);
-    if (!__syncthreads_and(ok)) {
-      // a stage that never arrived: flag it, let the other copies land, leave
-      if (threadIdx.x == 0) {
+    // a wait that gives up marks the pair; both warps of a pair leave after
+    // the same pair barrier (so neither is left waiting at it)
+    if (!mbar_wait(full + q, (unsigned)(k / NS) & 1u)) {
+      if (lane == 0) {
         atomicOr(dd.m.counters + 5, 8);
-        for (int p = 1; p < NS; p++) {
-          const int kk = k + p;
-          if (blockIdx.x + kk * gridDim.x < tl.tiles) mbar_wait(bars + kk % NS, (kk / NS) & 1u);
-        }
+        pair_abort[k & 1][pair] = 1;
       }
-      __syncthreads();
-      return;
+      if (STATS) pair_sync(pair);
+      break;
     }
     const int z = t / (g.ny / R), y = (t - z * (g.ny / R)) * R + r;
     const unsigned char *buf = stages + (size_t)q * tl.stage_bytes;
-    float Ga[3] = {dd.gbody[0], dd.gbody[1], dd.gbody[2]};
-    float Gb[3] = {Ga[0], Ga[1], Ga[2]};
-    if (brick_slot) {
-      const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
-      const int sl = __ldg(brick_slot + b);
-      if (sl >= 0) {
-        const float *p = Gs + (size_t)sl * SLOT_FLOATS + brick_local(x, y, z);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-          Ga[c] += __ldg(p + c * BRICK_CELLS);
-          Gb[c] += __ldg(p + c * BRICK_CELLS + 1);
-        }
-      }
-    }
     float da[Q], db[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -575,12 +592,22 @@ __global__ void __launch_bounds__(384, 2)
         db[i] = Word16<S>::lo(row[wr]);
       }
     }
-    // every thread has read stage q: it may be refilled
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int tn = t + NS * gridDim.x;
-      if (tn < tl.tiles)
-        rows_issue(f, g, R, tn, (unsigned char *)buf, bars + q, (unsigned)tl.stage_bytes);
+    // this warp has read stage q
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + q);
+    float Ga[3] = {dd.gbody[0], dd.gbody[1], dd.gbody[2]};
+    float Gb[3] = {Ga[0], Ga[1], Ga[2]};
+    if (brick_slot) {
+      const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
+      const int sl = __ldg(brick_slot + b);
+      if (sl >= 0) {
+        const float *p = Gs + (size_t)sl * SLOT_FLOATS + brick_local(x, y, z);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          Ga[c] += __ldg(p + c * BRICK_CELLS);
+          Gb[c] += __ldg(p + c * BRICK_CELLS + 1);
+        }
+      }
     }
     float dna[Q], dnb[Q], sta[4], stb[4];
     collide_math2(da, db, Ga, Gb, dd.tau, dd.om, dna, dnb, sta, stb);
@@ -592,18 +619,19 @@ __global__ void __launch_bounds__(384, 2)
       float sv[4];
       for (int c = 0; c < 4; c++) sv[c] = sta[c] + stb[c];
       const float ws = warp_sum4_split(sv);
-      // a warp covers 64 cells: one partial per PARTIAL_CELLS = two warps
-      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      if ((lane & 7) == 0) red[w][lane >> 3] = ws;
-      __syncthreads();
-      const int groups = blockDim.x / (PARTIAL_CELLS / 2);
-      if ((int)threadIdx.x < 4 * groups) {
-        const int gi = threadIdx.x >> 2, c = threadIdx.x & 3;
-        const double a = red[2 * gi][c] + red[2 * gi + 1][c];
-        const int64_t pidx = (int64_t)(cell0 / PARTIAL_CELLS) + gi;
+      // a warp covers 64 cells: one partial per PARTIAL_CELLS = a pair of
+      // warps, which meet at a barrier of their own (red double-buffered by
+      // tile, so that the first warp may write the next tile's sums while
+      // the second still reads these)
+      if ((lane & 7) == 0) red[k & 1][warp][lane >> 3] = ws;
+      pair_sync(pair);
+      if (pair_abort[k & 1][pair]) break;
+      if (!(warp & 1) && lane < 4) {
+        const int c = lane;
+        const double a = (double)red[k & 1][warp][c] + (double)red[k & 1][warp + 1][c];
+        const int64_t pidx = (int64_t)(cell0 / PARTIAL_CELLS) + pair;
         if (pidx < dd.cblocks) dd.partial[(size_t)pidx * 4 + c] = a;
       }
-      __syncthreads();  // (red is reused by the next tile)
     }
   }
 }
@@ -836,20 +864,20 @@ inline unsigned cell_blocks(const Geometry &g, int threads) {
 }
 
 // Tiling of the staged 16-bit collide: R the largest divisor of ny with
-// R nx / 2 <= 384 threads (two blocks of at most 85 registers per thread on
-// an SM) and R nx a multiple of 128 cells; three stages when they fit in
-// ~112 KB (two blocks per SM), else two within 200 KB.  False when no tiling
-// applies (the two-cell kernel runs instead).
+// R nx / 2 <= 256 consumer threads and R nx a multiple of 128 cells; as many
+// stages (up to 8) as fit in ~74 KB (three blocks per SM), else in ~110 KB (two
+// blocks), at least two.  False when no tiling applies (the two-cell kernel
+// runs instead).
 bool rows_tiling(const Geometry &g, RowsTiling &tl) {
-  if (g.nx % 8 || g.nx / 2 > 384) return false;
+  if (g.nx % 8 || g.nx / 2 > ROWS_MAX_CONSUMERS) return false;
   int R = 0;
-  for (int r = 1; r <= g.ny && r * g.nx / 2 <= 384; r++)
+  for (int r = 1; r <= g.ny && r * g.nx / 2 <= ROWS_MAX_CONSUMERS; r++)
     if (g.ny % r == 0 && (r * g.nx) % 128 == 0) R = r;
-  if (!R || (R * g.nx / 2) % 32) return false;
+  if (!R) return false;
   const int stage = Q * R * g.nx * 2;
-  int NS = 3;
-  if (NS * stage + 128 > 112 * 1024) NS = 2;
-  if (NS * stage + 128 > 200 * 1024) return false;
+  int NS = std::min(8, (74 * 1024 - 256) / stage);
+  if (NS < 2) NS = std::min(8, (110 * 1024 - 256) / stage);
+  if (NS < 2) return false;
   tl.R = R;
   tl.NS = NS;
   tl.tiles = g.nz * (g.ny / R);
@@ -859,8 +887,8 @@ bool rows_tiling(const Geometry &g, RowsTiling &tl) {
 
 template <typename S, bool STATS>
 cudaError_t launch_rows16(const DomainDesc &dd, int cur, const RowsTiling &tl, cudaStream_t st) {
-  const size_t smem = 128 + (size_t)tl.NS * tl.stage_bytes;
-  const int threads = tl.R * dd.g.nx / 2;
+  const size_t smem = 256 + (size_t)tl.NS * tl.stage_bytes;
+  const int threads = tl.R * dd.g.nx / 2 + 32;
   static size_t set_for = 0;  // (the attribute is per kernel instantiation)
   if (smem > set_for) {
     cudaError_t e = cudaFuncSetAttribute(collide_rows16_kernel<S, STATS>,
@@ -893,9 +921,10 @@ cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const Ba
   if (skip_active) return stats ? LBM_COLLIDE(true, true) : LBM_COLLIDE(false, true);
 #undef LBM_COLLIDE
   if constexpr (sizeof(S) == 2) {
-    // a single lattice whose rows tile: pulls staged by bulk copies
+    // a single lattice whose rows tile, with the staged kernel chosen (the
+    // autotuner picks it where it is faster): pulls staged by bulk copies
     RowsTiling tl{};
-    if (dims.nd == 1 && Dhost && rows_tiling(Dhost->g, tl))
+    if (dims.ls.collide_staged && dims.nd == 1 && Dhost && rows_tiling(Dhost->g, tl))
       return stats ? launch_rows16<S, true>(*Dhost, cur, tl, st)
                    : launch_rows16<S, false>(*Dhost, cur, tl, st);
     // two cells per thread (nx is a multiple of 4)

@@ -9,7 +9,7 @@ from paper_1904_02108_gb300 import workload as W
 pytestmark = pytest.mark.gpu
 
 OTHER = dict(collide_block=128, brick_blocks=152 * 8, point_block=512, moments_spb=1,
-             sort_blocks=152 * 8)
+             sort_blocks=152 * 8, collide_staged=1)
 WIDE = dict(collide_block=256, brick_blocks=152 * 32, point_block=128, moments_spb=2,
             sort_blocks=152 * 64)
 
@@ -60,6 +60,7 @@ def test_autotune_leaves_the_lattice_unchanged(gpu_lib, torch_cuda):
     assert a.launch_shape() == chosen
     assert chosen["collide_block"] in (128, 256)
     assert chosen["moments_spb"] in (1, 2, 4)
+    assert chosen["collide_staged"] == 0  # (FP32 storage: not a candidate)
     assert a.stats()["step"] == 3
     a.step(4, 5)
     b.step(4, 5)
@@ -71,7 +72,7 @@ def test_autotune_leaves_the_lattice_unchanged(gpu_lib, torch_cuda):
 def test_launch_shape_rejects_values_out_of_range(gpu_lib, torch_cuda):
     lat = _pair_lattice(gpu_lib, torch_cuda)
     for bad in (dict(collide_block=512), dict(point_block=1024), dict(moments_spb=8),
-                dict(brick_blocks=0), dict(sort_blocks=-1)):
+                dict(brick_blocks=0), dict(sort_blocks=-1), dict(collide_staged=2)):
         with pytest.raises(gpu_lib.LbmError):
             lat.set_launch_shape(**bad)
     lat.close()

@@ -82,12 +82,12 @@ def test_roundtrip_rounds_deviations_to_nearest(gpu_lib, orc, storage, u):
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 @pytest.mark.parametrize("case", ["single_propeller_32", "propeller_array_64", "box_48x64x80"])
 def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, case):
-    """A single lattice with 16-bit storage collides with the staged kernel
-    (rows of the pulls brought into shared memory by bulk copies), a batch
-    with the two-cell kernel; both use the same per-cell arithmetic and the
-    same partial sums, so populations and FP64 sums must agree bitwise.  The
-    shapes cover tiles of 16, 8 and 16 rows, the y and z seams and a lattice
-    whose rows are not a power of two."""
+    """A single lattice with 16-bit storage and the staged collide chosen
+    (rows of the pulls brought into shared memory by bulk copies) against a
+    batch, which keeps the two-cell kernel; both use the same per-cell
+    arithmetic and the same partial sums, so populations and FP64 sums must
+    agree bitwise.  The shapes cover tiles of 16, 8 and 8 rows, the y and z
+    seams and a lattice whose rows are not a power of two."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -103,6 +103,7 @@ def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, ca
                              [0.4, 2.2])
     st = torch.cuda.current_stream()
     a = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
+    a.set_launch_shape(collide_staged=1)
     b = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
     rng = W.SplitMix64(22)
     f0 = orc.init_equilibrium(shape, 1 + 0.01 * W.random_array(rng, shape),
