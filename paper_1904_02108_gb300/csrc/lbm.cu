@@ -273,8 +273,10 @@ __global__ void __launch_bounds__(256)
   collide_stream_cells<S, STATS, SKIP>(dd, cur);
 }
 
+// (five blocks of 256 per SM, as the single-lattice kernel gets with its
+// descriptor in the parameter bank)
 template <typename S, bool STATS, bool SKIP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
     collide_stream_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
   pdl_wait();
   collide_stream_cells<S, STATS, SKIP>(D[blockIdx.y], cur);
