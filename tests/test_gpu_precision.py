@@ -57,6 +57,38 @@ def test_storage_error_against_oracle(gpu_lib, orc, oracle_run, storage):
     lat.close()
 
 
+LONG_STEPS = 200
+
+
+@pytest.fixture(scope="module")
+def oracle_long_run(orc):
+    w = W.dense_array_64()
+    sim = orc.Simulation(w.shape, w.tau, w.props.as_dict(), n_iter=w.n_iter)
+    sim.step(LONG_STEPS)
+    return w, sim.fields()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_storage_error_over_a_long_run(gpu_lib, orc, oracle_long_run, storage):
+    """The same comparison over 200 steps: the error of the 16-bit forms
+    stays within the unit roundoff (it does not accumulate with the steps);
+    FP32 stays at its 1e-5 bar."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, (rho_o, U_o) = oracle_long_run
+    lat = gpu_lib.Lattice(w.shape, w.tau, storage=storage,
+                          stream=torch.cuda.current_stream())
+    lat.set_propellers(w.props)
+    lat.step(LONG_STEPS, w.n_iter)
+    _, U, _ = lat.fields()
+    err = rel_l2(U, U_o)
+    print("storage %s: rel L2(U) after %d steps = %.3e (bound %.3e)"
+          % (storage, LONG_STEPS, err, BOUND[storage]))
+    assert err < BOUND[storage]
+    lat.close()
+
+
 @pytest.mark.parametrize("storage,u", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
 def test_roundtrip_rounds_deviations_to_nearest(gpu_lib, orc, storage, u):
     """Stored deviations are f - t rounded to nearest in the 16-bit format:
