@@ -40,6 +40,23 @@ constexpr int OFF_W3 = OFF_W2T + H * LD2;
 constexpr int NB16 = OFF_W3 + 8 * LD2;            // BF16 elements
 constexpr int OFF_B = NB16 * 2;                   // bytes: FP32 biases follow
 constexpr int NBIAS = H + H + OUT;
+// The same weights for the tcgen05 kernels, in the canonical K-major layout
+// of the tensor-core shared-memory descriptors without swizzle: 8 x 8 BF16
+// core matrices of 128 contiguous bytes (8 rows of 16 B), the K-blocks of an
+// 8-row group next to each other (byte offset tc_ofs below).  W3 is padded
+// to 16 rows (the smallest N of an M = 128 MMA).  Then a status word that a
+// tensor-core kernel sets when one of its waits gives up.
+constexpr int OFF_TC = ((OFF_B + NBIAS * 4) + 127) / 128 * 128;  // bytes
+constexpr int TC_W1 = 0, TC_W2 = TC_W1 + H * IN * 2, TC_W3 = TC_W2 + H * H * 2;
+constexpr int TC_BYTES = TC_W3 + 16 * H * 2;
+constexpr int OFF_STATUS = OFF_TC + TC_BYTES;
+constexpr int PACKED_BYTES = OFF_STATUS + 16;
+
+// byte offset of element (row r, column k) of a K-major operand with kb
+// 8-column blocks per row group
+__host__ __device__ __forceinline__ int tc_ofs(int r, int k, int kb) {
+  return ((r >> 3) * kb + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
 // parameter offsets in P
 constexpr int P_W1 = 0, P_B1 = H * IN, P_W2 = P_B1 + H, P_B2 = P_W2 + H * H, P_W3 = P_B2 + H,
               P_B3 = P_W3 + OUT * H;
@@ -167,64 +184,261 @@ __device__ __forceinline__ void load_x(const float *__restrict__ X, int64_t row0
   xa[3] = pack_bf16(v11.x, v11.y);
 }
 
-// Inference.  mode 0: Y[n][3] = y.  mode 1 (warm start of the fixed point):
-// du[k] = du_prev[k] + scale * y, with du_prev read from du itself (zero when
-// !use_prev).  The domain variant takes n, X, the weights and du from
-// D[blockIdx.y].
-__device__ void mlp_forward_rows(int64_t n, const float *__restrict__ X, const void *packed,
-                                 float *__restrict__ Y, float4 *__restrict__ du, float scale,
-                                 int mode, int use_prev, MlpSmem &sm) {
-  load_weights(sm, packed);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-  for (int64_t row0 = ((int64_t)blockIdx.x * 8 + w) * 16; row0 < n;
-       row0 += (int64_t)gridDim.x * 8 * 16) {
-    uint32_t xa[4];
-    load_x(X, row0, n, xa);
-    Fwd f;
-    forward16(sm, xa, f);
-    // gather the three outputs of rows g and g+8 onto lane t == 0
-    const int src0 = g * 4, src1 = g * 4 + 1;
-    const float a0 = __shfl_sync(0xffffffffu, f.y[0], src0), a1 = __shfl_sync(0xffffffffu, f.y[1], src0),
-                a2 = __shfl_sync(0xffffffffu, f.y[0], src1);
-    const float c0 = __shfl_sync(0xffffffffu, f.y[2], src0), c1 = __shfl_sync(0xffffffffu, f.y[3], src0),
-                c2 = __shfl_sync(0xffffffffu, f.y[2], src1);
-    if (t == 0) {
-      const int64_t r[2] = {row0 + g, row0 + g + 8};
-      const float v[2][3] = {{a0, a1, a2}, {c0, c1, c2}};
+// ---- inference on the fifth-generation tensor cores (tcgen05) -------------
+//
+// One block of 128 threads (four warps) takes tiles of 128 samples.  Per tile
+// and layer, the activations are written to shared memory as BF16 in the
+// canonical K-major layout (tc_ofs), one thread issues the layer's
+// tcgen05.mma (M = 128 samples, N = 64 or 16 outputs, K = 16 per instruction,
+// BF16 inputs, FP32 accumulation in tensor memory), a tcgen05.commit signals
+// completion on an mbarrier, and each warp reads its 32 rows of the
+// accumulator back with tcgen05.ld (thread t holds sample t) for the
+// bias, SiLU and the next layer's operand.  Tensor memory: 128 columns per
+// block (layer 1 in columns 0-63, layer 2 in 64-127, layer 3 in 0-15 again
+// once layer 1 has been read).  Every wait is bounded: one that gives up sets
+// the status word of the packed weights, and the block stops, waits (bounded)
+// for its last MMA and frees its tensor memory.
+constexpr unsigned TC_SPIN_LIMIT = 1u << 24;
+constexpr int TC_COLS = 128;
+
+struct TcSmem {
+  __align__(128) unsigned char w[TC_BYTES];   // W1, W2, W3 (canonical layout)
+  __align__(128) unsigned char a1[128 * IN * 2];  // layer-1 operand (K = 16)
+  __align__(128) unsigned char a2[128 * H * 2];   // layer-2 and layer-3 operands
+  float bias[NBIAS];
+  uint64_t mbar;
+  uint32_t tmem;
+  int stop;
+};
+
+__device__ __forceinline__ uint32_t sm_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor, no swizzle: start address, byte distance
+// between K-adjacent core matrices (lbo) and between 8-row groups (sbo),
+// descriptor version 1 (bits 46-47)
+__device__ __forceinline__ uint64_t tc_desc(const void *p, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((sm_addr(p) >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24
+__host__ __device__ constexpr uint32_t tc_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          sm_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned phase) {
+  for (unsigned i = 0; i < TC_SPIN_LIMIT; i++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(sm_addr(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// generic-proxy writes of shared memory made visible to the tensor cores
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's row
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int q = 0; q < 2; q++) {
-        if (r[q] >= n) continue;
-        if (mode == 0) {
-          Y[3 * r[q]] = v[q][0];
-          Y[3 * r[q] + 1] = v[q][1];
-          Y[3 * r[q] + 2] = v[q][2];
-        } else {
-          float4 d = use_prev ? du[r[q]] : make_float4(0.f, 0.f, 0.f, 0.f);
-          d.x += scale * v[q][0];
-          d.y += scale * v[q][1];
-          d.z += scale * v[q][2];
-          du[r[q]] = d;
-        }
-      }
-    }
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// bias + SiLU of 64 accumulator columns (starting at column col) of this
+// thread's row, as the next layer's BF16 operand row t
+__device__ __forceinline__ void tc_hidden(uint32_t trow, int col, const float *bias,
+                                          unsigned char *a2, int t) {
+#pragma unroll
+  for (int c = 0; c < H / 16; c++) {
+    float z[16];
+    tc_ld16(trow + col + 16 * c, z);
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      w[i] = pack_bf16(silu(z[2 * i] + bias[16 * c + 2 * i]),
+                       silu(z[2 * i + 1] + bias[16 * c + 2 * i + 1]));
+    *(uint4 *)(a2 + tc_ofs(t, 16 * c, H / 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *(uint4 *)(a2 + tc_ofs(t, 16 * c + 8, H / 8)) = make_uint4(w[4], w[5], w[6], w[7]);
   }
 }
 
-__global__ void __launch_bounds__(256)
-    mlp_forward_kernel(int64_t n, const float *__restrict__ X, const void *packed,
-                       float *__restrict__ Y) {
-  __shared__ MlpSmem sm;
-  mlp_forward_rows(n, X, packed, Y, nullptr, 0.f, 0, 0, sm);
+// Inference.  mode 0: Y[n][3] = y.  mode 1 (warm start of the fixed point):
+// du[k] = du_prev[k] + scale * y, with du_prev read from du itself (zero when
+// !use_prev).
+__device__ void mlp_tc_rows(int64_t n, const float *__restrict__ X, const void *packed,
+                            float *__restrict__ Y, float4 *__restrict__ du, float scale, int mode,
+                            int use_prev, TcSmem &sm) {
+  const int t = threadIdx.x, warp = t >> 5;
+  {
+    const uint4 *src = (const uint4 *)((const char *)packed + OFF_TC);
+    uint4 *dst = (uint4 *)sm.w;
+    for (int i = t; i < TC_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    const float *b = (const float *)((const char *)packed + OFF_B);
+    for (int i = t; i < NBIAS; i += blockDim.x) sm.bias[i] = b[i];
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     sm_addr(&sm.tmem)),
+                 "r"(TC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&sm.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sm.stop = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+  const uint64_t w1 = tc_desc(sm.w + TC_W1, 128, 256);
+  unsigned phase = 0;
+  bool pending = false;  // an MMA group whose completion was not observed
+  for (int64_t row0 = (int64_t)blockIdx.x * 128; row0 < n; row0 += (int64_t)gridDim.x * 128) {
+    const int64_t row = row0 + t;
+    {
+      // x (16 features) -> BF16 operand row t
+      float4 v[4] = {};
+      if (row < n) {
+        const float4 *xr = (const float4 *)(X + row * IN);
+#pragma unroll
+        for (int i = 0; i < 4; i++) v[i] = xr[i];
+      }
+      *(uint4 *)(sm.a1 + tc_ofs(t, 0, IN / 8)) =
+          make_uint4(pack_bf16(v[0].x, v[0].y), pack_bf16(v[0].z, v[0].w),
+                     pack_bf16(v[1].x, v[1].y), pack_bf16(v[1].z, v[1].w));
+      *(uint4 *)(sm.a1 + tc_ofs(t, 8, IN / 8)) =
+          make_uint4(pack_bf16(v[2].x, v[2].y), pack_bf16(v[2].z, v[2].w),
+                     pack_bf16(v[3].x, v[3].y), pack_bf16(v[3].z, v[3].w));
+    }
+    float y[4];
+    bool ok = true;
+#pragma unroll 1
+    for (int layer = 0; layer < 3 && ok; layer++) {
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (t == 0) {
+        tc_fence_after();
+        if (layer == 0) {
+          tc_mma(tmem, tc_desc(sm.a1, 128, 256), w1, tc_idesc(128, H), 0);
+        } else {
+          // K = 64 in four steps of 16 (two core matrices, 256 B, each)
+          const unsigned char *wb = sm.w + (layer == 1 ? TC_W2 : TC_W3);
+          const uint32_t d = tmem + (layer == 1 ? 64 : 0);
+          const uint32_t idesc = tc_idesc(128, layer == 1 ? H : 16);
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            tc_mma(d, tc_desc(sm.a2 + 256 * k, 128, 1024), tc_desc(wb + 256 * k, 128, 1024),
+                   idesc, k > 0);
+        }
+        tc_commit(&sm.mbar);
+      }
+      pending = true;
+      ok = __syncthreads_and(tc_wait(&sm.mbar, phase)) != 0;
+      phase ^= 1u;
+      if (!ok) break;
+      pending = false;
+      tc_fence_after();
+      if (layer == 0) {
+        tc_hidden(trow, 0, sm.bias, sm.a2, t);
+      } else if (layer == 1) {
+        tc_hidden(trow, 64, sm.bias + H, sm.a2, t);
+      } else {
+        float z[16];
+        tc_ld16(trow, z);
+#pragma unroll
+        for (int i = 0; i < OUT; i++) y[i] = z[i] + sm.bias[2 * H + i];
+      }
+    }
+    if (!ok) {
+      if (t == 0) atomicOr((unsigned *)((char *)packed + OFF_STATUS), 1u);
+      break;
+    }
+    if (row < n) {
+      if (mode == 0) {
+        Y[3 * row] = y[0];
+        Y[3 * row + 1] = y[1];
+        Y[3 * row + 2] = y[2];
+      } else {
+        float4 d = use_prev ? du[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+        d.x += scale * y[0];
+        d.y += scale * y[1];
+        d.z += scale * y[2];
+        du[row] = d;
+      }
+    }
+  }
+  // the last MMA group must be done before the tensor memory is freed
+  if (pending) (void)tc_wait(&sm.mbar, phase ^ 1u);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TC_COLS)
+                 : "memory");
+  }
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
+    mlp_forward_kernel(int64_t n, const float *__restrict__ X, const void *packed,
+                       float *__restrict__ Y) {
+  __shared__ TcSmem sm;
+  mlp_tc_rows(n, X, packed, Y, nullptr, 0.f, 0, 0, sm);
+}
+
+__global__ void __launch_bounds__(128)
     mlp_warm_kernel(const DomainDesc *__restrict__ D, int use_prev) {
   pdl_wait();
-  __shared__ MlpSmem sm;
+  __shared__ TcSmem sm;
   const DomainDesc &d = D[blockIdx.y];
   if (d.np == 0 || !d.mlp_packed) return;
-  mlp_forward_rows(d.np, d.feat, d.mlp_packed, nullptr, d.du, MLP_VSCALE, 1, use_prev, sm);
+  mlp_tc_rows(d.np, d.feat, d.mlp_packed, nullptr, d.du, MLP_VSCALE, 1, use_prev, sm);
 }
 
 // Shared memory of the training kernel: weights plus the block's 128 samples
@@ -480,6 +694,28 @@ __global__ void mlp_pack_kernel(const float *__restrict__ P, void *packed) {
       bias[j] = j < H ? P[P_B1 + j] : (j < 2 * H ? P[P_B2 + j - H] : P[P_B3 + j - 2 * H]);
     }
   }
+  // the tensor-core copies (rows = outputs, K = inputs) and the status word
+  unsigned char *tc = (unsigned char *)packed + OFF_TC;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < H * IN + H * H + 16 * H;
+       e += gridDim.x * blockDim.x) {
+    float v;
+    int ofs;
+    if (e < H * IN) {
+      const int r = e / IN, k = e % IN;
+      v = P[P_W1 + r * IN + k];
+      ofs = TC_W1 + tc_ofs(r, k, IN / 8);
+    } else if (e < H * IN + H * H) {
+      const int q = e - H * IN, r = q / H, k = q % H;
+      v = P[P_W2 + r * H + k];
+      ofs = TC_W2 + tc_ofs(r, k, H / 8);
+    } else {
+      const int q = e - H * IN - H * H, r = q / H, k = q % H;
+      v = r < OUT ? P[P_W3 + r * H + k] : 0.f;
+      ofs = TC_W3 + tc_ofs(r, k, H / 8);
+    }
+    *(__nv_bfloat16 *)(tc + ofs) = __float2bfloat16_rn(v);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *(unsigned *)((char *)packed + OFF_STATUS) = 0u;
 }
 
 // Adam (Kingma & Ba) on the FP32 master parameters, bias-corrected.
@@ -498,7 +734,7 @@ __global__ void mlp_adam_kernel(float *__restrict__ P, float *__restrict__ m,
 
 }  // namespace
 
-size_t mlp_packed_bytes() { return (size_t)OFF_B + NBIAS * sizeof(float); }
+size_t mlp_packed_bytes() { return (size_t)PACKED_BYTES; }
 
 size_t mlp_train_smem_bytes() { return sizeof(TrainSmem); }
 
@@ -510,8 +746,8 @@ cudaError_t launch_mlp_pack(const float *P, void *packed, cudaStream_t st) {
 cudaError_t launch_mlp_forward(int64_t n, const float *X, const void *packed, float *Y,
                                cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((n + 127) / 128, 152 * 8);
-  mlp_forward_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, X, packed, Y);
+  const int64_t blocks = std::min<int64_t>((n + 127) / 128, 152 * 4);
+  mlp_forward_kernel<<<(unsigned)blocks, 128, 0, st>>>(n, X, packed, Y);
   return cudaGetLastError();
 }
 
@@ -519,9 +755,9 @@ cudaError_t launch_mlp_warm(const DomainDesc *D, const BatchDims &dims, int use_
                             cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
   const int64_t want = (dims.max_points + 127) / 128;
-  const int64_t cap = std::max<int64_t>(1, 152 * 8 / std::max(1, dims.nd));
+  const int64_t cap = std::max<int64_t>(1, 152 * 4 / std::max(1, dims.nd));
   const unsigned bx = (unsigned)std::max<int64_t>(1, std::min(want, cap));
-  return launch_pdl(mlp_warm_kernel, dim3(bx, dims.nd), dim3(256), 0, st, D, use_prev);
+  return launch_pdl(mlp_warm_kernel, dim3(bx, dims.nd), dim3(128), 0, st, D, use_prev);
 }
 
 cudaError_t launch_mlp_loss_grad(int64_t n, const float *X, const float *T, const void *packed,
