@@ -1,23 +1,28 @@
 // Per-point MLP of the learned warm start (not in the paper): inference and
-// training kernels on the BF16 tensor cores with FP32 accumulation.
+// training kernels on the fifth-generation (tcgen05) tensor cores, BF16
+// operands, FP32 accumulation in tensor memory.
 //
 //   y = W3 s(W2 s(W1 x + b1) + b2) + b3,   s(v) = v / (1 + e^-v)   (SiLU)
 //   x: 16 features, hidden 64 and 64, y: 3 outputs.
 //
 // Parameters (FP32 master copy, owned by the caller): one flat vector
 // P = [W1 (64x16 row-major, out x in), b1 (64), W2 (64x64), b2 (64),
-// W3 (3x64), b3 (3)].  The kernels read a packed BF16 copy made by
-// launch_mlp_pack: W1, W2, W2 transposed and W3 zero-padded to 8 rows, each
-// row padded for conflict-free shared-memory fragment loads, plus the FP32
-// biases.
+// W3 (3x64), b3 (3)].  The kernels read a packed copy made by
+// launch_mlp_pack: the FP32 biases, then the BF16 weights in the canonical
+// K-major layout of the tensor cores' shared-memory operands (W1, W2, W3
+// padded to 16 rows, and W2 transposed for the backward pass), then a status
+// word.
 //
-// One warp handles 16 samples with mma.sync.m16n8k16 (A row-major 16x16 BF16,
-// B column-major 16x8 BF16, C 16x8 FP32).  The C fragment of one layer is
-// re-packed in registers as the A fragment of the next.  The training kernel
-// recomputes the forward pass, back-propagates the mean 0.5 |y - t|^2 loss
-// and forms the weight gradients of its 128 samples as tensor-core products
-// over the sample dimension; per-block partial gradients are summed by a
-// second kernel in a fixed order.
+// A block takes 128 samples (one per thread, four warps): each layer is one
+// to eight tcgen05.mma with M = 128 samples (K = 16 per instruction) whose
+// accumulators live in tensor memory; the epilogues (bias, SiLU, the
+// derivative) read them back with tcgen05.ld and write the next operand to
+// shared memory.  The training kernel recomputes the forward pass,
+// back-propagates the mean 0.5 |y - t|^2 loss and forms the weight gradients
+// of its 128 samples as tensor-core products over the sample dimension (the
+// operands transposed in shared memory, a row of ones giving the bias
+// gradients); per-block partial gradients are summed by a second kernel in a
+// fixed order.
 #include <math.h>
 #include <stdint.h>
 
@@ -30,25 +35,21 @@ namespace lbmibm {
 namespace {
 
 constexpr int IN = MLP_IN, H = MLP_HIDDEN, OUT = MLP_OUT;
-// padded row lengths (BF16 elements) of the packed matrices
-constexpr int LD1 = 24;   // W1 rows (16 used)
-constexpr int LD2 = 72;   // W2, W2^T, W3 rows (64 used)
-constexpr int OFF_W1 = 0;
-constexpr int OFF_W2 = OFF_W1 + H * LD1;
-constexpr int OFF_W2T = OFF_W2 + H * LD2;
-constexpr int OFF_W3 = OFF_W2T + H * LD2;
-constexpr int NB16 = OFF_W3 + 8 * LD2;            // BF16 elements
-constexpr int OFF_B = NB16 * 2;                   // bytes: FP32 biases follow
 constexpr int NBIAS = H + H + OUT;
-// The same weights for the tcgen05 kernels, in the canonical K-major layout
-// of the tensor-core shared-memory descriptors without swizzle: 8 x 8 BF16
-// core matrices of 128 contiguous bytes (8 rows of 16 B), the K-blocks of an
-// 8-row group next to each other (byte offset tc_ofs below).  W3 is padded
-// to 16 rows (the smallest N of an M = 128 MMA).  Then a status word that a
-// tensor-core kernel sets when one of its waits gives up.
-constexpr int OFF_TC = ((OFF_B + NBIAS * 4) + 127) / 128 * 128;  // bytes
+// parameter offsets in P
+constexpr int P_W1 = 0, P_B1 = H * IN, P_W2 = P_B1 + H, P_B2 = P_W2 + H * H, P_W3 = P_B2 + H,
+              P_B3 = P_W3 + OUT * H;
+// packed copy (bytes): FP32 biases [b1, b2, b3]; the BF16 weights in the
+// canonical K-major layout of the tensor-core shared-memory descriptors
+// without swizzle (8 x 8 core matrices of 128 contiguous bytes, 8 rows of
+// 16 B; the K-blocks of an 8-row group next to each other: tc_ofs); a status
+// word that a tensor-core kernel sets when one of its waits gives up
+constexpr int OFF_B = 0;
+constexpr int OFF_TC = (NBIAS * 4 + 127) / 128 * 128;
 constexpr int TC_W1 = 0, TC_W2 = TC_W1 + H * IN * 2, TC_W3 = TC_W2 + H * H * 2;
-constexpr int TC_BYTES = TC_W3 + 16 * H * 2;
+constexpr int TC_FWD_BYTES = TC_W3 + 16 * H * 2;  // W1, W2, W3 (16 rows)
+constexpr int TC_W2T = TC_FWD_BYTES;              // W2^T (rows = inputs)
+constexpr int TC_BYTES = TC_W2T + H * H * 2;
 constexpr int OFF_STATUS = OFF_TC + TC_BYTES;
 constexpr int PACKED_BYTES = OFF_STATUS + 16;
 
@@ -57,9 +58,6 @@ constexpr int PACKED_BYTES = OFF_STATUS + 16;
 __host__ __device__ __forceinline__ int tc_ofs(int r, int k, int kb) {
   return ((r >> 3) * kb + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
-// parameter offsets in P
-constexpr int P_W1 = 0, P_B1 = H * IN, P_W2 = P_B1 + H, P_B2 = P_W2 + H * H, P_W3 = P_B2 + H,
-              P_B3 = P_W3 + OUT * H;
 
 __device__ __forceinline__ float silu(float v) { return v / (1.f + __expf(-v)); }
 __device__ __forceinline__ float silu_grad(float v) {
@@ -70,118 +68,6 @@ __device__ __forceinline__ float silu_grad(float v) {
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// two consecutive BF16 of a padded row in shared memory, as one register
-__device__ __forceinline__ uint32_t ld2(const __nv_bfloat16 *s, int row, int ld, int col) {
-  return *reinterpret_cast<const uint32_t *>(s + row * ld + col);
-}
-
-struct MlpSmem {
-  __nv_bfloat16 w[NB16];
-  float bias[NBIAS];
-};
-
-__device__ void load_weights(MlpSmem &sm, const void *packed) {
-  const uint4 *src = (const uint4 *)packed;
-  uint4 *dst = (uint4 *)sm.w;
-  for (int i = threadIdx.x; i < NB16 * 2 / 16; i += blockDim.x) dst[i] = src[i];
-  const float *b = (const float *)((const char *)packed + OFF_B);
-  for (int i = threadIdx.x; i < NBIAS; i += blockDim.x) sm.bias[i] = b[i];
-}
-
-// Forward pass of the warp's 16 samples.  xa: A fragment of the inputs.
-// z1, z2: pre-activations (C fragments, 8 n-tiles x 4), h1a, h2a: the
-// activations as A fragments (4 k-chunks x 4), y: C fragment of the output.
-struct Fwd {
-  float z1[8][4], z2[8][4], y[4];
-  uint32_t h1a[4][4], h2a[4][4];
-};
-
-__device__ __forceinline__ void c_to_a(const float h[8][4], uint32_t a[4][4]) {
-#pragma unroll
-  for (int kc = 0; kc < 4; kc++) {
-    a[kc][0] = pack_bf16(h[2 * kc][0], h[2 * kc][1]);
-    a[kc][1] = pack_bf16(h[2 * kc][2], h[2 * kc][3]);
-    a[kc][2] = pack_bf16(h[2 * kc + 1][0], h[2 * kc + 1][1]);
-    a[kc][3] = pack_bf16(h[2 * kc + 1][2], h[2 * kc + 1][3]);
-  }
-}
-
-__device__ __forceinline__ void forward16(const MlpSmem &sm, const uint32_t xa[4], Fwd &f) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const __nv_bfloat16 *W1 = sm.w + OFF_W1, *W2 = sm.w + OFF_W2, *W3 = sm.w + OFF_W3;
-  float h[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    mma_bf16(c, xa, ld2(W1, nt * 8 + g, LD1, 2 * t), ld2(W1, nt * 8 + g, LD1, 2 * t + 8));
-    const float bb0 = sm.bias[nt * 8 + 2 * t], bb1 = sm.bias[nt * 8 + 2 * t + 1];
-    f.z1[nt][0] = c[0] + bb0;
-    f.z1[nt][1] = c[1] + bb1;
-    f.z1[nt][2] = c[2] + bb0;
-    f.z1[nt][3] = c[3] + bb1;
-#pragma unroll
-    for (int q = 0; q < 4; q++) h[nt][q] = silu(f.z1[nt][q]);
-  }
-  c_to_a(h, f.h1a);
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int kc = 0; kc < 4; kc++)
-      mma_bf16(c, f.h1a[kc], ld2(W2, nt * 8 + g, LD2, kc * 16 + 2 * t),
-               ld2(W2, nt * 8 + g, LD2, kc * 16 + 2 * t + 8));
-    const float bb0 = sm.bias[H + nt * 8 + 2 * t], bb1 = sm.bias[H + nt * 8 + 2 * t + 1];
-    f.z2[nt][0] = c[0] + bb0;
-    f.z2[nt][1] = c[1] + bb1;
-    f.z2[nt][2] = c[2] + bb0;
-    f.z2[nt][3] = c[3] + bb1;
-#pragma unroll
-    for (int q = 0; q < 4; q++) h[nt][q] = silu(f.z2[nt][q]);
-  }
-  c_to_a(h, f.h2a);
-  float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int kc = 0; kc < 4; kc++)
-    mma_bf16(c, f.h2a[kc], ld2(W3, g, LD2, kc * 16 + 2 * t), ld2(W3, g, LD2, kc * 16 + 2 * t + 8));
-  // columns 2t, 2t+1 of rows g, g+8; only columns 0..2 exist
-  const float bb0 = 2 * t < OUT ? sm.bias[2 * H + 2 * t] : 0.f;
-  const float bb1 = 2 * t + 1 < OUT ? sm.bias[2 * H + 2 * t + 1] : 0.f;
-  f.y[0] = c[0] + bb0;
-  f.y[1] = c[1] + bb1;
-  f.y[2] = c[2] + bb0;
-  f.y[3] = c[3] + bb1;
-}
-
-// A fragment of 16 samples x 16 features from FP32 rows in global memory
-// (rows >= n read as zero).
-__device__ __forceinline__ void load_x(const float *__restrict__ X, int64_t row0, int64_t n,
-                                       uint32_t xa[4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int64_t r0 = row0 + g, r1 = row0 + g + 8;
-  float2 v00 = make_float2(0.f, 0.f), v01 = v00, v10 = v00, v11 = v00;
-  if (r0 < n) {
-    v00 = *(const float2 *)(X + r0 * IN + 2 * t);
-    v01 = *(const float2 *)(X + r0 * IN + 2 * t + 8);
-  }
-  if (r1 < n) {
-    v10 = *(const float2 *)(X + r1 * IN + 2 * t);
-    v11 = *(const float2 *)(X + r1 * IN + 2 * t + 8);
-  }
-  xa[0] = pack_bf16(v00.x, v00.y);
-  xa[1] = pack_bf16(v10.x, v10.y);
-  xa[2] = pack_bf16(v01.x, v01.y);
-  xa[3] = pack_bf16(v11.x, v11.y);
 }
 
 // ---- inference on the fifth-generation tensor cores (tcgen05) -------------
@@ -202,7 +88,7 @@ constexpr unsigned TC_SPIN_LIMIT = 1u << 24;
 constexpr int TC_COLS = 128;
 
 struct TcSmem {
-  __align__(128) unsigned char w[TC_BYTES];   // W1, W2, W3 (canonical layout)
+  __align__(128) unsigned char w[TC_FWD_BYTES];  // W1, W2, W3 (canonical layout)
   __align__(128) unsigned char a1[128 * IN * 2];  // layer-1 operand (K = 16)
   __align__(128) unsigned char a2[128 * H * 2];   // layer-2 and layer-3 operands
   float bias[NBIAS];
@@ -314,7 +200,7 @@ __device__ void mlp_tc_rows(int64_t n, const float *__restrict__ X, const void *
   {
     const uint4 *src = (const uint4 *)((const char *)packed + OFF_TC);
     uint4 *dst = (uint4 *)sm.w;
-    for (int i = t; i < TC_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = t; i < TC_FWD_BYTES / 16; i += blockDim.x) dst[i] = src[i];
     const float *b = (const float *)((const char *)packed + OFF_B);
     for (int i = t; i < NBIAS; i += blockDim.x) sm.bias[i] = b[i];
   }
@@ -441,215 +327,271 @@ __global__ void __launch_bounds__(128)
   mlp_tc_rows(d.np, d.feat, d.mlp_packed, nullptr, d.du, MLP_VSCALE, 1, use_prev, sm);
 }
 
-// Shared memory of the training kernel: weights plus the block's 128 samples
-// of x, dz1, h1, dz2, h2 (BF16) and dy (FP32) for the weight gradients.
+// ---- training: forward, backward and weight gradients of 128 samples -----
+//
+// Tensor memory (256 columns): z1 = W1 x in 0-63, z2 = W2 h1 in 64-127 and y
+// in 128-143 for the forward pass; then dh1 = dz2 W2 in 144-207, the weight
+// gradient of layer 2 (with the bias gradient in its column 64) over 64-143
+// once z2 and y have been read, and that of layer 1 (bias in column 16) in
+// 208-239.  Shared-memory operands (BF16, canonical layout): x, h1, h2 and
+// dz2 sample-major for the forward and backward products; x^T, h1^T (each
+// with a row of ones) and dz^T (dz2^T, then dz1^T, 64 rows padded to 128
+// with zeros) for the products over the samples.
+constexpr int TR_COLS = 256;
+constexpr int KB_S = 128 / 8;  // K-blocks of an operand whose K is the 128 samples
+
 struct TrainSmem {
-  MlpSmem m;
-  float w3[OUT * H];                // W3 in FP32 for the first backward step
-  __nv_bfloat16 x[128][IN + 8];
-  __nv_bfloat16 h1[128][H + 8], dz1[128][H + 8];
-  __nv_bfloat16 h2[128][H + 8], dz2[128][H + 8];
+  __align__(128) unsigned char w[TC_BYTES];            // W1, W2, W3, W2^T
+  __align__(128) unsigned char x[128 * IN * 2];        // [s][16]
+  __align__(128) unsigned char xT[32 * 128 * 2];       // [16 + ones + pad][s]
+  __align__(128) unsigned char h1[128 * H * 2];        // [s][64]
+  __align__(128) unsigned char h1T[80 * 128 * 2];      // [64 + ones + pad][s]
+  __align__(128) unsigned char h2[128 * H * 2];        // [s][64]
+  __align__(128) unsigned char dz2[128 * H * 2];       // [s][64]
+  __align__(128) unsigned char dzT[128 * 128 * 2];     // [64 + zero pad][s]
+  float w3[OUT * H];                                   // W3 in FP32
+  float bias[NBIAS];
   float dy[128][4];
-  float red[8][NBIAS];
-  float loss[8];
+  float loss[4];
+  uint64_t mbar;
+  uint32_t tmem;
 };
 
-// One block = 8 warps = 128 samples.  Writes its partial gradient (FP32,
-// layout of P) and partial loss.
-__global__ void __launch_bounds__(256)
+// this thread's row of a sample-major operand with 64 columns, from 64
+// FP32 values
+__device__ __forceinline__ void put_row64(unsigned char *op, int s, const float v[H]) {
+#pragma unroll
+  for (int c = 0; c < H / 8; c++)
+    *(uint4 *)(op + tc_ofs(s, 8 * c, H / 8)) =
+        make_uint4(pack_bf16(v[8 * c], v[8 * c + 1]), pack_bf16(v[8 * c + 2], v[8 * c + 3]),
+                   pack_bf16(v[8 * c + 4], v[8 * c + 5]), pack_bf16(v[8 * c + 6], v[8 * c + 7]));
+}
+
+// column s of a transposed operand (rows 0 .. m-1, K = the 128 samples)
+template <int M>
+__device__ __forceinline__ void put_col(unsigned char *op, int s, const float v[M]) {
+#pragma unroll
+  for (int r = 0; r < M; r++)
+    *(__nv_bfloat16 *)(op + tc_ofs(r, s, KB_S)) = __float2bfloat16_rn(v[r]);
+}
+
+// 64 accumulator columns (from col) of this thread's row
+__device__ __forceinline__ void tc_ld64(uint32_t trow, int col, float v[H]) {
+#pragma unroll
+  for (int c = 0; c < H / 16; c++) tc_ld16(trow + col + 16 * c, v + 16 * c);
+}
+
+// one tensor-core round of the block: thread 0 issues `issue` after every
+// thread's shared-memory writes, and every thread waits for the products
+template <typename Issue>
+__device__ __forceinline__ bool tc_round(TrainSmem &sm, unsigned &phase, Issue issue) {
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    issue();
+    tc_commit(&sm.mbar);
+  }
+  const bool ok = __syncthreads_and(tc_wait(&sm.mbar, phase)) != 0;
+  phase ^= 1u;
+  if (ok) tc_fence_after();
+  return ok;
+}
+
+// One block = 128 samples (one per thread).  Writes its partial gradient
+// (FP32, layout of P) and partial loss.
+__global__ void __launch_bounds__(128)
     mlp_train_kernel(int64_t n, const float *__restrict__ X, const float *__restrict__ T,
                      const void *packed, const float *__restrict__ P, float *__restrict__ part,
                      float *__restrict__ part_loss, float inv_n) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   TrainSmem &sm = *reinterpret_cast<TrainSmem *>(smraw);
-  load_weights(sm.m, packed);
-  for (int i = threadIdx.x; i < OUT * H; i += blockDim.x) sm.w3[i] = P[P_W3 + i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-  const int64_t row0 = (int64_t)blockIdx.x * 128 + w * 16;
-  uint32_t xa[4];
-  load_x(X, row0, n, xa);
-  Fwd f;
-  forward16(sm.m, xa, f);
-  const int lr0 = w * 16 + g, lr1 = lr0 + 8;  // local rows
-  const int64_t gr0 = row0 + g, gr1 = row0 + g + 8;
-  // dy = (y - t) / n for valid rows and columns; loss
-  float dy[4], loss = 0.f;
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const int col = 2 * t + (q & 1);
-    const int64_t row = q < 2 ? gr0 : gr1;
-    float e = 0.f;
-    if (col < OUT && row < n) e = f.y[q] - T[3 * row + col];
-    loss += 0.5f * e * e;
-    dy[q] = e * inv_n;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  {
+    const uint4 *src = (const uint4 *)((const char *)packed + OFF_TC);
+    for (int i = t; i < TC_BYTES / 16; i += blockDim.x) ((uint4 *)sm.w)[i] = src[i];
+    const float *b = (const float *)((const char *)packed + OFF_B);
+    for (int i = t; i < NBIAS; i += blockDim.x) sm.bias[i] = b[i];
+    for (int i = t; i < OUT * H; i += blockDim.x) sm.w3[i] = P[P_W3 + i];
+    // the rows of ones (bias gradients) and the zero padding of the
+    // transposed operands
+    for (int i = t; i < 32 * 128 * 2 / 16; i += blockDim.x) ((uint4 *)sm.xT)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = t; i < 80 * 128 * 2 / 16; i += blockDim.x) ((uint4 *)sm.h1T)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = t; i < 128 * 128 * 2 / 16; i += blockDim.x) ((uint4 *)sm.dzT)[i] = make_uint4(0, 0, 0, 0);
   }
-  if (t < 2) {
-    sm.dy[lr0][2 * t] = dy[0];
-    sm.dy[lr0][2 * t + 1] = dy[1];
-    sm.dy[lr1][2 * t] = dy[2];
-    sm.dy[lr1][2 * t + 1] = dy[3];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     sm_addr(&sm.tmem)),
+                 "r"(TR_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(&sm.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  *(__nv_bfloat16 *)(sm.xT + tc_ofs(IN, t, KB_S)) = __float2bfloat16_rn(1.f);
+  *(__nv_bfloat16 *)(sm.h1T + tc_ofs(H, t, KB_S)) = __float2bfloat16_rn(1.f);
+  const uint32_t tmem = sm.tmem;
+  const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+  const int64_t row = (int64_t)blockIdx.x * 128 + t;
+  const bool valid = row < n;
+  const unsigned char *W1 = sm.w + TC_W1, *W2 = sm.w + TC_W2, *W3 = sm.w + TC_W3,
+                      *W2T = sm.w + TC_W2T;
+  unsigned phase = 0;
+  bool ok = true;
+  {
+    float x[IN] = {};
+    if (valid)
+#pragma unroll
+      for (int i = 0; i < IN; i++) x[i] = X[row * IN + i];
+    *(uint4 *)(sm.x + tc_ofs(t, 0, IN / 8)) =
+        make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]),
+                   pack_bf16(x[6], x[7]));
+    *(uint4 *)(sm.x + tc_ofs(t, 8, IN / 8)) =
+        make_uint4(pack_bf16(x[8], x[9]), pack_bf16(x[10], x[11]), pack_bf16(x[12], x[13]),
+                   pack_bf16(x[14], x[15]));
+    put_col<IN>(sm.xT, t, x);
+  }
+  // forward, layer 1: z1 = W1 x (columns 0-63)
+  ok = tc_round(sm, phase, [&] {
+    tc_mma(tmem, tc_desc(sm.x, 128, 256), tc_desc(W1, 128, 256), tc_idesc(128, H), 0);
+  });
+  if (ok) {
+    float z[H];
+    tc_ld64(trow, 0, z);
+#pragma unroll
+    for (int i = 0; i < H; i++) z[i] = silu(z[i] + sm.bias[i]);
+    put_row64(sm.h1, t, z);
+    put_col<H>(sm.h1T, t, z);
+    // layer 2: z2 = W2 h1 (columns 64-127)
+    ok = tc_round(sm, phase, [&] {
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        tc_mma(tmem + 64, tc_desc(sm.h1 + 256 * k, 128, 1024),
+               tc_desc(W2 + 256 * k, 128, 1024), tc_idesc(128, H), k > 0);
+    });
+  }
+  if (ok) {
+    float z[H];
+    tc_ld64(trow, 64, z);
+#pragma unroll
+    for (int i = 0; i < H; i++) z[i] = silu(z[i] + sm.bias[H + i]);
+    put_row64(sm.h2, t, z);
+    // layer 3: y (columns 128-143)
+    ok = tc_round(sm, phase, [&] {
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        tc_mma(tmem + 128, tc_desc(sm.h2 + 256 * k, 128, 1024),
+               tc_desc(W3 + 256 * k, 128, 1024), tc_idesc(128, 16), k > 0);
+    });
+  }
+  float loss = 0.f;
+  if (ok) {
+    // dy = (y - t) / n; dh2 = dy W3 (FP32); dz2 = dh2 s'(z2)
+    float yv[16];
+    tc_ld16(trow + 128, yv);
+    float dy[OUT];
+#pragma unroll
+    for (int c = 0; c < OUT; c++) {
+      const float e = valid ? yv[c] + sm.bias[2 * H + c] - T[3 * row + c] : 0.f;
+      loss += 0.5f * e * e;
+      dy[c] = e * inv_n;
+      sm.dy[t][c] = dy[c];
+    }
+    float z[H];
+    tc_ld64(trow, 64, z);
+#pragma unroll
+    for (int i = 0; i < H; i++) {
+      float dh = 0.f;
+#pragma unroll
+      for (int c = 0; c < OUT; c++) dh += dy[c] * sm.w3[c * H + i];
+      z[i] = dh * silu_grad(z[i] + sm.bias[H + i]);
+    }
+    put_row64(sm.dz2, t, z);
+    put_col<H>(sm.dzT, t, z);
+    // dh1 = dz2 W2 (columns 144-207) and the layer-2 gradient
+    // sum_s dz2^T [h1 | 1] (columns 64-143, over z2 and y)
+    ok = tc_round(sm, phase, [&] {
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        tc_mma(tmem + 144, tc_desc(sm.dz2 + 256 * k, 128, 1024),
+               tc_desc(W2T + 256 * k, 128, 1024), tc_idesc(128, H), k > 0);
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        tc_mma(tmem + 64, tc_desc(sm.dzT + 256 * k, 128, 2048),
+               tc_desc(sm.h1T + 256 * k, 128, 2048), tc_idesc(128, 80), k > 0);
+    });
+  }
+  if (ok) {
+    // dz1 = dh1 s'(z1); the layer-1 gradient sum_s dz1^T [x | 1] (208-239)
+    float dh[H], z[H];
+    tc_ld64(trow, 144, dh);
+    tc_ld64(trow, 0, z);
+#pragma unroll
+    for (int i = 0; i < H; i++) z[i] = dh[i] * silu_grad(z[i] + sm.bias[i]);
+    put_col<H>(sm.dzT, t, z);
+    ok = tc_round(sm, phase, [&] {
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        tc_mma(tmem + 208, tc_desc(sm.dzT + 256 * k, 128, 2048),
+               tc_desc(sm.xT + 256 * k, 128, 2048), tc_idesc(128, 32), k > 0);
+    });
+  }
+  float *pb = part + (size_t)blockIdx.x * MLP_NPARAM;
+  if (ok) {
+    // rows 0-63 of the gradients (lanes of warps 0 and 1): one row per thread
+    if (warp < 2) {
+      float g[16];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        tc_ld16(trow + 64 + 16 * c, g);
+#pragma unroll
+        for (int i = 0; i < 16; i++) pb[P_W2 + t * H + 16 * c + i] = g[i];
+      }
+      tc_ld16(trow + 128, g);
+      pb[P_B2 + t] = g[0];
+      float g1[16], g2[16];
+      tc_ld16(trow + 208, g1);
+      tc_ld16(trow + 224, g2);
+#pragma unroll
+      for (int i = 0; i < IN; i++) pb[P_W1 + t * IN + i] = g1[i];
+      pb[P_B1 + t] = g2[0];
+    }
+    // layer 3 in FP32 on the CUDA cores (N = 3): dW3 = dy^T h2, db3
+    for (int e = t; e < OUT * H + OUT; e += blockDim.x) {
+      float s = 0.f;
+      if (e < OUT * H) {
+        const int c = e / H, i = e % H;
+        for (int r = 0; r < 128; r++)
+          s += sm.dy[r][c] * __bfloat162float(*(const __nv_bfloat16 *)(sm.h2 + tc_ofs(r, i, H / 8)));
+        pb[P_W3 + e] = s;
+      } else {
+        for (int r = 0; r < 128; r++) s += sm.dy[r][e - OUT * H];
+        pb[P_B3 + e - OUT * H] = s;
+      }
+    }
+  } else {
+    if (t == 0) atomicOr((unsigned *)((char *)packed + OFF_STATUS), 1u);
+    for (int e = t; e < MLP_NPARAM; e += blockDim.x) pb[e] = 0.f;
+    // the last product group must be done before the tensor memory is freed
+    (void)tc_wait(&sm.mbar, phase ^ 1u);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-  if (lane == 0) sm.loss[w] = loss;
-  // stage x, h1, h2 for the weight gradients
-  {
-    const float2 *xr0 = (const float2 *)(X + (gr0 < n ? gr0 : 0) * IN);
-    const float2 *xr1 = (const float2 *)(X + (gr1 < n ? gr1 : 0) * IN);
-    // x rows in BF16 (zero for rows >= n)
-    const float2 a = gr0 < n ? xr0[t] : make_float2(0.f, 0.f),
-                 b = gr0 < n ? xr0[t + 4] : make_float2(0.f, 0.f),
-                 c = gr1 < n ? xr1[t] : make_float2(0.f, 0.f),
-                 d = gr1 < n ? xr1[t + 4] : make_float2(0.f, 0.f);
-    *(uint32_t *)&sm.x[lr0][2 * t] = pack_bf16(a.x, a.y);
-    *(uint32_t *)&sm.x[lr0][2 * t + 8] = pack_bf16(b.x, b.y);
-    *(uint32_t *)&sm.x[lr1][2 * t] = pack_bf16(c.x, c.y);
-    *(uint32_t *)&sm.x[lr1][2 * t + 8] = pack_bf16(d.x, d.y);
-  }
-#pragma unroll
-  for (int kc = 0; kc < 4; kc++) {
-    *(uint32_t *)&sm.h1[lr0][kc * 16 + 2 * t] = f.h1a[kc][0];
-    *(uint32_t *)&sm.h1[lr1][kc * 16 + 2 * t] = f.h1a[kc][1];
-    *(uint32_t *)&sm.h1[lr0][kc * 16 + 2 * t + 8] = f.h1a[kc][2];
-    *(uint32_t *)&sm.h1[lr1][kc * 16 + 2 * t + 8] = f.h1a[kc][3];
-    *(uint32_t *)&sm.h2[lr0][kc * 16 + 2 * t] = f.h2a[kc][0];
-    *(uint32_t *)&sm.h2[lr1][kc * 16 + 2 * t] = f.h2a[kc][1];
-    *(uint32_t *)&sm.h2[lr0][kc * 16 + 2 * t + 8] = f.h2a[kc][2];
-    *(uint32_t *)&sm.h2[lr1][kc * 16 + 2 * t + 8] = f.h2a[kc][3];
-  }
-  __syncwarp();
-  // dh2 = dy W3 (K = 3, FP32), dz2 = dh2 s'(z2)
-  const float dyr0[3] = {sm.dy[lr0][0], sm.dy[lr0][1], sm.dy[lr0][2]};
-  const float dyr1[3] = {sm.dy[lr1][0], sm.dy[lr1][1], sm.dy[lr1][2]};
-  float dz[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int col = nt * 8 + 2 * t + (q & 1);
-      const float *dr = q < 2 ? dyr0 : dyr1;
-      const float dh = dr[0] * sm.w3[col] + dr[1] * sm.w3[H + col] + dr[2] * sm.w3[2 * H + col];
-      dz[nt][q] = dh * silu_grad(f.z2[nt][q]);
-    }
-  }
-  uint32_t dz2a[4][4];
-  c_to_a(dz, dz2a);
-#pragma unroll
-  for (int kc = 0; kc < 4; kc++) {
-    *(uint32_t *)&sm.dz2[lr0][kc * 16 + 2 * t] = dz2a[kc][0];
-    *(uint32_t *)&sm.dz2[lr1][kc * 16 + 2 * t] = dz2a[kc][1];
-    *(uint32_t *)&sm.dz2[lr0][kc * 16 + 2 * t + 8] = dz2a[kc][2];
-    *(uint32_t *)&sm.dz2[lr1][kc * 16 + 2 * t + 8] = dz2a[kc][3];
-  }
-  // dh1 = dz2 W2 (B[k=o][n=i] = W2[o][i] = W2T[i][o]), dz1 = dh1 s'(z1)
-  const __nv_bfloat16 *W2T = sm.m.w + OFF_W2T;
-#pragma unroll
-  for (int nt = 0; nt < 8; nt++) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int kc = 0; kc < 4; kc++)
-      mma_bf16(c, dz2a[kc], ld2(W2T, nt * 8 + g, LD2, kc * 16 + 2 * t),
-               ld2(W2T, nt * 8 + g, LD2, kc * 16 + 2 * t + 8));
-#pragma unroll
-    for (int q = 0; q < 4; q++) dz[nt][q] = c[q] * silu_grad(f.z1[nt][q]);
-  }
-  uint32_t dz1a[4][4];
-  c_to_a(dz, dz1a);
-#pragma unroll
-  for (int kc = 0; kc < 4; kc++) {
-    *(uint32_t *)&sm.dz1[lr0][kc * 16 + 2 * t] = dz1a[kc][0];
-    *(uint32_t *)&sm.dz1[lr1][kc * 16 + 2 * t] = dz1a[kc][1];
-    *(uint32_t *)&sm.dz1[lr0][kc * 16 + 2 * t + 8] = dz1a[kc][2];
-    *(uint32_t *)&sm.dz1[lr1][kc * 16 + 2 * t + 8] = dz1a[kc][3];
-  }
+  if (lane == 0) sm.loss[warp] = loss;
+  tc_fence_before();
   __syncthreads();
-  float *pb = part + (size_t)blockIdx.x * MLP_NPARAM;
-  // Weight gradients over the block's 128 samples (K = sample):
-  //   dW2[o][i] = sum_r dz2[r][o] h1[r][i], dW1[o][i] = sum_r dz1[r][o] x[r][i]
-  // A[m = o][k = r] = dz[r][o], B[k = r][n = i] = h[r][i], both gathered from
-  // the sample-major tiles.  Warp w owns output rows 16 (w >> 1) .. +15 and
-  // half of the columns.
-  {
-    const int m0 = (w >> 1) * 16;
-    auto afrag = [&](const __nv_bfloat16 (*dzt)[H + 8], int k0, uint32_t a[4]) {
-      auto e = [&](int k, int m) { return dzt[k0 + k][m0 + m]; };
-      a[0] = pack_bf16(__bfloat162float(e(2 * t, g)), __bfloat162float(e(2 * t + 1, g)));
-      a[1] = pack_bf16(__bfloat162float(e(2 * t, g + 8)), __bfloat162float(e(2 * t + 1, g + 8)));
-      a[2] = pack_bf16(__bfloat162float(e(2 * t + 8, g)), __bfloat162float(e(2 * t + 9, g)));
-      a[3] = pack_bf16(__bfloat162float(e(2 * t + 8, g + 8)), __bfloat162float(e(2 * t + 9, g + 8)));
-    };
-    // dW2: 4 n-tiles per warp
-    {
-      float c[4][4] = {};
-      const int n0 = (w & 1) * 32;
-      for (int k0 = 0; k0 < 128; k0 += 16) {
-        uint32_t a[4];
-        afrag(sm.dz2, k0, a);
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-          const int nn = n0 + j * 8 + g;
-          const uint32_t b0 = pack_bf16(__bfloat162float(sm.h1[k0 + 2 * t][nn]),
-                                        __bfloat162float(sm.h1[k0 + 2 * t + 1][nn]));
-          const uint32_t b1 = pack_bf16(__bfloat162float(sm.h1[k0 + 2 * t + 8][nn]),
-                                        __bfloat162float(sm.h1[k0 + 2 * t + 9][nn]));
-          mma_bf16(c[j], a, b0, b1);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const int col = n0 + j * 8 + 2 * t;
-        pb[P_W2 + (m0 + g) * H + col] = c[j][0];
-        pb[P_W2 + (m0 + g) * H + col + 1] = c[j][1];
-        pb[P_W2 + (m0 + g + 8) * H + col] = c[j][2];
-        pb[P_W2 + (m0 + g + 8) * H + col + 1] = c[j][3];
-      }
-    }
-    // dW1: one n-tile per warp (N = 16)
-    {
-      float c[4] = {};
-      const int n0 = (w & 1) * 8;
-      for (int k0 = 0; k0 < 128; k0 += 16) {
-        uint32_t a[4];
-        afrag(sm.dz1, k0, a);
-        const int nn = n0 + g;
-        const uint32_t b0 = pack_bf16(__bfloat162float(sm.x[k0 + 2 * t][nn]),
-                                      __bfloat162float(sm.x[k0 + 2 * t + 1][nn]));
-        const uint32_t b1 = pack_bf16(__bfloat162float(sm.x[k0 + 2 * t + 8][nn]),
-                                      __bfloat162float(sm.x[k0 + 2 * t + 9][nn]));
-        mma_bf16(c, a, b0, b1);
-      }
-      const int col = n0 + 2 * t;
-      pb[P_W1 + (m0 + g) * IN + col] = c[0];
-      pb[P_W1 + (m0 + g) * IN + col + 1] = c[1];
-      pb[P_W1 + (m0 + g + 8) * IN + col] = c[2];
-      pb[P_W1 + (m0 + g + 8) * IN + col + 1] = c[3];
-    }
-  }
-  // dW3[c][o] = sum_r dy[r][c] h2[r][o] (N = 3: FP32 dot products), biases
-  for (int e = threadIdx.x; e < OUT * H; e += blockDim.x) {
-    const int cc = e / H, o = e % H;
-    float s = 0.f;
-    for (int r = 0; r < 128; r++) s += sm.dy[r][cc] * __bfloat162float(sm.h2[r][o]);
-    pb[P_W3 + e] = s;
-  }
-  for (int e = threadIdx.x; e < NBIAS; e += blockDim.x) {
-    float s = 0.f;
-    if (e < H) {
-      for (int r = 0; r < 128; r++) s += __bfloat162float(sm.dz1[r][e]);
-      pb[P_B1 + e] = s;
-    } else if (e < 2 * H) {
-      for (int r = 0; r < 128; r++) s += __bfloat162float(sm.dz2[r][e - H]);
-      pb[P_B2 + e - H] = s;
-    } else {
-      for (int r = 0; r < 128; r++) s += sm.dy[r][e - 2 * H];
-      pb[P_B3 + e - 2 * H] = s;
-    }
-  }
-  if (threadIdx.x == 0) {
-    float l = 0.f;
-    for (int q = 0; q < 8; q++) l += sm.loss[q];
-    part_loss[blockIdx.x] = l * inv_n;
+  if (t == 0) part_loss[blockIdx.x] = ((sm.loss[0] + sm.loss[1]) + (sm.loss[2] + sm.loss[3])) * inv_n;
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TR_COLS)
+                 : "memory");
   }
 }
 
@@ -670,34 +612,21 @@ __global__ void mlp_reduce_kernel(int nblocks, const float *__restrict__ part,
   }
 }
 
-// FP32 parameters -> packed BF16 matrices (padded rows, W2 also transposed,
-// W3 zero-padded to 8 rows) + FP32 biases.
+
+// FP32 parameters -> packed copy: FP32 biases, BF16 weights in the canonical
+// layout (rows = outputs, K = inputs; W3 padded to 16 rows; W2^T with rows =
+// inputs), status word cleared.
 __global__ void mlp_pack_kernel(const float *__restrict__ P, void *packed) {
-  __nv_bfloat16 *w = (__nv_bfloat16 *)packed;
   float *bias = (float *)((char *)packed + OFF_B);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < NB16 + NBIAS;
-       e += gridDim.x * blockDim.x) {
-    if (e < OFF_W2) {
-      const int r = e / LD1, c = e % LD1;
-      w[e] = __float2bfloat16_rn(c < IN ? P[P_W1 + r * IN + c] : 0.f);
-    } else if (e < OFF_W2T) {
-      const int r = (e - OFF_W2) / LD2, c = (e - OFF_W2) % LD2;
-      w[e] = __float2bfloat16_rn(c < H ? P[P_W2 + r * H + c] : 0.f);
-    } else if (e < OFF_W3) {
-      const int r = (e - OFF_W2T) / LD2, c = (e - OFF_W2T) % LD2;
-      w[e] = __float2bfloat16_rn(c < H ? P[P_W2 + c * H + r] : 0.f);
-    } else if (e < NB16) {
-      const int r = (e - OFF_W3) / LD2, c = (e - OFF_W3) % LD2;
-      w[e] = __float2bfloat16_rn(r < OUT && c < H ? P[P_W3 + r * H + c] : 0.f);
-    } else {
-      const int j = e - NB16;
-      bias[j] = j < H ? P[P_B1 + j] : (j < 2 * H ? P[P_B2 + j - H] : P[P_B3 + j - 2 * H]);
-    }
-  }
-  // the tensor-core copies (rows = outputs, K = inputs) and the status word
   unsigned char *tc = (unsigned char *)packed + OFF_TC;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < H * IN + H * H + 16 * H;
+  const int nw = H * IN + H * H + 16 * H + H * H;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nw + NBIAS;
        e += gridDim.x * blockDim.x) {
+    if (e >= nw) {
+      const int j = e - nw;
+      bias[j] = j < H ? P[P_B1 + j] : (j < 2 * H ? P[P_B2 + j - H] : P[P_B3 + j - 2 * H]);
+      continue;
+    }
     float v;
     int ofs;
     if (e < H * IN) {
@@ -708,10 +637,15 @@ __global__ void mlp_pack_kernel(const float *__restrict__ P, void *packed) {
       const int q = e - H * IN, r = q / H, k = q % H;
       v = P[P_W2 + r * H + k];
       ofs = TC_W2 + tc_ofs(r, k, H / 8);
-    } else {
+    } else if (e < H * IN + H * H + 16 * H) {
       const int q = e - H * IN - H * H, r = q / H, k = q % H;
       v = r < OUT ? P[P_W3 + r * H + k] : 0.f;
       ofs = TC_W3 + tc_ofs(r, k, H / 8);
+    } else {
+      // W2^T: row r = input of layer 2, column k = output
+      const int q = e - H * IN - H * H - 16 * H, r = q / H, k = q % H;
+      v = P[P_W2 + k * H + r];
+      ofs = TC_W2T + tc_ofs(r, k, H / 8);
     }
     *(__nv_bfloat16 *)(tc + ofs) = __float2bfloat16_rn(v);
   }
@@ -731,6 +665,7 @@ __global__ void mlp_adam_kernel(float *__restrict__ P, float *__restrict__ m,
   v[j] = vj;
   P[j] -= lr * (mj / c1) / (sqrtf(vj / c2) + eps);
 }
+
 
 }  // namespace
 
@@ -770,7 +705,7 @@ cudaError_t launch_mlp_loss_grad(int64_t n, const float *X, const float *T, cons
                                        (int)sizeof(TrainSmem));
   if (e != cudaSuccess) return e;
   float *part_loss = part + (size_t)nb * MLP_NPARAM;
-  mlp_train_kernel<<<nb, 256, sizeof(TrainSmem), st>>>(n, X, T, packed, P, part, part_loss,
+  mlp_train_kernel<<<nb, 128, sizeof(TrainSmem), st>>>(n, X, T, packed, P, part, part_loss,
                                                        1.f / (float)n);
   mlp_reduce_kernel<<<(MLP_NPARAM + 1 + 255) / 256, 256, 0, st>>>(nb, part, part_loss, grad,
                                                                   loss);
