@@ -369,6 +369,7 @@ def run_ours(args):
         line["paper_sweep"] = bench_paper_sweep()
         line["delta_kernels"] = bench_delta_kernels()
         line["point_order"] = bench_point_order()
+        line["mlp"] = bench_mlp()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         wcpu = W.dense_array_256()
         dt, cores = cpu_oracle_run(wcpu, 2)
@@ -623,6 +624,45 @@ def bench_point_order(steps=200, warmup=5):
         out["mlups"][name] = w.cells * steps / (ms / 1e3) / 1e6
         lat.close()
     return out
+
+
+def bench_mlp(reps=50):
+    """The learned start's network on the tensor cores: one inference pass
+    over the 89,600 points of the 256^3 array (mlp_forward_dev) and one
+    loss-gradient pass over a training batch of 16,384 samples
+    (mlp_loss_grad_dev), device time per call and the tensor FLOP rate
+    (2 x (16 x 64 + 64 x 64 + 64 x 3) = 10,624 FLOP per sample forward; the
+    backward adds the data gradient of layer 2 and the weight gradients of
+    layers 1 and 2, 2 x (64 x 64 + 64 x 64 + 16 x 64) = 18,432)."""
+    import numpy as np
+    import torch
+    from paper_1904_02108_gb300 import binding, learned, workload as W
+    st = torch.cuda.current_stream()
+    P = torch.tensor(learned.init_params(11), device="cuda")
+    packed = torch.empty(binding.mlp_packed_bytes(), dtype=torch.uint8, device="cuda")
+    binding.mlp_pack_dev(P, packed, st)
+    n_inf, n_tr = 89600, 16384
+    g = torch.Generator(device="cuda")
+    g.manual_seed(12)
+    X = torch.rand((n_inf, 16), device="cuda", generator=g) * 2 - 1
+    Y = torch.empty((n_inf, 3), device="cuda")
+    T = torch.rand((n_tr, 3), device="cuda", generator=g) - 0.5
+    grad = torch.zeros_like(P)
+    loss = torch.zeros(1, device="cuda")
+    scratch = torch.empty(binding.mlp_grad_scratch_bytes(n_tr), dtype=torch.uint8, device="cuda")
+    binding.mlp_forward_dev(X, packed, Y, st)
+    binding.mlp_loss_grad_dev(X[:n_tr].contiguous(), T, P, packed, grad, loss, scratch, st)
+    Xt = X[:n_tr].contiguous()
+    f_ms = _device_ms(lambda: [binding.mlp_forward_dev(X, packed, Y, st) for _ in range(reps)],
+                      st) / reps
+    t_ms = _device_ms(lambda: [binding.mlp_loss_grad_dev(Xt, T, P, packed, grad, loss, scratch, st)
+                               for _ in range(reps)], st) / reps
+    fwd, bwd = 10624, 18432
+    return {"inference": {"samples": n_inf, "ms": f_ms,
+                          "tflops": n_inf * fwd / (f_ms / 1e3) / 1e12},
+            "loss_grad": {"samples": n_tr, "ms": t_ms,
+                          "tflops": n_tr * (fwd + bwd) / (t_ms / 1e3) / 1e12},
+            "engine": "tcgen05.mma kind::f16, BF16 operands, FP32 accumulators in tensor memory"}
 
 
 def bench_precision(steps=100, warmup=5):

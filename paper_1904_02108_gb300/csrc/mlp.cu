@@ -79,13 +79,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // BF16 inputs, FP32 accumulation in tensor memory), a tcgen05.commit signals
 // completion on an mbarrier, and each warp reads its 32 rows of the
 // accumulator back with tcgen05.ld (thread t holds sample t) for the
-// bias, SiLU and the next layer's operand.  Tensor memory: 128 columns per
-// block (layer 1 in columns 0-63, layer 2 in 64-127, layer 3 in 0-15 again
-// once layer 1 has been read).  Every wait is bounded: one that gives up sets
+// bias, SiLU and the next layer's operand.  Tensor memory: 64 columns per
+// block, each layer's accumulator in columns 0-63 (0-15 for layer 3) once
+// the previous one has been read (its epilogue precedes the next issue).  Every wait is bounded: one that gives up sets
 // the status word of the packed weights, and the block stops, waits (bounded)
 // for its last MMA and frees its tensor memory.
 constexpr unsigned TC_SPIN_LIMIT = 1u << 24;
-constexpr int TC_COLS = 128;
+constexpr int TC_COLS = 64;
 
 struct TcSmem {
   __align__(128) unsigned char w[TC_FWD_BYTES];  // W1, W2, W3 (canonical layout)
@@ -255,7 +255,7 @@ __device__ void mlp_tc_rows(int64_t n, const float *__restrict__ X, const void *
         } else {
           // K = 64 in four steps of 16 (two core matrices, 256 B, each)
           const unsigned char *wb = sm.w + (layer == 1 ? TC_W2 : TC_W3);
-          const uint32_t d = tmem + (layer == 1 ? 64 : 0);
+          const uint32_t d = tmem;
           const uint32_t idesc = tc_idesc(128, layer == 1 ? H : 16);
 #pragma unroll
           for (int k = 0; k < 4; k++)
@@ -273,7 +273,7 @@ __device__ void mlp_tc_rows(int64_t n, const float *__restrict__ X, const void *
       if (layer == 0) {
         tc_hidden(trow, 0, sm.bias, sm.a2, t);
       } else if (layer == 1) {
-        tc_hidden(trow, 64, sm.bias + H, sm.a2, t);
+        tc_hidden(trow, 0, sm.bias + H, sm.a2, t);
       } else {
         float z[16];
         tc_ld16(trow, z);
@@ -681,7 +681,7 @@ cudaError_t launch_mlp_pack(const float *P, void *packed, cudaStream_t st) {
 cudaError_t launch_mlp_forward(int64_t n, const float *X, const void *packed, float *Y,
                                cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((n + 127) / 128, 152 * 4);
+  const int64_t blocks = std::min<int64_t>((n + 127) / 128, 152 * 6);
   mlp_forward_kernel<<<(unsigned)blocks, 128, 0, st>>>(n, X, packed, Y);
   return cudaGetLastError();
 }
@@ -690,7 +690,7 @@ cudaError_t launch_mlp_warm(const DomainDesc *D, const BatchDims &dims, int use_
                             cudaStream_t st) {
   if (dims.max_points <= 0) return cudaSuccess;
   const int64_t want = (dims.max_points + 127) / 128;
-  const int64_t cap = std::max<int64_t>(1, 152 * 4 / std::max(1, dims.nd));
+  const int64_t cap = std::max<int64_t>(1, 152 * 6 / std::max(1, dims.nd));
   const unsigned bx = (unsigned)std::max<int64_t>(1, std::min(want, cap));
   return launch_pdl(mlp_warm_kernel, dim3(bx, dims.nd), dim3(128), 0, st, D, use_prev);
 }
