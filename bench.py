@@ -220,7 +220,7 @@ def run_ours(args):
 
     w = W.dense_array_256()
     st = torch.cuda.current_stream()
-    lat = binding.Lattice(w.shape, w.tau, storage="f32", stream=st)
+    lat = binding.Lattice(w.shape, w.tau, storage=args.storage, stream=st)
     lat.set_propellers(w.props)
     if args.overlap:
         lat.set_overlap(True)
@@ -326,20 +326,21 @@ def run_ours(args):
     coll_ms, coll_n = stage["collide_stream"]
     per_launch_s = coll_ms / 1e3 / max(1, coll_n)
     active = s["active_bricks"]
+    pop_bytes = 4 if args.storage == "f32" else 2
     if args.overlap:
-        alg_bytes = (w.cells - 64 * active) * 19 * 4 * 2
+        alg_bytes = (w.cells - 64 * active) * 19 * pop_bytes * 2
     else:
-        alg_bytes = w.cells * 19 * 4 * 2 + active * 64 * 12
+        alg_bytes = w.cells * 19 * pop_bytes * 2 + active * 64 * 12
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = alg_bytes / per_launch_s / 1e9
-    traffic = _captured_traffic("collide_stream_traffic.json")
+    traffic = _captured_traffic("collide_stream_traffic.json") if args.storage == "f32" else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config(w, "f32"),
+        "config": _config(w, args.storage),
         "windows": {"n": WINDOWS, "steps_each": args.steps,
                     "ms_per_step": [round(t / args.steps, 5) for t in window_ms],
                     "value": "median window"},
@@ -706,6 +707,9 @@ def main():
                          "IBM stages (off by default: slower on this workload)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"],
+                    help="population storage of the timed workload (FP32 is the benchmark; "
+                         "the 16-bit forms for profiling their collide kernels)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, 16-bit and tolerance-mode measurements")
     args = ap.parse_args()
