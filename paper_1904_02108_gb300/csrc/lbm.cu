@@ -393,15 +393,19 @@ __device__ __forceinline__ void collide_pairs16(const DomainDesc &dd, int cur) {
   }
 }
 
+// (at most 64 registers, four blocks of 256 per SM: the kernel is bound by the
+// latency of its loads, and the extra warps pay for the few spilled values:
+// 0.815 against 0.776 of the copy bandwidth at 75 registers; at 48 registers
+// the spills dominate, 0.65)
 template <typename S, bool STATS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     collide_pairs16_kernel(const __grid_constant__ DomainDesc dd, int cur) {
   pdl_wait();
   collide_pairs16<S, STATS>(dd, cur);
 }
 
 template <typename S, bool STATS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     collide_pairs16_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
   pdl_wait();
   collide_pairs16<S, STATS>(D[blockIdx.y], cur);
