@@ -15,7 +15,9 @@
  *    rho[nz][ny][nx], U[3][nz][ny][nx] (FP32).  Lagrangian vectors are
  *    point-major: v[n][3].
  *  - Host pointers are read (inputs) or written (outputs) during the call;
- *    the library copies inputs and keeps no reference to caller memory.
+ *    the library copies inputs and keeps no reference to caller memory
+ *    (except the asynchronous calls, which say how long a buffer is used,
+ *    and ibm_update_points with mapped host transfers, lbm_set_host_io).
  *    Functions whose name ends in _dev take device pointers instead and are
  *    ordered on the handle's stream.
  *  - All device work is enqueued on the handle's CUDA stream (lbm_set_stream;
@@ -136,7 +138,9 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
  * per-step input of a caller that moves its own points (the paper's
  * immersedBoundary(object, U) with the object updated each step).  Positions
  * are not checked here; a non-finite one gives an unspecified point, never an
- * out-of-range access.  This entry point has no counterpart in the paper.
+ * out-of-range access.  With mapped host transfers (lbm_set_host_io) the
+ * buffers are instead read by the next step's kinematics.  This entry point
+ * has no counterpart in the paper.
  * Errors: LBM_EINVAL (n differs from the point count, X NULL), LBM_ECUDA. */
 int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_target);
 
@@ -246,6 +250,32 @@ int lbm_read_stats(lbm_t *h, lbm_stats *s);
  * LBM_ECUDA. */
 int ibm_read_points_async(lbm_t *h, double *x, float *u_interp, float *du);
 int lbm_read_sums_async(lbm_t *h, double *sums);
+
+/* How ibm_update_points, ibm_read_points_async and lbm_read_sums_async move
+ * data between host and device (no counterpart in the paper: pipelined host
+ * I/O of a caller that moves its points every step).
+ *  LBM_HOST_IO_COPY (default): copies enqueued on the handle's stream.
+ *  LBM_HOST_IO_MAPPED: for page-locked host buffers with a device mapping
+ *    (cudaHostAlloc / cudaMallocHost, or registered with
+ *    cudaHostRegisterMapped), the kernels access the host memory directly
+ *    (over NVLink-C2C on a Grace-Blackwell node), so that no copy operation
+ *    sits between the kernels of consecutive steps: the positions / targets
+ *    of ibm_update_points are read by the kinematics of the next step (which
+ *    writes them through to the handle's device copy), and the read-outs are
+ *    written by small kernels on the handle's stream.  The caller keeps an
+ *    uploaded buffer unchanged until the next step has run (an event recorded
+ *    on the stream after that lbm_step has completed), and a read-out buffer
+ *    valid until the stream has passed the call, as for asynchronous copies.
+ *    A step replayed from a captured graph, a batched step and lbm_save_state
+ *    copy a pending upload in stream order first.  Buffers that are not
+ *    device-mapped host memory are copied as in LBM_HOST_IO_COPY.
+ * Values and results are bitwise those of LBM_HOST_IO_COPY.  Switching to
+ * LBM_HOST_IO_COPY copies a pending upload first.  Errors: LBM_EINVAL (NULL
+ * handle or mode pointer, unknown mode), LBM_ECUDA. */
+#define LBM_HOST_IO_COPY 0
+#define LBM_HOST_IO_MAPPED 1
+int lbm_set_host_io(lbm_t *h, int mode);
+int lbm_get_host_io(lbm_t *h, int *mode);
 
 /* Full populations f[19][N] (FP32) of the current state, in the velocity
  * order of lbm_velocity_set, and their replacement.  Host buffers.

@@ -29,6 +29,7 @@ LBM_WNOTCONVERGED = 1
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 DELTA = {"cosine": 0, "peskin": 1}
 WARM = {"zero": 0, "previous": 1, "mlp": 2}
+HOST_IO = {"copy": 0, "mapped": 1}
 MLP_NPARAM = 5443
 MLP_VSCALE = 0.05
 MLP_LSCALE = 16.0
@@ -86,6 +87,8 @@ _SIGS = {
     "ibm_read_points": (_i, [_p, _p, _p, _p]),
     "ibm_read_points_async": (_i, [_p, _p, _p, _p]),
     "lbm_read_sums_async": (_i, [_p, _p]),
+    "lbm_set_host_io": (_i, [_p, _i]),
+    "lbm_get_host_io": (_i, [_p, _p]),
     "ibm_read_points_dev": (_i, [_p, _p, _p, _p]),
     "lbm_read_stats": (_i, [_p, _p]),
     "lbm_read_populations": (_i, [_p, _p]),
@@ -306,6 +309,16 @@ class Lattice:
         the host array sums[4]; valid once the stream has passed this call."""
         assert sums.dtype == np.float64 and sums.size >= 4
         self._c(load().lbm_read_sums_async(self.h, _ptr(sums)))
+
+    def set_host_io(self, mode="copy"):
+        """"copy" (default) or "mapped": uploads and read-outs of page-locked
+        host buffers done by the kernels through their device mapping."""
+        self._c(load().lbm_set_host_io(self.h, HOST_IO[mode]))
+
+    def host_io(self):
+        v = _c.c_int(0)
+        self._c(load().lbm_get_host_io(self.h, _c.byref(v)))
+        return {i: k for k, i in HOST_IO.items()}[v.value]
 
     def stats(self):
         s = LbmStats()

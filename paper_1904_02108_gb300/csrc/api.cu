@@ -156,6 +156,16 @@ struct lbm {
   float *tmp = nullptr;
   size_t tmp_bytes = 0;
 
+  // host transfers (lbm_set_host_io).  LBM_HOST_IO_MAPPED: uploads from and
+  // read-outs into page-locked host memory are done by kernels through its
+  // device mapping (no copy operations between the steps' kernels).  x_src /
+  // u_src: the device addresses of the last ibm_update_points' mapped
+  // buffers, read by the next step's kinematics and written through to X /
+  // utarget (or copied there before a replayed or batched step).
+  int host_io = LBM_HOST_IO_COPY;
+  const double *x_src = nullptr;
+  const float *u_src = nullptr;
+
   std::string err;
 };
 
@@ -243,7 +253,34 @@ int ensure_tmp(lbm_t *h, size_t bytes) {
   return LBM_OK;
 }
 
+// The device address of page-locked, device-mapped host memory p, else NULL
+// (pageable memory, device memory, NULL).
+const void *mapped_ptr(const void *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Moves mapped uploads still to be read into X / utarget with copies on s
+// (before a step whose kinematics will not read them itself).
+int flush_points(lbm_t *h, cudaStream_t s) {
+  if (h->x_src)
+    CK(h, cudaMemcpyAsync(h->X, h->x_src, sizeof(double) * 3 * h->np, cudaMemcpyDefault, s));
+  if (h->u_src)
+    CK(h, cudaMemcpyAsync(h->utarget, h->u_src, sizeof(float) * 3 * h->np, cudaMemcpyDefault,
+                          s));
+  h->x_src = nullptr;
+  h->u_src = nullptr;
+  return LBM_OK;
+}
+
 void free_points(lbm_t *h) {
+  h->x_src = nullptr;
+  h->u_src = nullptr;
   dfree(h->X);
   dfree(h->body);
   dfree(h->area);
@@ -497,6 +534,8 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
       if (body[k] > maxb) maxb = body[k];
     }
   if (n > 0 && !body) maxb = 0;
+  h->x_src = nullptr;  // (mapped uploads of the previous points are void)
+  h->u_src = nullptr;
   if (h->nb > 0 && maxb >= h->nb)
     return fail(h, LBM_EINVAL, "body index %d out of range of %d bodies", maxb, h->nb);
   CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
@@ -572,16 +611,28 @@ int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_targe
                               (long long)h->np);
   if (n == 0) return LBM_OK;
   if (!X) return fail(h, LBM_EINVAL, "X is NULL");
-  CK(h, cudaMemcpyAsync(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->st));
+  const void *mx = h->host_io == LBM_HOST_IO_MAPPED ? mapped_ptr(X) : nullptr;
+  const void *mu = mx && U_target ? mapped_ptr(U_target) : nullptr;
+  if (mx && (!U_target || mu)) {
+    // read by the next step's kinematics (an earlier mapped target without
+    // a new one stays to be read)
+    h->x_src = (const double *)mx;
+    if (mu) h->u_src = (const float *)mu;
+    if (U_target) h->targets_nonzero = false;
+  } else {
+    int r = flush_points(h, h->st);  // (earlier mapped uploads first)
+    if (r) return r;
+    CK(h, cudaMemcpyAsync(h->X, X, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->st));
+    if (U_target) {
+      CK(h, cudaMemcpyAsync(h->utarget, U_target, sizeof(float) * 3 * n,
+                            cudaMemcpyHostToDevice, h->st));
+      h->targets_nonzero = false;  // (not scanned here: checked on the device again)
+    }
+  }
   if (h->u0_mode == LBM_U0_BOX) {
     // the boxes of the moved points (bodies keep their indices)
     rest_boxes(X, h->body_host.empty() ? nullptr : h->body_host.data(), n, h->box_host);
     h->box_dirty = true;
-  }
-  if (U_target) {
-    CK(h, cudaMemcpyAsync(h->utarget, U_target, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
-                          h->st));
-    h->targets_nonzero = false;  // (not scanned here: checked on the device again)
   }
   return LBM_OK;
 }
@@ -726,6 +777,8 @@ struct StepCtx {
   cudaStream_t st, sti;
   bool split;
   cudaEvent_t ev_fork, ev_join;
+  const double *x_src;  // mapped uploads for this step's kinematics, or NULL
+  const float *u_src;
 };
 
 // Kinematics and slots on st; with split, the fork to sti and the collide of
@@ -734,7 +787,7 @@ static int enqueue_head(StepCtx &c) {
   lbm_t *h = c.acct;
   {
     StageTimer T(h, ST_KIN, c.st, 1);
-    CK(h, launch_prepare_points(c.D, c.dims, c.st));
+    CK(h, launch_prepare_points(c.D, c.dims, c.st, c.x_src, c.u_src));
   }
   {
     StageTimer T(h, ST_PAIRS, c.st, c.dims.work_off ? 2 : 1);
@@ -1049,6 +1102,13 @@ static void after_step(lbm_t *h, int n_iter) {
 
 static int step_once(lbm_t *h, int n_iter) {
   StepCtx c = ctx_of(h, h->st);
+  if (h->np > 0) {
+    // the kinematics read the mapped uploads themselves
+    c.x_src = h->x_src;
+    c.u_src = h->u_src;
+    h->x_src = nullptr;
+    h->u_src = nullptr;
+  }
   int r0 = ensure_split(h, c, false);
   if (r0) return r0;
   int warn = LBM_OK;
@@ -1170,6 +1230,12 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
   int warn = LBM_OK;
   int s = 0;
   const bool graphable = h->graph_on && (n_ibm_iter > 0 || h->np == 0);
+  // mapped uploads are read by the next eager step's kinematics; a replayed
+  // step gets them copied first
+  if (graphable && (h->have_du || h->np == 0) && n_steps >= 2) {
+    r = flush_points(h, h->st);
+    if (r) return r;
+  }
   while (s < n_steps) {
     // replay captured pairs of steps once the host-side decisions are steady
     const bool steady = h->have_du || h->np == 0;
@@ -1432,6 +1498,8 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
     if (h->warm == LBM_WARM_MLP && !h->mlp_packed && h->np > 0)
       return fail(h0, LBM_EINVAL, "learned warm start without weights");
     int r = sync_desc(h);
+    if (r) return r;
+    r = flush_points(h, h0->st);  // (batched kinematics read the device copies)
     if (r) return r;
   }
   uint64_t ver = b->shape_version;
@@ -1871,9 +1939,7 @@ int lbm_read_fields(lbm_t *h, float *rho, float *U, float *G) {
 int ibm_read_points_dev(lbm_t *h, double *x, float *u_interp, float *du) {
   if (!h) return LBM_EINVAL;
   if (h->np == 0) return LBM_OK;
-  if (x)
-    CK(h, cudaMemcpyAsync(x, h->xpos, sizeof(double) * 3 * h->np, cudaMemcpyDeviceToDevice,
-                          h->st));
+  if (x) CK(h, launch_copy_f64(3 * h->np, h->xpos, x, h->st));
   if (u_interp) CK(h, launch_pack_points(h->np, h->uint, u_interp, h->st));
   if (du) CK(h, launch_pack_points(h->np, h->du, du, h->st));
   return LBM_OK;
@@ -1883,6 +1949,14 @@ int ibm_read_points_async(lbm_t *h, double *x, float *u_interp, float *du) {
   if (!h) return LBM_EINVAL;
   const int64_t n = h->np;
   if (n == 0) return LBM_OK;
+  if (h->host_io == LBM_HOST_IO_MAPPED) {
+    // kernels write straight into device-mapped host buffers
+    void *mx = x ? (void *)mapped_ptr(x) : nullptr, *mu = u_interp ? (void *)mapped_ptr(u_interp)
+                                                                   : nullptr;
+    void *md = du ? (void *)mapped_ptr(du) : nullptr;
+    if ((!x || mx) && (!u_interp || mu) && (!du || md))
+      return ibm_read_points_dev(h, (double *)mx, (float *)mu, (float *)md);
+  }
   int r = ensure_tmp(h, sizeof(double) * 3 * n + sizeof(float) * 6 * n);
   if (r) return r;
   double *dx = (double *)h->tmp;
@@ -1905,8 +1979,30 @@ int ibm_read_points(lbm_t *h, double *x, float *u_interp, float *du) {
 
 int lbm_read_sums_async(lbm_t *h, double *sums) {
   if (!h || !sums) return LBM_EINVAL;
-  if (h->sums_valid)
+  if (!h->sums_valid) return LBM_OK;
+  void *ms = h->host_io == LBM_HOST_IO_MAPPED ? (void *)mapped_ptr(sums) : nullptr;
+  if (ms)
+    CK(h, launch_copy_f64(4, h->sums, (double *)ms, h->st));
+  else
     CK(h, cudaMemcpyAsync(sums, h->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  return LBM_OK;
+}
+
+int lbm_set_host_io(lbm_t *h, int mode) {
+  if (!h) return LBM_EINVAL;
+  if (mode != LBM_HOST_IO_COPY && mode != LBM_HOST_IO_MAPPED)
+    return fail(h, LBM_EINVAL, "unknown host transfer mode %d", mode);
+  if (mode == LBM_HOST_IO_COPY) {
+    const int r = flush_points(h, h->st);
+    if (r) return r;
+  }
+  h->host_io = mode;
+  return LBM_OK;
+}
+
+int lbm_get_host_io(lbm_t *h, int *mode) {
+  if (!h || !mode) return LBM_EINVAL;
+  *mode = h->host_io;
   return LBM_OK;
 }
 
@@ -2030,6 +2126,10 @@ const char kMagic[8] = {'L', 'B', 'M', 'I', 'B', 'M', '0', '1'};
 
 int lbm_save_state(lbm_t *h, void *buf, size_t *len) {
   if (!h || !len) return LBM_EINVAL;
+  if (buf) {
+    const int rf = flush_points(h, h->st);  // (the last mapped upload belongs to the state)
+    if (rf) return rf;
+  }
   const size_t pop = (size_t)Q * h->g.ncell * storage_bytes(h->storage);
   const size_t np = (size_t)h->np, nb = (size_t)h->nb;
   const size_t need = sizeof(StateHeader) + pop + np * (3 * 8 + 4 + 4 + 12 + 16) +

@@ -125,8 +125,12 @@ __device__ __forceinline__ Trig body_trig(const Bodies &bd, int b, int64_t t) {
 // a block whose points span more takes them per point.
 constexpr int TRIG_CACHE = 16;
 
+// Xsrc / Usrc (single lattice, else NULL): new positions / targets read
+// from device-mapped host memory by this step and written through to the
+// domain's X / utarget (an upload that needs no copy of its own).
 __global__ void __launch_bounds__(512, 2)
-    prepare_points_kernel(const DomainDesc *__restrict__ D) {
+    prepare_points_kernel(const DomainDesc *__restrict__ D, const double *__restrict__ Xsrc,
+                          const float *__restrict__ Usrc) {
   pdl_wait();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
@@ -174,7 +178,22 @@ __global__ void __launch_bounds__(512, 2)
   if (!in) return;
   double x[3];
   float u[3];
-  const double *X = p.X + 3 * k;
+  const double *X = (Xsrc ? Xsrc : p.X) + 3 * k;
+  // (write-through into the handle's own buffers, which a single lattice's
+  // descriptor lists as read-only inputs of the step)
+  if (Xsrc) {
+    double *Xd = const_cast<double *>(d.X) + 3 * k;
+    Xd[0] = X[0];
+    Xd[1] = X[1];
+    Xd[2] = X[2];
+  }
+  const float *ut = Usrc ? Usrc : p.utarget;
+  if (Usrc) {
+    float *Ud = const_cast<float *>(d.utarget) + 3 * k;
+    Ud[0] = Usrc[3 * k];
+    Ud[1] = Usrc[3 * k + 1];
+    Ud[2] = Usrc[3 * k + 2];
+  }
   if (bd.nb > 0) {
     // Alg. 1, first iteration: x(t) = M(t) [x_rest, 1], u_k = x(t) - x(t-1)
     const int b = body;
@@ -193,9 +212,9 @@ __global__ void __launch_bounds__(512, 2)
     x[0] = X[0];
     x[1] = X[1];
     x[2] = X[2];
-    u[0] = p.utarget ? p.utarget[3 * k] : 0.f;
-    u[1] = p.utarget ? p.utarget[3 * k + 1] : 0.f;
-    u[2] = p.utarget ? p.utarget[3 * k + 2] : 0.f;
+    u[0] = ut ? ut[3 * k] : 0.f;
+    u[1] = ut ? ut[3 * k + 1] : 0.f;
+    u[2] = ut ? ut[3 * k + 2] : 0.f;
   }
   if (xpos) {
     xpos[3 * k] = x[0];
@@ -1741,6 +1760,7 @@ __global__ void store_desc_kernel(DomainDesc dd, DomainDesc *__restrict__ D) {
 }
 
 __global__ void pack_points_kernel(int64_t n, const float4 *__restrict__ a, float *__restrict__ o) {
+  pdl_wait();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const float4 v = a[k];
@@ -1792,12 +1812,14 @@ cudaError_t brick_moments_typed(const DomainDesc *D, const BatchDims &dims, int 
 
 }  // namespace
 
-cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
+cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st,
+                                  const double *Xsrc, const float *Usrc) {
   if (dims.max_points <= 0) return cudaSuccess;
   const int pb = dims.ls.point_block;
   if (pb != 128 && pb != 256 && pb != 512) return cudaErrorInvalidValue;
+  if ((Xsrc || Usrc) && dims.nd != 1) return cudaErrorInvalidValue;
   return launch_pdl(prepare_points_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0,
-                    st, D);
+                    st, D, Xsrc, Usrc);
 }
 
 cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {
@@ -2004,8 +2026,19 @@ cudaError_t launch_slots_to_dense(const Geometry &g, const BrickMap &m, const fl
 
 cudaError_t launch_pack_points(int64_t n, const float4 *a, float *out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  pack_points_kernel<<<nblk(n, 256), 256, 0, st>>>(n, a, out);
-  return cudaGetLastError();
+  return launch_pdl(pack_points_kernel, dim3(nblk(n, 256)), dim3(256), 0, st, n, a, out);
+}
+
+// n doubles from device memory to o (device or device-mapped host memory).
+__global__ void copy_f64_kernel(int64_t n, const double *__restrict__ a, double *__restrict__ o) {
+  pdl_wait();
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) o[k] = a[k];
+}
+
+cudaError_t launch_copy_f64(int64_t n, const double *a, double *out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  return launch_pdl(copy_f64_kernel, dim3(nblk(n, 256)), dim3(256), 0, st, n, a, out);
 }
 
 }  // namespace lbmibm

@@ -57,7 +57,8 @@ struct PointsIn {
 // ---- step kernels over a batch of domains (D: device array of dims.nd) ----
 // Kinematics (Alg. 1, first iteration; each block computes the rotation of
 // its points' bodies once) + per-point weights + brick counts.
-cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
+cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st,
+                                  const double *Xsrc = nullptr, const float *Usrc = nullptr);
 // counted bricks -> slots (1 launch)
 cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // a batch's work list from the domains' slot counts (1 launch when
@@ -142,5 +143,6 @@ cudaError_t launch_store_desc(const DomainDesc &dd, DomainDesc *D, cudaStream_t 
 cudaError_t launch_slots_to_dense(const Geometry &g, const BrickMap &m, const float *Gs,
                                   float *F, cudaStream_t st);
 cudaError_t launch_pack_points(int64_t n, const float4 *a, float *out, cudaStream_t st);
+cudaError_t launch_copy_f64(int64_t n, const double *a, double *out, cudaStream_t st);
 
 }  // namespace lbmibm
