@@ -150,6 +150,15 @@ __global__ void __launch_bounds__(512, 2)
   }
   const bool in = k < p.np;
   const int body = (bd.nb > 0 && in) ? (p.body ? p.body[k] : 0) : -1;
+  // the point's position first: its latency (host memory for a mapped
+  // upload) overlaps the block's rotation set-up below
+  double X[3] = {0.0, 0.0, 0.0};
+  if (in) {
+    const double *Xk = (Xsrc ? Xsrc : p.X) + 3 * k;
+    X[0] = Xk[0];
+    X[1] = Xk[1];
+    X[2] = Xk[2];
+  }
   __shared__ Trig strig[TRIG_CACHE];
   __shared__ int sb_lo, sb_hi;
   int b0 = 0, nbk = 0;
@@ -178,7 +187,6 @@ __global__ void __launch_bounds__(512, 2)
   if (!in) return;
   double x[3];
   float u[3];
-  const double *X = (Xsrc ? Xsrc : p.X) + 3 * k;
   // (write-through into the handle's own buffers, which a single lattice's
   // descriptor lists as read-only inputs of the step)
   if (Xsrc) {
