@@ -27,8 +27,8 @@ __device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &
 
 // Pull of Eq. 4: d[i] = stored d_i at X - e_i (periodic).  PF: loads with a
 // 64-byte L2 prefetch size (for the scattered 4-cell rows of the active
-// bricks; the dense collide reads whole lines anyway).
-template <typename S, bool PF = false>
+// bricks); STREAM: with a 256-byte one (the dense rows of the collide).
+template <typename S, bool PF = false, bool STREAM = false>
 __device__ __forceinline__ void pull(const S *__restrict__ f, const Geometry &g, int x, int y,
                                      int z, float d[Q]) {
   const uint32_t nx = g.nx, ny = g.ny;
@@ -43,7 +43,8 @@ __device__ __forceinline__ void pull(const S *__restrict__ f, const Geometry &g,
 #pragma unroll
   for (int i = 0; i < Q; i++) {
     const uint32_t src = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * nx + X[ex(i) + 1];
-    d[i] = PF ? Store<S>::ld_pf(f + (size_t)i * N + src) : Store<S>::ld(f + (size_t)i * N + src);
+    const S *q = f + (size_t)i * N + src;
+    d[i] = PF ? Store<S>::ld_pf(q) : (STREAM ? Store<S>::ld_stream(q) : Store<S>::ld(q));
   }
 }
 

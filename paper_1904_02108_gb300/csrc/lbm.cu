@@ -179,7 +179,7 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
                                              float Gx, float Gy, float Gz, float tau,
                                              float om, float st[4]) {
   float d[Q], dn[Q];
-  pull<S>(src, g, x, y, z, d);
+  pull<S, false, true>(src, g, x, y, z, d);
   collide_math(d, Gx, Gy, Gz, tau, om, dn, st);
   const size_t N = (size_t)g.ncell;
 #pragma unroll
@@ -357,15 +357,15 @@ __device__ __forceinline__ void collide_pairs16(const DomainDesc &dd, int cur) {
       const uint32_t row = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * hw;
       const uint32_t *fi = src + (size_t)i * NW + row;
       if (ex(i) == 0) {
-        const uint32_t w = __ldg(fi + w0);
+        const uint32_t w = ldw_stream(fi + w0);
         da[i] = Word16<S>::lo(w);
         db[i] = Word16<S>::hi(w);
       } else if (ex(i) > 0) {
-        da[i] = Word16<S>::hi(__ldg(fi + wl));
-        db[i] = Word16<S>::lo(__ldg(fi + w0));
+        da[i] = Word16<S>::hi(ldw_stream(fi + wl));
+        db[i] = Word16<S>::lo(ldw_stream(fi + w0));
       } else {
-        da[i] = Word16<S>::hi(__ldg(fi + w0));
-        db[i] = Word16<S>::lo(__ldg(fi + wr));
+        da[i] = Word16<S>::hi(ldw_stream(fi + w0));
+        db[i] = Word16<S>::lo(ldw_stream(fi + wr));
       }
     }
     float dna[Q], dnb[Q], sta[4], stb[4];
