@@ -117,6 +117,17 @@ struct lbm {
   // device descriptor of this lattice (a batch of one) and the step counter
   DomainDesc *desc = nullptr;
   DomainDesc desc_host{};
+  // Steps prepared ahead: a step's kinematics and pair lists built on ahead_st
+  // while the step before it collides.  The prepared step writes the other of
+  // two brick maps (the colliding step still reads its own), so it runs on
+  // desc_alt, the descriptor identical to desc but for the brick map; the two
+  // swap when it becomes the current step.
+  DomainDesc *desc_alt = nullptr;
+  DomainDesc desc_host_alt{};
+  int *bslot_alt = nullptr;
+  cudaStream_t ahead_st = nullptr;
+  cudaEvent_t ev_ahead_go = nullptr, ev_ahead_done = nullptr;
+  bool pairs_ahead = false;  // the next step's pairs are built (or on their way)
   int64_t *t_dev = nullptr;
   bool desc_dirty = true;
   uint64_t version = 1;  // changes whenever a pointer in the descriptor does
@@ -394,6 +405,7 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->phase);
   dfree(h->m.brick_count);
   dfree(h->m.brick_slot);
+  dfree(h->bslot_alt);
   dfree(h->m.counters);
   dfree(h->m.tiles);
   dfree(h->partial);
@@ -404,12 +416,16 @@ void lbm_destroy(lbm_t *h) {
   dfree(h->state);
   if (h->state_host) cudaFreeHost(h->state_host);
   dfree(h->desc);
+  dfree(h->desc_alt);
   dfree(h->t_dev);
   dfree(h->Ufull);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ibm_st) cudaStreamDestroy(h->ibm_st);
   if (h->ibm_cap) cudaStreamDestroy(h->ibm_cap);
+  if (h->ahead_st) cudaStreamDestroy(h->ahead_st);
+  if (h->ev_ahead_go) cudaEventDestroy(h->ev_ahead_go);
+  if (h->ev_ahead_done) cudaEventDestroy(h->ev_ahead_done);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -468,6 +484,8 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   if (e == cudaSuccess) e = cudaMemset(h->m.brick_count, 0, sizeof(int) * h->g.nbrick);
   if (e == cudaSuccess) e = dalloc(&h->m.brick_slot, h->g.nbrick);
   if (e == cudaSuccess) e = cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick);
+  if (e == cudaSuccess) e = dalloc(&h->bslot_alt, h->g.nbrick);
+  if (e == cudaSuccess) e = cudaMemset(h->bslot_alt, 0xff, sizeof(int) * h->g.nbrick);
   if (e == cudaSuccess) e = dalloc(&h->m.counters, BRICK_COUNTERS);
   if (e == cudaSuccess) e = cudaMemset(h->m.counters, 0, BRICK_COUNTERS * sizeof(int));
   {
@@ -482,6 +500,7 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   if (e == cudaSuccess) e = dalloc(&h->ticket, 1);
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dalloc(&h->desc, 1);
+  if (e == cudaSuccess) e = dalloc(&h->desc_alt, 1);
   if (e == cudaSuccess) e = dalloc(&h->t_dev, 1);
   if (e == cudaSuccess) e = cudaMemset(h->t_dev, 0, sizeof(int64_t));
   if (e == cudaSuccess) e = dalloc(&h->state, 1);
@@ -600,6 +619,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, cudaMemset(h->uint, 0, sizeof(float4) * n));
   } else {
     CK(h, cudaMemset(h->m.brick_slot, 0xff, sizeof(int) * h->g.nbrick));
+    CK(h, cudaMemset(h->bslot_alt, 0xff, sizeof(int) * h->g.nbrick));
     CK(h, cudaMemset(h->m.counters, 0, 2 * sizeof(int)));
   }
   return LBM_OK;
@@ -741,6 +761,10 @@ static int sync_desc(lbm_t *h) {
   CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
   CK(h, cudaMemcpy(h->desc, &d, sizeof d, cudaMemcpyHostToDevice));
   h->desc_host = d;
+  DomainDesc da = d;
+  da.m.brick_slot = h->bslot_alt;
+  CK(h, cudaMemcpy(h->desc_alt, &da, sizeof da, cudaMemcpyHostToDevice));
+  h->desc_host_alt = da;
   h->desc_dirty = false;
   h->version++;
   return LBM_OK;
@@ -779,12 +803,16 @@ struct StepCtx {
   cudaEvent_t ev_fork, ev_join;
   const double *x_src;  // mapped uploads for this step's kinematics, or NULL
   const float *u_src;
+  bool pairs_done;  // kinematics and pair lists were built ahead (ahead_st)
+  bool ahead;       // build the next step's after this step's fixed point
+  long long t_next; // the next step's index (its kinematics)
 };
 
 // Kinematics and slots on st; with split, the fork to sti and the collide of
 // the cells outside the active bricks on st.
 static int enqueue_head(StepCtx &c) {
   lbm_t *h = c.acct;
+  if (c.pairs_done) return LBM_OK;  // (never split)
   {
     StageTimer T(h, ST_KIN, c.st, 1);
     CK(h, launch_prepare_points(c.D, c.dims, c.st, c.x_src, c.u_src));
@@ -812,7 +840,7 @@ static int enqueue_prefix(StepCtx &c, bool *warm_out) {
   const bool warm = (c.warm_mode == LBM_WARM_PREVIOUS && c.have_du) || mlp;
   *warm_out = warm;
   const cudaStream_t s = c.sti;
-  {
+  if (!c.pairs_done) {
     StageTimer T(h, ST_PAIRS, s, 2);
     CK(h, launch_pair_lists(c.D, c.dims, s));
   }
@@ -902,6 +930,38 @@ static int enqueue_fixed_loop(StepCtx &c, int n_iter, bool warm) {
   return LBM_OK;
 }
 
+// The next step's kinematics and pair lists on ahead_st (a stream of the
+// greatest priority), once this step's fixed point is done with its own:
+// they need no populations, so they run while this step collides (an
+// HBM-bound pass that leaves SM slots and L2 to them).  They write the other
+// brick map, through desc_alt, and finish before the next step's first
+// kernel on st (ev_ahead_done).
+static int enqueue_ahead(StepCtx &c) {
+  lbm_t *h = c.acct;
+  if (!h->ahead_st) {
+    int lo = 0, hi = 0;
+    CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(h, cudaStreamCreateWithPriority(&h->ahead_st, cudaStreamNonBlocking, hi));
+  }
+  if (!h->ev_ahead_go) CK(h, cudaEventCreateWithFlags(&h->ev_ahead_go, cudaEventDisableTiming));
+  if (!h->ev_ahead_done)
+    CK(h, cudaEventCreateWithFlags(&h->ev_ahead_done, cudaEventDisableTiming));
+  CK(h, cudaEventRecord(h->ev_ahead_go, c.st));
+  CK(h, cudaStreamWaitEvent(h->ahead_st, h->ev_ahead_go, 0));
+  const DomainDesc *Dn = h->desc_alt;
+  {
+    StageTimer T(h, ST_KIN, h->ahead_st, 1);
+    CK(h, launch_prepare_points(Dn, c.dims, h->ahead_st, nullptr, nullptr, c.t_next));
+  }
+  {
+    StageTimer T(h, ST_PAIRS, h->ahead_st, 3);
+    CK(h, launch_compact(Dn, c.dims, h->ahead_st));
+    CK(h, launch_pair_lists(Dn, c.dims, h->ahead_st));
+  }
+  CK(h, cudaEventRecord(h->ev_ahead_done, h->ahead_st));
+  return LBM_OK;
+}
+
 // The collide of the cells with the IBM force (split: the active bricks on
 // sti, then the join), and the end of the step on st.
 static int enqueue_suffix(StepCtx &c) {
@@ -934,6 +994,10 @@ static int enqueue_step(StepCtx &c, int n_iter) {
     if (r) return r;
     r = enqueue_fixed_loop(c, n_iter, warm);
     if (r) return r;
+    if (c.ahead) {
+      r = enqueue_ahead(c);
+      if (r) return r;
+    }
   }
   return enqueue_suffix(c);
 }
@@ -1100,8 +1164,26 @@ static void after_step(lbm_t *h, int n_iter) {
   h->t++;
 }
 
-static int step_once(lbm_t *h, int n_iter) {
+// Makes the handle's stream wait for a step prepared ahead (its kinematics
+// and pairs), which is then the current step's; no-op when there is none.
+static int join_ahead(lbm_t *h, bool *was_pending = nullptr) {
+  if (was_pending) *was_pending = h->pairs_ahead;
+  if (!h->pairs_ahead) return LBM_OK;
+  h->pairs_ahead = false;
+  CK(h, cudaStreamWaitEvent(h->st, h->ev_ahead_done, 0));
+  return LBM_OK;
+}
+
+// ahead: also prepare the next step (its kinematics and pair lists) while this
+// one collides; the caller makes the next step the next call of step_once.
+static int step_once(lbm_t *h, int n_iter, bool ahead = false) {
+  bool pre = false;
+  int rj = join_ahead(h, &pre);
+  if (rj) return rj;
   StepCtx c = ctx_of(h, h->st);
+  c.pairs_done = pre;
+  c.ahead = ahead && h->np > 0 && !h->overlap;
+  c.t_next = (long long)h->t + 1;
   if (h->np > 0) {
     // the kinematics read the mapped uploads themselves
     c.x_src = h->x_src;
@@ -1120,11 +1202,23 @@ static int step_once(lbm_t *h, int n_iter) {
     if (r) return r;
     warn = tolerance_loop(c, warm);
     if (warn < 0) return warn;
+    if (c.ahead) {
+      r = enqueue_ahead(c);
+      if (r) return r;
+    }
     r = enqueue_suffix(c);
     if (r) return r;
   } else {
     int r = enqueue_step(c, n_iter);
     if (r) return r;
+  }
+  if (c.ahead) {
+    // the prepared step becomes the current one: its descriptor and brick map
+    std::swap(h->desc, h->desc_alt);
+    std::swap(h->desc_host, h->desc_host_alt);
+    std::swap(h->m.brick_slot, h->bslot_alt);
+    h->pairs_ahead = true;
+    h->version++;  // (a captured step holds the other descriptor)
   }
   after_step(h, n_iter);
   return warn;
@@ -1259,8 +1353,15 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
       s += 2;
       continue;
     }
-    r = step_once(h, n_ibm_iter);
-    if (r < 0) return r;
+    // the next step of this call prepared while this one collides (eager
+    // steps without stage timing; never past the call, so that every read-out
+    // and every other entry point sees the last step's state)
+    const bool ahead = !graphable && !h->timing && s + 1 < n_steps;
+    r = step_once(h, n_ibm_iter, ahead);
+    if (r < 0) {
+      join_ahead(h);
+      return r;
+    }
     if (r == LBM_WNOTCONVERGED) warn = r;
     s++;
   }

@@ -127,10 +127,12 @@ constexpr int TRIG_CACHE = 16;
 
 // Xsrc / Usrc (single lattice, else NULL): new positions / targets read
 // from device-mapped host memory by this step and written through to the
-// domain's X / utarget (an upload that needs no copy of its own).
+// domain's X / utarget (an upload that needs no copy of its own).  t_step >=
+// 0: the step whose kinematics to compute (given when the step is prepared
+// while the one before it, which advances the device's counter, still runs).
 __global__ void __launch_bounds__(512, 2)
     prepare_points_kernel(const DomainDesc *__restrict__ D, const double *__restrict__ Xsrc,
-                          const float *__restrict__ Usrc) {
+                          const float *__restrict__ Usrc, long long t_step) {
   pdl_wait();
   const DomainDesc &d = D[blockIdx.y];
   const Geometry g = d.g;
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(512, 2)
     __syncthreads();
     b0 = sb_lo;
     nbk = sb_hi >= 0 ? sb_hi - sb_lo + 1 : 0;
-    tstep = *d.t;
+    tstep = t_step >= 0 ? (int64_t)t_step : *d.t;
     if (nbk <= TRIG_CACHE && (int)threadIdx.x < nbk)
       strig[threadIdx.x] = body_trig(bd, b0 + threadIdx.x, tstep);
     __syncthreads();
@@ -1821,13 +1823,13 @@ cudaError_t brick_moments_typed(const DomainDesc *D, const BatchDims &dims, int 
 }  // namespace
 
 cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st,
-                                  const double *Xsrc, const float *Usrc) {
+                                  const double *Xsrc, const float *Usrc, long long t_step) {
   if (dims.max_points <= 0) return cudaSuccess;
   const int pb = dims.ls.point_block;
   if (pb != 128 && pb != 256 && pb != 512) return cudaErrorInvalidValue;
   if ((Xsrc || Usrc) && dims.nd != 1) return cudaErrorInvalidValue;
   return launch_pdl(prepare_points_kernel, dim3(nblk(dims.max_points, pb), dims.nd), dim3(pb), 0,
-                    st, D, Xsrc, Usrc);
+                    st, D, Xsrc, Usrc, t_step);
 }
 
 cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStream_t st) {

@@ -56,9 +56,12 @@ struct PointsIn {
 };
 // ---- step kernels over a batch of domains (D: device array of dims.nd) ----
 // Kinematics (Alg. 1, first iteration; each block computes the rotation of
-// its points' bodies once) + per-point weights + brick counts.
+// its points' bodies once) + per-point weights + brick counts.  t_step >= 0:
+// the kinematics of that step (a step prepared ahead, while the step before
+// it still runs); else of the device's step counter.
 cudaError_t launch_prepare_points(const DomainDesc *D, const BatchDims &dims, cudaStream_t st,
-                                  const double *Xsrc = nullptr, const float *Usrc = nullptr);
+                                  const double *Xsrc = nullptr, const float *Usrc = nullptr,
+                                  long long t_step = -1);
 // counted bricks -> slots (1 launch)
 cudaError_t launch_compact(const DomainDesc *D, const BatchDims &dims, cudaStream_t st);
 // a batch's work list from the domains' slot counts (1 launch when
