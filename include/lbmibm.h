@@ -167,7 +167,11 @@ int lbm_set_body_force(lbm_t *h, double gx, double gy, double gz);
  * Errors: LBM_EINVAL (n_steps < 0, n_ibm_iter < 0), LBM_ECUDA.  The call
  * does not wait for the GPU: a step whose FP64 mass or momentum sum is not
  * finite (stats on) is reported as LBM_ENONFINITE by the next
- * lbm_read_stats. */
+ * lbm_read_stats.  In a call of several eager steps (no captured graphs, no
+ * stage timing, no overlapped step) the kinematics and pair lists of each
+ * step after the first are built on an internal stream while the step
+ * before it collides; the results are bitwise those of one-step calls, and
+ * no work of a later step is left pending when the call returns. */
 int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter);
 
 /* The iteration that solves the fixed point of Sec. 3 in lbm_step.
