@@ -55,7 +55,8 @@ class LbmStats(_c.Structure):
 
 class LaunchShape(_c.Structure):
     _fields_ = [("collide_block", _i), ("brick_blocks", _i), ("point_block", _i),
-                ("moments_spb", _i), ("sort_blocks", _i), ("collide_staged", _i)]
+                ("moments_spb", _i), ("sort_blocks", _i), ("collide_staged", _i),
+                ("sort_blocks_ahead", _i)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -949,6 +949,8 @@ static int enqueue_ahead(StepCtx &c) {
   CK(h, cudaEventRecord(h->ev_ahead_go, c.st));
   CK(h, cudaStreamWaitEvent(h->ahead_st, h->ev_ahead_go, 0));
   const DomainDesc *Dn = h->desc_alt;
+  BatchDims da = c.dims;
+  da.ls.sort_blocks = da.ls.sort_blocks_ahead;
   {
     StageTimer T(h, ST_KIN, h->ahead_st, 1);
     CK(h, launch_prepare_points(Dn, c.dims, h->ahead_st, nullptr, nullptr, c.t_next));
@@ -956,7 +958,7 @@ static int enqueue_ahead(StepCtx &c) {
   {
     StageTimer T(h, ST_PAIRS, h->ahead_st, 3);
     CK(h, launch_compact(Dn, c.dims, h->ahead_st));
-    CK(h, launch_pair_lists(Dn, c.dims, h->ahead_st));
+    CK(h, launch_pair_lists(Dn, da, h->ahead_st));
   }
   CK(h, cudaEventRecord(h->ev_ahead_done, h->ahead_st));
   return LBM_OK;
@@ -1702,14 +1704,15 @@ bool shape_ok(const lbm_launch_shape &s) {
   return (s.collide_block == 128 || s.collide_block == 256) &&
          (s.point_block == 128 || s.point_block == 256 || s.point_block == 512) &&
          s.brick_blocks >= 1 && s.brick_blocks <= (1 << 20) && s.sort_blocks >= 1 &&
-         s.sort_blocks <= (1 << 20) &&
+         s.sort_blocks <= (1 << 20) && s.sort_blocks_ahead >= 1 &&
+         s.sort_blocks_ahead <= (1 << 20) &&
          (s.moments_spb == 1 || s.moments_spb == 2 || s.moments_spb == 4) &&
          (s.collide_staged == 0 || s.collide_staged == 1);
 }
 
 lbm_launch_shape to_c(const LaunchShape &l) {
   return {l.collide_block, l.brick_blocks, l.point_block, l.moments_spb, l.sort_blocks,
-          l.collide_staged};
+          l.collide_staged, l.sort_blocks_ahead};
 }
 
 LaunchShape from_c(const lbm_launch_shape &c) {
@@ -1720,6 +1723,7 @@ LaunchShape from_c(const lbm_launch_shape &c) {
   l.moments_spb = c.moments_spb;
   l.sort_blocks = c.sort_blocks;
   l.collide_staged = c.collide_staged;
+  l.sort_blocks_ahead = c.sort_blocks_ahead;
   return l;
 }
 
@@ -1808,6 +1812,8 @@ std::vector<TuneParam> tune_params(bool points, bool staged) {
                   (1 << ST_KIN) | (1 << ST_PAIRS) | (1 << ST_UPDATE)});
     ps.push_back({&LaunchShape::moments_spb, {1, 2, 4}, 1 << ST_INIT});
     ps.push_back({&LaunchShape::sort_blocks, {152 * 8, 152 * 16, 152 * 32, 152 * 64},
+                  1 << ST_PAIRS});
+    ps.push_back({&LaunchShape::sort_blocks_ahead, {152 * 2, 152 * 4, 152 * 8, 152 * 32},
                   1 << ST_PAIRS});
   }
   return ps;

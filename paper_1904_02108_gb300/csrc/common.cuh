@@ -331,6 +331,9 @@ struct LaunchShape {
   int collide_staged = 0;        // 16-bit storage, single lattice: the pulls
                                  // staged in shared memory by bulk copies (1)
                                  // or loaded by the threads (0)
+  int sort_blocks_ahead = 152 * 4;  // grid of the sort of a step prepared
+                                    // ahead (it runs beside the previous
+                                    // step's collide: few blocks)
 };
 
 // Cells per FP64 partial sum of the collide kernel.

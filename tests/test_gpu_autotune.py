@@ -9,9 +9,9 @@ from paper_1904_02108_gb300 import workload as W
 pytestmark = pytest.mark.gpu
 
 OTHER = dict(collide_block=128, brick_blocks=152 * 8, point_block=512, moments_spb=1,
-             sort_blocks=152 * 8, collide_staged=1)
+             sort_blocks=152 * 8, collide_staged=1, sort_blocks_ahead=1)
 WIDE = dict(collide_block=256, brick_blocks=152 * 32, point_block=128, moments_spb=2,
-            sort_blocks=152 * 64)
+            sort_blocks=152 * 64, sort_blocks_ahead=152 * 64)
 
 
 @pytest.fixture(scope="module")
@@ -72,7 +72,8 @@ def test_autotune_leaves_the_lattice_unchanged(gpu_lib, torch_cuda):
 def test_launch_shape_rejects_values_out_of_range(gpu_lib, torch_cuda):
     lat = _pair_lattice(gpu_lib, torch_cuda)
     for bad in (dict(collide_block=512), dict(point_block=1024), dict(moments_spb=8),
-                dict(brick_blocks=0), dict(sort_blocks=-1), dict(collide_staged=2)):
+                dict(brick_blocks=0), dict(sort_blocks=-1), dict(collide_staged=2),
+                dict(sort_blocks_ahead=0)):
         with pytest.raises(gpu_lib.LbmError):
             lat.set_launch_shape(**bad)
     lat.close()
