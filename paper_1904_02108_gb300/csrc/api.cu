@@ -128,6 +128,10 @@ struct lbm {
   cudaStream_t ahead_st = nullptr;
   cudaEvent_t ev_ahead_go = nullptr, ev_ahead_done = nullptr;
   bool pairs_ahead = false;  // the next step's pairs are built (or on their way)
+  double *xpos_alt = nullptr;  // the prepared step's positions (read-outs keep xpos)
+  // ev_ahead_go marks the end of the last step's fixed point, so that moved
+  // points given by ibm_update_points can have the next step prepared at once
+  bool loop_mark = false;
   int64_t *t_dev = nullptr;
   bool desc_dirty = true;
   uint64_t version = 1;  // changes whenever a pointer in the descriptor does
@@ -276,6 +280,7 @@ const void *mapped_ptr(const void *p) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+
 // Moves mapped uploads still to be read into X / utarget with copies on s
 // (before a step whose kinematics will not read them itself).
 int flush_points(lbm_t *h, cudaStream_t s) {
@@ -304,6 +309,7 @@ void free_points(lbm_t *h) {
   dfree(h->cg);
   dfree(h->cg_part);
   dfree(h->xpos);
+  dfree(h->xpos_alt);
   dfree(h->m.slot_brick);
   dfree(h->m.order);
   dfree(h->pm.count);
@@ -366,6 +372,12 @@ void rest_boxes(const double *X, const int *body, int64_t n, std::vector<double>
 
 extern "C" {
 
+// (the steps prepared ahead; defined with the step below)
+static int discard_ahead(lbm_t *h);
+static BatchDims dims_of(const lbm_t *h);
+static int launch_ahead_chain(lbm_t *h, const BatchDims &dims, const double *Xsrc,
+                              const float *Usrc, long long t_step);
+
 void lbm_default_opts(lbm_opts *o) {
   if (!o) return;
   memset(o, 0, sizeof *o);
@@ -395,6 +407,7 @@ void lbm_velocity_set(int *e, double *t) {
 
 void lbm_destroy(lbm_t *h) {
   if (!h) return;
+  discard_ahead(h);
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
   dfree(h->f[0]);
@@ -553,6 +566,10 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
       if (body[k] > maxb) maxb = body[k];
     }
   if (n > 0 && !body) maxb = 0;
+  {
+    const int ra = discard_ahead(h);  // (the prepared step's points are void)
+    if (ra) return ra;
+  }
   h->x_src = nullptr;  // (mapped uploads of the previous points are void)
   h->u_src = nullptr;
   if (h->nb > 0 && maxb >= h->nb)
@@ -573,6 +590,7 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
     CK(h, dalloc(&h->cg, 5 * n));
     CK(h, dalloc(&h->cg_part, 2 * ((n + 255) / 256)));
     CK(h, dalloc(&h->xpos, 3 * n));
+    CK(h, dalloc(&h->xpos_alt, 3 * n));
     CK(h, dalloc(&h->m.slot_brick, ms));
     CK(h, dalloc(&h->m.order, (size_t)ORDER_BUCKETS * ms));
     CK(h, dalloc(&h->pm.count, ms));
@@ -631,8 +649,28 @@ int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_targe
                               (long long)h->np);
   if (n == 0) return LBM_OK;
   if (!X) return fail(h, LBM_EINVAL, "X is NULL");
+  if (h->pairs_ahead) {
+    // a step prepared from earlier positions: these supersede them
+    const int ra = discard_ahead(h);
+    if (ra) return ra;
+  }
   const void *mx = h->host_io == LBM_HOST_IO_MAPPED ? mapped_ptr(X) : nullptr;
   const void *mu = mx && U_target ? mapped_ptr(U_target) : nullptr;
+  if (mx && (!U_target || mu) && h->loop_mark && !h->pairs_ahead) {
+    // the last step's fixed point is marked (ev_ahead_go): the next step's
+    // kinematics (reading these buffers) and pair lists start now, beside
+    // that step's collide
+    h->loop_mark = false;
+    const float *us = mu ? (const float *)mu : h->u_src;
+    if (U_target) h->targets_nonzero = false;
+    h->x_src = nullptr;
+    h->u_src = nullptr;
+    if (h->u0_mode == LBM_U0_BOX) {
+      rest_boxes(X, h->body_host.empty() ? nullptr : h->body_host.data(), n, h->box_host);
+      h->box_dirty = true;
+    }
+    return launch_ahead_chain(h, dims_of(h), (const double *)mx, us, (long long)h->t);
+  }
   if (mx && (!U_target || mu)) {
     // read by the next step's kinematics (an earlier mapped target without
     // a new one stays to be read)
@@ -660,6 +698,10 @@ int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_targe
 int ibm_set_bodies(lbm_t *h, int nb, const double *centre, const double *omega,
                    const double *phase) {
   if (!h) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   if (nb < 0) return fail(h, LBM_EINVAL, "nb = %d < 0", nb);
   if (nb > 0 && (!centre || !omega || !phase))
     return fail(h, LBM_EINVAL, "centre/omega/phase must be given");
@@ -700,6 +742,10 @@ int lbm_set_body_force(lbm_t *h, double gx, double gy, double gz) {
 int64_t lbm_time(const lbm_t *h) { return h ? h->t : -1; }
 int lbm_set_time(lbm_t *h, int64_t t) {
   if (!h) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   CK(h, h->st ? cudaStreamSynchronize(h->st) : cudaDeviceSynchronize());
   CK(h, cudaMemcpy(h->t_dev, &t, sizeof t, cudaMemcpyHostToDevice));
   h->t = t;
@@ -763,6 +809,7 @@ static int sync_desc(lbm_t *h) {
   h->desc_host = d;
   DomainDesc da = d;
   da.m.brick_slot = h->bslot_alt;
+  da.xpos = h->xpos_alt;
   CK(h, cudaMemcpy(h->desc_alt, &da, sizeof da, cudaMemcpyHostToDevice));
   h->desc_host_alt = da;
   h->desc_dirty = false;
@@ -805,6 +852,7 @@ struct StepCtx {
   const float *u_src;
   bool pairs_done;  // kinematics and pair lists were built ahead (ahead_st)
   bool ahead;       // build the next step's after this step's fixed point
+  bool mark_loop;   // else record ev_ahead_go there (see lbm_t::loop_mark)
   long long t_next; // the next step's index (its kinematics)
 };
 
@@ -936,8 +984,7 @@ static int enqueue_fixed_loop(StepCtx &c, int n_iter, bool warm) {
 // HBM-bound pass that leaves SM slots and L2 to them).  They write the other
 // brick map, through desc_alt, and finish before the next step's first
 // kernel on st (ev_ahead_done).
-static int enqueue_ahead(StepCtx &c) {
-  lbm_t *h = c.acct;
+static int ensure_ahead(lbm_t *h) {
   if (!h->ahead_st) {
     int lo = 0, hi = 0;
     CK(h, cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -946,22 +993,42 @@ static int enqueue_ahead(StepCtx &c) {
   if (!h->ev_ahead_go) CK(h, cudaEventCreateWithFlags(&h->ev_ahead_go, cudaEventDisableTiming));
   if (!h->ev_ahead_done)
     CK(h, cudaEventCreateWithFlags(&h->ev_ahead_done, cudaEventDisableTiming));
-  CK(h, cudaEventRecord(h->ev_ahead_go, c.st));
+  return LBM_OK;
+}
+
+// The chain of step t_step on ahead_st after ev_ahead_go, into the other
+// brick map (desc_alt); Xsrc / Usrc: mapped uploads it reads (else the
+// device copies).
+static int launch_ahead_chain(lbm_t *h, const BatchDims &dims, const double *Xsrc,
+                              const float *Usrc, long long t_step) {
   CK(h, cudaStreamWaitEvent(h->ahead_st, h->ev_ahead_go, 0));
   const DomainDesc *Dn = h->desc_alt;
-  BatchDims da = c.dims;
+  BatchDims da = dims;
   da.ls.sort_blocks = da.ls.sort_blocks_ahead;
   {
     StageTimer T(h, ST_KIN, h->ahead_st, 1);
-    CK(h, launch_prepare_points(Dn, c.dims, h->ahead_st, nullptr, nullptr, c.t_next));
+    CK(h, launch_prepare_points(Dn, dims, h->ahead_st, Xsrc, Usrc, t_step));
   }
   {
     StageTimer T(h, ST_PAIRS, h->ahead_st, 3);
-    CK(h, launch_compact(Dn, c.dims, h->ahead_st));
+    CK(h, launch_compact(Dn, dims, h->ahead_st));
     CK(h, launch_pair_lists(Dn, da, h->ahead_st));
   }
   CK(h, cudaEventRecord(h->ev_ahead_done, h->ahead_st));
+  h->pairs_ahead = true;
   return LBM_OK;
+}
+
+// After this step's fixed point: the next step's chain (c.ahead), or only the
+// mark of the fixed point's end for an upload to start it (c.mark_loop).
+static int enqueue_ahead(StepCtx &c) {
+  lbm_t *h = c.acct;
+  if (!c.ahead && !c.mark_loop) return LBM_OK;
+  int r = ensure_ahead(h);
+  if (r) return r;
+  CK(h, cudaEventRecord(h->ev_ahead_go, c.st));
+  if (!c.ahead) return LBM_OK;
+  return launch_ahead_chain(h, c.dims, nullptr, nullptr, c.t_next);
 }
 
 // The collide of the cells with the IBM force (split: the active bricks on
@@ -996,10 +1063,8 @@ static int enqueue_step(StepCtx &c, int n_iter) {
     if (r) return r;
     r = enqueue_fixed_loop(c, n_iter, warm);
     if (r) return r;
-    if (c.ahead) {
-      r = enqueue_ahead(c);
-      if (r) return r;
-    }
+    r = enqueue_ahead(c);
+    if (r) return r;
   }
   return enqueue_suffix(c);
 }
@@ -1166,10 +1231,28 @@ static void after_step(lbm_t *h, int n_iter) {
   h->t++;
 }
 
-// Makes the handle's stream wait for a step prepared ahead (its kinematics
-// and pairs), which is then the current step's; no-op when there is none.
-static int join_ahead(lbm_t *h, bool *was_pending = nullptr) {
-  if (was_pending) *was_pending = h->pairs_ahead;
+// The prepared step (kinematics and pair lists built ahead) becomes the
+// current one: the handle's stream waits for its chain, and its descriptor,
+// brick map and positions become the handle's.  No-op when there is none.
+static int take_ahead(lbm_t *h, bool *taken) {
+  *taken = h->pairs_ahead;
+  if (!h->pairs_ahead) return LBM_OK;
+  h->pairs_ahead = false;
+  CK(h, cudaStreamWaitEvent(h->st, h->ev_ahead_done, 0));
+  std::swap(h->desc, h->desc_alt);
+  std::swap(h->desc_host, h->desc_host_alt);
+  std::swap(h->m.brick_slot, h->bslot_alt);
+  std::swap(h->xpos, h->xpos_alt);
+  h->version++;  // (a captured step holds the other descriptor)
+  return LBM_OK;
+}
+
+// A prepared step that will not be taken (the points, bodies, time or
+// transfer mode change, or the next steps are replayed or batched): the
+// handle's stream waits for its chain, whose writes stay in the other brick
+// map; its write-through of mapped uploads into the device copies stands.
+static int discard_ahead(lbm_t *h) {
+  h->loop_mark = false;
   if (!h->pairs_ahead) return LBM_OK;
   h->pairs_ahead = false;
   CK(h, cudaStreamWaitEvent(h->st, h->ev_ahead_done, 0));
@@ -1180,11 +1263,16 @@ static int join_ahead(lbm_t *h, bool *was_pending = nullptr) {
 // one collides; the caller makes the next step the next call of step_once.
 static int step_once(lbm_t *h, int n_iter, bool ahead = false) {
   bool pre = false;
-  int rj = join_ahead(h, &pre);
+  int rj = take_ahead(h, &pre);
   if (rj) return rj;
+  h->loop_mark = false;
   StepCtx c = ctx_of(h, h->st);
   c.pairs_done = pre;
-  c.ahead = ahead && h->np > 0 && !h->overlap;
+  const bool can = h->np > 0 && !h->overlap && !h->timing;
+  c.ahead = ahead && can;
+  // a one-step call in mapped transfer mode marks its fixed point's end, for
+  // the next upload of moved points (ibm_update_points) to start the next step
+  c.mark_loop = !c.ahead && can && h->host_io == LBM_HOST_IO_MAPPED && !h->graph_on;
   c.t_next = (long long)h->t + 1;
   if (h->np > 0) {
     // the kinematics read the mapped uploads themselves
@@ -1204,24 +1292,15 @@ static int step_once(lbm_t *h, int n_iter, bool ahead = false) {
     if (r) return r;
     warn = tolerance_loop(c, warm);
     if (warn < 0) return warn;
-    if (c.ahead) {
-      r = enqueue_ahead(c);
-      if (r) return r;
-    }
+    r = enqueue_ahead(c);
+    if (r) return r;
     r = enqueue_suffix(c);
     if (r) return r;
   } else {
     int r = enqueue_step(c, n_iter);
     if (r) return r;
   }
-  if (c.ahead) {
-    // the prepared step becomes the current one: its descriptor and brick map
-    std::swap(h->desc, h->desc_alt);
-    std::swap(h->desc_host, h->desc_host_alt);
-    std::swap(h->m.brick_slot, h->bslot_alt);
-    h->pairs_ahead = true;
-    h->version++;  // (a captured step holds the other descriptor)
-  }
+  h->loop_mark = c.mark_loop;
   after_step(h, n_iter);
   return warn;
 }
@@ -1347,6 +1426,8 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
         h->g_cur = h->cur;
         h->g_version = h->version;
       }
+      r = discard_ahead(h);
+      if (r) return r;
       r = replay(h, h->st, h->cap_stream, h->ev_in, h->ev_out, h->gexec);
       if (r) return r;
       h->nlaunch += h->g_launches;
@@ -1361,7 +1442,7 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
     const bool ahead = !graphable && !h->timing && s + 1 < n_steps;
     r = step_once(h, n_ibm_iter, ahead);
     if (r < 0) {
-      join_ahead(h);
+      discard_ahead(h);
       return r;
     }
     if (r == LBM_WNOTCONVERGED) warn = r;
@@ -1378,6 +1459,10 @@ int lbm_set_graph(lbm_t *h, int on) {
 
 int lbm_set_overlap(lbm_t *h, int on) {
   if (!h) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   if (h->overlap != (on != 0)) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->ibm_st) cudaStreamSynchronize(h->ibm_st);
@@ -1600,7 +1685,9 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
       return fail(h0, LBM_EINVAL, "points refer to a missing body");
     if (h->warm == LBM_WARM_MLP && !h->mlp_packed && h->np > 0)
       return fail(h0, LBM_EINVAL, "learned warm start without weights");
-    int r = sync_desc(h);
+    int r = discard_ahead(h);
+    if (r) return r;
+    r = sync_desc(h);
     if (r) return r;
     r = flush_points(h, h0->st);  // (batched kinematics read the device copies)
     if (r) return r;
@@ -1888,6 +1975,10 @@ int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s) {
 
 int lbm_autotune(lbm_t *h, int n_ibm_iter, int steps_per_trial, lbm_launch_shape *chosen) {
   if (!h) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   if (n_ibm_iter <= 0 || steps_per_trial < 1)
     return fail(h, LBM_EINVAL, "autotune needs n_ibm_iter > 0 and steps_per_trial >= 1");
   Snapshot sn;
@@ -1961,6 +2052,8 @@ int lbm_batch_autotune(lbm_batch_t *b, int n_ibm_iter, int steps_per_trial,
     return fail(h0, LBM_EINVAL, "autotune needs n_ibm_iter > 0 and steps_per_trial >= 1");
   std::vector<Snapshot> sn(b->hs.size());
   int r = LBM_OK;
+  for (lbm_t *h : b->hs)
+    if (r == LBM_OK) r = discard_ahead(h);
   for (size_t i = 0; i < b->hs.size() && r == LBM_OK; i++) r = snapshot_take(b->hs[i], sn[i]);
   bool points = false;
   for (lbm_t *h : b->hs) points = points || h->np > 0;
@@ -2097,6 +2190,10 @@ int lbm_read_sums_async(lbm_t *h, double *sums) {
 
 int lbm_set_host_io(lbm_t *h, int mode) {
   if (!h) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   if (mode != LBM_HOST_IO_COPY && mode != LBM_HOST_IO_MAPPED)
     return fail(h, LBM_EINVAL, "unknown host transfer mode %d", mode);
   if (mode == LBM_HOST_IO_COPY) {
@@ -2115,6 +2212,10 @@ int lbm_get_host_io(lbm_t *h, int *mode) {
 
 int lbm_read_stats(lbm_t *h, lbm_stats *s) {
   if (!h || !s) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   memset(s, 0, sizeof *s);
   double sums[4] = {0, 0, 0, 0};
   if (h->sums_valid) {
@@ -2233,6 +2334,10 @@ const char kMagic[8] = {'L', 'B', 'M', 'I', 'B', 'M', '0', '1'};
 
 int lbm_save_state(lbm_t *h, void *buf, size_t *len) {
   if (!h || !len) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   if (buf) {
     const int rf = flush_points(h, h->st);  // (the last mapped upload belongs to the state)
     if (rf) return rf;
@@ -2293,6 +2398,10 @@ int lbm_save_state(lbm_t *h, void *buf, size_t *len) {
 
 int lbm_load_state(lbm_t *h, const void *buf, size_t len) {
   if (!h || !buf) return LBM_EINVAL;
+  {
+    const int ra = discard_ahead(h);  // (a prepared step would not be taken)
+    if (ra) return ra;
+  }
   if (len < sizeof(StateHeader)) return fail(h, LBM_ESTATE, "state buffer too short");
   StateHeader hd;
   memcpy(&hd, buf, sizeof hd);

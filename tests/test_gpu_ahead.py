@@ -111,3 +111,30 @@ def test_points_moved_between_calls(gpu_lib, torch_cuda):
         _same(a, b)
     a.close()
     b.close()
+
+
+def test_uploads_start_the_next_step(gpu_lib, torch_cuda):
+    """Mapped transfers, one step per call, the rest pose of rotating bodies
+    uploaded from page-locked memory before every step (the next step's
+    kinematics and pair lists then start at the upload, beside the step
+    before it), with read-outs of fields, points and stats between the
+    steps: bitwise the same as copies and blocking calls."""
+    torch = torch_cuda
+    w = W.dense_array_64()
+    st = torch.cuda.current_stream()
+    a, b = (gpu_lib.Lattice(w.shape, w.tau, warm="previous", stream=st) for _ in range(2))
+    for lat in (a, b):
+        lat.set_propellers(w.props)
+    a.set_host_io("mapped")
+    X = torch.from_numpy(np.ascontiguousarray(w.props.xrest)).pin_memory().numpy()
+    L = gpu_lib.load()
+    for k in range(6):
+        gpu_lib._check(L.ibm_update_points(a.h, len(X), gpu_lib._ptr(X), None), a.h)
+        b.update_points(w.props.xrest)
+        a.step(1, 5)
+        b.step(1, 5)
+        if k % 2:
+            _same(a, b)
+    _same(a, b)
+    a.close()
+    b.close()
