@@ -139,8 +139,14 @@ int ibm_set_points(lbm_t *h, int64_t n, const double *X, const float *U_target,
  * immersedBoundary(object, U) with the object updated each step).  Positions
  * are not checked here; a non-finite one gives an unspecified point, never an
  * out-of-range access.  With mapped host transfers (lbm_set_host_io) the
- * buffers are instead read by the next step's kinematics.  This entry point
- * has no counterpart in the paper.
+ * buffers are instead read by the next step's kinematics; when the last step
+ * ran as a one-step call in that mode, the next step's kinematics and pair
+ * lists start at this call, on an internal stream beside that step's
+ * collide (the next lbm_step takes them; a later ibm_update_points,
+ * ibm_set_points, ibm_set_bodies, lbm_set_time, lbm_set_host_io,
+ * lbm_load_state, lbm_save_state, lbm_read_stats, lbm_autotune, a batched or
+ * replayed step discards them, the positions staying uploaded).  This entry
+ * point has no counterpart in the paper.
  * Errors: LBM_EINVAL (n differs from the point count, X NULL), LBM_ECUDA. */
 int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_target);
 
@@ -270,6 +276,9 @@ int lbm_read_sums_async(lbm_t *h, double *sums);
  *    uploaded buffer unchanged until the next step has run (an event recorded
  *    on the stream after that lbm_step has completed), and a read-out buffer
  *    valid until the stream has passed the call, as for asynchronous copies.
+ *    A one-step call in this mode records an event after its fixed point, so
+ *    that the next upload can start the next step's kinematics and pair
+ *    lists beside this step's collide (see ibm_update_points).
  *    A step replayed from a captured graph, a batched step and lbm_save_state
  *    copy a pending upload in stream order first.  Buffers that are not
  *    device-mapped host memory are copied as in LBM_HOST_IO_COPY.
