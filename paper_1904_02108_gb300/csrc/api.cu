@@ -375,8 +375,8 @@ extern "C" {
 // (the steps prepared ahead; defined with the step below)
 static int discard_ahead(lbm_t *h);
 static BatchDims dims_of(const lbm_t *h);
-static int launch_ahead_chain(lbm_t *h, const BatchDims &dims, const double *Xsrc,
-                              const float *Usrc, long long t_step);
+static int launch_ahead_chain(lbm_t *h, const BatchDims &dims, const DomainDesc *Dn,
+                              const double *Xsrc, const float *Usrc, long long t_step);
 
 void lbm_default_opts(lbm_opts *o) {
   if (!o) return;
@@ -514,8 +514,8 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = dalloc(&h->desc, 1);
   if (e == cudaSuccess) e = dalloc(&h->desc_alt, 1);
-  if (e == cudaSuccess) e = dalloc(&h->t_dev, 1);
-  if (e == cudaSuccess) e = cudaMemset(h->t_dev, 0, sizeof(int64_t));
+  if (e == cudaSuccess) e = dalloc(&h->t_dev, 2);
+  if (e == cudaSuccess) e = cudaMemset(h->t_dev, 0, 2 * sizeof(int64_t));
   if (e == cudaSuccess) e = dalloc(&h->state, 1);
   if (e == cudaSuccess) e = cudaMemset(h->state, 0, sizeof(IbmState));
   if (e == cudaSuccess) e = cudaMallocHost((void **)&h->state_host, sizeof(IbmState));
@@ -669,7 +669,10 @@ int ibm_update_points(lbm_t *h, int64_t n, const double *X, const float *U_targe
       rest_boxes(X, h->body_host.empty() ? nullptr : h->body_host.data(), n, h->box_host);
       h->box_dirty = true;
     }
-    return launch_ahead_chain(h, dims_of(h), (const double *)mx, us, (long long)h->t);
+    const int rc = launch_ahead_chain(h, dims_of(h), h->desc_alt, (const double *)mx, us,
+                                      (long long)h->t);
+    if (rc == LBM_OK) h->pairs_ahead = true;
+    return rc;
   }
   if (mx && (!U_target || mu)) {
     // read by the next step's kinematics (an earlier mapped target without
@@ -853,6 +856,7 @@ struct StepCtx {
   bool pairs_done;  // kinematics and pair lists were built ahead (ahead_st)
   bool ahead;       // build the next step's after this step's fixed point
   bool mark_loop;   // else record ev_ahead_go there (see lbm_t::loop_mark)
+  const DomainDesc *D_next;  // the prepared step's descriptors (NULL: desc_alt)
   long long t_next; // the next step's index (its kinematics)
 };
 
@@ -999,10 +1003,9 @@ static int ensure_ahead(lbm_t *h) {
 // The chain of step t_step on ahead_st after ev_ahead_go, into the other
 // brick map (desc_alt); Xsrc / Usrc: mapped uploads it reads (else the
 // device copies).
-static int launch_ahead_chain(lbm_t *h, const BatchDims &dims, const double *Xsrc,
-                              const float *Usrc, long long t_step) {
+static int launch_ahead_chain(lbm_t *h, const BatchDims &dims, const DomainDesc *Dn,
+                              const double *Xsrc, const float *Usrc, long long t_step) {
   CK(h, cudaStreamWaitEvent(h->ahead_st, h->ev_ahead_go, 0));
-  const DomainDesc *Dn = h->desc_alt;
   BatchDims da = dims;
   da.ls.sort_blocks = da.ls.sort_blocks_ahead;
   {
@@ -1010,12 +1013,12 @@ static int launch_ahead_chain(lbm_t *h, const BatchDims &dims, const double *Xsr
     CK(h, launch_prepare_points(Dn, dims, h->ahead_st, Xsrc, Usrc, t_step));
   }
   {
-    StageTimer T(h, ST_PAIRS, h->ahead_st, 3);
+    StageTimer T(h, ST_PAIRS, h->ahead_st, dims.work_off ? 4 : 3);
     CK(h, launch_compact(Dn, dims, h->ahead_st));
+    CK(h, launch_batch_worklist(Dn, dims, h->ahead_st));
     CK(h, launch_pair_lists(Dn, da, h->ahead_st));
   }
   CK(h, cudaEventRecord(h->ev_ahead_done, h->ahead_st));
-  h->pairs_ahead = true;
   return LBM_OK;
 }
 
@@ -1028,7 +1031,11 @@ static int enqueue_ahead(StepCtx &c) {
   if (r) return r;
   CK(h, cudaEventRecord(h->ev_ahead_go, c.st));
   if (!c.ahead) return LBM_OK;
-  return launch_ahead_chain(h, c.dims, nullptr, nullptr, c.t_next);
+  r = launch_ahead_chain(h, c.dims, c.D_next ? c.D_next : h->desc_alt, nullptr, nullptr,
+                         c.t_next);
+  if (r) return r;
+  if (!c.D_next) h->pairs_ahead = true;  // (inside a capture the graph joins it)
+  return LBM_OK;
 }
 
 // The collide of the cells with the IBM force (split: the active bricks on
@@ -1327,8 +1334,16 @@ static int ensure_capture_stream(lbm_t *acct, cudaStream_t *cs, cudaEvent_t *a, 
 
 // Captures two steps of `c` (c.st is replaced by the capture stream) into
 // *exec; *launches receives the kernels per replay.
+// D_alt (Dhost_alt for a single lattice): the descriptors of the same
+// lattices with their other brick maps, or NULL.  With them the first step of
+// the pair runs on them and the second step's kinematics and pair lists are
+// built beside the first one's collide, on the primary descriptors (which the
+// second step then uses, so that after a replay the primary brick maps are
+// the current ones); the prepared step's index comes from the device (the one
+// the first step's kinematics used, plus one).
 static int capture_two_steps(StepCtx c, int n_iter, cudaStream_t cs, cudaGraphExec_t *exec,
-                             int64_t *launches) {
+                             int64_t *launches, const DomainDesc *D_alt = nullptr,
+                             const DomainDesc *Dhost_alt = nullptr) {
   lbm_t *h = c.acct;
   if (*exec) {
     cudaGraphExecDestroy(*exec);
@@ -1342,12 +1357,36 @@ static int capture_two_steps(StepCtx c, int n_iter, cudaStream_t cs, cudaGraphEx
   c.split = false;
   int r0 = ensure_split(h, c, true);
   if (r0) return r0;
+  const bool ahead = D_alt && !c.split && c.dims.max_points > 0;
+  if (ahead) {
+    r0 = ensure_ahead(h);
+    if (r0) return r0;
+  }
   CK(h, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  int r = enqueue_step(c, n_iter);
-  if (r == LBM_OK) {
-    c.cur ^= 1;
-    c.have_du = c.have_du || c.dims.max_points > 0;
+  int r = LBM_OK;
+  if (ahead) {
+    StepCtx a = c;
+    a.D = D_alt;
+    a.Dhost = Dhost_alt;
+    a.ahead = true;
+    a.D_next = c.D;
+    a.t_next = -2;
+    r = enqueue_step(a, n_iter);
+    if (r == LBM_OK && cudaStreamWaitEvent(cs, h->ev_ahead_done, 0) != cudaSuccess)
+      r = fail(h, LBM_ECUDA, "stream capture: joining the prepared step");
+    if (r == LBM_OK) {
+      c.cur ^= 1;
+      c.have_du = true;
+      c.pairs_done = true;
+      r = enqueue_step(c, n_iter);
+    }
+  } else {
     r = enqueue_step(c, n_iter);
+    if (r == LBM_OK) {
+      c.cur ^= 1;
+      c.have_du = c.have_du || c.dims.max_points > 0;
+      r = enqueue_step(c, n_iter);
+    }
   }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -1420,7 +1459,8 @@ int lbm_step(lbm_t *h, int n_steps, int n_ibm_iter) {
         r = ensure_capture_stream(h, &h->cap_stream, &h->ev_in, &h->ev_out);
         if (r) return r;
         r = capture_two_steps(ctx_of(h, h->st), n_ibm_iter, h->cap_stream, &h->gexec,
-                              &h->g_launches);
+                              &h->g_launches, h->timing ? nullptr : h->desc_alt,
+                              &h->desc_host_alt);
         if (r) return r;
         h->g_iters = n_ibm_iter;
         h->g_cur = h->cur;
@@ -1512,6 +1552,7 @@ int lbm_get_u0_strategy(const lbm_t *h) { return h ? h->u0_mode : -1; }
 struct lbm_batch {
   std::vector<lbm_t *> hs;
   DomainDesc *D = nullptr;
+  DomainDesc *D_alt = nullptr;  // the same with the handles' other brick maps
   uint64_t built_for = 0;  // sum of the handles' versions at the last build
   bool graph_on = false;
   cudaStream_t cap_stream = nullptr;
@@ -1544,9 +1585,12 @@ int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out) {
   b->hs.assign(handles, handles + n);
   b->shape = handles[0]->shape;
   if (cudaMalloc(&b->D, sizeof(DomainDesc) * n) != cudaSuccess ||
+      cudaMalloc(&b->D_alt, sizeof(DomainDesc) * n) != cudaSuccess ||
       cudaMalloc(&b->work_off, sizeof(int) * ((size_t)(ORDER_BUCKETS + 1) * n + 2)) !=
           cudaSuccess) {
     if (b->D) cudaFree(b->D);
+    if (b->D_alt) cudaFree(b->D_alt);
+    if (b->work_off) cudaFree(b->work_off);
     delete b;
     return fail(nullptr, LBM_ENOMEM, "batch descriptors");
   }
@@ -1558,6 +1602,7 @@ void lbm_batch_destroy(lbm_batch_t *b) {
   if (!b) return;
   cudaDeviceSynchronize();
   if (b->D) cudaFree(b->D);
+  if (b->D_alt) cudaFree(b->D_alt);
   if (b->work_off) cudaFree(b->work_off);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -1710,11 +1755,18 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
     }
   }
   if (ver != b->built_for) {
-    std::vector<DomainDesc> hd;
-    for (lbm_t *h : b->hs) hd.push_back(host_desc(h));
+    std::vector<DomainDesc> hd, ha;
+    for (lbm_t *h : b->hs) {
+      hd.push_back(host_desc(h));
+      ha.push_back(hd.back());
+      ha.back().m.brick_slot = h->bslot_alt;
+      ha.back().xpos = h->xpos_alt;
+    }
     // (earlier steps of the batch may still read the old descriptors)
     CK(h0, h0->st ? cudaStreamSynchronize(h0->st) : cudaDeviceSynchronize());
     CK(h0, cudaMemcpy(b->D, hd.data(), sizeof(DomainDesc) * hd.size(), cudaMemcpyHostToDevice));
+    CK(h0, cudaMemcpy(b->D_alt, ha.data(), sizeof(DomainDesc) * ha.size(),
+                      cudaMemcpyHostToDevice));
     b->built_for = ver;
   }
   StepCtx c{};
@@ -1736,7 +1788,8 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
       if (!b->gexec || b->g_iters != n_ibm_iter || b->g_cur != c.cur || b->g_version != ver) {
         int r = ensure_capture_stream(h0, &b->cap_stream, &b->ev_in, &b->ev_out);
         if (r) return r;
-        r = capture_two_steps(c, n_ibm_iter, b->cap_stream, &b->gexec, &b->g_launches);
+        r = capture_two_steps(c, n_ibm_iter, b->cap_stream, &b->gexec, &b->g_launches,
+                              b->D_alt);
         if (r) return r;
         b->g_iters = n_ibm_iter;
         b->g_cur = c.cur;

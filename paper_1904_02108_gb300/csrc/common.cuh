@@ -278,7 +278,8 @@ struct DomainDesc {
   float om;           // 1 / tau (FP32, rounded to nearest)
   float gbody[3];
   void *f[2];         // the two population lattices
-  int64_t *t;         // device step counter
+  int64_t *t;         // [0] device step counter, [1] the step the last
+                      // prepare_points computed
   const double *X;    // [np][3] rest or fixed positions
   const int *body;    // [np]
   const float *area;  // [np]

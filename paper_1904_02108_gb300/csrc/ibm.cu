@@ -127,9 +127,13 @@ constexpr int TRIG_CACHE = 16;
 
 // Xsrc / Usrc (single lattice, else NULL): new positions / targets read
 // from device-mapped host memory by this step and written through to the
-// domain's X / utarget (an upload that needs no copy of its own).  t_step >=
-// 0: the step whose kinematics to compute (given when the step is prepared
-// while the one before it, which advances the device's counter, still runs).
+// domain's X / utarget (an upload that needs no copy of its own).  The step
+// whose kinematics to compute: t_step >= 0 (given when the step is prepared
+// while the one before it, which advances the device's counter at its end,
+// still runs), -1 the device's counter t[0], -2 one after the step the last
+// prepare_points computed (t[1]: a step prepared inside a captured graph,
+// whose index is not known on the host).  A launch in the first two forms
+// records its step in t[1] (a domain with a counter).
 __global__ void __launch_bounds__(512, 2)
     prepare_points_kernel(const DomainDesc *__restrict__ D, const double *__restrict__ Xsrc,
                           const float *__restrict__ Usrc, long long t_step) {
@@ -144,6 +148,7 @@ __global__ void __launch_bounds__(512, 2)
   const PairMap pm = d.pm;
   double *__restrict__ xpos = d.xpos;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0 && d.t && t_step != -2) d.t[1] = t_step >= 0 ? (int64_t)t_step : d.t[0];
   if (k == 0) {
     m.counters[0] = 0;
     m.counters[1] = 0;
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(512, 2)
     __syncthreads();
     b0 = sb_lo;
     nbk = sb_hi >= 0 ? sb_hi - sb_lo + 1 : 0;
-    tstep = t_step >= 0 ? (int64_t)t_step : *d.t;
+    tstep = t_step >= 0 ? (int64_t)t_step : (t_step == -2 ? d.t[1] + 1 : d.t[0]);
     if (nbk <= TRIG_CACHE && (int)threadIdx.x < nbk)
       strig[threadIdx.x] = body_trig(bd, b0 + threadIdx.x, tstep);
     __syncthreads();

@@ -46,6 +46,12 @@ def test_graph_replay_is_bitwise_eager(gpu_lib, torch_cuda, warm):
     a.step(11, 5)
     b.step(11, 5)  # one eager step, then five replayed pairs
     assert np.array_equal(a.populations(), b.populations())
+    # read-outs after replays (in a replayed pair the second step's pair
+    # lists are built beside the first one's collide, into the brick map and
+    # positions the read-outs use)
+    for x, y in zip(a.points(), b.points()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.fields()[2], b.fields()[2])
     sa, sb = a.stats(), b.stats()
     assert sa["step"] == sb["step"] == 11 and sa["mass"] == sb["mass"]
     assert sb["kernel_launches"] == sa["kernel_launches"]
@@ -70,7 +76,9 @@ def test_batch_is_bitwise_per_lattice_stepping(gpu_lib, torch_cuda, graph):
         assert ss["step"] == sb["step"] == 6
         assert ss["mass"] == sb["mass"] and ss["momentum"] == sb["momentum"]
         if s.np:
-            assert np.array_equal(s.points()[2], b.points()[2])
+            for x, y in zip(s.points(), b.points()):
+                assert np.array_equal(x, y)
+            assert np.array_equal(s.fields()[2], b.fields()[2])
     batch.close()
     for lat in single + batched:
         lat.close()
