@@ -118,3 +118,45 @@ def test_dense_array_256_paper_loop_to_tolerance(gpu_lib, orc):
     assert rel_l2(U, U_o) < 1e-5
     assert rel_l2(G, sim.G) < 1e-4
     lat.close()
+
+
+def test_dense_array_256_steps_prepared_ahead_are_single_steps(gpu_lib):
+    """At the full size (about 10,000 active bricks, pair lists of up to 128
+    points, the small sort grid of a prepared step): one call of six steps,
+    whose later steps are prepared beside the collide before them, against
+    six one-step calls, and, in mapped transfer mode, six steps each started
+    by the upload of the rest pose: bitwise the same populations, points,
+    forces and sums."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.dense_array_256()
+    st = torch.cuda.current_stream()
+    a = gpu_lib.Lattice(w.shape, w.tau, stream=st, warm="previous")
+    b = gpu_lib.Lattice(w.shape, w.tau, stream=st, warm="previous")
+    for lat in (a, b):
+        lat.set_propellers(w.props)
+    a.step(6, w.n_iter)
+    for _ in range(6):
+        b.step(1, w.n_iter)
+
+    def same():
+        assert np.array_equal(a.deviations(), b.deviations())
+        for x, y in zip(a.points(), b.points()):
+            assert np.array_equal(x, y)
+        assert np.array_equal(a.fields()[2], b.fields()[2])
+        sa, sb = a.stats(), b.stats()
+        assert sa["mass"] == sb["mass"] and sa["momentum"] == sb["momentum"]
+        assert sa["step"] == sb["step"]
+
+    same()
+    a.set_host_io("mapped")
+    X = torch.from_numpy(np.ascontiguousarray(w.props.xrest)).pin_memory().numpy()
+    L = gpu_lib.load()
+    for _ in range(6):
+        gpu_lib._check(L.ibm_update_points(a.h, len(X), gpu_lib._ptr(X), None), a.h)
+        a.step(1, w.n_iter)
+        b.step(1, w.n_iter)
+    same()
+    a.close()
+    b.close()
