@@ -113,16 +113,24 @@ def test_points_moved_between_calls(gpu_lib, torch_cuda):
     b.close()
 
 
-def test_uploads_start_the_next_step(gpu_lib, torch_cuda):
+@pytest.mark.parametrize("mode", ["fixed", "loop_to_tol", "cg_to_tol"])
+def test_uploads_start_the_next_step(gpu_lib, torch_cuda, mode):
     """Mapped transfers, one step per call, the rest pose of rotating bodies
     uploaded from page-locked memory before every step (the next step's
     kinematics and pair lists then start at the upload, beside the step
     before it), with read-outs of fields, points and stats between the
-    steps: bitwise the same as copies and blocking calls."""
+    steps: bitwise the same as copies and blocking calls; with the fixed
+    count, and iterating the paper's loop or conjugate gradients to a
+    residual target."""
     torch = torch_cuda
     w = W.dense_array_64()
     st = torch.cuda.current_stream()
-    a, b = (gpu_lib.Lattice(w.shape, w.tau, warm="previous", stream=st) for _ in range(2))
+    kw = dict(warm="previous")
+    n_iter = 5
+    if mode != "fixed":
+        kw.update(ibm_tol=1e-3, ibm_max_iter=400, solver="cg" if mode == "cg_to_tol" else "mdf")
+        n_iter = 0
+    a, b = (gpu_lib.Lattice(w.shape, w.tau, stream=st, **kw) for _ in range(2))
     for lat in (a, b):
         lat.set_propellers(w.props)
     a.set_host_io("mapped")
@@ -131,8 +139,8 @@ def test_uploads_start_the_next_step(gpu_lib, torch_cuda):
     for k in range(6):
         gpu_lib._check(L.ibm_update_points(a.h, len(X), gpu_lib._ptr(X), None), a.h)
         b.update_points(w.props.xrest)
-        a.step(1, 5)
-        b.step(1, 5)
+        a.step(1, n_iter)
+        b.step(1, n_iter)
         if k % 2:
             _same(a, b)
     _same(a, b)
