@@ -815,14 +815,33 @@ struct BrickSmem {
 // are added as h0 + h1 in both.  Returns the row's four cells per component;
 // on return the first chunk's pairs are staged (all of them when cnt <=
 // SP_CHUNK).
+// Packed FP32x2 multiply and fma (each half rounds as the scalar operation).
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "mul.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n\t.reg .b64 a, b, c, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+      "mov.b64 c, {%6, %7};\n\tfma.rn.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+
 __device__ __forceinline__ void brick_gather(BrickSmem &sm, const PairMap &pm, int p0, int cnt,
                                              const float4 *__restrict__ vals, float4 out[3],
                                              bool scale_by_w = false) {
   const int t = threadIdx.x & 31;
   const int grp = t >> 4, tg = t & 15, yl = tg & 3, zl = tg >> 2;
-  float acc[4][3];
+  // cells 0, 1 and 2, 3 of the row per component, as packed pairs
+  float2 A01[3], A23[3];
 #pragma unroll
-  for (int a = 0; a < 4; a++) acc[a][0] = acc[a][1] = acc[a][2] = 0.f;
+  for (int c = 0; c < 3; c++) A01[c] = A23[c] = make_float2(0.f, 0.f);
   for (int c0 = 0; c0 < cnt; c0 += SP_CHUNK) {
     __syncwarp();
     for (int q = t; q < SP_CHUNK; q += 32) {
@@ -853,14 +872,26 @@ __device__ __forceinline__ void brick_gather(BrickSmem &sm, const PairMap &pm, i
       const float wyz = sm.swy[j][yl] * sm.swz[j][zl];
       const float4 wx = sm.swx[j];
       const float4 v = sm.sv[j];
-      const float w0 = wx.x * wyz, w1 = wx.y * wyz, w2 = wx.z * wyz, w3 = wx.w * wyz;
-      acc[0][0] += w0 * v.x; acc[0][1] += w0 * v.y; acc[0][2] += w0 * v.z;
-      acc[1][0] += w1 * v.x; acc[1][1] += w1 * v.y; acc[1][2] += w1 * v.z;
-      acc[2][0] += w2 * v.x; acc[2][1] += w2 * v.y; acc[2][2] += w2 * v.z;
-      acc[3][0] += w3 * v.x; acc[3][1] += w3 * v.y; acc[3][2] += w3 * v.z;
+      const float2 yz = make_float2(wyz, wyz);
+      const float2 w01 = mul2(make_float2(wx.x, wx.y), yz), w23 = mul2(make_float2(wx.z, wx.w), yz);
+      const float vc[3] = {v.x, v.y, v.z};
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const float2 vv = make_float2(vc[c], vc[c]);
+        A01[c] = fma2(w01, vv, A01[c]);
+        A23[c] = fma2(w23, vv, A23[c]);
+      }
     }
   }
   __syncwarp();
+  float acc[4][3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[0][c] = A01[c].x;
+    acc[1][c] = A01[c].y;
+    acc[2][c] = A23[c].x;
+    acc[3][c] = A23[c].y;
+  }
 #pragma unroll
   for (int a = 0; a < 4; a++)
 #pragma unroll
