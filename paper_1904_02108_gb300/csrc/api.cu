@@ -132,6 +132,11 @@ struct lbm {
   // ev_ahead_go marks the end of the last step's fixed point, so that moved
   // points given by ibm_update_points can have the next step prepared at once
   bool loop_mark = false;
+  // the end-of-step sums of a step followed by another in the same call run
+  // on ahead_st after its collide (ev_collided), joined before the next
+  // collide (ev_finished), which rewrites the partials they read
+  cudaEvent_t ev_collided = nullptr, ev_finished = nullptr;
+  bool finish_pending = false;
   int64_t *t_dev = nullptr;
   bool desc_dirty = true;
   uint64_t version = 1;  // changes whenever a pointer in the descriptor does
@@ -439,6 +444,8 @@ void lbm_destroy(lbm_t *h) {
   if (h->ahead_st) cudaStreamDestroy(h->ahead_st);
   if (h->ev_ahead_go) cudaEventDestroy(h->ev_ahead_go);
   if (h->ev_ahead_done) cudaEventDestroy(h->ev_ahead_done);
+  if (h->ev_collided) cudaEventDestroy(h->ev_collided);
+  if (h->ev_finished) cudaEventDestroy(h->ev_finished);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -857,6 +864,7 @@ struct StepCtx {
   bool ahead;       // build the next step's after this step's fixed point
   bool mark_loop;   // else record ev_ahead_go there (see lbm_t::loop_mark)
   const DomainDesc *D_next;  // the prepared step's descriptors (NULL: desc_alt)
+  bool defer_finish;         // the end-of-step sums on ahead_st (lbm_t::finish_pending)
   long long t_next; // the next step's index (its kinematics)
 };
 
@@ -997,6 +1005,8 @@ static int ensure_ahead(lbm_t *h) {
   if (!h->ev_ahead_go) CK(h, cudaEventCreateWithFlags(&h->ev_ahead_go, cudaEventDisableTiming));
   if (!h->ev_ahead_done)
     CK(h, cudaEventCreateWithFlags(&h->ev_ahead_done, cudaEventDisableTiming));
+  if (!h->ev_collided) CK(h, cudaEventCreateWithFlags(&h->ev_collided, cudaEventDisableTiming));
+  if (!h->ev_finished) CK(h, cudaEventCreateWithFlags(&h->ev_finished, cudaEventDisableTiming));
   return LBM_OK;
 }
 
@@ -1050,8 +1060,23 @@ static int enqueue_suffix(StepCtx &c) {
     CK(h, cudaEventRecord(c.ev_join, c.sti));
     CK(h, cudaStreamWaitEvent(c.st, c.ev_join, 0));
   } else {
+    if (h->finish_pending && !c.D_next) {
+      // the previous step's sums (on ahead_st) have read its partials
+      CK(h, cudaStreamWaitEvent(c.st, h->ev_finished, 0));
+      h->finish_pending = false;
+    }
     StageTimer T(h, ST_COLLIDE, c.st);
     CK(h, launch_collide_stream(c.storage, c.D, c.Dhost, c.dims, c.cur, c.stats, 0, c.st));
+  }
+  if (c.defer_finish) {
+    // (the next step of the call waits for these sums before its collide)
+    CK(h, cudaEventRecord(h->ev_collided, c.st));
+    CK(h, cudaStreamWaitEvent(h->ahead_st, h->ev_collided, 0));
+    StageTimer T(h, ST_STATS, h->ahead_st);
+    CK(h, launch_finish_step(c.D, c.dims, c.stats, c.split, h->ahead_st));
+    CK(h, cudaEventRecord(h->ev_finished, h->ahead_st));
+    h->finish_pending = true;
+    return LBM_OK;
   }
   {
     StageTimer T(h, ST_STATS, c.st);
@@ -1260,6 +1285,10 @@ static int take_ahead(lbm_t *h, bool *taken) {
 // map; its write-through of mapped uploads into the device copies stands.
 static int discard_ahead(lbm_t *h) {
   h->loop_mark = false;
+  if (h->finish_pending) {
+    h->finish_pending = false;
+    CK(h, cudaStreamWaitEvent(h->st, h->ev_finished, 0));
+  }
   if (!h->pairs_ahead) return LBM_OK;
   h->pairs_ahead = false;
   CK(h, cudaStreamWaitEvent(h->st, h->ev_ahead_done, 0));
@@ -1277,6 +1306,8 @@ static int step_once(lbm_t *h, int n_iter, bool ahead = false) {
   c.pairs_done = pre;
   const bool can = h->np > 0 && !h->overlap && !h->timing;
   c.ahead = ahead && can;
+  // (the box pre-computation reads the step counter the sums advance)
+  c.defer_finish = c.ahead && h->u0_mode != LBM_U0_BOX;
   // a one-step call in mapped transfer mode marks its fixed point's end, for
   // the next upload of moved points (ibm_update_points) to start the next step
   c.mark_loop = !c.ahead && can && h->host_io == LBM_HOST_IO_MAPPED && !h->graph_on;
