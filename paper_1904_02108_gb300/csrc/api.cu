@@ -1402,6 +1402,7 @@ static int capture_two_steps(StepCtx c, int n_iter, cudaStream_t cs, cudaGraphEx
     a.ahead = true;
     a.D_next = c.D;
     a.t_next = -2;
+    a.defer_finish = h->u0_mode != LBM_U0_BOX;  // (joined before the second collide)
     r = enqueue_step(a, n_iter);
     if (r == LBM_OK && cudaStreamWaitEvent(cs, h->ev_ahead_done, 0) != cudaSuccess)
       r = fail(h, LBM_ECUDA, "stream capture: joining the prepared step");
