@@ -487,6 +487,7 @@ int lbm_create_ex(const lbm_opts *o, lbm_t **out) {
   h->g.nbz = o->nz / 4;
   h->g.ncell = ncell;
   h->g.nbrick = h->g.nbx * h->g.nby * h->g.nbz;
+  geometry_divisors(h->g);
   h->tau = o->tau;
   h->storage = o->storage;
   h->delta = o->delta;
@@ -2608,6 +2609,7 @@ bool spread_geometry(int nx, int ny, int nz, Geometry &g) {
   g.nbz = nz / 4;
   g.ncell = (int64_t)nx * ny * nz;
   g.nbrick = g.nbx * g.nby * g.nbz;
+  geometry_divisors(g);
   return g.ncell < (1LL << 31);
 }
 

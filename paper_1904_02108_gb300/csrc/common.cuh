@@ -160,7 +160,38 @@ struct Geometry {
   int nbx, nby, nbz;  // bricks
   int64_t ncell;      // nx*ny*nz
   int nbrick;         // nbx*nby*nbz
+  // n / nx and r / ny as a multiply-high and shifts (unsigned division by an
+  // invariant integer, Granlund and Montgomery 1994, Sec. 4): the multipliers
+  // and the shift pairs (sh1 | sh2 << 8); mx == 0 means "not set, divide"
+  uint32_t mx, my;
+  int shx, shy;
 };
+
+// m' = floor(2^32 (2^l - d) / d) + 1 with l = ceil(log2 d), sh1 = min(l, 1),
+// sh2 = l - sh1; then n / d = (t + ((n - t) >> sh1)) >> sh2 with
+// t = (m' n) >> 32, exact for every 32-bit n (d in [1, 2^31]).
+inline void divisor_magic(uint32_t d, uint32_t &m, int &sh) {
+  int l = 0;
+  while ((1ull << l) < d) l++;
+  m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  const int s1 = l > 0 ? 1 : 0;
+  sh = s1 | ((l - s1) << 8);
+}
+
+__host__ __device__ __forceinline__ uint32_t div_magic(uint32_t n, uint32_t m, int sh) {
+#ifdef __CUDA_ARCH__
+  const uint32_t t = __umulhi(n, m);
+#else
+  const uint32_t t = (uint32_t)(((uint64_t)n * m) >> 32);
+#endif
+  return (t + ((n - t) >> (sh & 0xff))) >> (sh >> 8);
+}
+
+// Fills the division constants of g from nx and ny.
+inline void geometry_divisors(Geometry &g) {
+  divisor_magic((uint32_t)g.nx, g.mx, g.shx);
+  divisor_magic((uint32_t)g.ny, g.my, g.shy);
+}
 
 __host__ __device__ __forceinline__ int brick_local(int x, int y, int z) {
   return ((z & 3) * 4 + (y & 3)) * 4 + (x & 3);

@@ -8,7 +8,8 @@
 namespace lbmibm {
 
 // (x, y, z) of the cell with linear index n = (z ny + y) nx + x; shifts and
-// masks when nx and ny are powers of two (the same for every thread).
+// masks when nx and ny are powers of two (the same for every thread), else
+// the multiply-high division when the geometry carries its constants.
 __device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &x, int &y,
                                             int &z) {
   const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
@@ -17,6 +18,13 @@ __device__ __forceinline__ void cell_coords(uint32_t n, const Geometry &g, int &
     x = (int)(n & (nx - 1));
     y = (int)(r & (ny - 1));
     z = (int)(r >> (__ffs((int)ny) - 1));
+    return;
+  }
+  if (g.mx) {
+    const uint32_t r = div_magic(n, g.mx, g.shx);
+    x = (int)(n - r * nx);
+    z = (int)div_magic(r, g.my, g.shy);
+    y = (int)(r - (uint32_t)z * ny);
     return;
   }
   const uint32_t r = n / nx;

@@ -40,8 +40,6 @@ __device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ float vrcp(float a) { return __fdiv_rn(1.f, a); }
-__device__ __forceinline__ float vneg(float a) { return -a; }
-__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
 // The packed operations in PTX with an explicit rounding mode: the code
 // generator neither fuses nor reorders them (the packed intrinsics were
 // fused, a multiply and a following add becoming one fma, which rounds
@@ -110,7 +108,6 @@ __device__ __forceinline__ void collide_core(const V d[Q], V Gx, V Gy, V Gz, flo
   st[1] = vfma(rho, Gx, jx);
   st[2] = vfma(rho, Gy, jy);
   st[3] = vfma(rho, Gz, jz);
-  const V vom = vsplat<V>(om);
   // Eq. 3 minus t_i: t_i (c0 + rho (3 e.u + 4.5 (e.u)^2)) with c0 the part
   // common to every direction; opposite directions share 4.5 rho (e.u)^2.
   // Every product that meets an addition is one fma (no separate multiply
@@ -119,8 +116,13 @@ __device__ __forceinline__ void collide_core(const V d[Q], V Gx, V Gy, V Gz, flo
   const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
   const V c0 = vfma(vmul(vsplat<V>(-1.5f), rho), usq, drho);
   const V r3 = vmul(vsplat<V>(3.f), rho), r45 = vmul(vsplat<V>(4.5f), rho);
-  const V nr3 = vneg(r3);
-  dn[0] = vfma(vom, vfma(vsplat<V>(wt(0)), c0, vneg(d[0])), d[0]);
+  const V nr3 = vmul(vsplat<V>(-3.f), rho);
+  // d + om (t_i E - d) as d - om (d - t_i E): negating both factors of the
+  // outer product and the inner fma's result leaves every rounding as it was
+  // (round-to-nearest is odd), and the packed form then needs no negated
+  // copy of d
+  const V nom = vsplat<V>(-om);
+  dn[0] = vfma(nom, vfma(vsplat<V>(-wt(0)), c0, d[0]), d[0]);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     // e_i . u with the components of e_i in {-1, 0, 1}
@@ -137,9 +139,9 @@ __device__ __forceinline__ void collide_core(const V d[Q], V Gx, V Gy, V Gz, flo
     }
     const V sym = vfma(r45, vmul(eu, eu), c0);
     const V ep = vfma(r3, eu, sym), em = vfma(nr3, eu, sym);  // E/t_i for e_i and -e_i
-    const V w = vsplat<V>(wt(i));
-    dn[i] = vfma(vom, vfma(w, ep, vneg(d[i])), d[i]);
-    dn[i + 1] = vfma(vom, vfma(w, em, vneg(d[i + 1])), d[i + 1]);
+    const V nw = vsplat<V>(-wt(i));
+    dn[i] = vfma(nom, vfma(nw, ep, d[i]), d[i]);
+    dn[i + 1] = vfma(nom, vfma(nw, em, d[i + 1]), d[i + 1]);
   }
 }
 
