@@ -327,10 +327,13 @@ typedef struct {
                         128, 256 or 512                                    */
   int moments_spb;   /* bricks per block of the moments kernel: 1, 2 or 4   */
   int sort_blocks;   /* blocks of the pair sort (a warp per brick), >= 1   */
-  int collide_staged; /* 16-bit storage, single lattice: 1 brings the pulled
-                         rows into shared memory with bulk asynchronous
-                         copies (rows of 8k cells, 16-byte aligned; other
-                         sizes fall back), 0 pulls them with loads         */
+  int collide_staged; /* 16-bit storage: 0 pulls two x-neighbouring cells
+                         per thread with 4-byte loads; 1 (single lattice)
+                         brings the pulled rows into shared memory with
+                         bulk asynchronous copies (rows of 8k cells,
+                         16-byte aligned; other sizes fall back to 0); 2
+                         takes four cells per thread (8-byte loads and
+                         stores, blocks of 128 whatever collide_block)     */
   int sort_blocks_ahead; /* blocks of the pair sort of a step prepared while
                             the step before it collides (lbm_step), >= 1  */
 } lbm_launch_shape;

@@ -1880,7 +1880,7 @@ bool shape_ok(const lbm_launch_shape &s) {
          s.sort_blocks <= (1 << 20) && s.sort_blocks_ahead >= 1 &&
          s.sort_blocks_ahead <= (1 << 20) &&
          (s.moments_spb == 1 || s.moments_spb == 2 || s.moments_spb == 4) &&
-         (s.collide_staged == 0 || s.collide_staged == 1);
+         (s.collide_staged >= 0 && s.collide_staged <= 2);
 }
 
 lbm_launch_shape to_c(const LaunchShape &l) {
@@ -1975,7 +1975,7 @@ struct TuneParam {
 std::vector<TuneParam> tune_params(bool points, bool staged) {
   std::vector<TuneParam> ps;
   ps.push_back({&LaunchShape::collide_block, {128, 256}, 1 << ST_COLLIDE});
-  if (staged) ps.push_back({&LaunchShape::collide_staged, {0, 1}, 1 << ST_COLLIDE});
+  if (staged) ps.push_back({&LaunchShape::collide_staged, {0, 1, 2}, 1 << ST_COLLIDE});
   if (points) {
     ps.push_back({&LaunchShape::brick_blocks,
                   {152 * 16, 152 * 32, 152 * 64, 152 * 128},
@@ -2154,7 +2154,7 @@ int lbm_batch_autotune(lbm_batch_t *b, int n_ibm_iter, int steps_per_trial,
   bool timing = false;
   if (r == LBM_OK)
     r = coordinate_search(
-        shape, points, false, steps_per_trial,
+        shape, points, h0->storage != LBM_STORE_F32, steps_per_trial,
         [&](const LaunchShape &l) {
           lbm_launch_shape c = to_c(l);
           return lbm_batch_set_launch_shape(b, &c);

@@ -431,6 +431,148 @@ __global__ void __launch_bounds__(256, 4)
   collide_pairs16<S, STATS>(D[blockIdx.y], cur);
 }
 
+// 16-bit storage: four x-neighbouring cells (x0 a multiple of 4, so one
+// brick) per thread, as two packed pairs A = (x0, x0 + 1) and
+// B = (x0 + 2, x0 + 3).  A direction's pulls are the two words at x0 / 2 of
+// its source row (one 8-byte load) and, for e_x = +1 / -1, the word before /
+// after them; byte permutes assemble each pair's word of two deviations,
+// which the pair reads as collide_pairs16 reads its words, and the two
+// pairs' results leave as one 8-byte store per direction.  A warp covers the
+// 128 cells of one FP64 partial and sums them in collide_pairs16's FP32 tree
+// (pair q meets q ^ 16, q ^ 8, ..., q ^ 1; pairs 2L and 2L + 1 sit in lane L,
+// so the lane exchanges are 8, 4, 2, 1 and the last level is within the
+// lane): populations and sums are bitwise those of the two-cell kernel.
+__device__ __forceinline__ uint2 ldw2_stream(const uint32_t *p) {
+  uint2 v;
+  asm("ld.global.nc.L2::256B.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
+template <typename S>
+__device__ __forceinline__ void pair_words(const uint32_t w[Q], const float Ga[3],
+                                           const float Gb[3], float tau, float om,
+                                           uint32_t r[Q], float sv[4]) {
+  float da[Q], db[Q], dna[Q], dnb[Q], sta[4], stb[4];
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    da[i] = Word16<S>::lo(w[i]);
+    db[i] = Word16<S>::hi(w[i]);
+  }
+  collide_math2(da, db, Ga, Gb, tau, om, dna, dnb, sta, stb);
+#pragma unroll
+  for (int i = 0; i < Q; i++) r[i] = Word16<S>::pack(dna[i], dnb[i]);
+#pragma unroll
+  for (int c = 0; c < 4; c++) sv[c] = sta[c] + stb[c];
+}
+
+template <typename S, bool STATS>
+__device__ __forceinline__ void collide_quads16(const DomainDesc &dd, int cur) {
+  const Geometry g = dd.g;
+  if ((int64_t)blockIdx.x * blockDim.x * 4 >= g.ncell) return;
+  const uint32_t *__restrict__ src = (const uint32_t *)dd.f[cur];
+  uint32_t *__restrict__ dst = (uint32_t *)dd.f[cur ^ 1];
+  const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
+  float vA[4] = {0.f, 0.f, 0.f, 0.f}, vB[4] = {0.f, 0.f, 0.f, 0.f};
+  const uint32_t n = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (n < (uint32_t)g.ncell) {
+    int x, y, z;
+    cell_coords(n, g, x, y, z);
+    float G[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) G[k][c] = dd.gbody[c];
+    if (brick_slot) {
+      const int b = ((z >> 2) * g.nby + (y >> 2)) * g.nbx + (x >> 2);
+      const int sl = __ldg(brick_slot + b);
+      if (sl >= 0) {
+        const float *p = dd.Gs + (size_t)sl * SLOT_FLOATS + brick_local(x, y, z);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) G[k][c] += __ldg(p + c * BRICK_CELLS + k);
+      }
+    }
+    // word offsets of the rows y - e_y, z - e_z and of x0 - 2, x0, x0 + 4
+    const uint32_t ny = g.ny, hw = (uint32_t)g.nx >> 1;
+    const uint32_t ym = y == 0 ? ny - 1 : y - 1, yp = y == (int)ny - 1 ? 0 : y + 1;
+    const uint32_t zm = z == 0 ? g.nz - 1 : z - 1, zp = z == g.nz - 1 ? 0 : z + 1;
+    const uint32_t Y[3] = {yp, (uint32_t)y, ym}, Z[3] = {zp, (uint32_t)z, zm};
+    const uint32_t w0 = (uint32_t)x >> 1;
+    const uint32_t wl = w0 == 0 ? hw - 1 : w0 - 1, wr = w0 + 2 == hw ? 0 : w0 + 2;
+    const size_t NW = (size_t)g.ncell >> 1;
+    uint32_t wa[Q], wb[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const uint32_t row = (Z[ez(i) + 1] * ny + Y[ey(i) + 1]) * hw;
+      const uint32_t *fi = src + (size_t)i * NW + row;
+      const uint2 m = ldw2_stream(fi + w0);
+      if (ex(i) == 0) {
+        wa[i] = m.x;
+        wb[i] = m.y;
+      } else if (ex(i) > 0) {
+        // cells x0 - 1 .. x0 + 2: the high half of each word, then the low
+        // half of the next
+        wa[i] = __byte_perm(ldw_stream(fi + wl), m.x, 0x5432);
+        wb[i] = __byte_perm(m.x, m.y, 0x5432);
+      } else {
+        // cells x0 + 1 .. x0 + 4
+        wa[i] = __byte_perm(m.x, m.y, 0x5432);
+        wb[i] = __byte_perm(m.y, ldw_stream(fi + wr), 0x5432);
+      }
+    }
+    const uint32_t wn = n >> 1;
+    uint32_t ra[Q], rb[Q];
+    pair_words<S>(wa, G[0], G[1], dd.tau, dd.om, ra, vA);
+    pair_words<S>(wb, G[2], G[3], dd.tau, dd.om, rb, vB);
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+      *reinterpret_cast<uint2 *>(dst + (size_t)i * NW + wn) = make_uint2(ra[i], rb[i]);
+  }
+  if (STATS) {
+    const int lane = threadIdx.x & 31;
+    const bool h8 = lane & 8, h4 = lane & 4;
+    // pair q ^ 16 (lane ^ 8): the half-warps' lanes with bit 3 keep
+    // components 2, 3
+    const float bA0 = (h8 ? vA[2] : vA[0]) + __shfl_xor_sync(0xffffffffu, h8 ? vA[0] : vA[2], 8);
+    const float bA1 = (h8 ? vA[3] : vA[1]) + __shfl_xor_sync(0xffffffffu, h8 ? vA[1] : vA[3], 8);
+    const float bB0 = (h8 ? vB[2] : vB[0]) + __shfl_xor_sync(0xffffffffu, h8 ? vB[0] : vB[2], 8);
+    const float bB1 = (h8 ? vB[3] : vB[1]) + __shfl_xor_sync(0xffffffffu, h8 ? vB[1] : vB[3], 8);
+    // q ^ 8 (lane ^ 4): lanes with bit 2 keep the second of the two
+    float cA = (h4 ? bA1 : bA0) + __shfl_xor_sync(0xffffffffu, h4 ? bA0 : bA1, 4);
+    float cB = (h4 ? bB1 : bB0) + __shfl_xor_sync(0xffffffffu, h4 ? bB0 : bB1, 4);
+    // q ^ 4, q ^ 2 (lane ^ 2, lane ^ 1), then q ^ 1 within the lane
+    cA += __shfl_xor_sync(0xffffffffu, cA, 2);
+    cB += __shfl_xor_sync(0xffffffffu, cB, 2);
+    cA += __shfl_xor_sync(0xffffffffu, cA, 1);
+    cB += __shfl_xor_sync(0xffffffffu, cB, 1);
+    const float c = cA + cB;
+    // lanes 0, 4, 8, 12 hold components 0..3 of the first 64 cells, lanes
+    // 16.. the same of the next 64; the partial is their FP64 sum
+    const float o = __shfl_down_sync(0xffffffffu, c, 16);
+    const int64_t pidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (lane < 16 && (lane & 3) == 0 && pidx < dd.cblocks)
+      dd.partial[(size_t)pidx * 4 + (lane >> 2)] = (double)c + (double)o;
+  }
+}
+
+// (128 registers, four blocks of 128 per SM: the two pairs' words and the
+// first pair's results stay in registers; bounded to 96 or 80 registers the
+// spills cost more than the extra warps bring)
+template <typename S, bool STATS>
+__global__ void __launch_bounds__(128, 4)
+    collide_quads16_kernel(const __grid_constant__ DomainDesc dd, int cur) {
+  pdl_wait();
+  collide_quads16<S, STATS>(dd, cur);
+}
+
+template <typename S, bool STATS>
+__global__ void __launch_bounds__(128, 4)
+    collide_quads16_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
+  pdl_wait();
+  collide_quads16<S, STATS>(D[blockIdx.y], cur);
+}
+
 // 16-bit storage, single lattice: the pulls staged in shared memory by the
 // bulk-copy engine.  A tile is R consecutive rows (y) of one z plane, whole
 // rows in x; for each population the R source rows (the tile's rows shifted by
@@ -950,9 +1092,19 @@ cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const Ba
     // a single lattice whose rows tile, with the staged kernel chosen (the
     // autotuner picks it where it is faster): pulls staged by bulk copies
     RowsTiling tl{};
-    if (dims.ls.collide_staged && dims.nd == 1 && Dhost && rows_tiling(Dhost->g, tl))
+    if (dims.ls.collide_staged == 1 && dims.nd == 1 && Dhost && rows_tiling(Dhost->g, tl))
       return stats ? launch_rows16<S, true>(*Dhost, cur, tl, st)
                    : launch_rows16<S, false>(*Dhost, cur, tl, st);
+    // four cells per thread (nx is a multiple of 4), blocks of 128
+    if (dims.ls.collide_staged == 2) {
+      const dim3 grid4((unsigned)((dims.max_cells + 511) / 512), dims.nd), block4(128);
+#define LBM_QUADS(ST)                                                                     \
+  (dims.nd == 1 && Dhost                                                                  \
+       ? launch_pdl(collide_quads16_kernel<S, ST>, grid4, block4, 0, st, *Dhost, cur)     \
+       : launch_pdl(collide_quads16_batch_kernel<S, ST>, grid4, block4, 0, st, D, cur))
+      return stats ? LBM_QUADS(true) : LBM_QUADS(false);
+#undef LBM_QUADS
+    }
     // two cells per thread (nx is a multiple of 4)
     const dim3 grid2((unsigned)((dims.max_cells + 2 * bs - 1) / (2 * bs)), dims.nd);
 #define LBM_PAIRS(ST)                                                                     \

@@ -72,7 +72,7 @@ def test_autotune_leaves_the_lattice_unchanged(gpu_lib, torch_cuda):
 def test_launch_shape_rejects_values_out_of_range(gpu_lib, torch_cuda):
     lat = _pair_lattice(gpu_lib, torch_cuda)
     for bad in (dict(collide_block=512), dict(point_block=1024), dict(moments_spb=8),
-                dict(brick_blocks=0), dict(sort_blocks=-1), dict(collide_staged=2),
+                dict(brick_blocks=0), dict(sort_blocks=-1), dict(collide_staged=3),
                 dict(sort_blocks_ahead=0)):
         with pytest.raises(gpu_lib.LbmError):
             lat.set_launch_shape(**bad)

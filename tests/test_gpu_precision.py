@@ -111,15 +111,17 @@ def test_roundtrip_rounds_deviations_to_nearest(gpu_lib, orc, storage, u):
     lat.close()
 
 
+@pytest.mark.parametrize("staged", [1, 2])
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 @pytest.mark.parametrize("case", ["single_propeller_32", "propeller_array_64", "box_48x64x80"])
-def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, case):
-    """A single lattice with 16-bit storage and the staged collide chosen
-    (rows of the pulls brought into shared memory by bulk copies) against a
-    batch, which keeps the two-cell kernel; both use the same per-cell
-    arithmetic and the same partial sums, so populations and FP64 sums must
-    agree bitwise.  The shapes cover tiles of 16, 8 and 8 rows, the y and z
-    seams and a lattice whose rows are not a power of two."""
+def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, case, staged):
+    """A single lattice with 16-bit storage and the staged collide (1: rows of
+    the pulls brought into shared memory by bulk copies) or the four-cell
+    collide (2: two packed pairs per thread, 8-byte pulls and stores) chosen,
+    against a batch, which keeps the two-cell kernel; all use the same
+    per-cell arithmetic and the same partial sums, so populations and FP64
+    sums must agree bitwise.  The shapes cover tiles of 16, 8 and 8 rows, the
+    y and z seams and a lattice whose rows are not a power of two."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -135,7 +137,7 @@ def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, ca
                              [0.4, 2.2])
     st = torch.cuda.current_stream()
     a = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
-    a.set_launch_shape(collide_staged=1)
+    a.set_launch_shape(collide_staged=staged)
     b = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
     rng = W.SplitMix64(22)
     f0 = orc.init_equilibrium(shape, 1 + 0.01 * W.random_array(rng, shape),
@@ -153,3 +155,43 @@ def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, ca
     batch.close()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_four_cell_batch_is_bitwise_single_two_cell_lattices(gpu_lib, orc, storage):
+    """A batch of two uneven lattices (one whose cell count leaves the last
+    128-cell partial half full) stepped by the four-cell collide against the
+    same lattices stepped alone by the two-cell kernel: bitwise populations
+    and FP64 sums."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    st = torch.cuda.current_stream()
+    w = W.dense_array_64()
+    specs = [((64, 64, 64), w.props), ((36, 20, 12), None)]
+    rng = W.SplitMix64(23)
+    singles, members = [], []
+    for shape, props in specs:
+        f0 = orc.init_equilibrium(shape, 1 + 0.01 * W.random_array(rng, shape),
+                                  0.02 * W.random_array(rng, (3,) + shape))
+        for group in (singles, members):
+            lat = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
+            if props is not None:
+                lat.set_propellers(props)
+            else:
+                lat.set_body_force((1e-5, -2e-5, 3e-5))
+            lat.set_populations(f0)
+            group.append(lat)
+    batch = gpu_lib.Batch(members)
+    batch.set_launch_shape(collide_staged=2)
+    for _ in range(3):
+        for lat in singles:
+            lat.step(1, 5)
+        batch.step(1, 5)
+    for a, b in zip(singles, members):
+        assert np.array_equal(a.deviations(), b.deviations())
+        sa, sb = a.stats(), b.stats()
+        assert sa["mass"] == sb["mass"] and sa["momentum"] == sb["momentum"]
+    batch.close()
+    for lat in singles + members:
+        lat.close()
