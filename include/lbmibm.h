@@ -338,7 +338,7 @@ typedef struct {
                             the step before it collides (lbm_step), >= 1  */
 } lbm_launch_shape;
 
-/* The handle's launch shape (defaults: 256, 9728, 256, 4, 4864, 0, 608).  Set
+/* The handle's launch shape (defaults: 256, 9728, 256, 4, 4864, 2, 608).  Set
  * returns LBM_EINVAL for a value outside the ranges above. */
 int lbm_get_launch_shape(lbm_t *h, lbm_launch_shape *out);
 int lbm_set_launch_shape(lbm_t *h, const lbm_launch_shape *s);

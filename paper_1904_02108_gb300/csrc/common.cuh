@@ -360,9 +360,10 @@ struct LaunchShape {
                                  // (64 threads each): 1, 2 or 4
   int sort_blocks = 152 * 32;    // grid of the sort kernel (a warp per slot,
                                  // four per block)
-  int collide_staged = 0;        // 16-bit storage, single lattice: the pulls
-                                 // staged in shared memory by bulk copies (1)
-                                 // or loaded by the threads (0)
+  int collide_staged = 2;        // 16-bit storage: four cells per thread (2),
+                                 // two cells per thread (0), or (single
+                                 // lattice) the pulls staged in shared memory
+                                 // by bulk copies (1)
   int sort_blocks_ahead = 152 * 4;  // grid of the sort of a step prepared
                                     // ahead (it runs beside the previous
                                     // step's collide: few blocks)

@@ -556,18 +556,18 @@ __device__ __forceinline__ void collide_quads16(const DomainDesc &dd, int cur) {
   }
 }
 
-// (128 registers, four blocks of 128 per SM: the two pairs' words and the
-// first pair's results stay in registers; bounded to 96 or 80 registers the
-// spills cost more than the extra warps bring)
+// (at most 96 registers, five blocks of 128 per SM: 0.905 of the copy
+// bandwidth at 384^3 against 0.851 at 128 registers (four blocks) and 0.744
+// at 80 (six blocks, where the spills dominate))
 template <typename S, bool STATS>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 5)
     collide_quads16_kernel(const __grid_constant__ DomainDesc dd, int cur) {
   pdl_wait();
   collide_quads16<S, STATS>(dd, cur);
 }
 
 template <typename S, bool STATS>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 5)
     collide_quads16_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
   pdl_wait();
   collide_quads16<S, STATS>(D[blockIdx.y], cur);

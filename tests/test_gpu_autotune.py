@@ -60,7 +60,7 @@ def test_autotune_leaves_the_lattice_unchanged(gpu_lib, torch_cuda):
     assert a.launch_shape() == chosen
     assert chosen["collide_block"] in (128, 256)
     assert chosen["moments_spb"] in (1, 2, 4)
-    assert chosen["collide_staged"] == 0  # (FP32 storage: not a candidate)
+    assert chosen["collide_staged"] == 2  # (FP32 storage: not a candidate, the default kept)
     assert a.stats()["step"] == 3
     a.step(4, 5)
     b.step(4, 5)

@@ -146,6 +146,7 @@ def test_staged_collide_is_bitwise_the_two_cell_kernel(gpu_lib, orc, storage, ca
         lat.set_propellers(props)
         lat.set_populations(f0)
     batch = gpu_lib.Batch([b])
+    batch.set_launch_shape(collide_staged=0)
     for _ in range(3):
         a.step(1, 5)
         batch.step(1, 5)
@@ -176,6 +177,7 @@ def test_four_cell_batch_is_bitwise_single_two_cell_lattices(gpu_lib, orc, stora
                                   0.02 * W.random_array(rng, (3,) + shape))
         for group in (singles, members):
             lat = gpu_lib.Lattice(shape, 0.7, storage=storage, warm="previous", stream=st)
+            lat.set_launch_shape(collide_staged=0)
             if props is not None:
                 lat.set_propellers(props)
             else:
