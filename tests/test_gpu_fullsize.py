@@ -1,7 +1,8 @@
 """Parity at the benchmark's full size and launch configuration: the 256^3
 array of 64 propellers (89,600 points, 5 iterations per step) against the
 FP64 oracle on the whole lattice: two steps from rest, ten steps from the
-previous step's force, and the paper's loop iterated to a residual target."""
+previous step's force, and the paper's loop iterated to a residual target;
+and the 16-bit form at 384^3 against the kernel the oracle tests pin."""
 import numpy as np
 import pytest
 
@@ -160,3 +161,31 @@ def test_dense_array_256_steps_prepared_ahead_are_single_steps(gpu_lib):
     same()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_dense_array_384_16bit_four_cell_collide_is_two_cell(gpu_lib, storage):
+    """The 16-bit form at its benchmark size and launch shape (384^3, 216
+    propellers, 302,400 points; the four-cell collide, 96 registers, blocks of
+    128) against the two-cell collide that the smaller parity tests pin to the
+    oracle: three coupled steps from rest under a body force, bitwise
+    populations, point values and FP64 sums."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = W.dense_array_384()
+    st = torch.cuda.current_stream()
+    out = []
+    for staged in (2, 0):
+        lat = gpu_lib.Lattice(w.shape, w.tau, storage=storage, warm="previous", stream=st)
+        lat.set_launch_shape(collide_staged=staged, collide_block=128)
+        lat.set_propellers(w.props)
+        lat.set_body_force((2e-6, -1e-6, 3e-6))
+        lat.step(3, w.n_iter)
+        s = lat.stats()
+        out.append((lat.deviations(), lat.points()[2], s["mass"], tuple(s["momentum"])))
+        lat.close()
+    (fa, da, ma, ja), (fb, db, mb, jb) = out
+    assert np.array_equal(fa, fb)
+    assert np.array_equal(da, db)
+    assert ma == mb and ja == jb
