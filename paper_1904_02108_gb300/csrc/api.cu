@@ -1597,6 +1597,11 @@ struct lbm_batch {
   LaunchShape shape;
   uint64_t shape_version = 0;  // changes with the shape (a new capture)
   int *work_off = nullptr;     // [(ORDER_BUCKETS + 1) n + 2] the step's work list
+  // the collide's block tables (128, 256, 512 cells per block, one
+  // allocation): (domain, block within the domain) for every block of cells
+  // a domain has, so that no block of the grid falls past its domain
+  int2 *cblk = nullptr;
+  int cblk_off[3] = {0, 0, 0}, ncblk[3] = {0, 0, 0};
   std::string err;
 };
 
@@ -1617,13 +1622,27 @@ int lbm_batch_create(int n, lbm_t *const *handles, lbm_batch_t **out) {
   lbm_batch_t *b = new lbm_batch();
   b->hs.assign(handles, handles + n);
   b->shape = handles[0]->shape;
+  std::vector<int2> tab;
+  for (int l = 0; l < 3; l++) {
+    const int64_t cpb = 128 << l;
+    b->cblk_off[l] = (int)tab.size();
+    for (int d = 0; d < n; d++) {
+      const int64_t nb = (handles[d]->g.ncell + cpb - 1) / cpb;
+      for (int64_t k = 0; k < nb; k++) tab.push_back(make_int2(d, (int)k));
+    }
+    b->ncblk[l] = (int)tab.size() - b->cblk_off[l];
+  }
   if (cudaMalloc(&b->D, sizeof(DomainDesc) * n) != cudaSuccess ||
       cudaMalloc(&b->D_alt, sizeof(DomainDesc) * n) != cudaSuccess ||
       cudaMalloc(&b->work_off, sizeof(int) * ((size_t)(ORDER_BUCKETS + 1) * n + 2)) !=
+          cudaSuccess ||
+      cudaMalloc(&b->cblk, sizeof(int2) * tab.size()) != cudaSuccess ||
+      cudaMemcpy(b->cblk, tab.data(), sizeof(int2) * tab.size(), cudaMemcpyHostToDevice) !=
           cudaSuccess) {
     if (b->D) cudaFree(b->D);
     if (b->D_alt) cudaFree(b->D_alt);
     if (b->work_off) cudaFree(b->work_off);
+    if (b->cblk) cudaFree(b->cblk);
     delete b;
     return fail(nullptr, LBM_ENOMEM, "batch descriptors");
   }
@@ -1637,6 +1656,7 @@ void lbm_batch_destroy(lbm_batch_t *b) {
   if (b->D) cudaFree(b->D);
   if (b->D_alt) cudaFree(b->D_alt);
   if (b->work_off) cudaFree(b->work_off);
+  if (b->cblk) cudaFree(b->cblk);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
@@ -1775,6 +1795,10 @@ int lbm_batch_step(lbm_batch_t *b, int n_steps, int n_ibm_iter) {
   dims.nd = (int)b->hs.size();
   dims.ls = b->shape;
   if (dims.nd > 1) dims.work_off = b->work_off;
+  for (int l = 0; l < 3; l++) {
+    dims.cblk[l] = b->cblk + b->cblk_off[l];
+    dims.ncblk[l] = b->ncblk[l];
+  }
   bool have_du = false;
   for (lbm_t *h : b->hs) {
     ver = ver * 1000003u + h->version;

@@ -386,6 +386,11 @@ struct BatchDims {
   // per-brick kernels then run one grid over the active slots of all
   // domains; NULL for a single lattice
   const int *work_off = nullptr;
+  // a batch's collide block tables for 128, 256 and 512 cells per block
+  // (device, (domain, block within the domain) per block of cells that some
+  // domain has, domain-major) and their lengths; NULL for a single lattice
+  const int2 *cblk[3] = {nullptr, nullptr, nullptr};
+  int ncblk[3] = {0, 0, 0};
 };
 
 }  // namespace lbmibm

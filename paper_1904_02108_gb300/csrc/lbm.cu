@@ -227,14 +227,16 @@ __device__ __forceinline__ float warp_sum4_split(const float a[4]) {
 
 // One thread per cell.  dd is the domain of this block: a kernel parameter
 // for a single lattice (constant bank, no dependent loads before the first
-// population load), or D[blockIdx.y] of a batch.  SKIP: the cells of the
+// population load), or a batch's domain from its block table; bx is the
+// block's index within the domain.  SKIP: the cells of the
 // step's active bricks are left to collide_active_kernel (they need the IBM
 // force, the others do not); otherwise every cell, with its brick's force.
 template <typename S, bool STATS, bool SKIP>
-__device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int cur) {
+__device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int cur,
+                                                     uint32_t bx) {
   const Geometry g = dd.g;
   // blocks past this domain's cells (batches of unequal domains) leave at once
-  if ((int64_t)blockIdx.x * blockDim.x >= g.ncell) return;
+  if ((int64_t)bx * blockDim.x >= g.ncell) return;
   const S *__restrict__ src = (const S *)dd.f[cur];
   S *__restrict__ dst = (S *)dd.f[cur ^ 1];
   const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
@@ -242,7 +244,7 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
   const float *__restrict__ Gs = dd.Gs;
   double *__restrict__ partial = dd.partial;
   float sv[4] = {0.f, 0.f, 0.f, 0.f};
-  const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t n = bx * blockDim.x + threadIdx.x;
   if (n < (uint32_t)g.ncell) {
     int x, y, z;
     cell_coords(n, g, x, y, z);
@@ -280,7 +282,7 @@ __device__ __forceinline__ void collide_stream_cells(const DomainDesc &dd, int c
       const int gi = threadIdx.x >> 2, c = threadIdx.x & 3;
       const double a = ((red[4 * gi][c] + red[4 * gi + 1][c]) + red[4 * gi + 2][c]) +
                        red[4 * gi + 3][c];
-      const int64_t pidx = (int64_t)blockIdx.x * groups + gi;
+      const int64_t pidx = (int64_t)bx * groups + gi;
       if (pidx < dd.cblocks) partial[(size_t)pidx * 4 + c] = a;
     }
   }
@@ -290,16 +292,18 @@ template <typename S, bool STATS, bool SKIP>
 __global__ void __launch_bounds__(256)
     collide_stream_kernel(const __grid_constant__ DomainDesc dd, int cur) {
   pdl_wait();
-  collide_stream_cells<S, STATS, SKIP>(dd, cur);
+  collide_stream_cells<S, STATS, SKIP>(dd, cur, blockIdx.x);
 }
 
 // (five blocks of 256 per SM, as the single-lattice kernel gets with its
 // descriptor in the parameter bank)
 template <typename S, bool STATS, bool SKIP>
 __global__ void __launch_bounds__(256, 5)
-    collide_stream_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
+    collide_stream_batch_kernel(const DomainDesc *__restrict__ D, const int2 *__restrict__ blk,
+                                int cur) {
   pdl_wait();
-  collide_stream_cells<S, STATS, SKIP>(D[blockIdx.y], cur);
+  const int2 e = blk[blockIdx.x];
+  collide_stream_cells<S, STATS, SKIP>(D[e.x], cur, e.y);
 }
 
 // 16-bit storage: two x-neighbouring cells (x0 even, x0 + 1) per thread.
@@ -337,15 +341,15 @@ struct Word16<__half> {
 };
 
 template <typename S, bool STATS>
-__device__ __forceinline__ void collide_pairs16(const DomainDesc &dd, int cur) {
+__device__ __forceinline__ void collide_pairs16(const DomainDesc &dd, int cur, uint32_t bx) {
   const Geometry g = dd.g;
-  if ((int64_t)blockIdx.x * blockDim.x * 2 >= g.ncell) return;
+  if ((int64_t)bx * blockDim.x * 2 >= g.ncell) return;
   const uint32_t *__restrict__ src = (const uint32_t *)dd.f[cur];
   uint32_t *__restrict__ dst = (uint32_t *)dd.f[cur ^ 1];
   const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
   const float *__restrict__ Gs = dd.Gs;
   float sv[4] = {0.f, 0.f, 0.f, 0.f};
-  const uint32_t n = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const uint32_t n = 2 * (bx * blockDim.x + threadIdx.x);
   if (n < (uint32_t)g.ncell) {
     int x, y, z;
     cell_coords(n, g, x, y, z);
@@ -407,7 +411,7 @@ __device__ __forceinline__ void collide_pairs16(const DomainDesc &dd, int cur) {
     if ((int)threadIdx.x < 4 * groups) {
       const int gi = threadIdx.x >> 2, c = threadIdx.x & 3;
       const double a = red[2 * gi][c] + red[2 * gi + 1][c];
-      const int64_t pidx = (int64_t)blockIdx.x * groups + gi;
+      const int64_t pidx = (int64_t)bx * groups + gi;
       if (pidx < dd.cblocks) dd.partial[(size_t)pidx * 4 + c] = a;
     }
   }
@@ -421,14 +425,16 @@ template <typename S, bool STATS>
 __global__ void __launch_bounds__(256, 4)
     collide_pairs16_kernel(const __grid_constant__ DomainDesc dd, int cur) {
   pdl_wait();
-  collide_pairs16<S, STATS>(dd, cur);
+  collide_pairs16<S, STATS>(dd, cur, blockIdx.x);
 }
 
 template <typename S, bool STATS>
 __global__ void __launch_bounds__(256, 4)
-    collide_pairs16_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
+    collide_pairs16_batch_kernel(const DomainDesc *__restrict__ D, const int2 *__restrict__ blk,
+                                 int cur) {
   pdl_wait();
-  collide_pairs16<S, STATS>(D[blockIdx.y], cur);
+  const int2 e = blk[blockIdx.x];
+  collide_pairs16<S, STATS>(D[e.x], cur, e.y);
 }
 
 // 16-bit storage: four x-neighbouring cells (x0 a multiple of 4, so one
@@ -466,14 +472,14 @@ __device__ __forceinline__ void pair_words(const uint32_t w[Q], const float Ga[3
 }
 
 template <typename S, bool STATS>
-__device__ __forceinline__ void collide_quads16(const DomainDesc &dd, int cur) {
+__device__ __forceinline__ void collide_quads16(const DomainDesc &dd, int cur, uint32_t bx) {
   const Geometry g = dd.g;
-  if ((int64_t)blockIdx.x * blockDim.x * 4 >= g.ncell) return;
+  if ((int64_t)bx * blockDim.x * 4 >= g.ncell) return;
   const uint32_t *__restrict__ src = (const uint32_t *)dd.f[cur];
   uint32_t *__restrict__ dst = (uint32_t *)dd.f[cur ^ 1];
   const int *__restrict__ brick_slot = dd.np > 0 ? dd.m.brick_slot : nullptr;
   float vA[4] = {0.f, 0.f, 0.f, 0.f}, vB[4] = {0.f, 0.f, 0.f, 0.f};
-  const uint32_t n = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const uint32_t n = 4 * (bx * blockDim.x + threadIdx.x);
   if (n < (uint32_t)g.ncell) {
     int x, y, z;
     cell_coords(n, g, x, y, z);
@@ -550,7 +556,7 @@ __device__ __forceinline__ void collide_quads16(const DomainDesc &dd, int cur) {
     // lanes 0, 4, 8, 12 hold components 0..3 of the first 64 cells, lanes
     // 16.. the same of the next 64; the partial is their FP64 sum
     const float o = __shfl_down_sync(0xffffffffu, c, 16);
-    const int64_t pidx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t pidx = ((int64_t)bx * blockDim.x + threadIdx.x) >> 5;
     if (lane < 16 && (lane & 3) == 0 && pidx < dd.cblocks)
       dd.partial[(size_t)pidx * 4 + (lane >> 2)] = (double)c + (double)o;
   }
@@ -563,14 +569,16 @@ template <typename S, bool STATS>
 __global__ void __launch_bounds__(128, 5)
     collide_quads16_kernel(const __grid_constant__ DomainDesc dd, int cur) {
   pdl_wait();
-  collide_quads16<S, STATS>(dd, cur);
+  collide_quads16<S, STATS>(dd, cur, blockIdx.x);
 }
 
 template <typename S, bool STATS>
 __global__ void __launch_bounds__(128, 5)
-    collide_quads16_batch_kernel(const DomainDesc *__restrict__ D, int cur) {
+    collide_quads16_batch_kernel(const DomainDesc *__restrict__ D, const int2 *__restrict__ blk,
+                                 int cur) {
   pdl_wait();
-  collide_quads16<S, STATS>(D[blockIdx.y], cur);
+  const int2 e = blk[blockIdx.x];
+  collide_quads16<S, STATS>(D[e.x], cur, e.y);
 }
 
 // 16-bit storage, single lattice: the pulls staged in shared memory by the
@@ -1076,16 +1084,30 @@ cudaError_t launch_rows16(const DomainDesc &dd, int cur, const RowsTiling &tl, c
                     tl);
 }
 
+// A batch's collide grid: one block per block of cells that some domain has
+// (cpb cells each), from the batch's table; grid.x = 0 when it has none.
+inline void batch_grid(const BatchDims &dims, int cpb, dim3 &grid, const int2 *&blk) {
+  const int l = cpb == 128 ? 0 : (cpb == 256 ? 1 : 2);
+  grid = dim3((unsigned)(dims.cblk[l] ? dims.ncblk[l] : 0));
+  blk = dims.cblk[l];
+}
+
 template <typename S>
 cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const BatchDims &dims,
                           int cur, int stats, int skip_active, cudaStream_t st) {
   const int bs = dims.ls.collide_block;
   if (bs != 128 && bs != 256) return cudaErrorInvalidValue;
-  const dim3 grid((unsigned)((dims.max_cells + bs - 1) / bs), dims.nd), block(bs);
+  const bool single = dims.nd == 1 && Dhost;
+  const dim3 grid((unsigned)((dims.max_cells + bs - 1) / bs)), block(bs);
+  dim3 bgrid;
+  const int2 *blk = nullptr;
+  if (!single) {
+    batch_grid(dims, bs, bgrid, blk);
+    if (!blk) return cudaErrorInvalidValue;
+  }
 #define LBM_COLLIDE(ST, SK)                                                                 \
-  (dims.nd == 1 && Dhost                                                                    \
-       ? launch_pdl(collide_stream_kernel<S, ST, SK>, grid, block, 0, st, *Dhost, cur)      \
-       : launch_pdl(collide_stream_batch_kernel<S, ST, SK>, grid, block, 0, st, D, cur))
+  (single ? launch_pdl(collide_stream_kernel<S, ST, SK>, grid, block, 0, st, *Dhost, cur)   \
+          : launch_pdl(collide_stream_batch_kernel<S, ST, SK>, bgrid, block, 0, st, D, blk, cur))
   if (skip_active) return stats ? LBM_COLLIDE(true, true) : LBM_COLLIDE(false, true);
 #undef LBM_COLLIDE
   if constexpr (sizeof(S) == 2) {
@@ -1097,27 +1119,26 @@ cudaError_t collide_typed(const DomainDesc *D, const DomainDesc *Dhost, const Ba
                    : launch_rows16<S, false>(*Dhost, cur, tl, st);
     // four cells per thread (nx is a multiple of 4), blocks of 128
     if (dims.ls.collide_staged == 2) {
-      const dim3 grid4((unsigned)((dims.max_cells + 511) / 512), dims.nd), block4(128);
-#define LBM_QUADS(ST)                                                                     \
-  (dims.nd == 1 && Dhost                                                                  \
-       ? launch_pdl(collide_quads16_kernel<S, ST>, grid4, block4, 0, st, *Dhost, cur)     \
-       : launch_pdl(collide_quads16_batch_kernel<S, ST>, grid4, block4, 0, st, D, cur))
+      const dim3 grid4((unsigned)((dims.max_cells + 511) / 512)), block4(128);
+      if (!single) batch_grid(dims, 512, bgrid, blk);
+#define LBM_QUADS(ST)                                                                        \
+  (single ? launch_pdl(collide_quads16_kernel<S, ST>, grid4, block4, 0, st, *Dhost, cur)     \
+          : launch_pdl(collide_quads16_batch_kernel<S, ST>, bgrid, block4, 0, st, D, blk, cur))
       return stats ? LBM_QUADS(true) : LBM_QUADS(false);
 #undef LBM_QUADS
     }
     // two cells per thread (nx is a multiple of 4)
-    const dim3 grid2((unsigned)((dims.max_cells + 2 * bs - 1) / (2 * bs)), dims.nd);
-#define LBM_PAIRS(ST)                                                                     \
-  (dims.nd == 1 && Dhost                                                                  \
-       ? launch_pdl(collide_pairs16_kernel<S, ST>, grid2, block, 0, st, *Dhost, cur)      \
-       : launch_pdl(collide_pairs16_batch_kernel<S, ST>, grid2, block, 0, st, D, cur))
+    const dim3 grid2((unsigned)((dims.max_cells + 2 * bs - 1) / (2 * bs)));
+    if (!single) batch_grid(dims, 2 * bs, bgrid, blk);
+#define LBM_PAIRS(ST)                                                                        \
+  (single ? launch_pdl(collide_pairs16_kernel<S, ST>, grid2, block, 0, st, *Dhost, cur)      \
+          : launch_pdl(collide_pairs16_batch_kernel<S, ST>, bgrid, block, 0, st, D, blk, cur))
     return stats ? LBM_PAIRS(true) : LBM_PAIRS(false);
 #undef LBM_PAIRS
   }
 #define LBM_COLLIDE(ST, SK)                                                                 \
-  (dims.nd == 1 && Dhost                                                                    \
-       ? launch_pdl(collide_stream_kernel<S, ST, SK>, grid, block, 0, st, *Dhost, cur)      \
-       : launch_pdl(collide_stream_batch_kernel<S, ST, SK>, grid, block, 0, st, D, cur))
+  (single ? launch_pdl(collide_stream_kernel<S, ST, SK>, grid, block, 0, st, *Dhost, cur)   \
+          : launch_pdl(collide_stream_batch_kernel<S, ST, SK>, bgrid, block, 0, st, D, blk, cur))
   return stats ? LBM_COLLIDE(true, false) : LBM_COLLIDE(false, false);
 #undef LBM_COLLIDE
 }
