@@ -795,6 +795,27 @@ __global__ void __launch_bounds__(128)
 
 // ---- the brick kernels: one warp per active brick ---------------------------
 
+// Loads issued where they are written (inline PTX the compiler does not move
+// past the branch on the stop flag that follows them): in tolerance mode a
+// pass reads the flag beside its first loads, one round trip instead of two.
+__device__ __forceinline__ int4 ld_early(const int4 *p) {
+  int4 v;
+  asm volatile("ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int ld_early(const int *p) {
+  int v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+// the stop flag (written by an earlier kernel, read-only in this one)
+__device__ __forceinline__ bool stopped(const DomainDesc &d, int tol_mode) {
+  return tol_mode && ld_early(&d.state->done);
+}
+
+
 // A warp stages up to SP_CHUNK pairs of its brick at a time: their brick-local
 // weights and spread values.  96 pairs (6.9 KB of shared memory per warp)
 // hold all pairs of 97 % of the bricks of a dense propeller array and leave
@@ -1196,14 +1217,16 @@ __global__ void __launch_bounds__(32, 32)
     });
   } else {
     const DomainDesc &d = D[blockIdx.y];
-    if (tol_mode && d.state->done) return;
     const BrickMap m = d.m;
     const PairMap pm = d.pm;
     const float4 *__restrict__ vals = d.du;
     const float *__restrict__ U0s = d.U0s;
     float *__restrict__ Gs = d.Gs;
     float *__restrict__ res = tol_mode ? d.res : nullptr;
-    const int nslots = active_slots(m);
+    // active_slots(m), its counters loaded beside the stop flag
+    const int c0 = ld_early(m.counters), c1 = ld_early(m.counters + 1);
+    if (stopped(d, tol_mode)) return;
+    const int nslots = (c1 & 4) ? 0 : (c0 < m.max_slots ? c0 : m.max_slots);
     const int t = threadIdx.x, r = t & 15;
     for (int b = blockIdx.x; b < nslots; b += gridDim.x) {
       const int s = slot_in_order(m, b);
@@ -1354,13 +1377,13 @@ __global__ void __launch_bounds__(512)
   const DomainDesc &d = D[blockIdx.y];
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.np) return;
-  if (tol_mode && d.state->done) return;
   const PointPrep pp = d.pp;
   const PairMap pm = d.pm;
   float4 *__restrict__ du = d.du;
   float4 *__restrict__ uint = d.uint;
   const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
-  const int4 a = pk[0], b = pk[1];
+  const int4 a = ld_early(pk), b = ld_early(pk + 1);
+  if (stopped(d, tol_mode)) return;
   const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
   float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
@@ -1407,9 +1430,9 @@ constexpr int CG_BLOCK = 256;  // threads of the CG point kernels (fixed: the
                                // block sums of delta do not depend on the
                                // launch shape)
 
-__device__ __forceinline__ float4 shares_sum(const PairMap &pm, int64_t k) {
-  const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
-  const int4 a = pk[0], b = pk[1];
+// the sum of a point's pair shares in brick order, from its eight pair
+// indices (-1: none)
+__device__ __forceinline__ float4 shares_of(const PairMap &pm, int4 a, int4 b) {
   const int idx[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
   float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
@@ -1422,6 +1445,11 @@ __device__ __forceinline__ float4 shares_sum(const PairMap &pm, int64_t k) {
     }
   }
   return make_float4(ux, uy, uz, 0.f);
+}
+
+__device__ __forceinline__ float4 shares_sum(const PairMap &pm, int64_t k) {
+  const int4 *pk = (const int4 *)(pm.point_pairs + 8 * k);
+  return shares_of(pm, pk[0], pk[1]);
 }
 
 // r_0 = u_k - I[U0 + G_0] from the shares brick_init left, v_0 = s r_0,
@@ -1478,9 +1506,9 @@ __global__ void __launch_bounds__(32, 32)
   __shared__ BrickSmem sm;
   const int t = threadIdx.x, r = t & 15;
   for_each_slot<WL, true>(D, off, nd, blockIdx.x, gridDim.x, [&](const DomainDesc &d, int s) {
-    if (tol_mode && d.state->done) return;
     const PairMap &pm = d.pm;
-    const int p0 = pm.start[s], cnt = pm.count[s];
+    const int p0 = ld_early(pm.start + s), cnt = ld_early(pm.count + s);
+    if (stopped(d, tol_mode)) return;
     float4 R[3];
     brick_gather(sm, pm, p0, cnt, d.cg + d.np, R);
     float e = 0.f;
@@ -1530,12 +1558,19 @@ __global__ void __launch_bounds__(CG_BLOCK) cg_dot_kernel(const DomainDesc *__re
   const DomainDesc &d = D[blockIdx.y];
   const int nbk = (d.np + CG_BLOCK - 1) / CG_BLOCK;
   if ((int)blockIdx.x >= nbk) return;
-  if (tol_mode && d.state->done) return;
   const int t = threadIdx.x, b = blockIdx.x;
   const int64_t k = (int64_t)b * CG_BLOCK + t;
+  // the point's pair indices loaded beside the stop flag
+  int4 pa = make_int4(-1, -1, -1, -1), pb = pa;
+  if (k < d.np) {
+    const int4 *pk = (const int4 *)(d.pm.point_pairs + 8 * k);
+    pa = ld_early(pk);
+    pb = ld_early(pk + 1);
+  }
+  if (stopped(d, tol_mode)) return;
   float e = 0.f;
   if (k < d.np) {
-    const float4 a = shares_sum(d.pm, k);
+    const float4 a = shares_of(d.pm, pa, pb);
     d.cg[4 * (int64_t)d.np + k] = a;
     e = d.pp.ut[k].w * ((a.x * a.x + a.y * a.y) + a.z * a.z);
   }
