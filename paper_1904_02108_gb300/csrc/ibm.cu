@@ -815,7 +815,6 @@ __device__ __forceinline__ bool stopped(const DomainDesc &d, int tol_mode) {
   return tol_mode && ld_early(&d.state->done);
 }
 
-
 // A warp stages up to SP_CHUNK pairs of its brick at a time: their brick-local
 // weights and spread values.  96 pairs (6.9 KB of shared memory per warp)
 // hold all pairs of 97 % of the bricks of a dense propeller array and leave
